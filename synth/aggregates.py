@@ -1,0 +1,325 @@
+"""Seeded rigid-aggregate suspensions.
+
+Aggregates are grown by random sequential attachment: each new bead touches
+(centre distance exactly 2a) a uniformly chosen existing bead in a uniform
+random direction; a placement closer than 2a(1 - 1e-12) to any existing bead
+of the same aggregate is rejected.  Aggregates are inserted into a periodic
+cube with uniform centres and uniform random orientations (normalised 4-D
+Gaussian quaternions); an insertion is rejected if any bead of another body
+comes within a surface gap h_gen.  Bead volume fraction
+phi = N_tot (4/3) pi a^3 / L^3.
+
+Returned positions are unwrapped per aggregate (an aggregate is never split
+across the box boundary); centres lie in [0, L).
+"""
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "random_attachment_aggregate",
+    "doublet",
+    "random_rotation",
+    "pack_suspension",
+    "box_for_phi",
+    "suspension",
+    "config_doublets",
+    "config_aggregates",
+    "random_forces",
+    "compress_suspension",
+]
+
+
+def random_attachment_aggregate(n_b, rng, a=1.0):
+    """Bead offsets (n_b, 3) of one aggregate, centred on its bead centroid."""
+    pts = [np.zeros(3)]
+    while len(pts) < n_b:
+        base = pts[rng.integers(len(pts))]
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        cand = base + 2.0 * a * d
+        P = np.array(pts)
+        if np.all(np.linalg.norm(P - cand, axis=1) >= 2.0 * a * (1.0 - 1e-12)):
+            pts.append(cand)
+    P = np.array(pts)
+    return P - P.mean(axis=0)
+
+
+def doublet(a=1.0):
+    return np.array([[-a, 0.0, 0.0], [a, 0.0, 0.0]])
+
+
+def random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def box_for_phi(n_tot, phi, a=1.0):
+    return (n_tot * (4.0 / 3.0) * math.pi * a ** 3 / phi) ** (1.0 / 3.0)
+
+
+class _Hash:
+    """Uniform cell hash over the periodic box for overlap rejection."""
+
+    def __init__(self, L, cell):
+        self.L = L
+        self.n = max(1, int(L // cell))
+        self.cell = L / self.n
+        self.cells = {}
+
+    def key(self, p):
+        c = np.floor((p % self.L) / self.cell).astype(int) % self.n
+        return tuple(c)
+
+    def near(self, p):
+        c = self.key(p)
+        n = self.n
+        rng = (-1, 0, 1) if n >= 3 else tuple(range(n))
+        out = []
+        seen = set()
+        for dx in rng:
+            for dy in rng:
+                for dz in rng:
+                    k = ((c[0] + dx) % n, (c[1] + dy) % n, (c[2] + dz) % n)
+                    if k in seen:
+                        continue
+                    seen.add(k)
+                    out.extend(self.cells.get(k, ()))
+        return out
+
+    def add(self, p, idx):
+        self.cells.setdefault(self.key(p), []).append(idx)
+
+
+def pack_suspension(shapes, L, rng, a=1.0, h_gen=0.1, max_tries=20000):
+    """Insert rigid shapes (list of (n_b,3) offset arrays) into a cube of side L.
+
+    Returns pos (N_tot, 3), body (N_tot,) int32."""
+    contact = 2.0 * a + h_gen
+    hsh = _Hash(L, contact)
+    allpos = []
+    body = []
+    for J, shp in enumerate(shapes):
+        for _ in range(max_tries):
+            R = random_rotation(rng)
+            c = rng.uniform(0.0, L, size=3)
+            P = c + shp @ R.T
+            ok = True
+            for p in P:
+                for j in hsh.near(p):
+                    d = allpos[j] - p
+                    d -= L * np.round(d / L)
+                    if d @ d < contact * contact:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if ok:
+                break
+        else:
+            raise RuntimeError("suspension packing jammed at body %d" % J)
+        for p in P:
+            hsh.add(p, len(allpos))
+            allpos.append(p)
+            body.append(J)
+    return np.array(allpos), np.array(body, dtype=np.int32)
+
+
+def suspension(n_agg, n_b, phi, seed, a=1.0, h_gen=0.1):
+    """n_agg random-attachment aggregates of n_b beads at bead volume fraction
+    phi.  Up to phi = 0.12 by random sequential insertion alone; denser
+    suspensions are compressed from phi = 0.12 (compress_suspension)."""
+    rng = np.random.default_rng(seed)
+    shapes = [random_attachment_aggregate(n_b, rng, a) for _ in range(n_agg)]
+    if phi > 0.12:
+        return compress_suspension(np.array(shapes), phi, seed + 1, a, h_gen)
+    L = box_for_phi(n_agg * n_b, phi, a)
+    pos, body = pack_suspension(shapes, L, rng, a, h_gen)
+    return pos, body, L
+
+
+def config_doublets(n_agg=16, L=40.0, seed=1, a=1.0):
+    """Rigid touching doublets (centre separation 2a) at uniform centres and
+    uniform random orientations in a cube of side L."""
+    rng = np.random.default_rng(seed)
+    shapes = [doublet(a) for _ in range(n_agg)]
+    pos, body = pack_suspension(shapes, L, rng, a, h_gen=0.1)
+    return pos, body, L
+
+
+def config_aggregates(n_agg, n_b, phi, seed=1, a=1.0):
+    return suspension(n_agg, n_b, phi, seed, a)
+
+
+def random_forces(n_agg, seed, scale=1.0):
+    """Seeded aggregate forces / torques (n_agg, 6), standard normal x scale."""
+    rng = np.random.default_rng(seed + 7919)
+    return scale * rng.normal(size=(n_agg, 6))
+
+
+# ---------------------------------------------------------------------------
+# dense packings: random sequential insertion at a looser density, then
+# affine compression of the centres with overlap-removing Monte Carlo moves
+# ---------------------------------------------------------------------------
+
+
+def _rot_from_quat(q):
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z)
+    R[..., 0, 1] = 2 * (x * y - w * z)
+    R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z)
+    R[..., 1, 1] = 1 - 2 * (x * x + z * z)
+    R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y)
+    R[..., 2, 1] = 2 * (y * z + w * x)
+    R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def _overlap_mask(P, body, L, contact, nbody):
+    """Bodies having any bead of another body closer than `contact`
+    (minimum image).  P (Nt, 3)."""
+    n = max(1, int(L // contact))
+    cs = L / n
+    c = np.floor((P % L) / cs).astype(np.int64) % n
+    cid = (c[:, 0] * n + c[:, 1]) * n + c[:, 2]
+    order = np.argsort(cid, kind="stable")
+    cnt = np.bincount(cid, minlength=n ** 3)
+    m = int(cnt.max())
+    table = -np.ones((n ** 3, m), dtype=np.int64)
+    start = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    sc = cid[order]
+    slot = np.arange(len(order)) - start[sc]
+    table[sc, slot] = order
+    bad = np.zeros(nbody, dtype=bool)
+    offs = (-1, 0, 1) if n >= 3 else tuple(range(n))
+    seen = set()
+    for dx in offs:
+        for dy in offs:
+            for dz in offs:
+                key = (dx % n, dy % n, dz % n)
+                if key in seen:
+                    continue
+                seen.add(key)
+                nc = (((c[:, 0] + dx) % n) * n + (c[:, 1] + dy) % n) * n + (c[:, 2] + dz) % n
+                J = table[nc]  # (Nt, m)
+                valid = J >= 0
+                Jc = np.where(valid, J, 0)
+                d = P[Jc] - P[:, None, :]
+                d -= L * np.round(d / L)
+                r2 = np.einsum("nmk,nmk->nm", d, d)
+                hit = valid & (r2 < contact * contact) & (body[Jc] != body[:, None])
+                bad[body[hit.any(axis=1)]] = True
+    return bad
+
+
+def _close_pairs(P, body, L, contact):
+    """Inter-body bead pairs (i < j) closer than `contact` (minimum image):
+    returns i, j, d = P[j] - P[i] (minimum image)."""
+    n = max(1, int(L // contact))
+    cs = L / n
+    c = np.floor((P % L) / cs).astype(np.int64) % n
+    cid = (c[:, 0] * n + c[:, 1]) * n + c[:, 2]
+    order = np.argsort(cid, kind="stable")
+    cnt = np.bincount(cid, minlength=n ** 3)
+    m = int(cnt.max())
+    table = -np.ones((n ** 3, m), dtype=np.int64)
+    start = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    sc = cid[order]
+    table[sc, np.arange(len(order)) - start[sc]] = order
+    I, J, D = [], [], []
+    offs = (-1, 0, 1) if n >= 3 else tuple(range(n))
+    seen = set()
+    for dx in offs:
+        for dy in offs:
+            for dz in offs:
+                key = (dx % n, dy % n, dz % n)
+                if key in seen:
+                    continue
+                seen.add(key)
+                nc = (((c[:, 0] + dx) % n) * n + (c[:, 1] + dy) % n) * n + (c[:, 2] + dz) % n
+                Jt = table[nc]
+                valid = Jt >= 0
+                Jc = np.where(valid, Jt, 0)
+                d = P[Jc] - P[:, None, :]
+                d -= L * np.round(d / L)
+                r2 = np.einsum("nmk,nmk->nm", d, d)
+                hit = valid & (r2 < contact * contact) & (body[Jc] != body[:, None])
+                hit &= Jc > np.arange(len(P))[:, None]
+                ii, kk = np.nonzero(hit)
+                I.append(ii)
+                J.append(Jc[ii, kk])
+                D.append(d[ii, kk])
+    return np.concatenate(I), np.concatenate(J), np.concatenate(D)
+
+
+def compress_suspension(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12,
+                        step=0.99, max_iter=4000):
+    """Pack equal-size rigid shapes at bead volume fraction phi.
+
+    Random sequential insertion at phi0, then repeated affine compression of
+    the body centres (factor `step` in L), each followed by a soft-repulsion
+    relaxation: every inter-body bead pair closer than 2a + h_gen pushes its
+    two bodies apart (rigid translation and rotation driven by the summed
+    pair forces and torques) until no such pair is left."""
+    rng = np.random.default_rng(seed)
+    N, nb_ = shapes.shape[0], shapes.shape[1]
+    Lt = box_for_phi(N * nb_, phi, a)
+    L = box_for_phi(N * nb_, min(phi0, phi), a)
+    pos, body = pack_suspension(list(shapes), L, rng, a, h_gen)
+    target = 2.0 * a + 1.01 * h_gen  # pairs closer than this are pushed ...
+    push = 2.0 * a + 1.25 * h_gen    # ... towards this separation
+    contact = 2.0 * a + h_gen
+    P = pos.reshape(N, nb_, 3)
+    C = P.mean(axis=1)
+    off = P - C[:, None, :]
+    bodyidx = np.repeat(np.arange(N), nb_)
+
+    def beads():
+        return (C[:, None, :] + off).reshape(-1, 3)
+
+    def rotate(off_, w):
+        th = np.linalg.norm(w, axis=1)
+        k = np.where(th[:, None] > 0, w / np.maximum(th, 1e-300)[:, None], 0.0)
+        ct, st = np.cos(th)[:, None, None], np.sin(th)[:, None, None]
+        kx = np.einsum("nj,nbj->nb", k, off_)[..., None]
+        cr = np.cross(k[:, None, :], off_)
+        return off_ * ct + cr * st + k[:, None, :] * kx * (1 - ct)
+
+    while True:
+        for _ in range(max_iter):
+            Pb = beads()
+            i, j, d = _close_pairs(Pb, bodyidx, L, target)
+            if len(i) == 0:
+                break
+            r = np.linalg.norm(d, axis=1)
+            f = ((push - r) / np.maximum(r, 1e-12))[:, None] * d  # push j away from i
+            F = np.zeros((N, 3))
+            T = np.zeros((N, 3))
+            np.add.at(F, bodyidx[j], 0.5 * f)
+            np.add.at(F, bodyidx[i], -0.5 * f)
+            oi = off.reshape(-1, 3)[i]
+            oj = off.reshape(-1, 3)[j]
+            np.add.at(T, bodyidx[j], np.cross(oj, 0.5 * f))
+            np.add.at(T, bodyidx[i], np.cross(oi, -0.5 * f))
+            C = (C + 0.6 * F) % L
+            off = rotate(off, 0.6 * T / (np.einsum("nbk,nbk->n", off, off)[:, None] + a * a))
+        else:
+            raise RuntimeError("relaxation stalled at L=%.3f" % L)
+        if L <= Lt * (1 + 1e-12):
+            break
+        Ln = max(L * step, Lt)
+        C = C * (Ln / L)
+        L = Ln
+    Pb = beads()
+    assert len(_close_pairs(Pb, bodyidx, L, contact)[0]) == 0
+    return Pb, bodyidx.astype(np.int32), L
