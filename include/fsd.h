@@ -1,0 +1,186 @@
+/*
+ * fsd.h — C ABI of the GB300 (sm_103a) library for the per-time-step
+ * saddle-point solve of fast Stokesian dynamics for rigid multi-bead
+ * aggregates (arxiv 2607.25161).
+ *
+ * The operation (Sec. 2.3.3, Eq. spm_agg; Algorithm 1 steps 1, 4, 5):
+ *
+ *   [ M_inf        B Sigma^T ] [ F      ]   [ (E.(x - X) ; 0) ; E_inf        ]
+ *   [ Sigma B^T   -RR_FU^nf  ] [ U-U_inf] = [ -(FF^P + RR_FE^nf : E_inf)     ]
+ *
+ * M_inf is the periodic FTS-level RPY mobility applied matrix-free by the
+ * positively split Ewald method (real-space pair sum + Gaussian spreading,
+ * FFT, Green's function, interpolation; Sec. 2.2), RR^nf = Sigma R^nf Sigma^T
+ * the near-field lubrication resistance of bead pairs on different bodies
+ * (Sec. 2.3.2), Sigma the rigid-body constraint (Eq. gc, Eq. sigma).  GMRES
+ * with the block-triangular preconditioner of Table 1 (M_inf ~ I/zeta,
+ * block-diagonal Schur complement, one 6x6 LU per aggregate) solves it.
+ *
+ * Units: any consistent set; the defaults are a = 1, eta = 1.
+ * Imposed flow: simple shear, flow along x, gradient along y (Sec. 3.1.1):
+ *   u_inf = gamma y e_x,  E_inf = gamma/2 (e_x e_y + e_y e_x),
+ *   Omega_inf = -gamma/2 e_z, origin of y at 0.
+ *
+ * Pointers: every array argument may be HOST or DEVICE memory (detected with
+ * cudaPointerGetAttributes).  Device arrays are read / written on the
+ * context's stream (ready when that stream is); host arrays are copied
+ * synchronously.  The caller owns every array it passes; the library never
+ * keeps a caller pointer after a call returns.  The context owns all device
+ * workspace.
+ *
+ * Orderings: beads are identified by their index in the bead_pos array given
+ * to fsd_setup, aggregates by their id (dense 0..N-1).  Every input and output
+ * uses those orderings; internally beads are regrouped per aggregate and
+ * aggregates sorted spatially.
+ *
+ * Errors: every call returns an fsd_status; no exception or abort crosses
+ * the ABI; fsd_last_error() gives a message.  FSD_ENOCONV still writes the
+ * best iterate and the stats.  FSD_EOVERLAP is a warning (beads of different
+ * aggregates closer than 2a (1 - 1e-6)); all outputs are still written.
+ */
+#ifndef FSD_H
+#define FSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsd_ctx fsd_ctx;
+
+typedef enum {
+  FSD_OK = 0,
+  FSD_EINVAL = 1,   /* invalid argument; nothing was changed            */
+  FSD_ENOMEM = 2,   /* device or host allocation failed                 */
+  FSD_ECUDA = 3,    /* a CUDA runtime call failed                       */
+  FSD_ENOCONV = 4,  /* Krylov solve did not reach tol within max_iter   */
+  FSD_ENUMERIC = 5, /* NaN / Inf, or a singular per-aggregate 6x6 block */
+  FSD_EOVERLAP = 6, /* warning: overlapping beads of different bodies   */
+  FSD_ETIMEOUT = 7  /* a bounded device wait gave up                    */
+} fsd_status;
+
+/* Precision of the operator applications inside the solve. */
+enum { FSD_FP64 = 0, FSD_MIXED = 1 };
+
+/* Flags. */
+enum {
+  FSD_FLAG_WARM_START = 1 /* start each solve from the previous solution */
+};
+
+typedef struct {
+  double a;              /* bead radius (1)                                        */
+  double eta;            /* viscosity (1)                                          */
+  double box;            /* side L of the periodic cube (required, > 0)            */
+  double xi;             /* Ewald splitting (Sec. 3.2); <= 0: 0.5 / a              */
+  double xerr;           /* accuracy target of the parameter rules (1e-6)          */
+  double rc;             /* real-space cut-off; <= 0: 2a + sqrt(-ln xerr)/xi       */
+  int grid;              /* FFT points per side; 0: k_c L / pi with
+                            k_c = 2 sqrt(-ln xerr) xi + 1 (Sec. 3.2), rounded up
+                            to an even 2,3,5-smooth size                           */
+  int P;                 /* Gaussian support in grid points per side (even, 4..24);
+                            0: 8                                                   */
+  double m_shape;        /* Gaussian shape factor; <= 0: 0.976 sqrt(pi P)          */
+  double lub_cutoff;     /* lubrication cut-off r_lub (0: no near field)           */
+  double precond_cutoff; /* r_p of the preconditioner (2.1 a, Sec. 2.2.2)          */
+  double lub_hmin;       /* gap clamp of the pair functions (1e-3 a)               */
+  double tol;            /* relative residual target (1e-6)                        */
+  int restart;           /* GMRES restart length (30)                              */
+  int max_iter;          /* Krylov iteration limit per solve (1000)                */
+  int precision;         /* FSD_FP64 or FSD_MIXED                                  */
+  int inner_restart;     /* mixed: FP32-operator GMRES iterations per outer step (30) */
+  double inner_tol;      /* mixed: inner relative tolerance (1e-4)                 */
+  int flags;             /* FSD_FLAG_*                                             */
+} fsd_params;
+
+typedef struct {
+  int iters;          /* Krylov iterations (all levels)                     */
+  int outer_iters;    /* outer iterations (restarts for FP64; refinement
+                         steps for mixed)                                   */
+  int matvec64;       /* FP64 saddle-operator applications                  */
+  int matvec32;       /* FP32 saddle-operator applications                  */
+  double rel_residual;/* true FP64 ||b - A x|| / ||b|| at exit              */
+  double ms_total;    /* wall time of the call (ms)                         */
+  int64_t n_pairs;    /* real-space neighbour pairs (directed)              */
+  int64_t n_lub;      /* lubrication pairs (directed)                       */
+  int grid;           /* FFT grid used                                      */
+  int P;              /* Gaussian support used                              */
+  double xi;          /* splitting used                                     */
+  double rc;          /* real-space cut-off used                            */
+} fsd_stats;
+
+/* Defaults above (box must still be set). */
+void fsd_default_params(fsd_params *p);
+
+/* Create a context for one suspension (Algorithm 1 set-up).
+ * n_beads >= 1; bead_pos [n_beads][3] (any periodic image: each aggregate is
+ * unwrapped by the minimum image about its first bead); agg_id [n_beads] with
+ * every id in 0..N-1 used at least once.  The body frame is the bead layout
+ * given here (orientation quaternion = identity), centred on the bead
+ * centroid X (equal bead masses, Sec. 2.3.1).  cuda_stream: a cudaStream_t or
+ * NULL for a stream the context creates.  On failure *ctx is NULL. */
+fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos,
+                     const int32_t *agg_id, const fsd_params *p,
+                     void *cuda_stream);
+
+/* One saddle-point solve at the current configuration (Algorithm 1 steps 1
+ * and 4).  agg_force_torque [N][6]: conservative force and torque about X
+ * per aggregate, FF^P (NULL = 0).  Outputs: agg_velocity [N][6] = (U, Omega)
+ * in the lab frame including U_inf(X), Omega_inf; agg_stresslet [N][9] =
+ * S^H + S^C (Eq. stress_comp a, d) as a symmetric 3x3, row-major (NULL to
+ * skip).  stats may be NULL. */
+fsd_status fsd_solve(fsd_ctx *ctx, const double *agg_force_torque,
+                     double shear_rate, double *agg_velocity,
+                     double *agg_stresslet, fsd_stats *stats);
+
+/* fsd_solve followed by the Euler-Maruyama rigid-body update (Sec. 2.4,
+ * Eq. EM1-EM3): X += U dt; q <- normalise(q + dt/2 (0, Omega) q);
+ * bead x = X + R(q) x_body.  agg_velocity may be NULL. */
+fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque,
+                    double shear_rate, double dt, double *agg_velocity,
+                    fsd_stats *stats);
+
+/* Current bead positions [n_beads][3] (unwrapped per aggregate) and
+ * orientation quaternions [N][4] (w, x, y, z); either may be NULL. */
+fsd_status fsd_get_beads(fsd_ctx *ctx, double *bead_pos, double *agg_quat);
+
+/* Operator access (parity tests and users composing their own solvers).
+ * Vectors use the solution layout: per bead 11 values (F: 3, L: 3, S: 5 in the
+ * orthonormal basis {(xx-yy)/sqrt2, (2zz-xx-yy)/sqrt6, sqrt2 xy, sqrt2 xz,
+ * sqrt2 yz}) in bead order, then per aggregate 6 values (U, Omega) in id order.
+ * precision: FSD_FP64 or FSD_MIXED (= the FP32 operator). */
+
+/* out[n_beads][11] = M_inf . in[n_beads][11]; part: 1 real space (incl. the
+ * self term), 2 wave space, 3 both (Sec. 2.2, Eq. UBff split). */
+fsd_status fsd_apply_mobility(fsd_ctx *ctx, const double *in, double *out,
+                              int part, int precision);
+
+/* y = A x, the saddle-point operator of Eq. spm_agg. */
+fsd_status fsd_apply_saddle(fsd_ctx *ctx, const double *x, double *y,
+                            int precision);
+
+/* z = P^-1 r, the block-triangular preconditioner (Table 1, aggregates). */
+fsd_status fsd_apply_precond(fsd_ctx *ctx, const double *r, double *z);
+
+/* out[N][6] = RR_FU^nf . dU[N][6] (Sigma R^nf Sigma^T, Eq. FH_agg). */
+fsd_status fsd_apply_lubrication(fsd_ctx *ctx, const double *dU, double *out,
+                                 int precision);
+
+/* Right-hand side of Eq. spm_agg (same layout as x). */
+fsd_status fsd_rhs(fsd_ctx *ctx, const double *agg_force_torque,
+                   double shear_rate, double *b);
+
+/* Parameters actually used (after the defaulting rules). */
+fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);
+
+/* Message of the last error on ctx (or of the last failed fsd_setup when ctx
+ * is NULL).  Valid until the next call on the same context. */
+const char *fsd_last_error(const fsd_ctx *ctx);
+
+void fsd_destroy(fsd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSD_H */

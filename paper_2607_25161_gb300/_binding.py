@@ -1,0 +1,222 @@
+"""ctypes binding of the FSD C ABI (include/fsd.h): argument marshalling only.
+
+Every array argument may be a NumPy array (host) or a torch CUDA tensor
+(device); device tensors are passed by pointer and used on the context's
+stream.  Nothing here computes any part of the method: all arithmetic runs in
+the CUDA library.  Loading fails loudly when the library is missing."""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfsd.so")
+
+FSD_OK, FSD_EINVAL, FSD_ENOMEM, FSD_ECUDA, FSD_ENOCONV, FSD_ENUMERIC, FSD_EOVERLAP, FSD_ETIMEOUT = range(8)
+FSD_FP64, FSD_MIXED = 0, 1
+FSD_FLAG_WARM_START = 1
+STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",
+                5: "FSD_ENUMERIC", 6: "FSD_EOVERLAP", 7: "FSD_ETIMEOUT"}
+
+# every entry point declared in include/fsd.h
+EXPORTS = (
+    "fsd_default_params", "fsd_setup", "fsd_solve", "fsd_step", "fsd_get_beads",
+    "fsd_apply_mobility", "fsd_apply_saddle", "fsd_apply_precond", "fsd_apply_lubrication",
+    "fsd_rhs", "fsd_get_params", "fsd_last_error", "fsd_destroy",
+)
+
+
+class FsdParams(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_double), ("eta", ctypes.c_double), ("box", ctypes.c_double),
+        ("xi", ctypes.c_double), ("xerr", ctypes.c_double), ("rc", ctypes.c_double),
+        ("grid", ctypes.c_int), ("P", ctypes.c_int), ("m_shape", ctypes.c_double),
+        ("lub_cutoff", ctypes.c_double), ("precond_cutoff", ctypes.c_double),
+        ("lub_hmin", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
+        ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_restart", ctypes.c_int),
+        ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FsdStats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("matvec64", ctypes.c_int),
+        ("matvec32", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double),
+        ("n_pairs", ctypes.c_int64), ("n_lub", ctypes.c_int64), ("grid", ctypes.c_int),
+        ("P", ctypes.c_int), ("xi", ctypes.c_double), ("rc", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libfsd.so and declare the signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("FSD CUDA library not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    lib.fsd_default_params.argtypes = [ctypes.POINTER(FsdParams)]
+    lib.fsd_default_params.restype = None
+    lib.fsd_setup.argtypes = [ctypes.POINTER(P), ctypes.c_int64, P, P, ctypes.POINTER(FsdParams), P]
+    lib.fsd_solve.argtypes = [P, P, D, P, P, ctypes.POINTER(FsdStats)]
+    lib.fsd_step.argtypes = [P, P, D, D, P, ctypes.POINTER(FsdStats)]
+    lib.fsd_get_beads.argtypes = [P, P, P]
+    lib.fsd_apply_mobility.argtypes = [P, P, P, I, I]
+    lib.fsd_apply_saddle.argtypes = [P, P, P, I]
+    lib.fsd_apply_precond.argtypes = [P, P, P]
+    lib.fsd_apply_lubrication.argtypes = [P, P, P, I]
+    lib.fsd_rhs.argtypes = [P, P, D, P]
+    lib.fsd_get_params.argtypes = [P, ctypes.POINTER(FsdParams)]
+    lib.fsd_last_error.argtypes = [P]
+    lib.fsd_last_error.restype = ctypes.c_char_p
+    lib.fsd_destroy.argtypes = [P]
+    lib.fsd_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("fsd_default_params", "fsd_last_error", "fsd_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class FsdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(arr):
+    """Pointer of a NumPy array or torch tensor (None passes through)."""
+    if arr is None:
+        return None
+    if hasattr(arr, "data_ptr"):
+        if not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(arr.data_ptr())
+    if not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_params(**kw):
+    lib = load()
+    p = FsdParams()
+    lib.fsd_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Suspension:
+    """One suspension behind an fsd_ctx (fsd_setup ... fsd_destroy)."""
+
+    def __init__(self, bead_pos, agg_id, box, stream=None, **params):
+        self.lib = load()
+        self._keep = []
+        pos = bead_pos if hasattr(bead_pos, "data_ptr") else np.ascontiguousarray(bead_pos, dtype=np.float64)
+        ids = agg_id if hasattr(agg_id, "data_ptr") else np.ascontiguousarray(agg_id, dtype=np.int32)
+        self.n_beads = int(pos.shape[0])
+        self.n_agg = int(ids.max()) + 1
+        self.params_in = default_params(box=float(box), **params)
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.fsd_setup(ctypes.byref(self.ctx), self.n_beads, _ptr(pos), _ptr(ids),
+                                ctypes.byref(self.params_in), stream)
+        if st != FSD_OK:
+            raise FsdError(st, self.lib.fsd_last_error(None).decode())
+
+    def _check(self, st, allow=(FSD_OK,)):
+        if st not in allow:
+            raise FsdError(st, self.lib.fsd_last_error(self.ctx).decode())
+        return st
+
+    @property
+    def params(self):
+        p = FsdParams()
+        self._check(self.lib.fsd_get_params(self.ctx, ctypes.byref(p)))
+        return p.as_dict()
+
+    def solve(self, ft=None, shear=0.0, vel=None, stresslet=None, allow=(FSD_OK, FSD_EOVERLAP)):
+        """fsd_solve; returns (velocity [N,6], stresslet [N,3,3], stats dict, status)."""
+        if vel is None:
+            vel = np.zeros((self.n_agg, 6))
+        if stresslet is None:
+            stresslet = np.zeros((self.n_agg, 3, 3))
+        st_ = FsdStats()
+        st = self.lib.fsd_solve(self.ctx, _ptr(ft), float(shear), _ptr(vel), _ptr(stresslet),
+                                ctypes.byref(st_))
+        self._check(st, allow)
+        return vel, stresslet, st_.as_dict(), st
+
+    def step(self, ft=None, shear=0.0, dt=1e-3, vel=None, allow=(FSD_OK, FSD_EOVERLAP)):
+        st_ = FsdStats()
+        st = self.lib.fsd_step(self.ctx, _ptr(ft), float(shear), float(dt), _ptr(vel),
+                               ctypes.byref(st_))
+        self._check(st, allow)
+        return st_.as_dict(), st
+
+    def beads(self):
+        pos = np.zeros((self.n_beads, 3))
+        q = np.zeros((self.n_agg, 4))
+        self._check(self.lib.fsd_get_beads(self.ctx, _ptr(pos), _ptr(q)))
+        return pos, q
+
+    def apply_mobility(self, F, part=3, precision=FSD_FP64, out=None):
+        F = F if hasattr(F, "data_ptr") else np.ascontiguousarray(F, dtype=np.float64)
+        if out is None:
+            out = np.zeros((self.n_beads, 11))
+        self._check(self.lib.fsd_apply_mobility(self.ctx, _ptr(F), _ptr(out), int(part), int(precision)))
+        return out
+
+    def apply_saddle(self, x, precision=FSD_FP64, out=None):
+        x = x if hasattr(x, "data_ptr") else np.ascontiguousarray(x, dtype=np.float64)
+        if out is None:
+            out = np.zeros(11 * self.n_beads + 6 * self.n_agg)
+        self._check(self.lib.fsd_apply_saddle(self.ctx, _ptr(x), _ptr(out), int(precision)))
+        return out
+
+    def apply_precond(self, r, out=None):
+        r = r if hasattr(r, "data_ptr") else np.ascontiguousarray(r, dtype=np.float64)
+        if out is None:
+            out = np.zeros(11 * self.n_beads + 6 * self.n_agg)
+        self._check(self.lib.fsd_apply_precond(self.ctx, _ptr(r), _ptr(out)))
+        return out
+
+    def apply_lubrication(self, dU, precision=FSD_FP64, out=None):
+        dU = dU if hasattr(dU, "data_ptr") else np.ascontiguousarray(dU, dtype=np.float64)
+        if out is None:
+            out = np.zeros((self.n_agg, 6))
+        self._check(self.lib.fsd_apply_lubrication(self.ctx, _ptr(dU), _ptr(out), int(precision)))
+        return out
+
+    def rhs(self, ft=None, shear=0.0, out=None):
+        if ft is not None and not hasattr(ft, "data_ptr"):
+            ft = np.ascontiguousarray(ft, dtype=np.float64)
+        if out is None:
+            out = np.zeros(11 * self.n_beads + 6 * self.n_agg)
+        self._check(self.lib.fsd_rhs(self.ctx, _ptr(ft), float(shear), _ptr(out)))
+        return out
+
+    def close(self):
+        if self.ctx:
+            self.lib.fsd_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

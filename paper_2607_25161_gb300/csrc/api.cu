@@ -1,0 +1,862 @@
+// C ABI of the FSD library (include/fsd.h): set-up (Algorithm 1 step 1
+// data), the saddle-point solve (step 4: GMRES with the block-triangular
+// preconditioner of Table 1), the rigid-body step (step 5), and operator
+// access.  Host orchestration only; every arithmetic step of the path runs in
+// the CUDA kernels of realspace.cu, wavespace.cu, nearfield.cu, krylov.cu.
+#include "fsd_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+struct fsd_ctx {
+  fsd::Ctx c;
+};
+
+namespace fsd {
+
+bool fft_size_ok(int n);
+void vec_scale_host(Ctx &c, double *y, const double *x, double s);
+
+static std::string g_setup_error;
+
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------ permutations
+__global__ void k_beads_in(int Nt, const int *__restrict__ perm, const double *__restrict__ user,
+                           double *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const double *u = user + 11 * (size_t)perm[i];
+  double *o = x + (size_t)i * LDB;
+  for (int k = 0; k < 11; ++k) o[k] = u[k];
+  o[11] = 0.0;
+}
+__global__ void k_beads_out(int Nt, const int *__restrict__ perm, const double *__restrict__ x,
+                            double *user) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  double *u = user + 11 * (size_t)perm[i];
+  const double *o = x + (size_t)i * LDB;
+  for (int k = 0; k < 11; ++k) u[k] = o[k];
+}
+__global__ void k_bodies_in(int N, const int *__restrict__ perm, const double *__restrict__ user,
+                            double *x, int w) {
+  int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= N) return;
+  for (int k = 0; k < w; ++k) x[(size_t)w * J + k] = user[(size_t)w * perm[J] + k];
+}
+__global__ void k_bodies_out(int N, const int *__restrict__ perm, const double *__restrict__ x,
+                             double *user, int w) {
+  int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= N) return;
+  for (int k = 0; k < w; ++k) user[(size_t)w * perm[J] + k] = x[(size_t)w * J + k];
+}
+__global__ void k_bead_pos_out(int Nt, const int *__restrict__ perm,
+                               const int *__restrict__ bead_body, const double *__restrict__ X,
+                               const double4 *__restrict__ lever, double *user) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const int J = bead_body[i];
+  const double4 r = lever[i];
+  double *u = user + 3 * (size_t)perm[i];
+  u[0] = X[3 * J] + r.x;
+  u[1] = X[3 * J + 1] + r.y;
+  u[2] = X[3 * J + 2] + r.z;
+}
+__global__ void k_nan_check(const double *__restrict__ x, int64_t n, int *flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    if (!(fabs(x[i]) <= 1e300)) atomicOr(flag, 1);
+}
+
+// Host or device input of `bytes` -> a device pointer (staged in `buf` when host).
+static const double *dev_in(Ctx &c, const double *p, size_t count, DBuf<double> &buf) {
+  if (!p) return nullptr;
+  if (is_device_ptr(p)) return p;
+  if (buf.n < count) buf.alloc(count);
+  FSD_CUDA(cudaMemcpyAsync(buf.p, p, count * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  return buf.p;
+}
+
+// ------------------------------------------------------------------ solver
+template <typename T>
+void apply_saddle(Ctx &c, const double *x, double *y) {
+  launch_realspace<T>(c, x, y, true, false);
+  launch_wavespace<T>(c, x, y);
+  launch_body_rows<T>(c, x, y, true);
+}
+template void apply_saddle<float>(Ctx &, const double *, double *);
+template void apply_saddle<double>(Ctx &, const double *, double *);
+
+struct KStats {
+  int iters = 0, m64 = 0, m32 = 0, outer = 0;
+};
+
+static double host_norm(Ctx &c, const double *x) {
+  double *d = c.hcol.p + 200;
+  norm2_dev(c, x, d);
+  FSD_CUDA(cudaMemcpyAsync(c.h_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  return std::sqrt(std::max(0.0, c.h_pinned[0]));
+}
+
+// Right-preconditioned restarted flexible GMRES (Z stores P^-1 v_j), CGS2
+// Arnoldi in FP64, Givens rotations on the host.  The operator precision is
+// T.  Solves A x = b from x (x_zero: x = 0).  Stops when the residual is
+// below tol * bnorm (the true residual when true_check), or after max_iter
+// iterations.  Returns the last residual / bnorm.
+template <typename T>
+static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol, int max_iter,
+                    int m, bool x_zero, bool true_check, KStats &st) {
+  const int64_t ld = c.nunk;
+  double *V = c.V.p, *Z = c.Z.p, *w = c.w.p;
+  int total = 0;
+  double rel = 1.0;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1);
+  while (true) {
+    if (x_zero) {
+      FSD_CUDA(cudaMemcpyAsync(V, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+      apply_saddle<T>(c, x, w);
+      (sizeof(T) == 8 ? st.m64 : st.m32)++;
+      FSD_CUDA(cudaMemcpyAsync(V, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      vec_axpby(c, V, -1.0, w, 1.0, ld);
+    }
+    const double beta = host_norm(c, V);
+    rel = beta / bnorm;
+    if (!(beta == beta)) throw Invalid{"NaN in the Krylov residual"};
+    if (beta <= tol * bnorm || total >= max_iter) return rel;
+    vec_scale_host(c, V, V, 1.0 / beta);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    double resid = beta;
+    for (; j < m && total < max_iter;) {
+      double *vj = V + (int64_t)j * ld, *zj = Z + (int64_t)j * ld;
+      launch_precond(c, vj, zj);
+      apply_saddle<T>(c, zj, w);
+      (sizeof(T) == 8 ? st.m64 : st.m32)++;
+      double *h1 = c.hcol.p, *h2 = c.hcol.p + 64, *hn = c.hcol.p + 128;
+      dot_multi(c, V, ld, j + 1, w, h1);
+      axpy_multi(c, w, V, ld, j + 1, h1, -1.0);
+      dot_multi(c, V, ld, j + 1, w, h2);
+      axpy_multi(c, w, V, ld, j + 1, h2, -1.0);
+      norm2_dev(c, w, hn);
+      FSD_CUDA(cudaMemcpyAsync(c.h_pinned, c.hcol.p, 192 * sizeof(double),
+                               cudaMemcpyDeviceToHost, c.stream));
+      FSD_CUDA(cudaStreamSynchronize(c.stream));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = c.h_pinned[i] + c.h_pinned[64 + i];
+      const double hnext = std::sqrt(std::max(0.0, c.h_pinned[128]));
+      if (!(hnext == hnext)) throw Invalid{"NaN in the Arnoldi process"};
+      // Givens
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[(size_t)j * m + j];
+      double den = std::hypot(a, hnext);
+      cs[j] = den > 0 ? a / den : 1.0;
+      sn[j] = den > 0 ? hnext / den : 0.0;
+      H[(size_t)j * m + j] = den;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      resid = std::fabs(g[j + 1]);
+      ++j;
+      ++total;
+      ++st.iters;
+      if (resid <= tol * bnorm || hnext <= 1e-300) break;
+      if (j < m) vec_scale_host(c, V + (int64_t)j * ld, w, 1.0 / hnext);
+    }
+    // y = H^-1 g (upper triangular j x j); x += Z y
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    if (x_zero) FSD_CUDA(cudaMemsetAsync(x, 0, ld * sizeof(double), c.stream));
+    std::memcpy(c.h_pinned + 256, y.data(), j * sizeof(double));
+    FSD_CUDA(cudaMemcpyAsync(c.hcol.p + 256, c.h_pinned + 256, j * sizeof(double),
+                             cudaMemcpyHostToDevice, c.stream));
+    axpy_multi(c, x, Z, ld, j, c.hcol.p + 256, 1.0);
+    x_zero = false;
+    rel = resid / bnorm;
+    if (resid <= tol * bnorm && !true_check) {
+      FSD_CUDA(cudaStreamSynchronize(c.stream));
+      return rel;
+    }
+    if (total >= max_iter && !true_check) {
+      FSD_CUDA(cudaStreamSynchronize(c.stream));
+      return rel;
+    }
+  }
+}
+
+// Solve A x = b.  FP64: restarted GMRES on the FP64 operator.  Mixed: FP64
+// iterative refinement; each correction from GMRES on the FP32 operator
+// (FP64 vectors, Arnoldi and LU), each residual from the FP64 operator.
+static double solve_system(Ctx &c, const double *b, double *x, KStats &st, bool warm) {
+  const int64_t ld = c.nunk;
+  const double bnorm = host_norm(c, b);
+  if (bnorm == 0.0) {
+    FSD_CUDA(cudaMemsetAsync(x, 0, ld * sizeof(double), c.stream));
+    return 0.0;
+  }
+  const double tol = c.prm.tol;
+  if (c.prm.precision == FSD_FP64) {
+    if (warm) FSD_CUDA(cudaMemcpyAsync(x, c.xprev.p, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    double rel = gmres<double>(c, b, x, bnorm, tol, c.prm.max_iter, c.m, !warm, true, st);
+    st.outer = 1;
+    return rel;
+  }
+  double *r = c.res.p, *d = c.t1.p;
+  if (warm) {
+    FSD_CUDA(cudaMemcpyAsync(x, c.xprev.p, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    apply_saddle<double>(c, x, c.w.p);
+    st.m64++;
+    FSD_CUDA(cudaMemcpyAsync(r, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    vec_axpby(c, r, -1.0, c.w.p, 1.0, ld);
+  } else {
+    FSD_CUDA(cudaMemsetAsync(x, 0, ld * sizeof(double), c.stream));
+    FSD_CUDA(cudaMemcpyAsync(r, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  }
+  double rel = host_norm(c, r) / bnorm;
+  const int max_outer = 50;
+  while (rel > tol && st.iters < c.prm.max_iter && st.outer < max_outer) {
+    const double rn = rel * bnorm;
+    // the correction only has to close the remaining gap to tol
+    const double itol = std::max(c.prm.inner_tol, 0.3 * tol / rel);
+    gmres<float>(c, r, d, rn, itol, c.m_in, c.m_in, true, false, st);
+    vec_axpby(c, x, 1.0, d, 1.0, ld);
+    apply_saddle<double>(c, x, c.w.p);
+    st.m64++;
+    FSD_CUDA(cudaMemcpyAsync(r, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    vec_axpby(c, r, -1.0, c.w.p, 1.0, ld);
+    rel = host_norm(c, r) / bnorm;
+    st.outer++;
+  }
+  return rel;
+}
+
+// --------------------------------------------------------------- set-up
+static int round_up_smooth_even(int n) {
+  if (n < 8) n = 8;
+  for (int m = n;; ++m)
+    if (fft_size_ok(m)) return m;
+}
+
+static uint32_t spread_bits(uint32_t v) {
+  v &= 0x3ff;
+  v = (v | (v << 16)) & 0x030000FF;
+  v = (v | (v << 8)) & 0x0300F00F;
+  v = (v | (v << 4)) & 0x030C30C3;
+  v = (v | (v << 2)) & 0x09249249;
+  return v;
+}
+
+static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
+                       const fsd_params &p, void *stream) {
+  if (n_beads < 1) throw Invalid{"n_beads must be >= 1"};
+  if (n_beads > (1 << 28)) throw Invalid{"n_beads too large"};
+  if (!bead_pos || !agg_id) throw Invalid{"bead_pos and agg_id are required"};
+  if (!(p.box > 0)) throw Invalid{"box must be > 0"};
+  if (!(p.a > 0) || !(p.eta > 0)) throw Invalid{"a and eta must be > 0"};
+  c.prm = p;
+  c.Nt = (int)n_beads;
+  c.L = p.box;
+  c.a = p.a;
+  c.eta = p.eta;
+  if (stream) {
+    c.stream = (cudaStream_t)stream;
+    c.own_stream = false;
+  } else {
+    FSD_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+    c.own_stream = true;
+  }
+  // ---- inputs to host
+  std::vector<double> pos(3 * (size_t)c.Nt);
+  std::vector<int32_t> ids(c.Nt);
+  if (is_device_ptr(bead_pos))
+    FSD_CUDA(cudaMemcpy(pos.data(), bead_pos, pos.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  else
+    std::memcpy(pos.data(), bead_pos, pos.size() * sizeof(double));
+  if (is_device_ptr(agg_id))
+    FSD_CUDA(cudaMemcpy(ids.data(), agg_id, ids.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  else
+    std::memcpy(ids.data(), agg_id, ids.size() * sizeof(int32_t));
+  int32_t mx = -1;
+  for (int i = 0; i < c.Nt; ++i) {
+    if (ids[i] < 0) throw Invalid{"agg_id must be >= 0"};
+    if (!(std::isfinite(pos[3 * i]) && std::isfinite(pos[3 * i + 1]) && std::isfinite(pos[3 * i + 2])))
+      throw Invalid{"bead_pos holds a non-finite value"};
+    mx = std::max(mx, ids[i]);
+  }
+  c.N = mx + 1;
+  std::vector<std::vector<int>> members(c.N);
+  for (int i = 0; i < c.Nt; ++i) members[ids[i]].push_back(i);
+  for (int J = 0; J < c.N; ++J)
+    if (members[J].empty()) throw Invalid{"agg_id values must be dense 0..N-1"};
+  // ---- per body: unwrap about the first bead, centroid, body frame
+  const double L = c.L;
+  std::vector<double> X(3 * (size_t)c.N), rb(3 * (size_t)c.Nt);
+  std::vector<double> unw(3 * (size_t)c.Nt);
+  for (int J = 0; J < c.N; ++J) {
+    const int f = members[J][0];
+    double s[3] = {0, 0, 0};
+    for (int i : members[J])
+      for (int d = 0; d < 3; ++d) {
+        double dd = pos[3 * i + d] - pos[3 * f + d];
+        dd -= L * std::nearbyint(dd / L);
+        unw[3 * i + d] = pos[3 * f + d] + dd;
+        s[d] += unw[3 * i + d];
+      }
+    for (int d = 0; d < 3; ++d) X[3 * J + d] = s[d] / members[J].size();
+  }
+  // ---- spatial order of bodies (Morton code of the wrapped centroid)
+  std::vector<uint64_t> key(c.N);
+  for (int J = 0; J < c.N; ++J) {
+    uint32_t cc[3];
+    for (int d = 0; d < 3; ++d) {
+      double w = X[3 * J + d] - L * std::floor(X[3 * J + d] / L);
+      int v = (int)(w / L * 1024.0);
+      cc[d] = (uint32_t)std::min(1023, std::max(0, v));
+    }
+    key[J] = ((uint64_t)(spread_bits(cc[0]) | (spread_bits(cc[1]) << 1) | (spread_bits(cc[2]) << 2)) << 32) | (uint32_t)J;
+  }
+  std::vector<int> order(c.N);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int x1, int x2) { return key[x1] < key[x2]; });
+  c.h_perm_body = order;
+  c.h_perm_bead.clear();
+  c.h_body_start.assign(c.N + 1, 0);
+  std::vector<int> bead_body(c.Nt);
+  std::vector<double> Xi(3 * (size_t)c.N), rbi(3 * (size_t)c.Nt), qi(4 * (size_t)c.N, 0.0);
+  for (int Ji = 0; Ji < c.N; ++Ji) {
+    const int J = order[Ji];
+    c.h_body_start[Ji] = (int)c.h_perm_bead.size();
+    for (int d = 0; d < 3; ++d) Xi[3 * Ji + d] = X[3 * J + d];
+    qi[4 * Ji] = 1.0;
+    for (int i : members[J]) {
+      const int ii = (int)c.h_perm_bead.size();
+      c.h_perm_bead.push_back(i);
+      bead_body[ii] = Ji;
+      for (int d = 0; d < 3; ++d) rbi[3 * ii + d] = unw[3 * i + d] - X[3 * J + d];
+    }
+  }
+  c.h_body_start[c.N] = c.Nt;
+  // ---- parameters (rules of Sec. 3.2 unless given)
+  const double a = c.a;
+  c.xi = p.xi > 0 ? p.xi : 0.5 / a;
+  const double xerr = p.xerr > 0 ? p.xerr : 1e-6;
+  c.prm.xerr = xerr;
+  const double lnx = std::sqrt(-std::log(xerr));
+  c.rc = p.rc > 0 ? p.rc : 2.0 * a + lnx / c.xi;
+  if (p.grid > 0) {
+    if (!fft_size_ok(p.grid)) throw Invalid{"grid must be even and 2,3,5-smooth (>= 8)"};
+    c.n = p.grid;
+  } else {
+    const double kc = 2.0 * lnx * c.xi + 1.0;
+    c.n = round_up_smooth_even((int)std::ceil(kc * L / kPi));
+  }
+  c.P = p.P > 0 ? p.P : 8;
+  if (c.P % 2 || c.P < 4 || c.P > 24) throw Invalid{"P must be even, 4..24"};
+  if (c.P > c.n) throw Invalid{"P must not exceed the grid size"};
+  c.m_shape = p.m_shape > 0 ? p.m_shape : 0.976 * std::sqrt(kPi * c.P);
+  c.h = L / c.n;
+  c.alpha = 2.0 * c.m_shape * c.m_shape / ((c.P * c.h) * (c.P * c.h));
+  if (c.rc >= 0.5 * L) throw Invalid{"real-space cut-off must be below L/2 (raise xi or the box)"};
+  if (p.lub_cutoff < 0) throw Invalid{"lub_cutoff must be >= 0"};
+  if (p.lub_cutoff >= 0.5 * L) throw Invalid{"lub_cutoff must be below L/2"};
+  c.prm.lub_cutoff = p.lub_cutoff > 2.0 * a ? p.lub_cutoff : 0.0;
+  c.prm.precond_cutoff = p.precond_cutoff > 0 ? p.precond_cutoff : 2.1 * a;
+  if (c.prm.lub_cutoff > 0) c.prm.precond_cutoff = std::min(c.prm.precond_cutoff, c.prm.lub_cutoff);
+  c.prm.lub_hmin = p.lub_hmin > 0 ? p.lub_hmin : 1e-3 * a;
+  c.prm.tol = p.tol > 0 ? p.tol : 1e-6;
+  c.m = p.restart > 0 ? std::min(p.restart, 60) : 30;
+  c.prm.restart = c.m;
+  c.prm.max_iter = p.max_iter > 0 ? p.max_iter : 1000;
+  if (p.precision != FSD_FP64 && p.precision != FSD_MIXED) throw Invalid{"precision must be 0 or 1"};
+  c.m_in = p.inner_restart > 0 ? std::min(p.inner_restart, 60) : 30;
+  c.prm.inner_restart = c.m_in;
+  c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-4;
+  c.prm.xi = c.xi;
+  c.prm.rc = c.rc;
+  c.prm.grid = c.n;
+  c.prm.P = c.P;
+  c.prm.m_shape = c.m_shape;
+  // ---- device state
+  const int Nt = c.Nt, N = c.N;
+  c.nunk = (int64_t)LDB * Nt + 6 * (int64_t)N;
+  c.body_start.alloc(N + 1);
+  c.bead_body.alloc(Nt);
+  c.perm_bead.alloc(Nt);
+  c.perm_body.alloc(N);
+  c.X.alloc(3 * (size_t)N);
+  c.q.alloc(4 * (size_t)N);
+  c.rbody.alloc(3 * (size_t)Nt);
+  c.pos64.alloc(4 * (size_t)Nt);
+  c.lever64.alloc(4 * (size_t)Nt);
+  c.op32.pos.alloc(4 * (size_t)Nt);
+  c.op32.lever.alloc(4 * (size_t)Nt);
+  FSD_CUDA(cudaMemcpy(c.body_start.p, c.h_body_start.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  FSD_CUDA(cudaMemcpy(c.bead_body.p, bead_body.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
+  FSD_CUDA(cudaMemcpy(c.perm_bead.p, c.h_perm_bead.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
+  FSD_CUDA(cudaMemcpy(c.perm_body.p, c.h_perm_body.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+  FSD_CUDA(cudaMemcpy(c.X.p, Xi.data(), Xi.size() * sizeof(double), cudaMemcpyHostToDevice));
+  FSD_CUDA(cudaMemcpy(c.q.p, qi.data(), qi.size() * sizeof(double), cudaMemcpyHostToDevice));
+  FSD_CUDA(cudaMemcpy(c.rbody.p, rbi.data(), rbi.size() * sizeof(double), cudaMemcpyHostToDevice));
+  // neighbour capacities from the mean density (grown on overflow)
+  const double dens = Nt / (L * L * L);
+  const double expect = dens * 4.0 / 3.0 * kPi * c.rc * c.rc * c.rc;
+  c.cap = ((int)(1.6 * expect + 64) + 31) / 32 * 32;
+  c.lcap = 16;
+  c.nbr.alloc((size_t)Nt * c.cap);
+  c.ncnt.alloc(Nt);
+  c.lnbr.alloc((size_t)Nt * c.lcap);
+  c.lcnt.alloc(Nt);
+  c.flags.alloc(8);
+  FSD_CUDA(cudaMallocHost(&c.h_flags, 8 * sizeof(int)));
+  c.brow.alloc(Nt + 1);
+  c.op64.bdiag.alloc((size_t)Nt * 36);
+  c.op32.bdiag.alloc((size_t)Nt * 36);
+  c.pdiag.alloc((size_t)Nt * 36);
+  c.schur.alloc((size_t)N * 36);
+  c.piv.alloc((size_t)N * 6);
+  c.fnf.alloc((size_t)Nt * 6);
+  c.snf.alloc((size_t)Nt * 5);
+  FSD_CUDA(cudaMemset(c.fnf.p, 0, (size_t)Nt * 6 * sizeof(double)));
+  FSD_CUDA(cudaMemset(c.snf.p, 0, (size_t)Nt * 5 * sizeof(double)));
+  const int mm = std::max(c.m, c.m_in);
+  c.V.alloc((size_t)(mm + 1) * c.nunk);
+  c.Z.alloc((size_t)mm * c.nunk);
+  c.w.alloc(c.nunk);
+  c.t1.alloc(c.nunk);
+  c.t2.alloc(c.nunk);
+  c.xsol.alloc(c.nunk);
+  c.rhs.alloc(c.nunk);
+  c.res.alloc(c.nunk);
+  c.xprev.alloc(c.nunk);
+  c.partial.alloc((size_t)64 * 4 * 152);
+  c.hcol.alloc(512);
+  FSD_CUDA(cudaMallocHost(&c.h_pinned, 512 * sizeof(double)));
+  build_real_table(c);
+  build_wave(c);
+  launch_wrap_positions(c);
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// Geometry-dependent preparation of one solve: positions, neighbour lists,
+// lubrication blocks, Schur LUs (Alg. 1 step 1).
+static void prepare(Ctx &c) {
+  c.last_warning = FSD_OK;
+  launch_wrap_positions(c);
+  build_neighbors(c);
+  {
+    // pair count for the real-space launch shape
+    std::vector<int> cnt(c.Nt);
+    FSD_CUDA(cudaMemcpyAsync(cnt.data(), c.ncnt.p, c.Nt * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    FSD_CUDA(cudaStreamSynchronize(c.stream));
+    int64_t s = 0;
+    for (int v : cnt) s += v;
+    c.n_pairs = s;
+  }
+  build_lubrication(c);
+}
+
+static void fill_stats(Ctx &c, fsd_stats *st, const KStats &k, double rel, double ms) {
+  if (!st) return;
+  st->iters = k.iters;
+  st->outer_iters = k.outer;
+  st->matvec64 = k.m64;
+  st->matvec32 = k.m32;
+  st->rel_residual = rel;
+  st->ms_total = ms;
+  st->n_pairs = c.n_pairs;
+  st->n_lub = c.n_lub;
+  st->grid = c.n;
+  st->P = c.P;
+  st->xi = c.xi;
+  st->rc = c.rc;
+}
+
+static fsd_status check_flags(Ctx &c) {
+  FSD_CUDA(cudaMemcpyAsync(c.h_flags, c.flags.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  if (c.h_flags[3]) {
+    c.last_error = "singular per-aggregate 6x6 preconditioner block";
+    return FSD_ENUMERIC;
+  }
+  return FSD_OK;
+}
+
+// One solve; vel_int / str_int are internal-order device outputs.
+static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, double *vel_int,
+                                 double *str_int, fsd_stats *stats, double t0_ms) {
+  auto t0 = std::chrono::steady_clock::now();
+  prepare(c);
+  fsd_status fl = check_flags(c);
+  const double *ft_int = nullptr;
+  if (ft_user) {
+    const double *d = dev_in(c, ft_user, 6 * (size_t)c.N, c.io_a);
+    if (c.t2.n < 6 * (size_t)c.N) c.t2.alloc(6 * (size_t)c.N);
+    k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d, c.t2.p, 6);
+    FSD_CUDA(cudaGetLastError());
+    ft_int = c.t2.p;
+  }
+  launch_rhs(c, ft_int, shear, c.rhs.p);
+  KStats ks;
+  const bool warm = (c.prm.flags & FSD_FLAG_WARM_START) && c.have_prev;
+  double rel = solve_system(c, c.rhs.p, c.xsol.p, ks, warm);
+  FSD_CUDA(cudaMemcpyAsync(c.xprev.p, c.xsol.p, c.nunk * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  c.have_prev = true;
+  launch_outputs(c, c.xsol.p, shear, vel_int, str_int);
+  FSD_CUDA(cudaMemsetAsync(c.flags.p + 6, 0, sizeof(int), c.stream));
+  k_nan_check<<<152, 256, 0, c.stream>>>(vel_int, 6 * (int64_t)c.N, c.flags.p + 6);
+  FSD_CUDA(cudaMemcpyAsync(c.h_flags, c.flags.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() + t0_ms;
+  fill_stats(c, stats, ks, rel, ms);
+  if (c.h_flags[6]) {
+    c.last_error = "non-finite aggregate velocity";
+    return FSD_ENUMERIC;
+  }
+  if (fl != FSD_OK) return fl;
+  if (!(rel <= c.prm.tol)) {
+    c.last_error = "Krylov solve stopped at relative residual " + std::to_string(rel);
+    return FSD_ENOCONV;
+  }
+  if (c.last_warning == FSD_EOVERLAP) {
+    c.last_error = "beads of different aggregates overlap (warning; results written)";
+    return FSD_EOVERLAP;
+  }
+  return FSD_OK;
+}
+
+// Write an internal-order device array of N x w to a user pointer (host or device).
+static void bodies_out(Ctx &c, const double *src_int, double *user, int w) {
+  if (!user) return;
+  if (is_device_ptr(user)) {
+    k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, src_int, user, w);
+    FSD_CUDA(cudaGetLastError());
+    FSD_CUDA(cudaStreamSynchronize(c.stream));
+  } else {
+    if (c.io_b.n < (size_t)w * c.N) c.io_b.alloc((size_t)w * c.N);
+    k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, src_int, c.io_b.p, w);
+    FSD_CUDA(cudaGetLastError());
+    FSD_CUDA(cudaMemcpyAsync(user, c.io_b.p, (size_t)w * c.N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    FSD_CUDA(cudaStreamSynchronize(c.stream));
+  }
+}
+
+}  // namespace fsd
+
+using namespace fsd;
+
+#define FSD_API_TRY try {
+#define FSD_API_CATCH(ctxp)                                                     \
+  }                                                                             \
+  catch (const CudaError &e) {                                                  \
+    std::string m = std::string(e.what) + ": " + cudaGetErrorString(e.e);       \
+    if (ctxp) (ctxp)->c.last_error = m; else g_setup_error = m;                 \
+    return e.e == cudaErrorMemoryAllocation ? FSD_ENOMEM : FSD_ECUDA;           \
+  }                                                                             \
+  catch (const Invalid &e) {                                                    \
+    if (ctxp) (ctxp)->c.last_error = e.msg; else g_setup_error = e.msg;         \
+    return FSD_EINVAL;                                                          \
+  }                                                                             \
+  catch (const std::bad_alloc &) {                                              \
+    if (ctxp) (ctxp)->c.last_error = "host allocation failed";                  \
+    else g_setup_error = "host allocation failed";                              \
+    return FSD_ENOMEM;                                                          \
+  }
+
+extern "C" {
+
+void fsd_default_params(fsd_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->a = 1.0;
+  p->eta = 1.0;
+  p->box = 0.0;
+  p->xi = 0.0;
+  p->xerr = 1e-6;
+  p->rc = 0.0;
+  p->grid = 0;
+  p->P = 8;
+  p->m_shape = 0.0;
+  p->lub_cutoff = 0.0;
+  p->precond_cutoff = 2.1;
+  p->lub_hmin = 1e-3;
+  p->tol = 1e-6;
+  p->restart = 30;
+  p->max_iter = 1000;
+  p->precision = FSD_FP64;
+  p->inner_restart = 30;
+  p->inner_tol = 1e-4;
+  p->flags = 0;
+}
+
+fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
+                     const fsd_params *p, void *cuda_stream) {
+  if (!ctx || !p) {
+    g_setup_error = "ctx and params are required";
+    return FSD_EINVAL;
+  }
+  *ctx = nullptr;
+  fsd_ctx *cx = nullptr;
+  FSD_API_TRY
+  cx = new fsd_ctx();
+  setup_impl(cx->c, n_beads, bead_pos, agg_id, *p, cuda_stream);
+  *ctx = cx;
+  return FSD_OK;
+  }
+  catch (const CudaError &e) {
+    g_setup_error = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+    fsd_destroy(cx);
+    return e.e == cudaErrorMemoryAllocation ? FSD_ENOMEM : FSD_ECUDA;
+  }
+  catch (const Invalid &e) {
+    g_setup_error = e.msg;
+    fsd_destroy(cx);
+    return FSD_EINVAL;
+  }
+  catch (const std::bad_alloc &) {
+    g_setup_error = "host allocation failed";
+    fsd_destroy(cx);
+    return FSD_ENOMEM;
+  }
+}
+
+fsd_status fsd_solve(fsd_ctx *ctx, const double *agg_force_torque, double shear_rate,
+                     double *agg_velocity, double *agg_stresslet, fsd_stats *stats) {
+  if (!ctx) return FSD_EINVAL;
+  if (!agg_velocity) {
+    ctx->c.last_error = "agg_velocity is required";
+    return FSD_EINVAL;
+  }
+  if (!std::isfinite(shear_rate)) {
+    ctx->c.last_error = "shear_rate must be finite";
+    return FSD_EINVAL;
+  }
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  auto t0 = std::chrono::steady_clock::now();
+  if (c.io_b.n < 16 * (size_t)c.N) c.io_b.alloc(16 * (size_t)c.N);
+  DBuf<double> &vel = c.io_b;
+  // internal outputs live in t1 (velocity) / res (stresslet) after the solve
+  double *vel_int = c.t1.p;
+  double *str_int = agg_stresslet ? c.res.p : nullptr;
+  fsd_status st = solve_internal(c, agg_force_torque, shear_rate, vel_int, str_int, stats, 0.0);
+  if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
+  (void)vel;
+  bodies_out(c, vel_int, agg_velocity, 6);
+  if (agg_stresslet) bodies_out(c, str_int, agg_stresslet, 9);
+  if (stats)
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque, double shear_rate, double dt,
+                    double *agg_velocity, fsd_stats *stats) {
+  if (!ctx) return FSD_EINVAL;
+  if (!std::isfinite(dt) || !std::isfinite(shear_rate)) {
+    ctx->c.last_error = "dt and shear_rate must be finite";
+    return FSD_EINVAL;
+  }
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  auto t0 = std::chrono::steady_clock::now();
+  double *vel_int = c.t1.p;
+  fsd_status st = solve_internal(c, agg_force_torque, shear_rate, vel_int, nullptr, stats, 0.0);
+  if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
+  if (agg_velocity) bodies_out(c, vel_int, agg_velocity, 6);
+  launch_integrate(c, vel_int, dt);
+  launch_wrap_positions(c);
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  if (stats)
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_get_beads(fsd_ctx *ctx, double *bead_pos, double *agg_quat) {
+  if (!ctx) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  launch_wrap_positions(c);
+  if (bead_pos) {
+    if (c.io_a.n < 3 * (size_t)c.Nt) c.io_a.alloc(3 * (size_t)c.Nt);
+    k_bead_pos_out<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, c.perm_bead.p, c.bead_body.p, c.X.p,
+                                                             (const double4 *)c.lever64.p, c.io_a.p);
+    FSD_CUDA(cudaGetLastError());
+    FSD_CUDA(cudaMemcpyAsync(bead_pos, c.io_a.p, 3 * (size_t)c.Nt * sizeof(double), cudaMemcpyDefault, c.stream));
+  }
+  if (agg_quat) {
+    if (c.io_b.n < 16 * (size_t)c.N) c.io_b.alloc(16 * (size_t)c.N);
+    k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, c.q.p, c.io_b.p, 4);
+    FSD_CUDA(cudaGetLastError());
+    FSD_CUDA(cudaMemcpyAsync(agg_quat, c.io_b.p, 4 * (size_t)c.N * sizeof(double), cudaMemcpyDefault, c.stream));
+  }
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+// ---- operator access: user-ordered vectors in and out
+
+static void vec_in(Ctx &c, const double *user, double *x, bool beads, bool bodies) {
+  // user layout: [Nt][11] then [N][6]
+  const size_t nb = 11 * (size_t)c.Nt, nbd = 6 * (size_t)c.N;
+  const size_t tot = (beads ? nb : 0) + (bodies ? nbd : 0);
+  const double *d = dev_in(c, user, tot, c.io_a);
+  FSD_CUDA(cudaMemsetAsync(x, 0, c.nunk * sizeof(double), c.stream));
+  if (beads) k_beads_in<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, c.perm_bead.p, d, x);
+  if (bodies)
+    k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d + (beads ? nb : 0),
+                                                         x + (int64_t)LDB * c.Nt, 6);
+  FSD_CUDA(cudaGetLastError());
+}
+
+static void vec_out(Ctx &c, const double *x, double *user, bool beads, bool bodies) {
+  const size_t nb = 11 * (size_t)c.Nt, nbd = 6 * (size_t)c.N;
+  const size_t tot = (beads ? nb : 0) + (bodies ? nbd : 0);
+  const bool dev = is_device_ptr(user);
+  double *d = user;
+  if (!dev) {
+    if (c.io_b.n < tot) c.io_b.alloc(tot);
+    d = c.io_b.p;
+  }
+  if (beads) k_beads_out<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, c.perm_bead.p, x, d);
+  if (bodies)
+    k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, x + (int64_t)LDB * c.Nt,
+                                                          d + (beads ? nb : 0), 6);
+  FSD_CUDA(cudaGetLastError());
+  if (!dev)
+    FSD_CUDA(cudaMemcpyAsync(user, d, tot * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+fsd_status fsd_apply_mobility(fsd_ctx *ctx, const double *in, double *out, int part, int precision) {
+  if (!ctx || !in || !out || part < 1 || part > 3) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  prepare(c);
+  vec_in(c, in, c.t1.p, true, false);
+  double *y = c.t2.p;
+  FSD_CUDA(cudaMemsetAsync(y, 0, c.nunk * sizeof(double), c.stream));
+  if (precision == FSD_FP64) {
+    if (part & 1) launch_realspace<double>(c, c.t1.p, y, false, false);
+    if (part & 2) launch_wavespace<double>(c, c.t1.p, y);
+  } else {
+    if (part & 1) launch_realspace<float>(c, c.t1.p, y, false, false);
+    if (part & 2) launch_wavespace<float>(c, c.t1.p, y);
+  }
+  vec_out(c, y, out, true, false);
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_apply_saddle(fsd_ctx *ctx, const double *x, double *y, int precision) {
+  if (!ctx || !x || !y) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  prepare(c);
+  vec_in(c, x, c.t1.p, true, true);
+  if (precision == FSD_FP64)
+    apply_saddle<double>(c, c.t1.p, c.t2.p);
+  else
+    apply_saddle<float>(c, c.t1.p, c.t2.p);
+  vec_out(c, c.t2.p, y, true, true);
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_apply_precond(fsd_ctx *ctx, const double *r, double *z) {
+  if (!ctx || !r || !z) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  prepare(c);
+  fsd_status fl = check_flags(c);
+  vec_in(c, r, c.t1.p, true, true);
+  launch_precond(c, c.t1.p, c.t2.p);
+  vec_out(c, c.t2.p, z, true, true);
+  return fl;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_apply_lubrication(fsd_ctx *ctx, const double *dU, double *out, int precision) {
+  if (!ctx || !dU || !out) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  prepare(c);
+  // dU in the aggregate slots of a solution vector
+  const double *d = dev_in(c, dU, 6 * (size_t)c.N, c.io_a);
+  FSD_CUDA(cudaMemsetAsync(c.t1.p, 0, c.nunk * sizeof(double), c.stream));
+  k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d, c.t1.p + (int64_t)LDB * c.Nt, 6);
+  FSD_CUDA(cudaGetLastError());
+  if (precision == FSD_FP64)
+    launch_lub_apply<double>(c, c.t1.p, c.t2.p);
+  else
+    launch_lub_apply<float>(c, c.t1.p, c.t2.p);
+  bodies_out(c, c.t2.p + (int64_t)LDB * c.Nt, out, 6);
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_rhs(fsd_ctx *ctx, const double *agg_force_torque, double shear_rate, double *b) {
+  if (!ctx || !b) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  prepare(c);
+  const double *ft_int = nullptr;
+  if (agg_force_torque) {
+    const double *d = dev_in(c, agg_force_torque, 6 * (size_t)c.N, c.io_a);
+    k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d, c.t2.p, 6);
+    FSD_CUDA(cudaGetLastError());
+    ft_int = c.t2.p;
+  }
+  launch_rhs(c, ft_int, shear_rate, c.t1.p);
+  vec_out(c, c.t1.p, b, true, true);
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p) {
+  if (!ctx || !p) return FSD_EINVAL;
+  *p = ctx->c.prm;
+  return FSD_OK;
+}
+
+const char *fsd_last_error(const fsd_ctx *ctx) {
+  if (!ctx) return g_setup_error.c_str();
+  return ctx->c.last_error.c_str();
+}
+
+void fsd_destroy(fsd_ctx *ctx) {
+  if (!ctx) return;
+  Ctx &c = ctx->c;
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  if (c.h_flags) cudaFreeHost(c.h_flags);
+  if (c.h_pinned) cudaFreeHost(c.h_pinned);
+  cudaStream_t s = c.stream;
+  bool own = c.own_stream;
+  delete ctx;
+  if (own && s) cudaStreamDestroy(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal declarations of the FSD library: context, device buffers and the
+// launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fsd.h"
+
+namespace fsd {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int LDB = 12;     // doubles per bead in a solution vector (11 + zero pad)
+constexpr int NFUNC = 7;    // radial functions of the real-space table
+constexpr int TCOEF = 10;   // polynomial coefficients per function per interval
+constexpr int BLK = 36;     // 6x6 block
+
+// ------------------------------------------------------------------ errors
+struct CudaError {
+  cudaError_t e;
+  const char *what;
+};
+
+#define FSD_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e__ = (call);                                                 \
+    if (e__ != cudaSuccess) throw ::fsd::CudaError{e__, #call};               \
+  } while (0)
+
+struct Invalid {
+  std::string msg;
+};
+
+// ----------------------------------------------------------- device buffer
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  void alloc(size_t count) {
+    free();
+    if (count == 0) count = 1;
+    FSD_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void free() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { free(); }
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+};
+
+// ------------------------------------------------- per-precision operator
+// Everything the FP32 or the FP64 operator needs beyond the shared geometry.
+template <typename T>
+struct OpData {
+  DBuf<T> table;      // real-space radial table [nint][NFUNC][TCOEF]
+  T self_real[3];     // real-space self mobilities (translation, rotation, strain)
+  DBuf<T> grid;       // 6 * n * n * (n + 2) (padded rows; in-place r2c)
+  DBuf<T> green;      // [m = kx^2+ky^2+kz^2][3]: (A fM^2, A fM fD, A fD^2)
+  DBuf<T> twiddle;    // [n] complex: exp(-2 pi i t / n)
+  DBuf<T> bval;       // lubrication BSR off-diagonal blocks [nnz][36]
+  DBuf<T> bdiag;      // lubrication BSR diagonal blocks [Nt][36]
+  DBuf<T> pos;        // wrapped positions [Nt][4] (x, y, z, 0)
+  DBuf<T> lever;      // r_b = x_b - X_J [Nt][4]
+};
+
+struct Ctx {
+  // ---- parameters
+  fsd_params prm{};
+  double L = 0, a = 1, eta = 1, xi = 0.5, rc = 0, alpha = 0, h = 0;
+  int n = 0, P = 8;
+  double m_shape = 0;
+  int Nt = 0, N = 0;
+  int64_t nunk = 0;  // padded length of a solution vector: LDB*Nt + 6*N
+  // ---- real-space table geometry
+  int tab_nint = 0;
+  double tab_h = 0;
+  // ---- stream
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // ---- geometry (internal order: beads grouped by aggregate, aggregates
+  //      sorted spatially)
+  std::vector<int> h_perm_bead;  // internal bead -> user bead
+  std::vector<int> h_perm_body;  // internal body -> user id
+  std::vector<int> h_body_start;
+  DBuf<int> body_start, bead_body, perm_bead, perm_body;
+  DBuf<double> X, q, rbody, pos64, lever64;
+  // ---- neighbour lists
+  int cap = 0, lcap = 0, ncell = 1;
+  DBuf<int> nbr, ncnt, lnbr, lcnt;
+  DBuf<int> cell_count, cell_start, cell_beads, cell_cursor;
+  DBuf<int> flags;  // [0] nbr overflow, [1] lub overflow, [2] overlap, [3] singular LU, [4] max count
+  int *h_flags = nullptr;  // pinned
+  // ---- lubrication BSR (rows = beads; diagonal separate)
+  DBuf<int> brow, bcol;
+  int nnz_cap = 0;
+  // ---- preconditioner
+  DBuf<double> schur;  // [N][36] LU factors
+  DBuf<int> piv;       // [N][6]
+  // ---- operators
+  OpData<double> op64;
+  OpData<float> op32;
+  // ---- Krylov workspace
+  int m = 30, m_in = 30;
+  DBuf<double> V, Z, w, t1, t2, xsol, rhs, res, xprev, partial, hcol;
+  double *h_pinned = nullptr;  // host pinned scratch (dots)
+  bool have_prev = false;
+  // ---- outputs / near field scratch
+  DBuf<double> fnf, snf;  // per bead near-field force [Nt][6], stresslet [Nt][5]
+  DBuf<double> pdiag;     // per bead preconditioner near-field diagonal block [Nt][36]
+  DBuf<double> io_a, io_b;     // staging for host / permuted I/O
+  std::string last_error;
+  fsd_status last_warning = FSD_OK;
+  int64_t n_pairs = 0, n_lub = 0;
+};
+
+// ------------------------------------------------------------ launchers
+// realspace.cu
+void build_real_table(Ctx &c);
+void build_neighbors(Ctx &c);  // cell list + mobility and lubrication lists
+template <typename T>
+void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint,
+                      bool self_only_real);
+void launch_wrap_positions(Ctx &c);  // pos64 / op*.pos / levers from X, q, rbody
+
+// wavespace.cu
+void build_wave(Ctx &c);
+template <typename T>
+void launch_wavespace(Ctx &c, const double *x, double *y);  // y += M_w x
+
+// nearfield.cu
+void build_lubrication(Ctx &c);  // BSR blocks (both precisions) + Schur LU
+template <typename T>
+void launch_body_rows(Ctx &c, const double *x, double *y, bool with_lub);  // y2 = Sigma B^T x1 - RR x2
+template <typename T>
+void launch_lub_apply(Ctx &c, const double *dU, double *out);  // out = RR dU
+void launch_precond(Ctx &c, const double *r, double *z);
+void launch_rhs(Ctx &c, const double *ft_internal, double shear, double *b);
+void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int,
+                    double *str_int);
+void launch_integrate(Ctx &c, const double *vel_int, double dt);
+
+// krylov.cu
+void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w,
+               double *out_dev);                   // out[j] = V_j . w, j < k
+void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k,
+                const double *coef_dev, double sign);  // w += sign * sum_j coef[j] V_j
+void vec_scale_host(Ctx &c, double *y, const double *x, double s);  // y = s x
+void vec_axpby(Ctx &c, double *y, double a, const double *x, double b,
+               int64_t n);                          // y = a x + b y
+void norm2_dev(Ctx &c, const double *x, double *out_dev);
+
+// api.cu (solver)
+template <typename T>
+void apply_saddle(Ctx &c, const double *x, double *y);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace fsd

@@ -1,0 +1,682 @@
+// Wave-space part of the PSE mobility (Sec. 2.2, Eq. UBff split; Sec. 3.2
+// grid rule): Gaussian spreading of the force and force-dipole densities,
+// a hand-written shared-memory mixed-radix (2,3,4,5) 3D FFT with the Green's
+// function scaling fused into the z pass, and interpolation of the velocity
+// and velocity gradient.
+//
+// Grids: six real fields on an n^3 grid, rows padded to n + 2 reals so that
+// the forward x pass writes its n/2 + 1 complex values in place:
+//   comps 0..2  monopole density g_F = sum_j F_j W(x - x_j)
+//   comps 3..5  dipole density   g_D = sum_j 2 alpha W(x - x_j) D_j (x - x_j),
+//                D = S + A, A y = (1/2) L x y
+// Spectral kernel (Hasimoto split, Gaussian window W_hat = exp(-k^2/(4 alpha))
+// removed twice):
+//   u_hat = A(k) (I - kk) [fM g_F_hat + fD g_D_hat],
+//   A(k) = (1 + k^2/(4 xi^2)) exp(-k^2/(4 xi^2) + k^2/(2 alpha)) / (eta k^2),
+// read-outs: velocity from fM u_hat, rotation / strain from grad (fD u_hat).
+#include "fsd_internal.cuh"
+
+#include <algorithm>
+
+namespace fsd {
+
+template <typename T>
+struct Cx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> csub(Cx<T> a, Cx<T> b) {
+  return {a.x - b.x, a.y - b.y};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cscale(Cx<T> a, T s) {
+  return {a.x * s, a.y * s};
+}
+// multiply by i * sg (sg = +-1)
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul_i(Cx<T> a, T sg) {
+  return {-sg * a.y, sg * a.x};
+}
+
+constexpr int kMaxStages = 16;
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[kMaxStages];
+};
+
+static FftPlan make_plan(int n) {
+  FftPlan p{};
+  p.n = n;
+  int m = n, k = 0;
+  while (m % 4 == 0) {
+    p.radix[k++] = 4;
+    m /= 4;
+  }
+  for (int f : {2, 3, 5})
+    while (m % f == 0) {
+      p.radix[k++] = f;
+      m /= f;
+    }
+  p.nst = k;
+  return p;
+}
+
+bool fft_size_ok(int n) {
+  if (n < 8 || n % 2) return false;
+  int m = n;
+  for (int f : {2, 3, 5})
+    while (m % f == 0) m /= f;
+  return m == 1;
+}
+
+// Small DFT of size R in registers, sign sg (-1 forward, +1 inverse).
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(Cx<T> *v, T sg) {
+  if (R == 2) {
+    Cx<T> a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if (R == 3) {
+    const T h = T(0.86602540378443864676);
+    Cx<T> t1 = cadd(v[1], v[2]);
+    Cx<T> t2 = {v[0].x - T(0.5) * t1.x, v[0].y - T(0.5) * t1.y};
+    Cx<T> t3 = cmul_i(cscale(csub(v[1], v[2]), h), sg);
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+  } else if (R == 4) {
+    Cx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    Cx<T> c = cadd(v[1], v[3]), d = cmul_i(csub(v[1], v[3]), sg);
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(b, d);
+    v[3] = csub(b, d);
+  } else if (R == 5) {
+    const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
+    const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);
+    Cx<T> a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    Cx<T> a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    Cx<T> x0 = v[0];
+    Cx<T> r1 = {x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y};
+    Cx<T> r2 = {x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y};
+    Cx<T> i1 = cmul_i(Cx<T>{s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y}, sg);
+    Cx<T> i2 = cmul_i(Cx<T>{s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y}, sg);
+    v[0] = {x0.x + a1.x + a2.x, x0.y + a1.y + a2.y};
+    v[1] = cadd(r1, i1);
+    v[4] = csub(r1, i1);
+    v[2] = cadd(r2, i2);
+    v[3] = csub(r2, i2);
+  }
+}
+
+// One Stockham stage of radix R over nl lines stored with stride ls:
+//   for butterfly j < n/R:  v_r = in[j + r n/R] w^(r k), k = j mod Ns,
+//   DFT_R, out[(j / Ns) Ns R + k + r Ns] = v_r.
+template <typename T, int R>
+__device__ __forceinline__ void stockham_stage(const Cx<T> *in, Cx<T> *out, int nl, int n, int ls,
+                                               int Ns, const Cx<T> *tw, T sg) {
+  const int nb = n / R;
+  const int total = nl * nb;
+  const int tstep = n / (Ns * R);
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int line = b / nb, j = b - line * nb;
+    const int k = j % Ns;
+    const Cx<T> *src = in + line * ls;
+    Cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      Cx<T> a = src[j + r * nb];
+      if (r > 0) {
+        int t = (r * k * tstep) % n;
+        Cx<T> w = tw[t];
+        w.y *= -sg;  // table holds exp(-2 pi i t / n)
+        a = cmul(a, w);
+      }
+      v[r] = a;
+    }
+    dft_small<T, R>(v, sg);
+    Cx<T> *dst = out + line * ls + (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * Ns] = v[r];
+  }
+}
+
+// Full transform of nl lines: data starts in A; returns the buffer holding
+// the result (A or B).  tw in shared memory holds exp(-2 pi i t / n).
+template <typename T>
+__device__ Cx<T> *fft_lines(Cx<T> *A, Cx<T> *B, int nl, int n, int ls, const FftPlan &plan,
+                            const Cx<T> *tw, T sg) {
+  Cx<T> *in = A, *out = B;
+  int Ns = 1;
+  for (int s = 0; s < plan.nst; ++s) {
+    const int R = plan.radix[s];
+    if (R == 4)
+      stockham_stage<T, 4>(in, out, nl, n, ls, Ns, tw, sg);
+    else if (R == 2)
+      stockham_stage<T, 2>(in, out, nl, n, ls, Ns, tw, sg);
+    else if (R == 3)
+      stockham_stage<T, 3>(in, out, nl, n, ls, Ns, tw, sg);
+    else
+      stockham_stage<T, 5>(in, out, nl, n, ls, Ns, tw, sg);
+    Ns *= R;
+    __syncthreads();
+    Cx<T> *t = in;
+    in = out;
+    out = t;
+  }
+  return in;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(Cx<T> *tw_s, const T *__restrict__ tw, int n) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) tw_s[t] = {tw[2 * t], tw[2 * t + 1]};
+}
+
+// ---------------------------------------------------------------- x passes
+// Forward: rows (c, z, y), c < 3; z = g_c + i g_{c+3}; after the DFT the two
+// half spectra are A_k = (Z_k + conj Z_{n-k})/2 and B_k = (Z_k - conj Z_{n-k})/(2i),
+// written in place into rows c and c + 3.
+template <typename T>
+__global__ void k_fft_x_fwd(T *grid, FftPlan plan, const T *__restrict__ tw, int NL) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = n + 1, rowlen = n + 2;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + n;
+  Cx<T> *B = A + NL * ls;
+  load_twiddles(tw_s, tw, n);
+  const int64_t nrows = 3LL * n * n;  // (c, z, y) with c < 3
+  const int64_t row0 = (int64_t)blockIdx.x * NL;
+  const int64_t comp_stride = (int64_t)n * n * rowlen;
+  for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
+    int l = e / n, xx = e - l * n;
+    int64_t row = row0 + l;
+    Cx<T> v = {T(0), T(0)};
+    if (row < nrows) {
+      const T *pr = grid + row * rowlen;  // comp c = row / (n*n) lies in the first 3 comps
+      v = {pr[xx], pr[3 * comp_stride + xx]};
+    }
+    A[l * ls + xx] = v;
+  }
+  __syncthreads();
+  Cx<T> *Z = fft_lines<T>(A, B, NL, n, ls, plan, tw_s, T(-1));
+  const int nh = n / 2 + 1;
+  for (int e = threadIdx.x; e < NL * nh; e += blockDim.x) {
+    int l = e / nh, k = e - l * nh;
+    int64_t row = row0 + l;
+    if (row >= nrows) continue;
+    Cx<T> zk = Z[l * ls + k];
+    Cx<T> zm = Z[l * ls + (k == 0 ? 0 : n - k)];
+    Cx<T> Ak = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    // (Z_k - conj Z_{n-k}) / (2i): (p + iq)/(2i) = (q - ip)/2
+    Cx<T> Bk = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
+    T *pr = grid + row * rowlen;
+    pr[2 * k] = Ak.x;
+    pr[2 * k + 1] = Ak.y;
+    pr[3 * comp_stride + 2 * k] = Bk.x;
+    pr[3 * comp_stride + 2 * k + 1] = Bk.y;
+  }
+}
+
+// Inverse: Z_k = A_k + i B_k (k <= n/2), conj(A_{n-k}) + i conj(B_{n-k})
+// beyond; the inverse DFT gives a + i b with a, b real.
+template <typename T>
+__global__ void k_fft_x_inv(T *grid, FftPlan plan, const T *__restrict__ tw, int NL) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = n + 1, rowlen = n + 2;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + n;
+  Cx<T> *B = A + NL * ls;
+  load_twiddles(tw_s, tw, n);
+  const int64_t nrows = 3LL * n * n;
+  const int64_t row0 = (int64_t)blockIdx.x * NL;
+  const int64_t comp_stride = (int64_t)n * n * rowlen;
+  for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
+    int l = e / n, k = e - l * n;
+    int64_t row = row0 + l;
+    Cx<T> v = {T(0), T(0)};
+    if (row < nrows) {
+      const T *pr = grid + row * rowlen;
+      if (k <= n / 2) {
+        Cx<T> a = {pr[2 * k], pr[2 * k + 1]};
+        Cx<T> b = {pr[3 * comp_stride + 2 * k], pr[3 * comp_stride + 2 * k + 1]};
+        v = {a.x - b.y, a.y + b.x};
+      } else {
+        int km = n - k;
+        Cx<T> a = {pr[2 * km], -pr[2 * km + 1]};
+        Cx<T> b = {pr[3 * comp_stride + 2 * km], -pr[3 * comp_stride + 2 * km + 1]};
+        v = {a.x - b.y, a.y + b.x};
+      }
+    }
+    A[l * ls + k] = v;
+  }
+  __syncthreads();
+  Cx<T> *Z = fft_lines<T>(A, B, NL, n, ls, plan, tw_s, T(1));
+  for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
+    int l = e / n, xx = e - l * n;
+    int64_t row = row0 + l;
+    if (row >= nrows) continue;
+    Cx<T> z = Z[l * ls + xx];
+    T *pr = grid + row * rowlen;
+    pr[xx] = z.x;
+    pr[3 * comp_stride + xx] = z.y;
+  }
+}
+
+// ---------------------------------------------------------------- y pass
+// Lines along y for fixed (comp, z), a tile of TX consecutive kx.
+template <typename T>
+__global__ void k_fft_y(T *grid, FftPlan plan, const T *__restrict__ tw, int TX, T sg) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + n;
+  Cx<T> *B = A + TX * ls;
+  load_twiddles(tw_s, tw, n);
+  const int ntile = (nh + TX - 1) / TX;
+  const int tile = blockIdx.x % ntile;
+  const int cz = blockIdx.x / ntile;  // comp * n + z
+  const int kx0 = tile * TX;
+  Cx<T> *base = (Cx<T> *)grid + (int64_t)cz * n * nh;  // rows of nh complex
+  for (int e = threadIdx.x; e < TX * n; e += blockDim.x) {
+    int yy = e / TX, t = e - yy * TX;
+    int kx = kx0 + t;
+    Cx<T> v = {T(0), T(0)};
+    if (kx < nh) v = base[(int64_t)yy * nh + kx];
+    A[t * ls + yy] = v;
+  }
+  __syncthreads();
+  Cx<T> *Z = fft_lines<T>(A, B, TX, n, ls, plan, tw_s, sg);
+  for (int e = threadIdx.x; e < TX * n; e += blockDim.x) {
+    int yy = e / TX, t = e - yy * TX;
+    int kx = kx0 + t;
+    if (kx < nh) base[(int64_t)yy * nh + kx] = Z[t * ls + yy];
+  }
+}
+
+// ------------------------------------------------------- z pass + Green
+// Lines along z for fixed y, TX consecutive kx, all six components:
+// forward DFT, Green's function, inverse DFT.
+template <typename T>
+__global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
+                              const T *__restrict__ green, int TX) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int NLn = 6 * TX;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + n;
+  Cx<T> *B = A + NLn * ls;
+  load_twiddles(tw_s, tw, n);
+  const int ntile = (nh + TX - 1) / TX;
+  const int tile = blockIdx.x % ntile;
+  const int yy = blockIdx.x / ntile;
+  const int kx0 = tile * TX;
+  Cx<T> *g = (Cx<T> *)grid;
+  const int64_t zstride = (int64_t)n * nh, cstride = (int64_t)n * zstride;
+  for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
+    int t = e % TX, rest = e / TX;
+    int zz = rest % n, comp = rest / n;
+    int kx = kx0 + t;
+    Cx<T> v = {T(0), T(0)};
+    if (kx < nh) v = g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx];
+    A[(comp * TX + t) * ls + zz] = v;
+  }
+  __syncthreads();
+  Cx<T> *Z = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(-1));
+  // Green's function, one (kx, ky, kz) per thread iteration
+  const int ky = yy <= n / 2 ? yy : yy - n;
+  for (int e = threadIdx.x; e < TX * n; e += blockDim.x) {
+    int t = e % TX, zz = e / TX;
+    int kx = kx0 + t;
+    int kz = zz <= n / 2 ? zz : zz - n;
+    int m = kx * kx + ky * ky + kz * kz;
+    Cx<T> gF[3], gD[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      gF[d] = Z[(d * TX + t) * ls + zz];
+      gD[d] = Z[((d + 3) * TX + t) * ls + zz];
+    }
+    Cx<T> oM[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
+    Cx<T> oD[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
+    if (m > 0 && kx < nh) {
+      const T t1 = green[3 * m], t2 = green[3 * m + 1], t3 = green[3 * m + 2];
+      const T kk[3] = {(T)kx, (T)ky, (T)kz};
+      const T im = T(1) / (T)m;
+      Cx<T> sF = {T(0), T(0)}, sD = {T(0), T(0)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        sF.x += kk[d] * gF[d].x;
+        sF.y += kk[d] * gF[d].y;
+        sD.x += kk[d] * gD[d].x;
+        sD.y += kk[d] * gD[d].y;
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Cx<T> pF = {gF[d].x - kk[d] * sF.x * im, gF[d].y - kk[d] * sF.y * im};
+        Cx<T> pD = {gD[d].x - kk[d] * sD.x * im, gD[d].y - kk[d] * sD.y * im};
+        oM[d] = {t1 * pF.x + t2 * pD.x, t1 * pF.y + t2 * pD.y};
+        oD[d] = {t2 * pF.x + t3 * pD.x, t2 * pF.y + t3 * pD.y};
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Z[(d * TX + t) * ls + zz] = oM[d];
+      Z[((d + 3) * TX + t) * ls + zz] = oD[d];
+    }
+  }
+  __syncthreads();
+  Cx<T> *O = Z;
+  Cx<T> *other = (Z == A) ? B : A;
+  Cx<T> *R = fft_lines<T>(O, other, NLn, n, ls, plan, tw_s, T(1));
+  for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
+    int t = e % TX, rest = e / TX;
+    int zz = rest % n, comp = rest / n;
+    int kx = kx0 + t;
+    if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + zz];
+  }
+}
+
+// ------------------------------------------------------------ spreading
+template <typename T>
+struct V4Of;
+template <>
+struct V4Of<float> {
+  using type = float4;
+};
+template <>
+struct V4Of<double> {
+  using type = double4;
+};
+
+template <typename T>
+__device__ __forceinline__ T exp_t(T x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+template <typename T>
+__device__ __forceinline__ T floor_t(T x);
+template <>
+__device__ __forceinline__ float floor_t<float>(float x) { return floorf(x); }
+template <>
+__device__ __forceinline__ double floor_t<double>(double x) { return floor(x); }
+
+constexpr int kMaxP = 24;
+
+// One warp per bead: 1D Gaussian factors in shared memory, then the P^3
+// points split over the lanes with atomic accumulation into the six fields.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread(int Nt, const typename V4Of<T>::type *__restrict__ pos,
+                                                const double *__restrict__ x, T *grid, int n, int P,
+                                                T h, T alpha, T cnorm) {
+  __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP];
+  __shared__ int si[8][3][kMaxP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= Nt) return;
+  const auto p = pos[i];
+  const T pc[3] = {p.x, p.y, p.z};
+  for (int e = lane; e < 3 * P; e += 32) {
+    int d = e / P, k = e - d * P;
+    int g0 = (int)floor_t<T>(pc[d] / h) - P / 2 + 1;
+    int g = g0 + k;
+    T yv = T(g) * h - pc[d];
+    sw[warp][d][k] = exp_t<T>(-alpha * yv * yv);
+    sy[warp][d][k] = yv;
+    si[warp][d][k] = ((g % n) + n) % n;
+  }
+  __syncwarp();
+  const double *xr = x + (size_t)i * LDB;
+  const T F0 = (T)xr[0], F1 = (T)xr[1], F2 = (T)xr[2];
+  const T L0 = (T)xr[3], L1 = (T)xr[4], L2 = (T)xr[5];
+  const T r2i = T(0.70710678118654752440), r6i = T(0.40824829046386301637);
+  const T s0 = (T)xr[6], s1 = (T)xr[7], s2 = (T)xr[8], s3 = (T)xr[9], s4 = (T)xr[10];
+  const T Sxx = r2i * s0 - r6i * s1, Syy = -r2i * s0 - r6i * s1, Szz = T(2) * r6i * s1;
+  const T Sxy = r2i * s2, Sxz = r2i * s3, Syz = r2i * s4;
+  // D = S + A with A y = (1/2) L x y
+  const T D00 = Sxx, D01 = Sxy - T(0.5) * L2, D02 = Sxz + T(0.5) * L1;
+  const T D10 = Sxy + T(0.5) * L2, D11 = Syy, D12 = Syz - T(0.5) * L0;
+  const T D20 = Sxz - T(0.5) * L1, D21 = Syz + T(0.5) * L0, D22 = Szz;
+  const int rowlen = n + 2;
+  const int64_t cs = (int64_t)n * n * rowlen;
+  const int P3 = P * P * P;
+  const T ta = T(2) * alpha;
+  for (int t = lane; t < P3; t += 32) {
+    int ix = t % P, iy = (t / P) % P, iz = t / (P * P);
+    T W = cnorm * sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
+    T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
+    T Wd = ta * W;
+    int64_t off = ((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * rowlen + si[warp][0][ix];
+    atomicAdd(grid + off, W * F0);
+    atomicAdd(grid + cs + off, W * F1);
+    atomicAdd(grid + 2 * cs + off, W * F2);
+    atomicAdd(grid + 3 * cs + off, Wd * (D00 * y0 + D01 * y1 + D02 * y2));
+    atomicAdd(grid + 4 * cs + off, Wd * (D10 * y0 + D11 * y1 + D12 * y2));
+    atomicAdd(grid + 5 * cs + off, Wd * (D20 * y0 + D21 * y1 + D22 * y2));
+  }
+}
+
+// One warp per bead: u = h^3 sum W u_M, G_ab = h^3 sum 2 alpha W y_b u_D,a;
+// omega = (1/2) curl, e = sym G projected; added to the bead row of y.
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::type *__restrict__ pos,
+                                                const T *__restrict__ grid, double *y, int n, int P,
+                                                T h, T alpha, T cnorm_h3) {
+  __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP];
+  __shared__ int si[8][3][kMaxP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= Nt) return;
+  const auto p = pos[i];
+  const T pc[3] = {p.x, p.y, p.z};
+  for (int e = lane; e < 3 * P; e += 32) {
+    int d = e / P, k = e - d * P;
+    int g0 = (int)floor_t<T>(pc[d] / h) - P / 2 + 1;
+    int g = g0 + k;
+    T yv = T(g) * h - pc[d];
+    sw[warp][d][k] = exp_t<T>(-alpha * yv * yv);
+    sy[warp][d][k] = yv;
+    si[warp][d][k] = ((g % n) + n) % n;
+  }
+  __syncwarp();
+  const int rowlen = n + 2;
+  const int64_t cs = (int64_t)n * n * rowlen;
+  const int P3 = P * P * P;
+  const T ta = T(2) * alpha;
+  T acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = T(0);
+  for (int t = lane; t < P3; t += 32) {
+    int ix = t % P, iy = (t / P) % P, iz = t / (P * P);
+    T W = sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
+    T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
+    int64_t off = ((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * rowlen + si[warp][0][ix];
+    T u0 = grid[off], u1 = grid[cs + off], u2 = grid[2 * cs + off];
+    T d0 = grid[3 * cs + off], d1 = grid[4 * cs + off], d2 = grid[5 * cs + off];
+    acc[0] += W * u0;
+    acc[1] += W * u1;
+    acc[2] += W * u2;
+    T Wd = ta * W;
+    T w0 = Wd * y0, w1 = Wd * y1, w2 = Wd * y2;
+    acc[3] += d0 * w0;  // G_00
+    acc[4] += d0 * w1;  // G_01
+    acc[5] += d0 * w2;  // G_02
+    acc[6] += d1 * w0;  // G_10
+    acc[7] += d1 * w1;  // G_11
+    acc[8] += d1 * w2;  // G_12
+    acc[9] += d2 * w0;  // G_20
+    acc[10] += d2 * w1; // G_21
+    acc[11] += d2 * w2; // G_22
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  if (lane != 0) return;
+  double a_[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a_[k] = (double)acc[k] * (double)cnorm_h3;
+  const double G00 = a_[3], G01 = a_[4], G02 = a_[5], G10 = a_[6], G11 = a_[7], G12 = a_[8],
+               G20 = a_[9], G21 = a_[10], G22 = a_[11];
+  const double r2i = 0.70710678118654752440, r6i = 0.40824829046386301637,
+               s2 = 1.41421356237309504880;
+  double *yr = y + (size_t)i * LDB;
+  yr[0] += a_[0];
+  yr[1] += a_[1];
+  yr[2] += a_[2];
+  yr[3] += 0.5 * (G21 - G12);
+  yr[4] += 0.5 * (G02 - G20);
+  yr[5] += 0.5 * (G10 - G01);
+  yr[6] += r2i * (G00 - G11);
+  yr[7] += r6i * (2.0 * G22 - G00 - G11);
+  yr[8] += s2 * 0.5 * (G01 + G10);
+  yr[9] += s2 * 0.5 * (G02 + G20);
+  yr[10] += s2 * 0.5 * (G12 + G21);
+}
+
+// ------------------------------------------------------------ host side
+
+static double j0h(double z) {
+  if (z < 1e-3) return 1.0 - z * z / 6.0 + z * z * z * z / 120.0;
+  return std::sin(z) / z;
+}
+static double fDh(double z) {
+  if (z < 1e-2) return 1.0 - z * z / 10.0 + z * z * z * z / 280.0;
+  return 3.0 * (std::sin(z) - z * std::cos(z)) / (z * z * z);
+}
+
+template <typename T>
+static void upload(DBuf<T> &buf, const std::vector<double> &v) {
+  std::vector<T> tv(v.begin(), v.end());
+  buf.alloc(tv.size());
+  FSD_CUDA(cudaMemcpy(buf.p, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+void build_wave(Ctx &c) {
+  const int n = c.n;
+  const size_t gsize = (size_t)6 * n * n * (n + 2);
+  c.op64.grid.alloc(gsize);
+  c.op32.grid.alloc(gsize);
+  // twiddles exp(-2 pi i t / n)
+  std::vector<double> tw(2 * n);
+  for (int t = 0; t < n; ++t) {
+    tw[2 * t] = std::cos(2.0 * kPi * t / n);
+    tw[2 * t + 1] = -std::sin(2.0 * kPi * t / n);
+  }
+  upload(c.op64.twiddle, tw);
+  upload(c.op32.twiddle, tw);
+  // Green table by m = kx^2 + ky^2 + kz^2
+  const int hm = n / 2;
+  const int mmax = 3 * hm * hm;
+  std::vector<double> gr(3 * (size_t)(mmax + 1), 0.0);
+  const double n3 = (double)n * n * n;
+  for (int m = 1; m <= mmax; ++m) {
+    double k = 2.0 * kPi * std::sqrt((double)m) / c.L;
+    double k2 = k * k;
+    double e = -k2 / (4.0 * c.xi * c.xi) + k2 / (2.0 * c.alpha);
+    double A = (1.0 + k2 / (4.0 * c.xi * c.xi)) * std::exp(e) / (c.eta * k2) / n3;
+    double fm = j0h(k * c.a), fd = fDh(k * c.a);
+    gr[3 * m] = A * fm * fm;
+    gr[3 * m + 1] = A * fm * fd;
+    gr[3 * m + 2] = A * fd * fd;
+  }
+  upload(c.op64.green, gr);
+  upload(c.op32.green, gr);
+}
+
+template <typename T>
+static OpData<T> &opd(Ctx &c);
+template <>
+OpData<double> &opd<double>(Ctx &c) {
+  return c.op64;
+}
+template <>
+OpData<float> &opd<float>(Ctx &c) {
+  return c.op32;
+}
+template <typename T>
+static const typename V4Of<T>::type *posp(Ctx &c);
+template <>
+const double4 *posp<double>(Ctx &c) {
+  return (const double4 *)c.pos64.p;
+}
+template <>
+const float4 *posp<float>(Ctx &c) {
+  return (const float4 *)c.op32.pos.p;
+}
+
+template <typename T>
+static void set_smem(const void *fn, size_t bytes) {
+  static bool done[8] = {};
+  (void)done;
+  FSD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <typename T>
+void launch_wavespace(Ctx &c, const double *x, double *y) {
+  OpData<T> &op = opd<T>(c);
+  const int n = c.n, P = c.P;
+  const T h = (T)c.h, alpha = (T)c.alpha;
+  const double cn = std::pow(c.alpha / kPi, 1.5);
+  const size_t gbytes = (size_t)6 * n * n * (n + 2) * sizeof(T);
+  FSD_CUDA(cudaMemsetAsync(op.grid.p, 0, gbytes, c.stream));
+  k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
+                                                      alpha, (T)cn);
+  FSD_CUDA(cudaGetLastError());
+  FftPlan plan = make_plan(n);
+  const int nh = n / 2 + 1;
+  const int threads = 256;
+  // x forward
+  {
+    const int NL = 8;
+    size_t sm = (size_t)(n + 2 * NL * (n + 1)) * sizeof(Cx<T>);
+    set_smem<T>((const void *)k_fft_x_fwd<T>, sm);
+    int blocks = ceil_div(3LL * n * n, NL);
+    k_fft_x_fwd<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p, NL);
+    FSD_CUDA(cudaGetLastError());
+  }
+  const int TXy = sizeof(T) == 8 ? 8 : 16;
+  const size_t smy = (size_t)(n + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
+  set_smem<T>((const void *)k_fft_y<T>, smy);
+  const int blocks_y = 6 * n * ceil_div(nh, TXy);
+  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, TXy, T(-1));
+  FSD_CUDA(cudaGetLastError());
+  {
+    const int TX = sizeof(T) == 8 ? 4 : 8;
+    size_t sm = (size_t)(n + 2 * 6 * TX * (n + 1)) * sizeof(Cx<T>);
+    set_smem<T>((const void *)k_fft_z_green<T>, sm);
+    int blocks = n * ceil_div(nh, TX);
+    k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p,
+                                                        op.green.p, TX);
+    FSD_CUDA(cudaGetLastError());
+  }
+  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, TXy, T(1));
+  FSD_CUDA(cudaGetLastError());
+  {
+    const int NL = 8;
+    size_t sm = (size_t)(n + 2 * NL * (n + 1)) * sizeof(Cx<T>);
+    set_smem<T>((const void *)k_fft_x_inv<T>, sm);
+    int blocks = ceil_div(3LL * n * n, NL);
+    k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p, NL);
+    FSD_CUDA(cudaGetLastError());
+  }
+  const double h3 = c.h * c.h * c.h;
+  k_interp<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.grid.p, y, n, P, h,
+                                                      alpha, (T)(cn * h3));
+  FSD_CUDA(cudaGetLastError());
+}
+
+template void launch_wavespace<float>(Ctx &, const double *, double *);
+template void launch_wavespace<double>(Ctx &, const double *, double *);
+
+}  // namespace fsd
