@@ -1,0 +1,386 @@
+"""Throughput benchmark of the rigid-aggregate FSD time step on GB300.
+
+Metric: bead-steps/sec (beads x timed steps / seconds) of the full step
+(neighbour lists, lubrication blocks, per-aggregate LUs, preconditioned
+saddle-point solve to a relative residual of 1e-6, outputs, rigid-body
+update) on 32768 beads = 4096 rigid 8-bead random-attachment aggregates at
+bead volume fraction 0.2 in simple shear (rate 1), lubrication cut-off 3a,
+constant xi = 0.5.  `value` is the mixed-precision path (FP32 operator inside
+FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path is
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank steps its own replica of the suspension (the
+single-suspension solve does not shard); value = beads x steps x ranks / the
+slowest rank's time.  --impl reference times the FP64 CPU oracle on a bounded
+32-bead sample of the same workload per step."""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bead-steps/sec at 32k beads (GMRES 1e-6), mixed vs FP64 on GB300; % HBM peak"
+UNIT = "bead-steps/s"
+
+WORKLOAD = dict(n_agg=4096, n_b=8, phi=0.2, seed=1, shear=1.0, lub=3.0, xi=0.5, tol=1e-6, dt=1e-3)
+SAMPLE_AGG = 4  # oracle sample: 4 aggregates x 8 beads at the same phi / generator
+
+
+def workload_name(w, L, prm):
+    return ("%d beads: %d rigid %d-bead random-attachment aggregates, phi %.2f, L %.2f, "
+            "shear %g, lubrication %ga, xi %.2f, grid %d^3, P %d, rc %.2f, GMRES %g"
+            % (w["n_agg"] * w["n_b"], w["n_agg"], w["n_b"], w["phi"], L, w["shear"], w["lub"],
+               prm["xi"], prm["grid"], prm["P"], prm["rc"], w["tol"]))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of this GPU during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- work model
+# Algorithmic work per launch of each kernel group ("Roofline").
+FLOP_PER_PAIR = 410  # FP32 flops of one directed FTS pair (operator form, FMA = 2)
+
+
+def group_work(group, s, prm, st, prec_bytes=4):
+    """(bound, algorithmic amount per launch, unit) for a kernel group."""
+    n = prm["grid"]
+    G = n * n * (n + 2)
+    Nt = s.n_beads
+    w = prec_bytes
+    if group == "realspace":
+        return "alu", st["n_pairs"] * FLOP_PER_PAIR, "TFLOP/s"
+    if group == "spread":
+        # zero + write the six density grids, read bead moments and positions
+        return "hbm", 2 * 6 * G * w + Nt * (12 * 8 + 4 * w), "GB/s"
+    if group == "fft_green":
+        # one forward and one inverse 3D transform of six real grids, each
+        # reading and writing every grid value once
+        return "hbm", 4 * 6 * G * w, "GB/s"
+    if group == "interp":
+        return "hbm", 6 * G * w + Nt * (12 * 8 + 4 * w), "GB/s"
+    return "hbm", None, "GB/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def traffic_for(group):
+    """dram bytes per launch of the group's kernel from the committed ncu
+    summary, if the kernel source has not changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(group)
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != e.get("source_sha256_16"):
+        return None
+    return e["bytes_per_launch"]
+
+
+# ------------------------------------------------------------ oracle arm
+def oracle_sample_step(seed):
+    import oracle as O
+    import synth
+
+    w = WORKLOAD
+    pos, body, L = synth.suspension(SAMPLE_AGG, w["n_b"], w["phi"], seed)
+    t = time.perf_counter()
+    O.solve(pos, body, L, gamma=w["shear"], rlub=w["lub"])
+    return len(pos), time.perf_counter() - t
+
+
+def cpu_baseline(steps=3):
+    beads, secs = 0, 0.0
+    for k in range(steps):
+        b, t = oracle_sample_step(100 + k)
+        beads += b
+        secs += t
+    return {"value": beads / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d oracle solves of a %d-bead sub-box (%d x %d-bead aggregates, phi %.2f, "
+                      "same generator, shear and lubrication), dense FP64 Ewald mobility + LAPACK; "
+                      "numpy BLAS default threads; %.1f s"
+                      % (steps, SAMPLE_AGG * WORKLOAD["n_b"], SAMPLE_AGG, WORKLOAD["n_b"],
+                         WORKLOAD["phi"], secs)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for k in range(args.warmup):
+        oracle_sample_step(200 + k)
+    beads, secs = 0, 0.0
+    for k in range(args.steps):
+        b, t = oracle_sample_step(300 + k)
+        beads += b
+        secs += t
+    v = beads / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "oracle sample per step: %d-bead sub-box of the 32768-bead "
+                                   "phi 0.2 workload" % (SAMPLE_AGG * WORKLOAD["n_b"])},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "one %d-bead oracle solve per step" % (SAMPLE_AGG * WORKLOAD["n_b"])},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import synth
+    import paper_2607_25161_gb300 as pkg
+    from __graft_entry__ import build
+
+    build()
+    w = WORKLOAD
+    pos, body, L = synth.suspension(w["n_agg"], w["n_b"], w["phi"], w["seed"])
+    Nt = len(pos)
+    stream = torch.cuda.Stream()
+    common = dict(xi=w["xi"], lub_cutoff=w["lub"], tol=w["tol"], flags=pkg.FSD_FLAG_COMOVING)
+
+    def make(prec):
+        return pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=prec, **common)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_steps(s, K, ft=None, vel=None):
+        """K steps timed with CUDA events on the library stream."""
+        launches, iters = 0, 0
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            st, _ = s.step(ft, w["shear"], w["dt"], vel=vel)
+            launches += st["kernel_launches"]
+            iters += st["iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1), launches, iters
+
+    # ---- mixed (headline)
+    s = make(pkg.FSD_MIXED)
+    prm = s.params
+    for _ in range(args.warmup):
+        s.step(None, w["shear"], w["dt"])
+    dev_id = local_rank
+    if os.environ.get("CUDA_VISIBLE_DEVICES"):
+        ids = os.environ["CUDA_VISIBLE_DEVICES"].split(",")
+        if local_rank < len(ids):
+            dev_id = ids[local_rank]
+    clk = ClockSampler(dev_id)
+    clk.start()
+    ms, launches, iters = timed_steps(s, args.steps)
+    clocks = clk.stop()
+    ms_max = max_over_ranks(ms)
+    value = Nt * args.steps * world / (ms_max / 1e3)
+
+    # ---- end to end: pinned host input and output every step
+    ft_h = torch.zeros((w["n_agg"], 6), dtype=torch.float64).pin_memory()
+    vel_h = torch.zeros((w["n_agg"], 6), dtype=torch.float64).pin_memory()
+    K2 = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        s.step(ft_h, w["shear"], w["dt"], vel=vel_h)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": Nt * K2 * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(ft_h.numel() * 8), "d2h_bytes_per_step": int(vel_h.numel() * 8),
+           "steps": K2, "api": "fsd_step with pinned host force/torque in and velocities out"}
+
+    # ---- profile pass: per kernel group device time (separate, not timed above)
+    s.profile(True)
+    PS = 2
+    stp = None
+    for _ in range(PS):
+        stp, _ = s.step(None, w["shear"], w["dt"])
+    prof = s.profile_read()
+    s.profile(False)
+    s.close()
+
+    # ---- plain FP64 path on the same initial configuration
+    s64 = make(pkg.FSD_FP64)
+    for _ in range(max(1, min(args.warmup, 2))):
+        s64.step(None, w["shear"], w["dt"])
+    K64 = max(2, min(args.steps, 5))
+    ms64, _, iters64 = timed_steps(s64, K64)
+    s64.profile(True)
+    st64, _ = s64.step(None, w["shear"], w["dt"])
+    prof64 = s64.profile_read()
+    s64.close()
+    ms64 = max_over_ranks(ms64)
+    fp64 = {"value": Nt * K64 * world / (ms64 / 1e3), "ms_per_step": ms64 / K64, "steps": K64,
+            "iters_per_step": iters64 / K64,
+            "kernel_ms_per_step": {g: round(v[0], 4) for g, v in prof64.items()}}
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel group (mixed path)
+    pk, pk_kind = peaks()
+    dom = max((g for g in prof if prof[g][1] > 0), key=lambda g: prof[g][0])
+    per_launch_ms = prof[dom][0] / prof[dom][1]
+    bound, work, unit = group_work(dom, s, prm, stp)
+    roof = {"kernel_group": dom, "bound": bound, "launch_ms": per_launch_ms}
+    if work is not None:
+        if bound == "alu":
+            mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+            achieved = work / (per_launch_ms / 1e3) / 1e12
+            roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": "FP32 ALU: 152 SM x 128 lanes x "
+                         "2 flop x %.0f MHz (%s clock)" % (mhz, pk_kind),
+                         "flops_per_launch": work})
+        else:
+            achieved = work / (per_launch_ms / 1e3) / 1e9
+            peak = pk.get("hbm_gbs", 6800.0)
+            roof.update({"achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": "hbm_gbs (%s)" % pk_kind,
+                         "bytes_per_launch": work})
+    roof["traffic"] = traffic_for(dom)
+
+    base = cpu_baseline(3) if world == 1 or rank == 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_name(w, L, prm), "beads": Nt, "aggregates": w["n_agg"],
+                   "precision": "mixed: FP32 operator in FP64 iterative refinement; FP64 Arnoldi, LU, residual",
+                   "l2": "working set per step > L2 (grids, Krylov basis, neighbour lists ~0.5 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "initial_guess": "zero each step",
+                   "integration": "disturbance motion only: X += (U - U_inf) dt, q by Omega - Omega_inf "
+                                  "(cubic periodic box, no Lees-Edwards images); each solve is the full sheared problem"},
+        "iters_per_step": iters / args.steps,
+        "fp64": fp64,
+        "kernel_ms_per_step": {g: round(v[0] / PS, 4) for g, v in prof.items()},
+        "roofline": roof,
+        "cpu_baseline": base,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -65,7 +65,14 @@ enum { FSD_FP64 = 0, FSD_MIXED = 1 };
 
 /* Flags. */
 enum {
-  FSD_FLAG_WARM_START = 1 /* start each solve from the previous solution */
+  FSD_FLAG_WARM_START = 1, /* start each solve from the previous solution */
+  FSD_FLAG_COMOVING = 2    /* fsd_step advances the bodies by the disturbance
+                              motion only: X += (U - U_inf(X)) dt and q by
+                              Omega - Omega_inf.  A cubic periodic box has no
+                              sheared (Lees-Edwards) images, so the imposed
+                              affine motion would drive bodies across the y
+                              boundary into each other; each solve is still
+                              the full sheared problem */
 };
 
 typedef struct {
@@ -107,6 +114,7 @@ typedef struct {
   int P;              /* Gaussian support used                              */
   double xi;          /* splitting used                                     */
   double rc;          /* real-space cut-off used                            */
+  int64_t kernel_launches; /* CUDA kernels this call launched               */
 } fsd_stats;
 
 /* Defaults above (box must still be set). */
@@ -169,6 +177,21 @@ fsd_status fsd_apply_lubrication(fsd_ctx *ctx, const double *dU, double *out,
 /* Right-hand side of Eq. spm_agg (same layout as x). */
 fsd_status fsd_rhs(fsd_ctx *ctx, const double *agg_force_torque,
                    double shear_rate, double *b);
+
+/* Opt-in profiler: device time per kernel group, from CUDA events recorded
+ * on the context's stream around each group (adds a few microseconds per
+ * group launch; leave off for throughput runs).  Groups, in order:
+ * realspace, spread, fft_green, interp, body_rows, precond, krylov,
+ * neighbors, lub_assembly, misc. */
+#define FSD_PROF_GROUPS 10
+/* on != 0: reset the counters and start recording; 0: stop. */
+fsd_status fsd_profile_enable(fsd_ctx *ctx, int on);
+/* ms[g] = accumulated device milliseconds, count[g] = timed launches of
+ * group g since the last enable; n >= FSD_PROF_GROUPS (either array may be
+ * NULL).  Synchronises the context's stream. */
+fsd_status fsd_profile_read(fsd_ctx *ctx, double *ms, int64_t *count, int n);
+/* Name of group g (NULL when out of range). */
+const char *fsd_profile_group_name(int g);
 
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);

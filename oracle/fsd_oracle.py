@@ -754,12 +754,17 @@ def quat_to_matrix(q):
     return R
 
 
-def integrate(X, q, r_body, body, U, dt):
+def integrate(X, q, r_body, body, U, dt, comoving_gamma=0.0):
     """Euler-Maruyama rigid-body update: X += U dt (Eq. EM1);
     q <- normalise(q + dt/2 (0, Omega) (x) q) (Eq. EM2, quaternion product);
     x_b = X + R(q) r_body (Eq. EM3 read as reconstruction about the new X)."""
-    X = X + U[:, 0:3] * dt
-    om = np.concatenate([np.zeros((U.shape[0], 1)), U[:, 3:6]], axis=1)
+    Ut = U.copy()
+    # disturbance motion only (U - U_inf, Omega - Omega_inf; the co-moving
+    # flag of the library): no affine advection in a box without sheared images
+    Ut[:, 0] -= comoving_gamma * X[:, 1]
+    Ut[:, 5] += 0.5 * comoving_gamma
+    X = X + Ut[:, 0:3] * dt
+    om = np.concatenate([np.zeros((U.shape[0], 1)), Ut[:, 3:6]], axis=1)
     q = q + 0.5 * dt * quat_mul(om, q)
     q = q / np.linalg.norm(q, axis=1, keepdims=True)
     R = quat_to_matrix(q)

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfsd.so")
 FSD_OK, FSD_EINVAL, FSD_ENOMEM, FSD_ECUDA, FSD_ENOCONV, FSD_ENUMERIC, FSD_EOVERLAP, FSD_ETIMEOUT = range(8)
 FSD_FP64, FSD_MIXED = 0, 1
 FSD_FLAG_WARM_START = 1
+FSD_FLAG_COMOVING = 2
 STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",
                 5: "FSD_ENUMERIC", 6: "FSD_EOVERLAP", 7: "FSD_ETIMEOUT"}
 
@@ -23,8 +24,10 @@ STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4
 EXPORTS = (
     "fsd_default_params", "fsd_setup", "fsd_solve", "fsd_step", "fsd_get_beads",
     "fsd_apply_mobility", "fsd_apply_saddle", "fsd_apply_precond", "fsd_apply_lubrication",
-    "fsd_rhs", "fsd_get_params", "fsd_last_error", "fsd_destroy",
+    "fsd_rhs", "fsd_get_params", "fsd_profile_enable", "fsd_profile_read",
+    "fsd_profile_group_name", "fsd_last_error", "fsd_destroy",
 )
+PROF_GROUPS = 10
 
 
 class FsdParams(ctypes.Structure):
@@ -48,6 +51,7 @@ class FsdStats(ctypes.Structure):
         ("matvec32", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double),
         ("n_pairs", ctypes.c_int64), ("n_lub", ctypes.c_int64), ("grid", ctypes.c_int),
         ("P", ctypes.c_int), ("xi", ctypes.c_double), ("rc", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -80,12 +84,17 @@ def load(path=LIB_PATH):
     lib.fsd_apply_lubrication.argtypes = [P, P, P, I]
     lib.fsd_rhs.argtypes = [P, P, D, P]
     lib.fsd_get_params.argtypes = [P, ctypes.POINTER(FsdParams)]
+    lib.fsd_profile_enable.argtypes = [P, I]
+    lib.fsd_profile_read.argtypes = [P, P, P, I]
+    lib.fsd_profile_group_name.argtypes = [I]
+    lib.fsd_profile_group_name.restype = ctypes.c_char_p
     lib.fsd_last_error.argtypes = [P]
     lib.fsd_last_error.restype = ctypes.c_char_p
     lib.fsd_destroy.argtypes = [P]
     lib.fsd_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("fsd_default_params", "fsd_last_error", "fsd_destroy"):
+        if name not in ("fsd_default_params", "fsd_last_error", "fsd_destroy",
+                        "fsd_profile_group_name"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -209,6 +218,17 @@ class Suspension:
             out = np.zeros(11 * self.n_beads + 6 * self.n_agg)
         self._check(self.lib.fsd_rhs(self.ctx, _ptr(ft), float(shear), _ptr(out)))
         return out
+
+    def profile(self, on=True):
+        self._check(self.lib.fsd_profile_enable(self.ctx, 1 if on else 0))
+
+    def profile_read(self):
+        """{group: (device ms, timed launches)} since profile(True)."""
+        ms = np.zeros(PROF_GROUPS)
+        cnt = np.zeros(PROF_GROUPS, dtype=np.int64)
+        self._check(self.lib.fsd_profile_read(self.ctx, _ptr(ms), _ptr(cnt), PROF_GROUPS))
+        return {self.lib.fsd_profile_group_name(g).decode(): (float(ms[g]), int(cnt[g]))
+                for g in range(PROF_GROUPS)}
 
     def close(self):
         if self.ctx:

@@ -22,6 +22,49 @@ void vec_scale_host(Ctx &c, double *y, const double *x, double s);
 
 static std::string g_setup_error;
 
+static const char *kProfNames[PG_COUNT] = {"realspace", "spread", "fft_green", "interp",
+                                           "body_rows", "precond", "krylov", "neighbors",
+                                           "lub_assembly", "misc"};
+
+static cudaEvent_t prof_event(Ctx &c) {
+  if (!c.ev_pool.empty()) {
+    cudaEvent_t e = c.ev_pool.back();
+    c.ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+ProfScope::ProfScope(Ctx &cx, int grp) : c(&cx), g(grp) {
+  if (!c->prof) return;
+  e0 = prof_event(*c);
+  if (e0) cudaEventRecord(e0, c->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!c->prof || !e0) return;
+  cudaEvent_t e1 = prof_event(*c);
+  if (!e1) return;
+  cudaEventRecord(e1, c->stream);
+  c->ev_pending.push_back({g, {e0, e1}});
+}
+
+void prof_collect(Ctx &c) {
+  for (auto &pr : c.ev_pending) {
+    cudaEventSynchronize(pr.second.second);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pr.second.first, pr.second.second) == cudaSuccess) {
+      c.prof_ms[pr.first] += ms;
+      c.prof_n[pr.first] += 1;
+    }
+    c.ev_pool.push_back(pr.second.first);
+    c.ev_pool.push_back(pr.second.second);
+  }
+  c.ev_pending.clear();
+}
+
 static bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -150,11 +193,10 @@ static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol
       apply_saddle<T>(c, zj, w);
       (sizeof(T) == 8 ? st.m64 : st.m32)++;
       double *h1 = c.hcol.p, *h2 = c.hcol.p + 64, *hn = c.hcol.p + 128;
-      dot_multi(c, V, ld, j + 1, w, h1);
-      axpy_multi(c, w, V, ld, j + 1, h1, -1.0);
-      dot_multi(c, V, ld, j + 1, w, h2);
-      axpy_multi(c, w, V, ld, j + 1, h2, -1.0);
-      norm2_dev(c, w, hn);
+      // classical Gram-Schmidt applied twice, three fused passes over V
+      cgs_pass(c, 0, V, ld, j + 1, w, nullptr, h1);
+      cgs_pass(c, 1, V, ld, j + 1, w, h1, h2);
+      cgs_pass(c, 2, V, ld, j + 1, w, h2, hn);
       FSD_CUDA(cudaMemcpyAsync(c.h_pinned, c.hcol.p, 192 * sizeof(double),
                                cudaMemcpyDeviceToHost, c.stream));
       FSD_CUDA(cudaStreamSynchronize(c.stream));
@@ -399,6 +441,11 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.prm.P = c.P;
   c.prm.m_shape = c.m_shape;
   // ---- device state
+  {
+    int dev = 0;
+    FSD_CUDA(cudaGetDevice(&dev));
+    FSD_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   const int Nt = c.Nt, N = c.N;
   c.nunk = (int64_t)LDB * Nt + 6 * (int64_t)N;
   c.body_start.alloc(N + 1);
@@ -450,7 +497,7 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.rhs.alloc(c.nunk);
   c.res.alloc(c.nunk);
   c.xprev.alloc(c.nunk);
-  c.partial.alloc((size_t)64 * 4 * 152);
+  c.partial.alloc(std::max<int64_t>((int64_t)64 * 4 * 152, cgs_partial_size(c.nunk, mm + 1)));
   c.hcol.alloc(512);
   FSD_CUDA(cudaMallocHost(&c.h_pinned, 512 * sizeof(double)));
   build_real_table(c);
@@ -507,6 +554,7 @@ static fsd_status check_flags(Ctx &c) {
 static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, double *vel_int,
                                  double *str_int, fsd_stats *stats, double t0_ms) {
   auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = c.launches;
   prepare(c);
   fsd_status fl = check_flags(c);
   const double *ft_int = nullptr;
@@ -514,6 +562,7 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
     const double *d = dev_in(c, ft_user, 6 * (size_t)c.N, c.io_a);
     if (c.t2.n < 6 * (size_t)c.N) c.t2.alloc(6 * (size_t)c.N);
     k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d, c.t2.p, 6);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     ft_int = c.t2.p;
   }
@@ -526,10 +575,12 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
   launch_outputs(c, c.xsol.p, shear, vel_int, str_int);
   FSD_CUDA(cudaMemsetAsync(c.flags.p + 6, 0, sizeof(int), c.stream));
   k_nan_check<<<152, 256, 0, c.stream>>>(vel_int, 6 * (int64_t)c.N, c.flags.p + 6);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaMemcpyAsync(c.h_flags, c.flags.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   FSD_CUDA(cudaStreamSynchronize(c.stream));
   double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() + t0_ms;
   fill_stats(c, stats, ks, rel, ms);
+  if (stats) stats->kernel_launches = c.launches - l0;
   if (c.h_flags[6]) {
     c.last_error = "non-finite aggregate velocity";
     return FSD_ENUMERIC;
@@ -551,11 +602,13 @@ static void bodies_out(Ctx &c, const double *src_int, double *user, int w) {
   if (!user) return;
   if (is_device_ptr(user)) {
     k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, src_int, user, w);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     FSD_CUDA(cudaStreamSynchronize(c.stream));
   } else {
     if (c.io_b.n < (size_t)w * c.N) c.io_b.alloc((size_t)w * c.N);
     k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, src_int, c.io_b.p, w);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     FSD_CUDA(cudaMemcpyAsync(user, c.io_b.p, (size_t)w * c.N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     FSD_CUDA(cudaStreamSynchronize(c.stream));
@@ -684,10 +737,12 @@ fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque, double shear_r
   double *vel_int = c.t1.p;
   fsd_status st = solve_internal(c, agg_force_torque, shear_rate, vel_int, nullptr, stats, 0.0);
   if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
+  const int64_t l1 = c.launches;
   if (agg_velocity) bodies_out(c, vel_int, agg_velocity, 6);
-  launch_integrate(c, vel_int, dt);
+  launch_integrate(c, vel_int, dt, shear_rate);
   launch_wrap_positions(c);
   FSD_CUDA(cudaStreamSynchronize(c.stream));
+  if (stats) stats->kernel_launches += c.launches - l1;
   if (stats)
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
@@ -703,12 +758,14 @@ fsd_status fsd_get_beads(fsd_ctx *ctx, double *bead_pos, double *agg_quat) {
     if (c.io_a.n < 3 * (size_t)c.Nt) c.io_a.alloc(3 * (size_t)c.Nt);
     k_bead_pos_out<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, c.perm_bead.p, c.bead_body.p, c.X.p,
                                                              (const double4 *)c.lever64.p, c.io_a.p);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     FSD_CUDA(cudaMemcpyAsync(bead_pos, c.io_a.p, 3 * (size_t)c.Nt * sizeof(double), cudaMemcpyDefault, c.stream));
   }
   if (agg_quat) {
     if (c.io_b.n < 16 * (size_t)c.N) c.io_b.alloc(16 * (size_t)c.N);
     k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, c.q.p, c.io_b.p, 4);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     FSD_CUDA(cudaMemcpyAsync(agg_quat, c.io_b.p, 4 * (size_t)c.N * sizeof(double), cudaMemcpyDefault, c.stream));
   }
@@ -726,9 +783,11 @@ static void vec_in(Ctx &c, const double *user, double *x, bool beads, bool bodie
   const double *d = dev_in(c, user, tot, c.io_a);
   FSD_CUDA(cudaMemsetAsync(x, 0, c.nunk * sizeof(double), c.stream));
   if (beads) k_beads_in<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, c.perm_bead.p, d, x);
+  FSD_LAUNCHED(c);
   if (bodies)
     k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d + (beads ? nb : 0),
                                                          x + (int64_t)LDB * c.Nt, 6);
+    FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
@@ -742,9 +801,11 @@ static void vec_out(Ctx &c, const double *x, double *user, bool beads, bool bodi
     d = c.io_b.p;
   }
   if (beads) k_beads_out<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, c.perm_bead.p, x, d);
+  FSD_LAUNCHED(c);
   if (bodies)
     k_bodies_out<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, x + (int64_t)LDB * c.Nt,
                                                           d + (beads ? nb : 0), 6);
+    FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   if (!dev)
     FSD_CUDA(cudaMemcpyAsync(user, d, tot * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -808,6 +869,7 @@ fsd_status fsd_apply_lubrication(fsd_ctx *ctx, const double *dU, double *out, in
   const double *d = dev_in(c, dU, 6 * (size_t)c.N, c.io_a);
   FSD_CUDA(cudaMemsetAsync(c.t1.p, 0, c.nunk * sizeof(double), c.stream));
   k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d, c.t1.p + (int64_t)LDB * c.Nt, 6);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   if (precision == FSD_FP64)
     launch_lub_apply<double>(c, c.t1.p, c.t2.p);
@@ -827,6 +889,7 @@ fsd_status fsd_rhs(fsd_ctx *ctx, const double *agg_force_torque, double shear_ra
   if (agg_force_torque) {
     const double *d = dev_in(c, agg_force_torque, 6 * (size_t)c.N, c.io_a);
     k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, d, c.t2.p, 6);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     ft_int = c.t2.p;
   }
@@ -842,6 +905,41 @@ fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p) {
   return FSD_OK;
 }
 
+fsd_status fsd_profile_enable(fsd_ctx *ctx, int on) {
+  if (!ctx) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  prof_collect(c);
+  if (on) {
+    for (int g = 0; g < PG_COUNT; ++g) {
+      c.prof_ms[g] = 0.0;
+      c.prof_n[g] = 0;
+    }
+  }
+  c.prof = on != 0;
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_profile_read(fsd_ctx *ctx, double *ms, int64_t *count, int n) {
+  if (!ctx || n < PG_COUNT) return FSD_EINVAL;
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  prof_collect(c);
+  for (int g = 0; g < PG_COUNT; ++g) {
+    if (ms) ms[g] = c.prof_ms[g];
+    if (count) count[g] = c.prof_n[g];
+  }
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+const char *fsd_profile_group_name(int g) {
+  if (g < 0 || g >= PG_COUNT) return nullptr;
+  return kProfNames[g];
+}
+
 const char *fsd_last_error(const fsd_ctx *ctx) {
   if (!ctx) return g_setup_error.c_str();
   return ctx->c.last_error.c_str();
@@ -853,6 +951,9 @@ void fsd_destroy(fsd_ctx *ctx) {
   if (c.stream) cudaStreamSynchronize(c.stream);
   if (c.h_flags) cudaFreeHost(c.h_flags);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
+  prof_collect(c);
+  for (cudaEvent_t e : c.ev_pool) cudaEventDestroy(e);
+  c.ev_pool.clear();
   cudaStream_t s = c.stream;
   bool own = c.own_stream;
   delete ctx;

@@ -71,15 +71,48 @@ struct OpData {
   DBuf<T> bdiag;      // lubrication BSR diagonal blocks [Nt][36]
   DBuf<T> pos;        // wrapped positions [Nt][4] (x, y, z, 0)
   DBuf<T> lever;      // r_b = x_b - X_J [Nt][4]
+  DBuf<T> packed;     // per bead (x, y, z, F, L, S6, 0) in the operator precision [Nt][16]
+};
+
+// Kernel groups timed by the opt-in profiler (CUDA events on the stream).
+enum ProfGroup {
+  PG_REAL = 0,  // real-space pair sum
+  PG_SPREAD,    // Gaussian spreading
+  PG_FFT,       // FFT passes incl. the fused Green's function
+  PG_INTERP,    // interpolation
+  PG_BODY,      // aggregate rows: constraint gather + lubrication BSR
+  PG_PRECOND,   // preconditioner apply
+  PG_KRYLOV,    // Arnoldi dots / updates / scaling
+  PG_NEIGHBOR,  // cell and neighbour lists
+  PG_LUB,       // lubrication assembly + Schur LUs
+  PG_MISC,      // rhs, outputs, integrator, permutations
+  PG_COUNT
+};
+
+struct Ctx;
+struct ProfScope {
+  Ctx *c;
+  int g;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(Ctx &cx, int grp);
+  ~ProfScope();
 };
 
 struct Ctx {
+  // ---- profiling and launch accounting
+  bool prof = false;
+  int64_t launches = 0;  // kernel launches issued by this context
+  double prof_ms[PG_COUNT] = {};
+  int64_t prof_n[PG_COUNT] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   // ---- parameters
   fsd_params prm{};
   double L = 0, a = 1, eta = 1, xi = 0.5, rc = 0, alpha = 0, h = 0;
   int n = 0, P = 8;
   double m_shape = 0;
   int Nt = 0, N = 0;
+  int num_sms = 152;
   int64_t nunk = 0;  // padded length of a solution vector: LDB*Nt + 6*N
   // ---- real-space table geometry
   int tab_nint = 0;
@@ -147,7 +180,7 @@ void launch_precond(Ctx &c, const double *r, double *z);
 void launch_rhs(Ctx &c, const double *ft_internal, double shear, double *b);
 void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int,
                     double *str_int);
-void launch_integrate(Ctx &c, const double *vel_int, double dt);
+void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear);
 
 // krylov.cu
 void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w,
@@ -155,6 +188,9 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w,
 void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k,
                 const double *coef_dev, double sign);  // w += sign * sum_j coef[j] V_j
 void vec_scale_host(Ctx &c, double *y, const double *x, double s);  // y = s x
+void cgs_pass(Ctx &c, int mode, const double *V, int64_t ld, int k, double *w,
+              const double *coef_dev, double *out_dev);  // fused Gram-Schmidt pass
+int64_t cgs_partial_size(int64_t nunk, int kmax);
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b,
                int64_t n);                          // y = a x + b y
 void norm2_dev(Ctx &c, const double *x, double *out_dev);
@@ -164,5 +200,10 @@ template <typename T>
 void apply_saddle(Ctx &c, const double *x, double *y);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// count a kernel launch (every <<<>>> site is followed by this)
+#define FSD_LAUNCHED(cx) (++(cx).launches)
+
+void prof_collect(Ctx &c);  // fold finished event pairs into prof_ms
 
 }  // namespace fsd

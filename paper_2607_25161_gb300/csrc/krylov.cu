@@ -59,13 +59,108 @@ __global__ void k_dot_final(const double *__restrict__ partial, int nb, int k, d
 }
 
 void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, double *out_dev) {
+  ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
   for (int k0 = 0; k0 < k; k0 += kDotChunk) {
     int kc = std::min(kDotChunk, k - k0);
     k_dot_partial<<<kDotBlocks, 256, 0, c.stream>>>(V, ld, k0, kc, w, n, c.partial.p);
+    FSD_LAUNCHED(c);
   }
   k_dot_final<<<k, 256, 0, c.stream>>>(c.partial.p, kDotBlocks, k, out_dev);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
+}
+
+// Fused classical Gram-Schmidt passes over the basis V (k vectors):
+//   MODE 0:  partial dots  V_j . w
+//   MODE 1:  w -= sum_j coef_j V_j, then partial dots V_j . w
+//   MODE 2:  w -= sum_j coef_j V_j, then partial ||w||^2
+// Each thread owns kE elements spaced by the grid's thread count (coalesced);
+// warp partials go to partial[j * nwarps + warp] (fixed reduction order).
+constexpr int kE = 4;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64_t ld, int k,
+                                             double *w, const double *__restrict__ coef,
+                                             int64_t n, double *partial) {
+  __shared__ double cs[64];
+  if (MODE > 0)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = coef[j];
+  __syncthreads();
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double wv[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const int64_t i = t0 + e * T;
+    wv[e] = i < n ? w[i] : 0.0;
+  }
+  if (MODE > 0) {
+    for (int j = 0; j < k; ++j) {
+      const double c = cs[j];
+      const double *vj = V + (int64_t)j * ld;
+#pragma unroll
+      for (int e = 0; e < kE; ++e) {
+        const int64_t i = t0 + e * T;
+        if (i < n) wv[e] -= c * vj[i];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const int64_t i = t0 + e * T;
+      if (i < n) w[i] = wv[e];
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = t0 >> 5;
+  const int64_t nwarps = T >> 5;
+  if (MODE == 2) {
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < kE; ++e) acc += wv[e] * wv[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) partial[gw] = acc;
+    return;
+  }
+  for (int j = 0; j < k; ++j) {
+    const double *vj = V + (int64_t)j * ld;
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const int64_t i = t0 + e * T;
+      if (i < n) acc += vj[i] * wv[e];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) partial[(int64_t)j * nwarps + gw] = acc;
+  }
+}
+
+static int cgs_blocks(int64_t n) { return std::max(1, ceil_div(n, 256LL * kE)); }
+
+// out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef.
+void cgs_pass(Ctx &c, int mode, const double *V, int64_t ld, int k, double *w,
+              const double *coef_dev, double *out_dev) {
+  ProfScope ps(c, PG_KRYLOV);
+  const int64_t n = c.nunk;
+  const int blocks = cgs_blocks(n);
+  const int nwarps = blocks * 8;
+  if (mode == 0)
+    k_cgs<0><<<blocks, 256, 0, c.stream>>>(V, ld, k, w, coef_dev, n, c.partial.p);
+  else if (mode == 1)
+    k_cgs<1><<<blocks, 256, 0, c.stream>>>(V, ld, k, w, coef_dev, n, c.partial.p);
+  else
+    k_cgs<2><<<blocks, 256, 0, c.stream>>>(V, ld, k, w, coef_dev, n, c.partial.p);
+  FSD_LAUNCHED(c);
+  const int kk = mode == 2 ? 1 : k;
+  k_dot_final<<<kk, 256, 0, c.stream>>>(c.partial.p, nwarps, kk, out_dev);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+int64_t cgs_partial_size(int64_t nunk, int kmax) {
+  return (int64_t)cgs_blocks(nunk) * 8 * (kmax + 1);
 }
 
 // w[i] += sign * sum_j coef[j] V_j[i]
@@ -85,9 +180,11 @@ __global__ void k_axpy_multi(double *w, const double *__restrict__ V, int64_t ld
 void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k, const double *coef_dev,
                 double sign) {
   if (k <= 0) return;
+  ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
   int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
   k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, k, coef_dev, sign, n);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
@@ -104,14 +201,18 @@ __global__ void k_axpby(double *y, double a, const double *__restrict__ x, doubl
 }
 
 void vec_scale_host(Ctx &c, double *y, const double *x, double s) {
+  ProfScope ps(c, PG_KRYLOV);
   int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * 152);
   k_scale<<<blocks, 256, 0, c.stream>>>(y, x, s, c.nunk);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b, int64_t n) {
+  ProfScope ps(c, PG_KRYLOV);
   int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
   k_axpby<<<blocks, 256, 0, c.stream>>>(y, a, x, b, n);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 

@@ -524,14 +524,18 @@ __global__ void k_outputs(int N, const int *__restrict__ body_start,
 
 // ---------------------------------------------------------------- integrator
 __global__ void k_integrate(int N, const double *__restrict__ vel, double dt, double *X,
-                            double *q) {
+                            double *q, double affine_gamma) {
   int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= N) return;
   const double *u = vel + 6 * (size_t)J;
-  for (int d = 0; d < 3; ++d) X[3 * J + d] += u[d] * dt;
+  // affine_gamma != 0: disturbance motion only (U - U_inf, Omega - Omega_inf)
+  const double ux = u[0] - affine_gamma * X[3 * J + 1];
+  X[3 * J] += ux * dt;
+  X[3 * J + 1] += u[1] * dt;
+  X[3 * J + 2] += u[2] * dt;
   double *qq = q + 4 * (size_t)J;
   const double w = qq[0], x = qq[1], y = qq[2], z = qq[3];
-  const double o0 = u[3], o1 = u[4], o2 = u[5];
+  const double o0 = u[3], o1 = u[4], o2 = u[5] + 0.5 * affine_gamma;
   // (0, Omega) (x) q
   const double dw = -(o0 * x + o1 * y + o2 * z);
   const double dx = o0 * w + (o1 * z - o2 * y);
@@ -555,6 +559,7 @@ static void strain6(double shear, double *e) {
 }
 
 void build_lubrication(Ctx &c) {
+  ProfScope ps(c, PG_LUB);
   const int Nt = c.Nt;
   // CSR rows from the lubrication neighbour counts
   std::vector<int> cnt(Nt);
@@ -578,11 +583,13 @@ void build_lubrication(Ctx &c) {
       Nt, (const double4 *)c.pos64.p, c.lnbr.p, c.lcnt.p, c.lcap, c.brow.p, c.bcol.p,
       c.op64.bval.p, c.op32.bval.p, c.op64.bdiag.p, c.op32.bdiag.p, c.pdiag.p, c.L, c.a, c.eta, rl,
       c.prm.precond_cutoff, c.prm.lub_hmin);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   const double zeta0 = 6.0 * kPi * c.eta * c.a;
   k_schur_lu<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
                                                       (const double4 *)c.lever64.p, c.pdiag.p,
                                                       zeta0, c.schur.p, c.piv.p, c.flags.p);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
@@ -609,42 +616,51 @@ OpData<float> &opx<float>(Ctx &c) {
 
 template <typename T>
 void launch_body_rows(Ctx &c, const double *x, double *y, bool with_lub) {
+  ProfScope ps(c, PG_BODY);
   OpData<T> &op = opx<T>(c);
   const int64_t off = (int64_t)LDB * c.Nt;
   const bool lub = with_lub && c.n_lub > 0;
   k_body_rows<T><<<ceil_div((int64_t)c.N * 32, 256), 256, 0, c.stream>>>(
       c.N, c.body_start.p, c.bead_body.p, lever_ptr<T>(c), x, y, c.brow.p, c.bcol.p, op.bval.p,
       op.bdiag.p, lub ? 1 : 0, off, T(1), T(-1));
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 // out = RR dU (aggregate rows only; the bead part of x is ignored).
 template <typename T>
 void launch_lub_apply(Ctx &c, const double *x, double *y) {
+  ProfScope ps(c, PG_BODY);
   OpData<T> &op = opx<T>(c);
   const int64_t off = (int64_t)LDB * c.Nt;
   k_body_rows<T><<<ceil_div((int64_t)c.N * 32, 256), 256, 0, c.stream>>>(
       c.N, c.body_start.p, c.bead_body.p, lever_ptr<T>(c), x, y, c.brow.p, c.bcol.p, op.bval.p,
       op.bdiag.p, c.n_lub > 0 ? 1 : 0, off, T(0), T(1));
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 void launch_precond(Ctx &c, const double *r, double *z) {
+  ProfScope ps(c, PG_PRECOND);
   const int64_t off = (int64_t)LDB * c.Nt;
   const double zeta0 = 6.0 * kPi * c.eta * c.a;
   k_precond_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(
       c.N, c.body_start.p, (const double4 *)c.lever64.p, r, z, c.schur.p, c.piv.p, zeta0, off);
+  FSD_LAUNCHED(c);
   k_precond_bead<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(
       c.Nt, c.bead_body.p, (const double4 *)c.lever64.p, r, z, zeta0, off);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 void launch_rhs(Ctx &c, const double *ft_int, double shear, double *b) {
+  ProfScope ps(c, PG_MISC);
   double e[6];
   strain6(shear, e);
   const int64_t off = (int64_t)LDB * c.Nt;
   k_rhs_bead<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, (const double4 *)c.lever64.p, e[0],
                                                        e[1], e[2], e[3], e[4], e[5], b);
+  FSD_LAUNCHED(c);
   const bool nf = c.n_lub > 0;
   if (nf) {
     const double rl = c.prm.lub_cutoff;
@@ -652,14 +668,17 @@ void launch_rhs(Ctx &c, const double *ft_int, double shear, double *b) {
         c.Nt, (const double4 *)c.pos64.p, (const double4 *)c.lever64.p, c.bead_body.p, c.lnbr.p,
         c.lcnt.p, c.lcap, nullptr, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.a,
         c.eta, rl, c.prm.lub_hmin);
+    FSD_LAUNCHED(c);
   }
   k_rhs_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
                                                       (const double4 *)c.lever64.p, c.fnf.p,
                                                       ft_int, b, off, nf ? 1 : 0);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int, double *str_int) {
+  ProfScope ps(c, PG_MISC);
   double e[6];
   strain6(shear, e);
   const int64_t off = (int64_t)LDB * c.Nt;
@@ -669,16 +688,21 @@ void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int, doub
         c.Nt, (const double4 *)c.pos64.p, (const double4 *)c.lever64.p, c.bead_body.p, c.lnbr.p,
         c.lcnt.p, c.lcap, x + off, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.a,
         c.eta, c.prm.lub_cutoff, c.prm.lub_hmin);
+    FSD_LAUNCHED(c);
   }
   k_outputs<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
                                                      (const double4 *)c.lever64.p, c.X.p, x,
                                                      c.fnf.p, c.snf.p, nf ? 1 : 0, shear, vel_int,
                                                      str_int, off);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
-void launch_integrate(Ctx &c, const double *vel_int, double dt) {
-  k_integrate<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, vel_int, dt, c.X.p, c.q.p);
+void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear) {
+  ProfScope ps(c, PG_MISC);
+  const double ag = (c.prm.flags & FSD_FLAG_COMOVING) ? shear : 0.0;
+  k_integrate<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, vel_int, dt, c.X.p, c.q.p, ag);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 

@@ -122,7 +122,7 @@ void build_real_table(Ctx &c) {
   c.tab_h = ht;
   c.tab_nint = nint;
   WaveQuad q = make_quad(c.xi, c.a, c.eta, 400);
-  std::vector<double> tab((size_t)nint * NFUNC * TCOEF);
+  std::vector<double> tab((size_t)nint * TCOEF * 8, 0.0);
   const int NC = TCOEF;
   double tk[NC];
   for (int k = 0; k < NC; ++k) tk[k] = std::cos(kPi * (k + 0.5) / NC);
@@ -144,11 +144,11 @@ void build_real_table(Ctx &c) {
         for (int k = 0; k < NC; ++k) s += v[k] * std::cos(j * kPi * (k + 0.5) / NC);
         cc[j] = (j == 0 ? 1.0 : 2.0) * s / NC;
       }
-      double *dst = &tab[((size_t)iv * NFUNC + f) * NC];
+      // layout [interval][power p][function, padded to 8]
       for (int p = 0; p < NC; ++p) {
         double s = 0.0;
         for (int j = 0; j < NC; ++j) s += cc[j] * cheb[j][p];
-        dst[p] = s;
+        tab[((size_t)iv * NC + p) * 8 + f] = s;
       }
     }
   }
@@ -212,6 +212,7 @@ void launch_wrap_positions(Ctx &c) {
   k_wrap_positions<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(
       c.Nt, c.L, c.bead_body.p, c.X.p, c.q.p, c.rbody.p, (double4 *)c.pos64.p,
       (double4 *)c.lever64.p, (float4 *)c.op32.pos.p, (float4 *)c.op32.lever.p);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
@@ -336,6 +337,7 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos, double L, i
 }
 
 void build_neighbors(Ctx &c) {
+  ProfScope ps(c, PG_NEIGHBOR);
   int nc = (int)std::floor(c.L / std::max(c.rc, c.prm.lub_cutoff));
   if (nc < 3) nc = 1;
   if (nc > 128) nc = 128;
@@ -352,17 +354,22 @@ void build_neighbors(Ctx &c) {
     FSD_CUDA(cudaMemsetAsync(c.cell_count.p, 0, ncells * sizeof(int), c.stream));
     FSD_CUDA(cudaMemsetAsync(c.flags.p, 0, 8 * sizeof(int), c.stream));
     k_cell_count<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, pos, c.L, nc, c.cell_count.p);
+    FSD_LAUNCHED(c);
     k_exclusive_scan<<<1, 1024, 0, c.stream>>>(ncells, c.cell_count.p, c.cell_start.p,
                                                c.cell_cursor.p);
+    FSD_LAUNCHED(c);
     k_cell_fill<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, pos, c.L, nc, c.cell_cursor.p,
                                                            c.cell_beads.p);
+    FSD_LAUNCHED(c);
     k_sort_cells<<<ceil_div(ncells, 128), 128, 0, c.stream>>>(ncells, c.cell_start.p,
                                                              c.cell_beads.p);
+    FSD_LAUNCHED(c);
     double rl = c.prm.lub_cutoff > 2.0 * c.a ? c.prm.lub_cutoff : 0.0;
     double ov = 2.0 * c.a * (1.0 - 1e-6);
     k_neighbors<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
         c.Nt, pos, c.L, nc, c.cell_start.p, c.cell_beads.p, c.bead_body.p, c.rc * c.rc,
         rl * rl, ov * ov, c.cap, c.lcap, c.nbr.p, c.ncnt.p, c.lnbr.p, c.lcnt.p, c.flags.p);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     FSD_CUDA(cudaMemcpyAsync(c.h_flags, c.flags.p, 8 * sizeof(int), cudaMemcpyDeviceToHost,
                              c.stream));
@@ -474,21 +481,54 @@ __device__ __forceinline__ void free_phi(const T inv, const T a2, const T c8, T 
   ph[6] = c8 * (T(-15) * i7 + T(42) * a2 * i9);
 }
 
+// Wave-part radial functions from the Chebyshev-fitted table (monomials in
+// t in [-1, 1] per interval), all seven functions per Horner step.
 template <typename T>
-__device__ __forceinline__ void wave_table(const T *__restrict__ tab, int nint, T inv_h, T r,
-                                           T *w) {
-  T s = r * inv_h;
+__device__ __forceinline__ void wave_table(const T *tab, int nint, T inv_h, T r, T *w);
+template <>
+__device__ __forceinline__ void wave_table<float>(const float *tab, int nint, float inv_h, float r,
+                                                  float *w) {
+  const float s = r * inv_h;
   int iv = (int)s;
   iv = iv < 0 ? 0 : (iv >= nint ? nint - 1 : iv);
-  const T t = T(2) * (s - T(iv)) - T(1);
-  const T *c = tab + (size_t)iv * NFUNC * TCOEF;
+  const float t = 2.f * (s - (float)iv) - 1.f;
+  const float4 *c = (const float4 *)(tab + (size_t)iv * TCOEF * 8);
+  float4 lo = c[2 * (TCOEF - 1)], hi = c[2 * (TCOEF - 1) + 1];
+  float v0 = lo.x, v1 = lo.y, v2 = lo.z, v3 = lo.w, v4 = hi.x, v5 = hi.y, v6 = hi.z;
 #pragma unroll
-  for (int f = 0; f < NFUNC; ++f) {
-    T v = __ldg(c + f * TCOEF + TCOEF - 1);
-#pragma unroll
-    for (int p = TCOEF - 2; p >= 0; --p) v = v * t + __ldg(c + f * TCOEF + p);
-    w[f] = v;
+  for (int p = TCOEF - 2; p >= 0; --p) {
+    lo = c[2 * p];
+    hi = c[2 * p + 1];
+    v0 = v0 * t + lo.x; v1 = v1 * t + lo.y; v2 = v2 * t + lo.z; v3 = v3 * t + lo.w;
+    v4 = v4 * t + hi.x; v5 = v5 * t + hi.y; v6 = v6 * t + hi.z;
   }
+  w[0] = v0; w[1] = v1; w[2] = v2; w[3] = v3; w[4] = v4; w[5] = v5; w[6] = v6;
+}
+template <>
+__device__ __forceinline__ void wave_table<double>(const double *tab, int nint, double inv_h,
+                                                   double r, double *w) {
+  const double s = r * inv_h;
+  int iv = (int)s;
+  iv = iv < 0 ? 0 : (iv >= nint ? nint - 1 : iv);
+  const double t = 2.0 * (s - (double)iv) - 1.0;
+  const double2 *c = (const double2 *)(tab + (size_t)iv * TCOEF * 8);
+  double v[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 a = c[4 * (TCOEF - 1) + q];
+    v[2 * q] = a.x;
+    v[2 * q + 1] = a.y;
+  }
+#pragma unroll
+  for (int p = TCOEF - 2; p >= 0; --p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 a = c[4 * p + q];
+      v[2 * q] = v[2 * q] * t + a.x;
+      v[2 * q + 1] = v[2 * q + 1] * t + a.y;
+    }
+#pragma unroll
+  for (int f = 0; f < NFUNC; ++f) w[f] = v[f];
 }
 
 template <typename T>
@@ -513,39 +553,108 @@ __device__ __forceinline__ void load_moments(const double *__restrict__ x, int j
   S6[5] = r2i * s5;
 }
 
+// Per-matvec packing of the source beads in the operator precision:
+// (x, y, z, F0 | F1, F2, L0, L1 | L2, Sxx, Syy, Szz | Sxy, Sxz, Syz, 0)
+// so that one neighbour costs four 16-byte loads (FP32) in the pair loop.
+template <typename T>
+__global__ void k_pack_sources(int Nt, const double4 *__restrict__ pos,
+                               const double *__restrict__ x, T *packed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  T F[3], Lm[3], S6[6];
+  load_moments<T>(x, i, F, Lm, S6);
+  const double4 p = pos[i];
+  T *o = packed + (size_t)i * 16;
+  o[0] = (T)p.x;
+  o[1] = (T)p.y;
+  o[2] = (T)p.z;
+  o[3] = F[0];
+  o[4] = F[1];
+  o[5] = F[2];
+  o[6] = Lm[0];
+  o[7] = Lm[1];
+  o[8] = Lm[2];
+  o[9] = S6[0];
+  o[10] = S6[1];
+  o[11] = S6[2];
+  o[12] = S6[3];
+  o[13] = S6[4];
+  o[14] = S6[5];
+  o[15] = T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_packed(const T *__restrict__ packed, int j, T *pj, T *F,
+                                            T *Lm, T *S6);
+template <>
+__device__ __forceinline__ void load_packed<float>(const float *__restrict__ packed, int j,
+                                                   float *pj, float *F, float *Lm, float *S6) {
+  const float4 *q = (const float4 *)(packed + (size_t)j * 16);
+  const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  pj[0] = a.x; pj[1] = a.y; pj[2] = a.z;
+  F[0] = a.w; F[1] = b.x; F[2] = b.y;
+  Lm[0] = b.z; Lm[1] = b.w; Lm[2] = c.x;
+  S6[0] = c.y; S6[1] = c.z; S6[2] = c.w; S6[3] = d.x; S6[4] = d.y; S6[5] = d.z;
+}
+template <>
+__device__ __forceinline__ void load_packed<double>(const double *__restrict__ packed, int j,
+                                                    double *pj, double *F, double *Lm,
+                                                    double *S6) {
+  const double2 *q = (const double2 *)(packed + (size_t)j * 16);
+  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  const double2 e = __ldg(q + 4), f = __ldg(q + 5), g = __ldg(q + 6), h = __ldg(q + 7);
+  pj[0] = a.x; pj[1] = a.y; pj[2] = b.x;
+  F[0] = b.y; F[1] = c.x; F[2] = c.y;
+  Lm[0] = d.x; Lm[1] = d.y; Lm[2] = e.x;
+  S6[0] = e.y; S6[1] = f.x; S6[2] = f.y; S6[3] = g.x; S6[4] = g.y; S6[5] = h.x;
+}
+
 // G lanes per target bead; the group sums its neighbours, reduces with warp
 // shuffles and its first lane writes the bead row:
 //   y_i = sum_j M_r(x_i - x_j) x_j + M_self,r x_i [+ (dU + dOm x r_i, dOm, 0)]
 template <typename T, int G>
 __global__ void __launch_bounds__(256) k_realspace(
-    int Nt, const typename RS<T>::V4 *__restrict__ pos, const int *__restrict__ nbr,
+    int Nt, const T *__restrict__ packed, const int *__restrict__ nbr,
     const int *__restrict__ ncnt, int cap, const double *__restrict__ x, double *__restrict__ y,
-    const T *__restrict__ tab, int nint, T inv_h, T L, T a, T c8, T self_t, T self_r,
+    const T *__restrict__ tab_g, int nint, T inv_h, T L, T a, T c8, T self_t, T self_r,
     T self_s, int add_constraint, const int *__restrict__ bead_body,
     const double4 *__restrict__ lever, int Nt_off) {
-  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  // the radial table is staged once per (persistent) CTA in shared memory
+  extern __shared__ __align__(16) unsigned char tab_raw[];
+  T *tab = (T *)tab_raw;
+  {
+    const int nv = nint * TCOEF * 8 * (int)sizeof(T) / 16;
+    const uint4 *src = (const uint4 *)tab_g;
+    uint4 *dst = (uint4 *)tab_raw;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  const int groups_per_block = blockDim.x / G;
   const int lane = threadIdx.x % G;
+  for (int gbase = blockIdx.x * groups_per_block; gbase < Nt; gbase += gridDim.x * groups_per_block) {
+  const int gid = gbase + threadIdx.x / G;
   const bool active = gid < Nt;
   const int i = active ? gid : Nt - 1;
   T acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = T(0);
-  const auto pi = pos[i];
+  const T *pio = packed + (size_t)i * 16;
+  const T pi0 = pio[0], pi1 = pio[1], pi2 = pio[2];
   const int cnt = active ? ncnt[i] : 0;
   const int *row = nbr + (size_t)i * cap;
   const T a2 = a * a, two_a = T(2) * a;
   const T invL = T(1) / L;
+#pragma unroll 2
   for (int k = lane; k < cnt; k += G) {
     const int j = __ldg(row + k);
-    const auto pj = pos[j];
-    T d0 = pi.x - pj.x, d1 = pi.y - pj.y, d2 = pi.z - pj.z;
+    T pj[3], F[3], Lm[3], S6[6];
+    load_packed<T>(packed, j, pj, F, Lm, S6);
+    T d0 = pi0 - pj[0], d1 = pi1 - pj[1], d2 = pi2 - pj[2];
     d0 -= L * rint_t<T>(d0 * invL);
     d1 -= L * rint_t<T>(d1 * invL);
     d2 -= L * rint_t<T>(d2 * invL);
     const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
     const T r = sqrt_t<T>(r2);
-    T F[3], Lm[3], S6[6];
-    load_moments<T>(x, j, F, Lm, S6);
     T wv[NFUNC];
     wave_table<T>(tab, nint, inv_h, r, wv);
     T ph[NFUNC];
@@ -569,7 +678,7 @@ __global__ void __launch_bounds__(256) k_realspace(
   for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off, G);
-  if (!active || lane != 0) return;
+  if (!active || lane != 0) continue;
   // self term and rigid-body constraint rows
   double xi_[11];
   const double *xr = x + (size_t)i * LDB;
@@ -605,6 +714,7 @@ __global__ void __launch_bounds__(256) k_realspace(
   double2 *yo = (double2 *)(y + (size_t)i * LDB);
 #pragma unroll
   for (int k = 0; k < 6; ++k) yo[k] = make_double2(o[2 * k], o[2 * k + 1]);
+  }
 }
 
 template <typename T>
@@ -631,24 +741,36 @@ OpData<float> &opdata<float>(Ctx &c) {
 
 template <typename T>
 void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, bool) {
+  ProfScope ps(c, PG_REAL);
   OpData<T> &op = opdata<T>(c);
   const int threads = 256;
+  if (op.packed.n < (size_t)c.Nt * 16) op.packed.alloc((size_t)c.Nt * 16);
+  k_pack_sources<T><<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, (const double4 *)c.pos64.p, x,
+                                                              op.packed.p);
+  FSD_LAUNCHED(c);
   const double avg = (double)c.n_pairs / std::max(1, c.Nt);
   int G = avg > 96 ? 32 : (avg > 40 ? 16 : (avg > 16 ? 8 : 4));
-  const int blocks = ceil_div((int64_t)c.Nt * G, threads);
+  const size_t smem = (size_t)c.tab_nint * TCOEF * 8 * sizeof(T);
+  int per_sm = 0;
   const T inv_h = (T)(1.0 / c.tab_h);
   const T c8 = (T)(1.0 / (8.0 * kPi * c.eta));
 #define FSD_RS_LAUNCH(GG)                                                                    \
-  k_realspace<T, GG><<<blocks, threads, 0, c.stream>>>(                                      \
-      c.Nt, pos_ptr<T>(c), c.nbr.p, c.ncnt.p, c.cap, x, y, op.table.p, c.tab_nint, inv_h,    \
+  FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>,                                          \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
+  FSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_realspace<T, GG>, threads, \
+                                                         smem));                             \
+  k_realspace<T, GG><<<std::min<int64_t>(ceil_div((int64_t)c.Nt * GG, threads),               \
+                                         (int64_t)std::max(1, per_sm) * c.num_sms),         \
+                       threads, smem, c.stream>>>(                                           \
+      c.Nt, op.packed.p, c.nbr.p, c.ncnt.p, c.cap, x, y, op.table.p, c.tab_nint, inv_h,      \
       (T)c.L, (T)c.a, c8, op.self_real[0], op.self_real[1], op.self_real[2],               \
       add_constraint ? 1 : 0, c.bead_body.p, (const double4 *)c.lever64.p,                   \
       (int)(LDB * (int64_t)c.Nt))
   switch (G) {
-    case 32: FSD_RS_LAUNCH(32); break;
-    case 16: FSD_RS_LAUNCH(16); break;
-    case 8: FSD_RS_LAUNCH(8); break;
-    default: FSD_RS_LAUNCH(4); break;
+    case 32: FSD_RS_LAUNCH(32); FSD_LAUNCHED(c); break;
+    case 16: FSD_RS_LAUNCH(16); FSD_LAUNCHED(c); break;
+    case 8: FSD_RS_LAUNCH(8); FSD_LAUNCHED(c); break;
+    default: FSD_RS_LAUNCH(4); FSD_LAUNCHED(c); break;
   }
 #undef FSD_RS_LAUNCH
   FSD_CUDA(cudaGetLastError());

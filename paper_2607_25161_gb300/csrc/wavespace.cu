@@ -47,27 +47,81 @@ __device__ __forceinline__ Cx<T> cmul_i(Cx<T> a, T sg) {
   return {-sg * a.y, sg * a.x};
 }
 
-constexpr int kMaxStages = 16;
-struct FftPlan {
-  int n;
-  int nst;
-  int radix[kMaxStages];
+constexpr int kMaxStages = 12;
+
+// Division by a runtime constant d for numerators below 2^31 without an
+// integer divide: q = (umulhi(x, m) + x) >> s with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, s = l (Granlund-Montgomery round-up
+// method; d = 1 gives m = s = 0).
+struct FastDiv {
+  uint32_t d, m, s;
 };
 
-static FftPlan make_plan(int n) {
+static FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{d, 0u, 0u};
+  if (d <= 1) return f;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  f.s = l;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f) {
+  return (__umulhi(x, f.m) + x) >> f.s;
+}
+
+struct FftStage {
+  int R, Ns, toff;   // radix, size of the sub-transforms already done, twiddle offset
+  FastDiv nb, ns;    // divisions by n / R and by Ns
+};
+
+struct FftPlan {
+  int n, nst, ntw;
+  FastDiv fn, fnh;   // divisions by n and by n/2 + 1
+  FftStage st[kMaxStages];
+};
+
+// Stages 4^a 2^b 3^c 5^d; per stage the twiddles exp(-2 pi i r k / (Ns R)),
+// r = 1..R-1, k < Ns, stored contiguously (complex) from toff.
+static FftPlan make_plan(int n, std::vector<double> *tw) {
   FftPlan p{};
   p.n = n;
+  p.fn = make_fastdiv(n);
+  p.fnh = make_fastdiv(n / 2 + 1);
   int m = n, k = 0;
+  std::vector<int> radices;
   while (m % 4 == 0) {
-    p.radix[k++] = 4;
+    radices.push_back(4);
     m /= 4;
   }
   for (int f : {2, 3, 5})
     while (m % f == 0) {
-      p.radix[k++] = f;
+      radices.push_back(f);
       m /= f;
     }
+  int Ns = 1, off = 0;
+  if (tw) tw->clear();
+  for (int R : radices) {
+    FftStage &s = p.st[k++];
+    s.R = R;
+    s.Ns = Ns;
+    s.toff = off;
+    s.nb = make_fastdiv(n / R);
+    s.ns = make_fastdiv(Ns);
+    for (int r = 1; r < R; ++r)
+      for (int kk = 0; kk < Ns; ++kk) {
+        const double ang = -2.0 * kPi * r * kk / ((double)Ns * R);
+        if (tw) {
+          tw->push_back(std::cos(ang));
+          tw->push_back(std::sin(ang));
+        }
+      }
+    off += (R - 1) * Ns;
+    Ns *= R;
+  }
   p.nst = k;
+  p.ntw = off;
   return p;
 }
 
@@ -120,55 +174,52 @@ __device__ __forceinline__ void dft_small(Cx<T> *v, T sg) {
 }
 
 // One Stockham stage of radix R over nl lines stored with stride ls:
-//   for butterfly j < n/R:  v_r = in[j + r n/R] w^(r k), k = j mod Ns,
-//   DFT_R, out[(j / Ns) Ns R + k + r Ns] = v_r.
+//   for butterfly j < n/R, k = j mod Ns, g = j div Ns:
+//   v_r = in[j + r n/R] w_(r,k),  DFT_R,  out[g Ns R + k + r Ns] = v_r.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(const Cx<T> *in, Cx<T> *out, int nl, int n, int ls,
-                                               int Ns, const Cx<T> *tw, T sg) {
+                                               const FftStage &st, const Cx<T> *tws, T sg) {
   const int nb = n / R;
+  const int Ns = st.Ns;
   const int total = nl * nb;
-  const int tstep = n / (Ns * R);
+  const Cx<T> *tw = tws + st.toff;
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int line = b / nb, j = b - line * nb;
-    const int k = j % Ns;
-    const Cx<T> *src = in + line * ls;
+    const int line = (int)fdiv((uint32_t)b, st.nb);
+    const int j = b - line * nb;
+    const int g = (int)fdiv((uint32_t)j, st.ns);
+    const int k = j - g * Ns;
+    const Cx<T> *src = in + line * ls + j;
     Cx<T> v[R];
+    v[0] = src[0];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      Cx<T> a = src[j + r * nb];
-      if (r > 0) {
-        int t = (r * k * tstep) % n;
-        Cx<T> w = tw[t];
-        w.y *= -sg;  // table holds exp(-2 pi i t / n)
-        a = cmul(a, w);
-      }
-      v[r] = a;
+    for (int r = 1; r < R; ++r) {
+      Cx<T> w = tw[(r - 1) * Ns + k];
+      w.y *= -sg;  // tables hold the forward twiddles
+      v[r] = cmul(src[r * nb], w);
     }
     dft_small<T, R>(v, sg);
-    Cx<T> *dst = out + line * ls + (j / Ns) * Ns * R + k;
+    Cx<T> *dst = out + line * ls + g * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[r * Ns] = v[r];
   }
 }
 
 // Full transform of nl lines: data starts in A; returns the buffer holding
-// the result (A or B).  tw in shared memory holds exp(-2 pi i t / n).
+// the result (A or B).
 template <typename T>
 __device__ Cx<T> *fft_lines(Cx<T> *A, Cx<T> *B, int nl, int n, int ls, const FftPlan &plan,
-                            const Cx<T> *tw, T sg) {
+                            const Cx<T> *tws, T sg) {
   Cx<T> *in = A, *out = B;
-  int Ns = 1;
   for (int s = 0; s < plan.nst; ++s) {
-    const int R = plan.radix[s];
-    if (R == 4)
-      stockham_stage<T, 4>(in, out, nl, n, ls, Ns, tw, sg);
-    else if (R == 2)
-      stockham_stage<T, 2>(in, out, nl, n, ls, Ns, tw, sg);
-    else if (R == 3)
-      stockham_stage<T, 3>(in, out, nl, n, ls, Ns, tw, sg);
+    const FftStage &st = plan.st[s];
+    if (st.R == 4)
+      stockham_stage<T, 4>(in, out, nl, n, ls, st, tws, sg);
+    else if (st.R == 2)
+      stockham_stage<T, 2>(in, out, nl, n, ls, st, tws, sg);
+    else if (st.R == 3)
+      stockham_stage<T, 3>(in, out, nl, n, ls, st, tws, sg);
     else
-      stockham_stage<T, 5>(in, out, nl, n, ls, Ns, tw, sg);
-    Ns *= R;
+      stockham_stage<T, 5>(in, out, nl, n, ls, st, tws, sg);
     __syncthreads();
     Cx<T> *t = in;
     in = out;
@@ -178,8 +229,8 @@ __device__ Cx<T> *fft_lines(Cx<T> *A, Cx<T> *B, int nl, int n, int ls, const Fft
 }
 
 template <typename T>
-__device__ __forceinline__ void load_twiddles(Cx<T> *tw_s, const T *__restrict__ tw, int n) {
-  for (int t = threadIdx.x; t < n; t += blockDim.x) tw_s[t] = {tw[2 * t], tw[2 * t + 1]};
+__device__ __forceinline__ void load_twiddles(Cx<T> *tw_s, const T *__restrict__ tw, int ntw) {
+  for (int t = threadIdx.x; t < ntw; t += blockDim.x) tw_s[t] = {tw[2 * t], tw[2 * t + 1]};
 }
 
 // ---------------------------------------------------------------- x passes
@@ -191,18 +242,18 @@ __global__ void k_fft_x_fwd(T *grid, FftPlan plan, const T *__restrict__ tw, int
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = n + 1, rowlen = n + 2;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
-  Cx<T> *A = tw_s + n;
+  Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + NL * ls;
-  load_twiddles(tw_s, tw, n);
+  load_twiddles(tw_s, tw, plan.ntw);
   const int64_t nrows = 3LL * n * n;  // (c, z, y) with c < 3
   const int64_t row0 = (int64_t)blockIdx.x * NL;
   const int64_t comp_stride = (int64_t)n * n * rowlen;
   for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
-    int l = e / n, xx = e - l * n;
-    int64_t row = row0 + l;
+    const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
+    const int64_t row = row0 + l;
     Cx<T> v = {T(0), T(0)};
     if (row < nrows) {
-      const T *pr = grid + row * rowlen;  // comp c = row / (n*n) lies in the first 3 comps
+      const T *pr = grid + row * rowlen;
       v = {pr[xx], pr[3 * comp_stride + xx]};
     }
     A[l * ls + xx] = v;
@@ -211,14 +262,14 @@ __global__ void k_fft_x_fwd(T *grid, FftPlan plan, const T *__restrict__ tw, int
   Cx<T> *Z = fft_lines<T>(A, B, NL, n, ls, plan, tw_s, T(-1));
   const int nh = n / 2 + 1;
   for (int e = threadIdx.x; e < NL * nh; e += blockDim.x) {
-    int l = e / nh, k = e - l * nh;
-    int64_t row = row0 + l;
+    const int l = (int)fdiv((uint32_t)e, plan.fnh), k = e - l * nh;
+    const int64_t row = row0 + l;
     if (row >= nrows) continue;
-    Cx<T> zk = Z[l * ls + k];
-    Cx<T> zm = Z[l * ls + (k == 0 ? 0 : n - k)];
-    Cx<T> Ak = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    const Cx<T> zk = Z[l * ls + k];
+    const Cx<T> zm = Z[l * ls + (k == 0 ? 0 : n - k)];
+    const Cx<T> Ak = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
     // (Z_k - conj Z_{n-k}) / (2i): (p + iq)/(2i) = (q - ip)/2
-    Cx<T> Bk = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
+    const Cx<T> Bk = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
     T *pr = grid + row * rowlen;
     pr[2 * k] = Ak.x;
     pr[2 * k + 1] = Ak.y;
@@ -234,26 +285,26 @@ __global__ void k_fft_x_inv(T *grid, FftPlan plan, const T *__restrict__ tw, int
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = n + 1, rowlen = n + 2;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
-  Cx<T> *A = tw_s + n;
+  Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + NL * ls;
-  load_twiddles(tw_s, tw, n);
+  load_twiddles(tw_s, tw, plan.ntw);
   const int64_t nrows = 3LL * n * n;
   const int64_t row0 = (int64_t)blockIdx.x * NL;
   const int64_t comp_stride = (int64_t)n * n * rowlen;
   for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
-    int l = e / n, k = e - l * n;
-    int64_t row = row0 + l;
+    const int l = (int)fdiv((uint32_t)e, plan.fn), k = e - l * n;
+    const int64_t row = row0 + l;
     Cx<T> v = {T(0), T(0)};
     if (row < nrows) {
       const T *pr = grid + row * rowlen;
       if (k <= n / 2) {
-        Cx<T> a = {pr[2 * k], pr[2 * k + 1]};
-        Cx<T> b = {pr[3 * comp_stride + 2 * k], pr[3 * comp_stride + 2 * k + 1]};
+        const Cx<T> a = {pr[2 * k], pr[2 * k + 1]};
+        const Cx<T> b = {pr[3 * comp_stride + 2 * k], pr[3 * comp_stride + 2 * k + 1]};
         v = {a.x - b.y, a.y + b.x};
       } else {
-        int km = n - k;
-        Cx<T> a = {pr[2 * km], -pr[2 * km + 1]};
-        Cx<T> b = {pr[3 * comp_stride + 2 * km], -pr[3 * comp_stride + 2 * km + 1]};
+        const int km = n - k;
+        const Cx<T> a = {pr[2 * km], -pr[2 * km + 1]};
+        const Cx<T> b = {pr[3 * comp_stride + 2 * km], -pr[3 * comp_stride + 2 * km + 1]};
         v = {a.x - b.y, a.y + b.x};
       }
     }
@@ -262,10 +313,10 @@ __global__ void k_fft_x_inv(T *grid, FftPlan plan, const T *__restrict__ tw, int
   __syncthreads();
   Cx<T> *Z = fft_lines<T>(A, B, NL, n, ls, plan, tw_s, T(1));
   for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
-    int l = e / n, xx = e - l * n;
-    int64_t row = row0 + l;
+    const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
+    const int64_t row = row0 + l;
     if (row >= nrows) continue;
-    Cx<T> z = Z[l * ls + xx];
+    const Cx<T> z = Z[l * ls + xx];
     T *pr = grid + row * rowlen;
     pr[xx] = z.x;
     pr[3 * comp_stride + xx] = z.y;
@@ -273,59 +324,61 @@ __global__ void k_fft_x_inv(T *grid, FftPlan plan, const T *__restrict__ tw, int
 }
 
 // ---------------------------------------------------------------- y pass
-// Lines along y for fixed (comp, z), a tile of TX consecutive kx.
+// Lines along y for fixed (comp, z), a tile of TX = 2^LTX consecutive kx.
 template <typename T>
-__global__ void k_fft_y(T *grid, FftPlan plan, const T *__restrict__ tw, int TX, T sg) {
+__global__ void k_fft_y(T *grid, FftPlan plan, const T *__restrict__ tw, int LTX, T sg) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int TX = 1 << LTX;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
-  Cx<T> *A = tw_s + n;
+  Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + TX * ls;
-  load_twiddles(tw_s, tw, n);
-  const int ntile = (nh + TX - 1) / TX;
-  const int tile = blockIdx.x % ntile;
+  load_twiddles(tw_s, tw, plan.ntw);
+  const int ntile = (nh + TX - 1) >> LTX;
   const int cz = blockIdx.x / ntile;  // comp * n + z
-  const int kx0 = tile * TX;
+  const int tile = blockIdx.x - cz * ntile;
+  const int kx0 = tile << LTX;
   Cx<T> *base = (Cx<T> *)grid + (int64_t)cz * n * nh;  // rows of nh complex
-  for (int e = threadIdx.x; e < TX * n; e += blockDim.x) {
-    int yy = e / TX, t = e - yy * TX;
-    int kx = kx0 + t;
+  for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
+    const int yy = e >> LTX, t = e & (TX - 1);
+    const int kx = kx0 + t;
     Cx<T> v = {T(0), T(0)};
     if (kx < nh) v = base[(int64_t)yy * nh + kx];
     A[t * ls + yy] = v;
   }
   __syncthreads();
   Cx<T> *Z = fft_lines<T>(A, B, TX, n, ls, plan, tw_s, sg);
-  for (int e = threadIdx.x; e < TX * n; e += blockDim.x) {
-    int yy = e / TX, t = e - yy * TX;
-    int kx = kx0 + t;
+  for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
+    const int yy = e >> LTX, t = e & (TX - 1);
+    const int kx = kx0 + t;
     if (kx < nh) base[(int64_t)yy * nh + kx] = Z[t * ls + yy];
   }
 }
 
 // ------------------------------------------------------- z pass + Green
-// Lines along z for fixed y, TX consecutive kx, all six components:
+// Lines along z for fixed y, TX = 2^LTX consecutive kx, all six components:
 // forward DFT, Green's function, inverse DFT.
 template <typename T>
 __global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
-                              const T *__restrict__ green, int TX) {
+                              const T *__restrict__ green, int LTX) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int TX = 1 << LTX;
   const int NLn = 6 * TX;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
-  Cx<T> *A = tw_s + n;
+  Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + NLn * ls;
-  load_twiddles(tw_s, tw, n);
-  const int ntile = (nh + TX - 1) / TX;
-  const int tile = blockIdx.x % ntile;
+  load_twiddles(tw_s, tw, plan.ntw);
+  const int ntile = (nh + TX - 1) >> LTX;
   const int yy = blockIdx.x / ntile;
-  const int kx0 = tile * TX;
+  const int tile = blockIdx.x - yy * ntile;
+  const int kx0 = tile << LTX;
   Cx<T> *g = (Cx<T> *)grid;
   const int64_t zstride = (int64_t)n * nh, cstride = (int64_t)n * zstride;
   for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
-    int t = e % TX, rest = e / TX;
-    int zz = rest % n, comp = rest / n;
-    int kx = kx0 + t;
+    const int t = e & (TX - 1), rest = e >> LTX;
+    const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+    const int kx = kx0 + t;
     Cx<T> v = {T(0), T(0)};
     if (kx < nh) v = g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx];
     A[(comp * TX + t) * ls + zz] = v;
@@ -334,11 +387,11 @@ __global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
   Cx<T> *Z = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(-1));
   // Green's function, one (kx, ky, kz) per thread iteration
   const int ky = yy <= n / 2 ? yy : yy - n;
-  for (int e = threadIdx.x; e < TX * n; e += blockDim.x) {
-    int t = e % TX, zz = e / TX;
-    int kx = kx0 + t;
-    int kz = zz <= n / 2 ? zz : zz - n;
-    int m = kx * kx + ky * ky + kz * kz;
+  for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
+    const int t = e & (TX - 1), zz = e >> LTX;
+    const int kx = kx0 + t;
+    const int kz = zz <= n / 2 ? zz : zz - n;
+    const int m = kx * kx + ky * ky + kz * kz;
     Cx<T> gF[3], gD[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -361,8 +414,8 @@ __global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
       }
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        Cx<T> pF = {gF[d].x - kk[d] * sF.x * im, gF[d].y - kk[d] * sF.y * im};
-        Cx<T> pD = {gD[d].x - kk[d] * sD.x * im, gD[d].y - kk[d] * sD.y * im};
+        const Cx<T> pF = {gF[d].x - kk[d] * sF.x * im, gF[d].y - kk[d] * sF.y * im};
+        const Cx<T> pD = {gD[d].x - kk[d] * sD.x * im, gD[d].y - kk[d] * sD.y * im};
         oM[d] = {t1 * pF.x + t2 * pD.x, t1 * pF.y + t2 * pD.y};
         oD[d] = {t2 * pF.x + t3 * pD.x, t2 * pF.y + t3 * pD.y};
       }
@@ -378,9 +431,9 @@ __global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
   Cx<T> *other = (Z == A) ? B : A;
   Cx<T> *R = fft_lines<T>(O, other, NLn, n, ls, plan, tw_s, T(1));
   for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
-    int t = e % TX, rest = e / TX;
-    int zz = rest % n, comp = rest / n;
-    int kx = kx0 + t;
+    const int t = e & (TX - 1), rest = e >> LTX;
+    const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+    const int kx = kx0 + t;
     if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + zz];
   }
 }
@@ -567,12 +620,9 @@ void build_wave(Ctx &c) {
   const size_t gsize = (size_t)6 * n * n * (n + 2);
   c.op64.grid.alloc(gsize);
   c.op32.grid.alloc(gsize);
-  // twiddles exp(-2 pi i t / n)
-  std::vector<double> tw(2 * n);
-  for (int t = 0; t < n; ++t) {
-    tw[2 * t] = std::cos(2.0 * kPi * t / n);
-    tw[2 * t + 1] = -std::sin(2.0 * kPi * t / n);
-  }
+  // per-stage twiddle tables of the plan
+  std::vector<double> tw;
+  make_plan(n, &tw);
   upload(c.op64.twiddle, tw);
   upload(c.op32.twiddle, tw);
   // Green table by m = kx^2 + ky^2 + kz^2
@@ -629,50 +679,67 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const T h = (T)c.h, alpha = (T)c.alpha;
   const double cn = std::pow(c.alpha / kPi, 1.5);
   const size_t gbytes = (size_t)6 * n * n * (n + 2) * sizeof(T);
+  {
+  ProfScope ps(c, PG_SPREAD);
   FSD_CUDA(cudaMemsetAsync(op.grid.p, 0, gbytes, c.stream));
   k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
                                                       alpha, (T)cn);
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
-  FftPlan plan = make_plan(n);
+  }
+  {
+  ProfScope ps(c, PG_FFT);
+  FftPlan plan = make_plan(n, nullptr);
   const int nh = n / 2 + 1;
   const int threads = 256;
+  const int ntw = plan.ntw;
   // x forward
   {
     const int NL = 8;
-    size_t sm = (size_t)(n + 2 * NL * (n + 1)) * sizeof(Cx<T>);
+    size_t sm = (size_t)(ntw + 2 * NL * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_fwd<T>, sm);
     int blocks = ceil_div(3LL * n * n, NL);
     k_fft_x_fwd<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p, NL);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
-  const int TXy = sizeof(T) == 8 ? 8 : 16;
-  const size_t smy = (size_t)(n + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
+  const int LTXy = sizeof(T) == 8 ? 3 : 4;
+  const int TXy = 1 << LTXy;
+  const size_t smy = (size_t)(ntw + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
   set_smem<T>((const void *)k_fft_y<T>, smy);
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
-  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, TXy, T(-1));
+  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, LTXy, T(-1));
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   {
-    const int TX = sizeof(T) == 8 ? 4 : 8;
-    size_t sm = (size_t)(n + 2 * 6 * TX * (n + 1)) * sizeof(Cx<T>);
+    const int LTX = sizeof(T) == 8 ? 2 : 3;
+    const int TX = 1 << LTX;
+    size_t sm = (size_t)(ntw + 2 * 6 * TX * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_z_green<T>, sm);
     int blocks = n * ceil_div(nh, TX);
     k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p,
-                                                        op.green.p, TX);
+                                                        op.green.p, LTX);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
-  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, TXy, T(1));
+  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, LTXy, T(1));
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   {
     const int NL = 8;
-    size_t sm = (size_t)(n + 2 * NL * (n + 1)) * sizeof(Cx<T>);
+    size_t sm = (size_t)(ntw + 2 * NL * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_inv<T>, sm);
     int blocks = ceil_div(3LL * n * n, NL);
     k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p, NL);
+    FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
+  }
+  ProfScope ps(c, PG_INTERP);
   const double h3 = c.h * c.h * c.h;
   k_interp<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.grid.p, y, n, P, h,
                                                       alpha, (T)(cn * h3));
+  FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 

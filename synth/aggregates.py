@@ -225,41 +225,20 @@ def _overlap_mask(P, body, L, contact, nbody):
 def _close_pairs(P, body, L, contact):
     """Inter-body bead pairs (i < j) closer than `contact` (minimum image):
     returns i, j, d = P[j] - P[i] (minimum image)."""
-    n = max(1, int(L // contact))
-    cs = L / n
-    c = np.floor((P % L) / cs).astype(np.int64) % n
-    cid = (c[:, 0] * n + c[:, 1]) * n + c[:, 2]
-    order = np.argsort(cid, kind="stable")
-    cnt = np.bincount(cid, minlength=n ** 3)
-    m = int(cnt.max())
-    table = -np.ones((n ** 3, m), dtype=np.int64)
-    start = np.concatenate([[0], np.cumsum(cnt)[:-1]])
-    sc = cid[order]
-    table[sc, np.arange(len(order)) - start[sc]] = order
-    I, J, D = [], [], []
-    offs = (-1, 0, 1) if n >= 3 else tuple(range(n))
-    seen = set()
-    for dx in offs:
-        for dy in offs:
-            for dz in offs:
-                key = (dx % n, dy % n, dz % n)
-                if key in seen:
-                    continue
-                seen.add(key)
-                nc = (((c[:, 0] + dx) % n) * n + (c[:, 1] + dy) % n) * n + (c[:, 2] + dz) % n
-                Jt = table[nc]
-                valid = Jt >= 0
-                Jc = np.where(valid, Jt, 0)
-                d = P[Jc] - P[:, None, :]
-                d -= L * np.round(d / L)
-                r2 = np.einsum("nmk,nmk->nm", d, d)
-                hit = valid & (r2 < contact * contact) & (body[Jc] != body[:, None])
-                hit &= Jc > np.arange(len(P))[:, None]
-                ii, kk = np.nonzero(hit)
-                I.append(ii)
-                J.append(Jc[ii, kk])
-                D.append(d[ii, kk])
-    return np.concatenate(I), np.concatenate(J), np.concatenate(D)
+    from scipy.spatial import cKDTree
+
+    W = np.mod(P, L)
+    W[W >= L] = 0.0
+    pr = cKDTree(W, boxsize=L).query_pairs(contact, output_type="ndarray")
+    if len(pr) == 0:
+        z = np.zeros(0, dtype=np.int64)
+        return z, z, np.zeros((0, 3))
+    i, j = pr[:, 0], pr[:, 1]
+    keep = body[i] != body[j]
+    i, j = i[keep], j[keep]
+    d = P[j] - P[i]
+    d -= L * np.round(d / L)
+    return i, j, d
 
 
 def compress_suspension(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12,

@@ -210,6 +210,20 @@ def test_step_moves_rigid_bodies(sysA, pkg):
         assert np.abs(d1 - d0).max() < 1e-12
 
 
+def test_comoving_step_drops_affine_advection(sysA, pkg):
+    pos, body, L = sysA["pos"], sysA["body"], sysA["L"]
+    s = pkg.Suspension(pos, body, L, flags=pkg.FSD_FLAG_COMOVING, **HI)
+    vel = np.zeros((body.max() + 1, 6))
+    s.step(None, 1.0, 0.01, vel=vel)
+    x1, q1 = s.beads()
+    s.close()
+    _, X0, r0 = O.body_geometry(pos, body, L)
+    Xo, qo, xo = O.integrate(X0, np.tile([1.0, 0, 0, 0], (len(X0), 1)), r0, body, vel, 0.01,
+                             comoving_gamma=1.0)
+    assert np.allclose(x1, xo, atol=1e-12)
+    assert np.allclose(q1, qo, atol=1e-14)
+
+
 def test_no_convergence_reports_status(sysA, pkg):
     pos, body, L = sysA["pos"], sysA["body"], sysA["L"]
     s = pkg.Suspension(pos, body, L, max_iter=2, restart=2, **{k: v for k, v in HI.items()})
