@@ -18,6 +18,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int LDB = 12;     // doubles per bead in a solution vector (11 + zero pad)
 constexpr int NFUNC = 7;    // radial functions of the real-space table
 constexpr int TCOEF = 10;   // polynomial coefficients per function per interval
+constexpr int TSTRIDE = TCOEF * 8 + 4;  // table values per interval (padded: bank spread)
 constexpr int BLK = 36;     // 6x6 block
 
 // ------------------------------------------------------------------ errors
@@ -64,7 +65,9 @@ template <typename T>
 struct OpData {
   DBuf<T> table;      // real-space radial table [nint][NFUNC][TCOEF]
   T self_real[3];     // real-space self mobilities (translation, rotation, strain)
-  DBuf<T> grid;       // 6 * n * n * (n + 2) (padded rows; in-place r2c)
+  DBuf<T> grid;       // spread densities, planar: [6][n^3]
+  DBuf<T> spec;       // half spectra, planar: [6][n][n][n/2 + 1] complex
+  DBuf<T> gout;       // velocity fields for interpolation, interleaved: [n^3][8] (6 used)
   DBuf<T> green;      // [m = kx^2+ky^2+kz^2][3]: (A fM^2, A fM fD, A fD^2)
   DBuf<T> twiddle;    // [n] complex: exp(-2 pi i t / n)
   DBuf<T> bval;       // lubrication BSR off-diagonal blocks [nnz][36]

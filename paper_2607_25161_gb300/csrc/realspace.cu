@@ -122,7 +122,7 @@ void build_real_table(Ctx &c) {
   c.tab_h = ht;
   c.tab_nint = nint;
   WaveQuad q = make_quad(c.xi, c.a, c.eta, 400);
-  std::vector<double> tab((size_t)nint * TCOEF * 8, 0.0);
+  std::vector<double> tab((size_t)nint * TSTRIDE, 0.0);
   const int NC = TCOEF;
   double tk[NC];
   for (int k = 0; k < NC; ++k) tk[k] = std::cos(kPi * (k + 0.5) / NC);
@@ -148,7 +148,7 @@ void build_real_table(Ctx &c) {
       for (int p = 0; p < NC; ++p) {
         double s = 0.0;
         for (int j = 0; j < NC; ++j) s += cc[j] * cheb[j][p];
-        tab[((size_t)iv * NC + p) * 8 + f] = s;
+        tab[(size_t)iv * TSTRIDE + (size_t)p * 8 + f] = s;
       }
     }
   }
@@ -492,7 +492,7 @@ __device__ __forceinline__ void wave_table<float>(const float *tab, int nint, fl
   int iv = (int)s;
   iv = iv < 0 ? 0 : (iv >= nint ? nint - 1 : iv);
   const float t = 2.f * (s - (float)iv) - 1.f;
-  const float4 *c = (const float4 *)(tab + (size_t)iv * TCOEF * 8);
+  const float4 *c = (const float4 *)(tab + (size_t)iv * TSTRIDE);
   float4 lo = c[2 * (TCOEF - 1)], hi = c[2 * (TCOEF - 1) + 1];
   float v0 = lo.x, v1 = lo.y, v2 = lo.z, v3 = lo.w, v4 = hi.x, v5 = hi.y, v6 = hi.z;
 #pragma unroll
@@ -511,7 +511,7 @@ __device__ __forceinline__ void wave_table<double>(const double *tab, int nint, 
   int iv = (int)s;
   iv = iv < 0 ? 0 : (iv >= nint ? nint - 1 : iv);
   const double t = 2.0 * (s - (double)iv) - 1.0;
-  const double2 *c = (const double2 *)(tab + (size_t)iv * TCOEF * 8);
+  const double2 *c = (const double2 *)(tab + (size_t)iv * TSTRIDE);
   double v[8];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -613,7 +613,7 @@ __device__ __forceinline__ void load_packed<double>(const double *__restrict__ p
 // shuffles and its first lane writes the bead row:
 //   y_i = sum_j M_r(x_i - x_j) x_j + M_self,r x_i [+ (dU + dOm x r_i, dOm, 0)]
 template <typename T, int G>
-__global__ void __launch_bounds__(256) k_realspace(
+__global__ void __launch_bounds__(256, 3) k_realspace(
     int Nt, const T *__restrict__ packed, const int *__restrict__ nbr,
     const int *__restrict__ ncnt, int cap, const double *__restrict__ x, double *__restrict__ y,
     const T *__restrict__ tab_g, int nint, T inv_h, T L, T a, T c8, T self_t, T self_r,
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(256) k_realspace(
   extern __shared__ __align__(16) unsigned char tab_raw[];
   T *tab = (T *)tab_raw;
   {
-    const int nv = nint * TCOEF * 8 * (int)sizeof(T) / 16;
+    const int nv = nint * TSTRIDE * (int)sizeof(T) / 16;
     const uint4 *src = (const uint4 *)tab_g;
     uint4 *dst = (uint4 *)tab_raw;
     for (int q = threadIdx.x; q < nv; q += blockDim.x) dst[q] = src[q];
@@ -750,15 +750,24 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, b
   FSD_LAUNCHED(c);
   const double avg = (double)c.n_pairs / std::max(1, c.Nt);
   int G = avg > 96 ? 32 : (avg > 40 ? 16 : (avg > 16 ? 8 : 4));
-  const size_t smem = (size_t)c.tab_nint * TCOEF * 8 * sizeof(T);
+  const size_t smem = (size_t)c.tab_nint * TSTRIDE * sizeof(T);
+  if (smem > 200 * 1024) throw Invalid{"real-space table too large (reduce rc or raise xi)"};
   int per_sm = 0;
   const T inv_h = (T)(1.0 / c.tab_h);
   const T c8 = (T)(1.0 / (8.0 * kPi * c.eta));
 #define FSD_RS_LAUNCH(GG)                                                                    \
-  FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>,                                          \
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
-  FSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_realspace<T, GG>, threads, \
-                                                         smem));                             \
+  {                                                                                          \
+    static size_t set_bytes = 0;                                                             \
+    static int occ = 0;                                                                      \
+    if (set_bytes != smem) {                                                                 \
+      FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>,                                      \
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+      FSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_realspace<T, GG>,       \
+                                                             threads, smem));                \
+      set_bytes = smem;                                                                      \
+    }                                                                                        \
+    per_sm = occ;                                                                            \
+  }                                                                                          \
   k_realspace<T, GG><<<std::min<int64_t>(ceil_div((int64_t)c.Nt * GG, threads),               \
                                          (int64_t)std::max(1, per_sm) * c.num_sms),         \
                        threads, smem, c.stream>>>(                                           \

@@ -4,8 +4,12 @@
 // function scaling fused into the z pass, and interpolation of the velocity
 // and velocity gradient.
 //
-// Grids: six real fields on an n^3 grid, rows padded to n + 2 reals so that
-// the forward x pass writes its n/2 + 1 complex values in place:
+// Grids: the spread densities are six planar real fields [6][n^3] (warp-wide
+// atomics on consecutive points merge into few L2 sector operations); the
+// forward x pass turns them into planar half spectra [6][n][n][n/2 + 1]
+// (complex) for the y / z passes; the inverse x pass writes the velocity
+// fields interleaved per point ([n^3][8], six used) so that interpolation
+// reads a point with two 16-byte loads:
 //   comps 0..2  monopole density g_F = sum_j F_j W(x - x_j)
 //   comps 3..5  dipole density   g_D = sum_j 2 alpha W(x - x_j) D_j (x - x_j),
 //                D = S + A, A y = (1/2) L x y
@@ -234,99 +238,158 @@ __device__ __forceinline__ void load_twiddles(Cx<T> *tw_s, const T *__restrict__
 }
 
 // ---------------------------------------------------------------- x passes
-// Forward: rows (c, z, y), c < 3; z = g_c + i g_{c+3}; after the DFT the two
-// half spectra are A_k = (Z_k + conj Z_{n-k})/2 and B_k = (Z_k - conj Z_{n-k})/(2i),
-// written in place into rows c and c + 3.
+// Forward: for each row (z, y) and pair p < 3, z = g_p + i g_{p+3}; after the
+// DFT the two half spectra are A_k = (Z_k + conj Z_{n-k})/2 and
+// B_k = (Z_k - conj Z_{n-k})/(2i), written to spec[p] and spec[p + 3].
 template <typename T>
-__global__ void k_fft_x_fwd(T *grid, FftPlan plan, const T *__restrict__ tw, int NL) {
+__device__ __forceinline__ void load6(const T *q, T *v);
+template <>
+__device__ __forceinline__ void load6<float>(const float *q, float *v) {
+  const float4 a = *(const float4 *)q;
+  const float2 b = *(const float2 *)(q + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+template <>
+__device__ __forceinline__ void load6<double>(const double *q, double *v) {
+  const double2 a = *(const double2 *)q, b = *(const double2 *)(q + 2),
+                c = *(const double2 *)(q + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+template <typename T>
+__device__ __forceinline__ void store6(T *q, const T *v);
+template <>
+__device__ __forceinline__ void store6<float>(float *q, const float *v) {
+  *(float4 *)q = make_float4(v[0], v[1], v[2], v[3]);
+  *(float2 *)(q + 4) = make_float2(v[4], v[5]);
+}
+template <>
+__device__ __forceinline__ void store6<double>(double *q, const double *v) {
+  *(double2 *)q = make_double2(v[0], v[1]);
+  *(double2 *)(q + 2) = make_double2(v[2], v[3]);
+  *(double2 *)(q + 4) = make_double2(v[4], v[5]);
+}
+
+template <typename T>
+__global__ void k_fft_x_fwd(const T *__restrict__ grid, Cx<T> *spec, FftPlan plan,
+                            const T *__restrict__ tw, int NL) {
+  // grid: planar [6][n^3]
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, rowlen = n + 2;
+  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int NLL = 3 * NL;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
-  Cx<T> *B = A + NL * ls;
+  Cx<T> *B = A + NLL * ls;
   load_twiddles(tw_s, tw, plan.ntw);
-  const int64_t nrows = 3LL * n * n;  // (c, z, y) with c < 3
+  const int64_t nrows = (int64_t)n * n;  // rows (z, y)
   const int64_t row0 = (int64_t)blockIdx.x * NL;
-  const int64_t comp_stride = (int64_t)n * n * rowlen;
-  for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
-    const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
-    const int64_t row = row0 + l;
-    Cx<T> v = {T(0), T(0)};
-    if (row < nrows) {
-      const T *pr = grid + row * rowlen;
-      v = {pr[xx], pr[3 * comp_stride + xx]};
+  {
+    const int64_t n3 = nrows * n;
+    const int total = NL * n;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 2 * blockDim.x) {
+      T v[2][6];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
+        const int64_t row = row0 + l;
+        const bool ok = e < total && row < nrows;
+        const int64_t o = row * n + xx;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[u][c] = ok ? grid[c * n3 + o] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= total) continue;
+        const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) A[(l * 3 + p) * ls + xx] = {v[u][p], v[u][p + 3]};
+      }
     }
-    A[l * ls + xx] = v;
   }
   __syncthreads();
-  Cx<T> *Z = fft_lines<T>(A, B, NL, n, ls, plan, tw_s, T(-1));
-  const int nh = n / 2 + 1;
-  for (int e = threadIdx.x; e < NL * nh; e += blockDim.x) {
-    const int l = (int)fdiv((uint32_t)e, plan.fnh), k = e - l * nh;
+  Cx<T> *Z = fft_lines<T>(A, B, NLL, n, ls, plan, tw_s, T(-1));
+  const int64_t cs = nrows * nh;
+  for (int e = threadIdx.x; e < NLL * nh; e += blockDim.x) {
+    const int lp = (int)fdiv((uint32_t)e, plan.fnh), k = e - lp * nh;
+    const int l = lp / 3, p = lp - 3 * l;
     const int64_t row = row0 + l;
     if (row >= nrows) continue;
-    const Cx<T> zk = Z[l * ls + k];
-    const Cx<T> zm = Z[l * ls + (k == 0 ? 0 : n - k)];
-    const Cx<T> Ak = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    const Cx<T> zk = Z[lp * ls + k];
+    const Cx<T> zm = Z[lp * ls + (k == 0 ? 0 : n - k)];
     // (Z_k - conj Z_{n-k}) / (2i): (p + iq)/(2i) = (q - ip)/2
-    const Cx<T> Bk = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
-    T *pr = grid + row * rowlen;
-    pr[2 * k] = Ak.x;
-    pr[2 * k + 1] = Ak.y;
-    pr[3 * comp_stride + 2 * k] = Bk.x;
-    pr[3 * comp_stride + 2 * k + 1] = Bk.y;
+    spec[p * cs + row * nh + k] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    spec[(p + 3) * cs + row * nh + k] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
   }
 }
 
 // Inverse: Z_k = A_k + i B_k (k <= n/2), conj(A_{n-k}) + i conj(B_{n-k})
-// beyond; the inverse DFT gives a + i b with a, b real.
+// beyond; the inverse DFT gives a + i b, stored as comps p and p + 3.
 template <typename T>
-__global__ void k_fft_x_inv(T *grid, FftPlan plan, const T *__restrict__ tw, int NL) {
+__global__ void k_fft_x_inv(T *grid, const Cx<T> *__restrict__ spec, FftPlan plan,
+                            const T *__restrict__ tw, int NL) {
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, rowlen = n + 2;
+  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int NLL = 3 * NL;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
-  Cx<T> *B = A + NL * ls;
+  Cx<T> *B = A + NLL * ls;
   load_twiddles(tw_s, tw, plan.ntw);
-  const int64_t nrows = 3LL * n * n;
+  const int64_t nrows = (int64_t)n * n;
   const int64_t row0 = (int64_t)blockIdx.x * NL;
-  const int64_t comp_stride = (int64_t)n * n * rowlen;
-  for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
-    const int l = (int)fdiv((uint32_t)e, plan.fn), k = e - l * n;
-    const int64_t row = row0 + l;
-    Cx<T> v = {T(0), T(0)};
-    if (row < nrows) {
-      const T *pr = grid + row * rowlen;
-      if (k <= n / 2) {
-        const Cx<T> a = {pr[2 * k], pr[2 * k + 1]};
-        const Cx<T> b = {pr[3 * comp_stride + 2 * k], pr[3 * comp_stride + 2 * k + 1]};
-        v = {a.x - b.y, a.y + b.x};
-      } else {
-        const int km = n - k;
-        const Cx<T> a = {pr[2 * km], -pr[2 * km + 1]};
-        const Cx<T> b = {pr[3 * comp_stride + 2 * km], -pr[3 * comp_stride + 2 * km + 1]};
-        v = {a.x - b.y, a.y + b.x};
+  const int64_t cs = nrows * nh;
+  {
+    constexpr int U = 4;
+    const int total = NLL * n;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+      Cx<T> a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int lp = (int)fdiv((uint32_t)e, plan.fn), k = e - lp * n;
+        const int l = lp / 3, p = lp - 3 * l;
+        const int64_t row = row0 + l;
+        const int kk = k <= n / 2 ? k : n - k;
+        if (e < total && row < nrows) {
+          a[u] = spec[p * cs + row * nh + kk];
+          b[u] = spec[(p + 3) * cs + row * nh + kk];
+        } else {
+          a[u] = {T(0), T(0)};
+          b[u] = {T(0), T(0)};
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= total) continue;
+        const int lp = (int)fdiv((uint32_t)e, plan.fn), k = e - lp * n;
+        // k <= n/2: a + i b;  beyond: conj(a) + i conj(b) of the mirrored bin
+        A[lp * ls + k] = k <= n / 2 ? Cx<T>{a[u].x - b[u].y, a[u].y + b[u].x}
+                                    : Cx<T>{a[u].x + b[u].y, -a[u].y + b[u].x};
       }
     }
-    A[l * ls + k] = v;
   }
   __syncthreads();
-  Cx<T> *Z = fft_lines<T>(A, B, NL, n, ls, plan, tw_s, T(1));
+  Cx<T> *Z = fft_lines<T>(A, B, NLL, n, ls, plan, tw_s, T(1));
   for (int e = threadIdx.x; e < NL * n; e += blockDim.x) {
     const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
     const int64_t row = row0 + l;
     if (row >= nrows) continue;
-    const Cx<T> z = Z[l * ls + xx];
-    T *pr = grid + row * rowlen;
-    pr[xx] = z.x;
-    pr[3 * comp_stride + xx] = z.y;
+    T v[6];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const Cx<T> z = Z[(l * 3 + p) * ls + xx];
+      v[p] = z.x;
+      v[p + 3] = z.y;
+    }
+    store6<T>(grid + (row * n + xx) * 8, v);
   }
 }
 
 // ---------------------------------------------------------------- y pass
 // Lines along y for fixed (comp, z), a tile of TX = 2^LTX consecutive kx.
 template <typename T>
-__global__ void k_fft_y(T *grid, FftPlan plan, const T *__restrict__ tw, int LTX, T sg) {
+__global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int LTX, T sg) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
   const int TX = 1 << LTX;
@@ -338,13 +401,25 @@ __global__ void k_fft_y(T *grid, FftPlan plan, const T *__restrict__ tw, int LTX
   const int cz = blockIdx.x / ntile;  // comp * n + z
   const int tile = blockIdx.x - cz * ntile;
   const int kx0 = tile << LTX;
-  Cx<T> *base = (Cx<T> *)grid + (int64_t)cz * n * nh;  // rows of nh complex
-  for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
-    const int yy = e >> LTX, t = e & (TX - 1);
-    const int kx = kx0 + t;
-    Cx<T> v = {T(0), T(0)};
-    if (kx < nh) v = base[(int64_t)yy * nh + kx];
-    A[t * ls + yy] = v;
+  Cx<T> *base = spec + (int64_t)cz * n * nh;  // rows of nh complex
+  {
+    constexpr int U = 8;
+    const int total = n << LTX;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+      Cx<T> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int yy = e >> LTX, t = e & (TX - 1);
+        const int kx = kx0 + t;
+        v[u] = (e < total && kx < nh) ? base[(int64_t)yy * nh + kx] : Cx<T>{T(0), T(0)};
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) A[(e & (TX - 1)) * ls + (e >> LTX)] = v[u];
+      }
+    }
   }
   __syncthreads();
   Cx<T> *Z = fft_lines<T>(A, B, TX, n, ls, plan, tw_s, sg);
@@ -359,7 +434,7 @@ __global__ void k_fft_y(T *grid, FftPlan plan, const T *__restrict__ tw, int LTX
 // Lines along z for fixed y, TX = 2^LTX consecutive kx, all six components:
 // forward DFT, Green's function, inverse DFT.
 template <typename T>
-__global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
+__global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
                               const T *__restrict__ green, int LTX) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
@@ -373,15 +448,31 @@ __global__ void k_fft_z_green(T *grid, FftPlan plan, const T *__restrict__ tw,
   const int yy = blockIdx.x / ntile;
   const int tile = blockIdx.x - yy * ntile;
   const int kx0 = tile << LTX;
-  Cx<T> *g = (Cx<T> *)grid;
+  Cx<T> *g = spec;
   const int64_t zstride = (int64_t)n * nh, cstride = (int64_t)n * zstride;
-  for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
-    const int t = e & (TX - 1), rest = e >> LTX;
-    const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
-    const int kx = kx0 + t;
-    Cx<T> v = {T(0), T(0)};
-    if (kx < nh) v = g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx];
-    A[(comp * TX + t) * ls + zz] = v;
+  {
+    constexpr int U = 8;
+    const int total = NLn * n;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+      Cx<T> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int t = e & (TX - 1), rest = e >> LTX;
+        const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+        const int kx = kx0 + t;
+        v[u] = (e < total && kx < nh) ? g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx]
+                                      : Cx<T>{T(0), T(0)};
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= total) continue;
+        const int t = e & (TX - 1), rest = e >> LTX;
+        const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+        A[(comp * TX + t) * ls + zz] = v[u];
+      }
+    }
   }
   __syncthreads();
   Cx<T> *Z = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(-1));
@@ -500,22 +591,21 @@ __global__ void __launch_bounds__(256) k_spread(int Nt, const typename V4Of<T>::
   const T D00 = Sxx, D01 = Sxy - T(0.5) * L2, D02 = Sxz + T(0.5) * L1;
   const T D10 = Sxy + T(0.5) * L2, D11 = Syy, D12 = Syz - T(0.5) * L0;
   const T D20 = Sxz - T(0.5) * L1, D21 = Syz + T(0.5) * L0, D22 = Szz;
-  const int rowlen = n + 2;
-  const int64_t cs = (int64_t)n * n * rowlen;
   const int P3 = P * P * P;
   const T ta = T(2) * alpha;
   for (int t = lane; t < P3; t += 32) {
-    int ix = t % P, iy = (t / P) % P, iz = t / (P * P);
-    T W = cnorm * sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
-    T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
-    T Wd = ta * W;
-    int64_t off = ((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * rowlen + si[warp][0][ix];
-    atomicAdd(grid + off, W * F0);
-    atomicAdd(grid + cs + off, W * F1);
-    atomicAdd(grid + 2 * cs + off, W * F2);
-    atomicAdd(grid + 3 * cs + off, Wd * (D00 * y0 + D01 * y1 + D02 * y2));
-    atomicAdd(grid + 4 * cs + off, Wd * (D10 * y0 + D11 * y1 + D12 * y2));
-    atomicAdd(grid + 5 * cs + off, Wd * (D20 * y0 + D21 * y1 + D22 * y2));
+    const int ix = t % P, iy = (t / P) % P, iz = t / (P * P);
+    const T W = cnorm * sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
+    const T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
+    const T Wd = ta * W;
+    T *q = grid + (((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * n + si[warp][0][ix]);
+    const int64_t n3 = (int64_t)n * n * n;
+    atomicAdd(q, W * F0);
+    atomicAdd(q + n3, W * F1);
+    atomicAdd(q + 2 * n3, W * F2);
+    atomicAdd(q + 3 * n3, Wd * (D00 * y0 + D01 * y1 + D02 * y2));
+    atomicAdd(q + 4 * n3, Wd * (D10 * y0 + D11 * y1 + D12 * y2));
+    atomicAdd(q + 5 * n3, Wd * (D20 * y0 + D21 * y1 + D22 * y2));
   }
 }
 
@@ -542,20 +632,18 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
     si[warp][d][k] = ((g % n) + n) % n;
   }
   __syncwarp();
-  const int rowlen = n + 2;
-  const int64_t cs = (int64_t)n * n * rowlen;
   const int P3 = P * P * P;
   const T ta = T(2) * alpha;
   T acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = T(0);
   for (int t = lane; t < P3; t += 32) {
-    int ix = t % P, iy = (t / P) % P, iz = t / (P * P);
-    T W = sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
-    T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
-    int64_t off = ((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * rowlen + si[warp][0][ix];
-    T u0 = grid[off], u1 = grid[cs + off], u2 = grid[2 * cs + off];
-    T d0 = grid[3 * cs + off], d1 = grid[4 * cs + off], d2 = grid[5 * cs + off];
+    const int ix = t % P, iy = (t / P) % P, iz = t / (P * P);
+    const T W = sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
+    const T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
+    T g6[6];
+    load6<T>(grid + ((((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * n + si[warp][0][ix]) << 3), g6);
+    const T u0 = g6[0], u1 = g6[1], u2 = g6[2], d0 = g6[3], d1 = g6[4], d2 = g6[5];
     acc[0] += W * u0;
     acc[1] += W * u1;
     acc[2] += W * u2;
@@ -617,9 +705,15 @@ static void upload(DBuf<T> &buf, const std::vector<double> &v) {
 
 void build_wave(Ctx &c) {
   const int n = c.n;
-  const size_t gsize = (size_t)6 * n * n * (n + 2);
+  const size_t gsize = (size_t)6 * n * n * n;
+  const size_t osize = (size_t)8 * n * n * n;
+  const size_t ssize = (size_t)6 * n * n * (n + 2);
   c.op64.grid.alloc(gsize);
   c.op32.grid.alloc(gsize);
+  c.op64.gout.alloc(osize);
+  c.op32.gout.alloc(osize);
+  c.op64.spec.alloc(ssize);
+  c.op32.spec.alloc(ssize);
   // per-stage twiddle tables of the plan
   std::vector<double> tw;
   make_plan(n, &tw);
@@ -665,11 +759,14 @@ const float4 *posp<float>(Ctx &c) {
   return (const float4 *)c.op32.pos.p;
 }
 
+// Raise a kernel's dynamic shared-memory limit once per (kernel, size).
 template <typename T>
 static void set_smem(const void *fn, size_t bytes) {
-  static bool done[8] = {};
-  (void)done;
+  static std::vector<std::pair<const void *, size_t>> done;
+  for (auto &d : done)
+    if (d.first == fn && d.second >= bytes) return;
   FSD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done.push_back({fn, bytes});
 }
 
 template <typename T>
@@ -678,7 +775,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const int n = c.n, P = c.P;
   const T h = (T)c.h, alpha = (T)c.alpha;
   const double cn = std::pow(c.alpha / kPi, 1.5);
-  const size_t gbytes = (size_t)6 * n * n * (n + 2) * sizeof(T);
+  const size_t gbytes = (size_t)6 * n * n * n * sizeof(T);
   {
   ProfScope ps(c, PG_SPREAD);
   FSD_CUDA(cudaMemsetAsync(op.grid.p, 0, gbytes, c.stream));
@@ -693,13 +790,14 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const int nh = n / 2 + 1;
   const int threads = 256;
   const int ntw = plan.ntw;
+  Cx<T> *spec = (Cx<T> *)op.spec.p;
   // x forward
   {
-    const int NL = 8;
-    size_t sm = (size_t)(ntw + 2 * NL * (n + 1)) * sizeof(Cx<T>);
+    const int NL = 4;
+    size_t sm = (size_t)(ntw + 2 * 3 * NL * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_fwd<T>, sm);
-    int blocks = ceil_div(3LL * n * n, NL);
-    k_fft_x_fwd<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p, NL);
+    int blocks = ceil_div((int64_t)n * n, NL);
+    k_fft_x_fwd<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p, NL);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
@@ -708,36 +806,36 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const size_t smy = (size_t)(ntw + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
   set_smem<T>((const void *)k_fft_y<T>, smy);
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
-  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, LTXy, T(-1));
+  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(-1));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   {
-    const int LTX = sizeof(T) == 8 ? 2 : 3;
+    const int LTX = 2;  // four kx columns: 6 x 4 lines keep 4 CTAs per SM (FP32)
     const int TX = 1 << LTX;
     size_t sm = (size_t)(ntw + 2 * 6 * TX * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_z_green<T>, sm);
     int blocks = n * ceil_div(nh, TX);
-    k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p,
-                                                        op.green.p, LTX);
+    k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p, op.green.p,
+                                                        LTX);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
-  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(op.grid.p, plan, op.twiddle.p, LTXy, T(1));
+  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   {
-    const int NL = 8;
-    size_t sm = (size_t)(ntw + 2 * NL * (n + 1)) * sizeof(Cx<T>);
+    const int NL = 4;
+    size_t sm = (size_t)(ntw + 2 * 3 * NL * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_inv<T>, sm);
-    int blocks = ceil_div(3LL * n * n, NL);
-    k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, plan, op.twiddle.p, NL);
+    int blocks = ceil_div((int64_t)n * n, NL);
+    k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p, NL);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
   }
   ProfScope ps(c, PG_INTERP);
   const double h3 = c.h * c.h * c.h;
-  k_interp<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.grid.p, y, n, P, h,
+  k_interp<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P, h,
                                                       alpha, (T)(cn * h3));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
