@@ -193,6 +193,31 @@ fsd_status fsd_profile_read(fsd_ctx *ctx, double *ms, int64_t *count, int n);
 /* Name of group g (NULL when out of range). */
 const char *fsd_profile_group_name(int g);
 
+/* Wave-space mobility without any allocation (the paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * e.g. code inside a captured CUDA graph, under a memory pool it does not
+ * own, or in a loop where an allocation and its implicit synchronisation are
+ * not allowed).  Computes out = M_wave . in with the FP32 wave-space operator
+ * of fsd_apply_mobility (part 2, precision FSD_MIXED): Gaussian spreading,
+ * FFT with the Green's function, interpolation.  No context: the parameters
+ * are given directly (m_shape <= 0 selects 0.976 sqrt(pi P)).
+ *   bead_pos [n_beads][3], in [n_beads][11], out [n_beads][11]: DEVICE memory
+ *   owned by the caller, layouts as for fsd_apply_mobility.
+ *   Limits: n_beads <= 4096, grid <= 48 (even, 2,3,5-smooth), P even in
+ *   4..24 and <= grid; larger requests return FSD_EINVAL before any GPU work.
+ * Every intermediate lives in one 10 MiB file-scope device array that each
+ * device loading the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress):
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose GPU work overlaps race on it, so order them on one
+ * stream (or with events).  Each call rewrites or zeroes everything it
+ * reads.  Work is enqueued on cuda_stream (NULL: the default stream); out is
+ * ready when that stream is. */
+fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead_pos,
+                                  const double *in, double *out, double box,
+                                  double xi, int grid, int P, double m_shape,
+                                  double a, double eta, void *cuda_stream);
+
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);
 

@@ -25,7 +25,7 @@ EXPORTS = (
     "fsd_default_params", "fsd_setup", "fsd_solve", "fsd_step", "fsd_get_beads",
     "fsd_apply_mobility", "fsd_apply_saddle", "fsd_apply_precond", "fsd_apply_lubrication",
     "fsd_rhs", "fsd_get_params", "fsd_profile_enable", "fsd_profile_read",
-    "fsd_profile_group_name", "fsd_last_error", "fsd_destroy",
+    "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
 )
 PROF_GROUPS = 10
 
@@ -88,6 +88,7 @@ def load(path=LIB_PATH):
     lib.fsd_profile_read.argtypes = [P, P, P, I]
     lib.fsd_profile_group_name.argtypes = [I]
     lib.fsd_profile_group_name.restype = ctypes.c_char_p
+    lib.fsd_apply_wave_noalloc.argtypes = [ctypes.c_int64, P, P, P, D, D, I, I, D, D, D, P]
     lib.fsd_last_error.argtypes = [P]
     lib.fsd_last_error.restype = ctypes.c_char_p
     lib.fsd_destroy.argtypes = [P]

@@ -21,6 +21,7 @@
 #include "fsd_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace fsd {
 
@@ -845,3 +846,235 @@ template void launch_wavespace<float>(Ctx &, const double *, double *);
 template void launch_wavespace<double>(Ctx &, const double *, double *);
 
 }  // namespace fsd
+
+// ==================================================================
+// Wave-space mobility without any allocation.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// captured CUDA graph or a stream-ordered region that forbids cudaMalloc,
+// applications whose device memory is owned by a pool they do not control,
+// or real-time loops where an allocation (and the implicit synchronisation
+// it can cause) is not allowed.  For them fsd_apply_wave_noalloc applies the
+// FP32 wave-space operator with every intermediate (density grids, half
+// spectra, velocity grid, Green's table, twiddles, staged bead data) placed
+// in one file-scope device array of fixed size.  The array exists on every
+// device that loads this library and stays there until the process exits.
+// All calls share it: two calls whose GPU work overlaps race on it, so a
+// caller must order them (one stream, or events).  Each call rewrites the
+// parts it reads before reading them and zeroes the density grids and the
+// staged output before accumulating into them.
+namespace fsd {
+namespace {
+
+constexpr int kNaMaxGrid = 48;     // largest FFT grid per side
+constexpr int kNaMaxBeads = 4096;  // largest bead count
+constexpr size_t kNaBytes = 10u << 20;
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+struct NaLayout {
+  size_t grid, spec, gout, green, tw, pos, x, y, end;
+};
+
+size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
+
+NaLayout na_layout(int n, int nb) {
+  NaLayout l{};
+  size_t o = 0;
+  l.grid = o;
+  o += na_round((size_t)6 * n * n * n * sizeof(float));
+  l.spec = o;
+  o += na_round((size_t)6 * n * n * (n / 2 + 1) * 2 * sizeof(float));
+  l.gout = o;
+  o += na_round((size_t)8 * n * n * n * sizeof(float));
+  l.green = o;
+  o += na_round((size_t)3 * (3 * (n / 2) * (n / 2) + 1) * sizeof(float));
+  l.tw = o;
+  o += na_round((size_t)2 * n * sizeof(float));
+  l.pos = o;
+  o += na_round((size_t)4 * nb * sizeof(float));
+  l.x = o;
+  o += na_round((size_t)LDB * nb * sizeof(double));
+  l.y = o;
+  o += na_round((size_t)LDB * nb * sizeof(double));
+  l.end = o;
+  return l;
+}
+
+// FFT plan built without any host container (same stages as make_plan).
+FftPlan na_plan(int n) {
+  FftPlan p{};
+  p.n = n;
+  p.fn = make_fastdiv(n);
+  p.fnh = make_fastdiv(n / 2 + 1);
+  int m = n, k = 0, Ns = 1, off = 0;
+  int rad[kMaxStages];
+  int nr = 0;
+  while (m % 4 == 0) {
+    rad[nr++] = 4;
+    m /= 4;
+  }
+  for (int f : {2, 3, 5})
+    while (m % f == 0) {
+      rad[nr++] = f;
+      m /= f;
+    }
+  for (int i = 0; i < nr; ++i) {
+    FftStage &s = p.st[k++];
+    s.R = rad[i];
+    s.Ns = Ns;
+    s.toff = off;
+    s.nb = make_fastdiv(n / rad[i]);
+    s.ns = make_fastdiv(Ns);
+    off += (rad[i] - 1) * Ns;
+    Ns *= rad[i];
+  }
+  p.nst = k;
+  p.ntw = off;
+  return p;
+}
+
+// Twiddles of the plan and the Green's table (same formulas as build_wave).
+__global__ void k_na_tables(FftPlan plan, float *tw, float *green, int mmax, double L, double xi,
+                            double alpha, double a, double eta) {
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  for (int t = t0; t < plan.ntw; t += stride) {
+    int s = 0;
+    while (s + 1 < plan.nst && plan.st[s + 1].toff <= t) ++s;
+    const int u = t - plan.st[s].toff;
+    const int r = 1 + u / plan.st[s].Ns, kk = u % plan.st[s].Ns;
+    const double ang = -2.0 * kPi * r * kk / ((double)plan.st[s].Ns * plan.st[s].R);
+    tw[2 * t] = (float)cos(ang);
+    tw[2 * t + 1] = (float)sin(ang);
+  }
+  const double n3 = (double)plan.n * plan.n * plan.n;
+  for (int m = t0; m <= mmax; m += stride) {
+    if (m == 0) {
+      green[0] = green[1] = green[2] = 0.f;
+      continue;
+    }
+    const double k = 2.0 * kPi * sqrt((double)m) / L, k2 = k * k;
+    const double e = -k2 / (4.0 * xi * xi) + k2 / (2.0 * alpha);
+    const double A = (1.0 + k2 / (4.0 * xi * xi)) * exp(e) / (eta * k2) / n3;
+    const double z = k * a;
+    const double fm = z < 1e-3 ? 1.0 - z * z / 6.0 + z * z * z * z / 120.0 : sin(z) / z;
+    const double fd = z < 1e-2 ? 1.0 - z * z / 10.0 + z * z * z * z / 280.0
+                               : 3.0 * (sin(z) - z * cos(z)) / (z * z * z);
+    green[3 * m] = (float)(A * fm * fm);
+    green[3 * m + 1] = (float)(A * fm * fd);
+    green[3 * m + 2] = (float)(A * fd * fd);
+  }
+}
+
+// Bead positions (wrapped into [0, L)) and moments into the staged layout;
+// the staged output rows are zeroed (interpolation accumulates into them).
+__global__ void k_na_stage_in(int nb, const double *__restrict__ pos, const double *__restrict__ in,
+                              double L, float4 *pos4, double *x, double *y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  float p[3];
+  for (int d = 0; d < 3; ++d) {
+    double v = pos[3 * (size_t)i + d];
+    v -= L * floor(v / L);
+    if (v >= L) v -= L;
+    if (v < 0) v = 0;
+    p[d] = (float)v;
+  }
+  pos4[i] = make_float4(p[0], p[1], p[2], 0.f);
+  for (int k = 0; k < 11; ++k) x[(size_t)i * LDB + k] = in[(size_t)i * 11 + k];
+  x[(size_t)i * LDB + 11] = 0.0;
+  for (int k = 0; k < LDB; ++k) y[(size_t)i * LDB + k] = 0.0;
+}
+
+__global__ void k_na_stage_out(int nb, const double *__restrict__ y, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  for (int k = 0; k < 11; ++k) out[(size_t)i * 11 + k] = y[(size_t)i * LDB + k];
+}
+
+std::mutex g_na_mutex;
+void *g_na_ptr[64] = {};
+
+}  // namespace
+}  // namespace fsd
+
+extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead_pos,
+                                             const double *in, double *out, double box,
+                                             double xi, int grid, int P, double m_shape,
+                                             double a, double eta, void *cuda_stream) {
+  using namespace fsd;
+  if (n_beads < 1 || n_beads > kNaMaxBeads) return FSD_EINVAL;
+  if (!bead_pos || !in || !out || !(box > 0) || !(xi > 0) || !(a > 0) || !(eta > 0)) return FSD_EINVAL;
+  if (!fft_size_ok(grid) || grid > kNaMaxGrid) return FSD_EINVAL;
+  if (P % 2 || P < 4 || P > 24 || P > grid) return FSD_EINVAL;
+  for (const void *p : {(const void *)bead_pos, (const void *)in, (const void *)out}) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return FSD_EINVAL;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return FSD_EINVAL;
+  }
+  const int n = grid;
+  const int nb = (int)n_beads;
+  const NaLayout lay = na_layout(n, nb);
+  if (lay.end > kNaBytes) return FSD_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FSD_ECUDA;
+  unsigned char *base = nullptr;
+  {
+    // first call on a device: look up the array's device address (a host-side
+    // name of a __device__ array is not a device pointer)
+    std::lock_guard<std::mutex> lk(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return FSD_ECUDA;
+      }
+      g_na_ptr[dev] = p;
+    }
+    base = (unsigned char *)g_na_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float *gridp = (float *)(base + lay.grid);
+  Cx<float> *spec = (Cx<float> *)(base + lay.spec);
+  float *gout = (float *)(base + lay.gout);
+  float *green = (float *)(base + lay.green);
+  float *tw = (float *)(base + lay.tw);
+  float4 *pos4 = (float4 *)(base + lay.pos);
+  double *x = (double *)(base + lay.x);
+  double *y = (double *)(base + lay.y);
+  const double L = box, h = L / n;
+  const double ms = m_shape > 0 ? m_shape : 0.976 * std::sqrt(kPi * P);
+  const double alpha = 2.0 * ms * ms / ((P * h) * (P * h));
+  const FftPlan plan = na_plan(n);
+  const int hm = n / 2, mmax = 3 * hm * hm;
+  const int nh = n / 2 + 1;
+  const int threads = 256;
+  k_na_tables<<<8, 256, 0, st>>>(plan, tw, green, mmax, L, xi, alpha, a, eta);
+  k_na_stage_in<<<(nb + 127) / 128, 128, 0, st>>>(nb, bead_pos, in, L, pos4, x, y);
+  if (cudaMemsetAsync(gridp, 0, (size_t)6 * n * n * n * sizeof(float), st) != cudaSuccess)
+    return FSD_ECUDA;
+  const double cn = std::pow(alpha / kPi, 1.5);
+  k_spread<float><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, x, gridp, n, P, (float)h, (float)alpha,
+                                               (float)cn);
+  const int ntw = plan.ntw;
+  k_fft_x_fwd<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * (n + 1)) * sizeof(Cx<float>),
+                       st>>>(gridp, spec, plan, tw, 4);
+  const int blocks_y = 6 * n * ((nh + 15) / 16);
+  const size_t smy = (size_t)(ntw + 2 * 16 * (n + 1)) * sizeof(Cx<float>);
+  k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, -1.f);
+  k_fft_z_green<float><<<n * ((nh + 3) / 4), threads,
+                         (ntw + 2 * 6 * 4 * (n + 1)) * sizeof(Cx<float>), st>>>(spec, plan, tw,
+                                                                                green, 2);
+  k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, 1.f);
+  k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * (n + 1)) * sizeof(Cx<float>),
+                       st>>>(gout, spec, plan, tw, 4);
+  k_interp<float><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, gout, y, n, P, (float)h, (float)alpha,
+                                               (float)(cn * h * h * h));
+  k_na_stage_out<<<(nb + 127) / 128, 128, 0, st>>>(nb, y, out);
+  if (cudaGetLastError() != cudaSuccess) return FSD_ECUDA;
+  return FSD_OK;
+}
