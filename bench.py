@@ -104,7 +104,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- work model
-# Algorithmic work per launch of each kernel group ("Roofline").
+# Algorithmic work per launch of each kernel group.
 FLOP_PER_PAIR = 410  # FP32 flops of one directed FTS pair (operator form, FMA = 2)
 
 

@@ -22,7 +22,7 @@ with u^B = 0 and F^B = 0, assembled as ONE dense matrix and solved by LAPACK
   different bodies closer than the lubrication cut-off (Alg. 1 step 1).
 * Sigma: the rigid-body constraint of Eq. gc / Eq. sigma.
 
-Readings of points where the paper is silent (all listed in the design doc):
+Readings of points where the paper is silent:
 * E.(x - X) on the bead rows (Eq. spm_agg; the table's X - x is a typo).
 * FTS source/read-out factors: j0(ka) for force / velocity, 3 j1(ka)/(ka)
   for torque, stresslet / rotation, strain.
@@ -61,7 +61,7 @@ def strain_basis():
     """Orthonormal basis E_m (m = 0..4) of symmetric traceless 3x3 matrices.
 
     A stresslet / strain is stored as its 5 coordinates s_m = E_m : S, so
-    S : E = sum_m s_m e_m (the 5N reduced space)."""
+    S : E = sum_m s_m e_m (Sec. 2.1: the reduced 5N space of stresslets / strains)."""
     E = np.zeros((5, 3, 3))
     s2, s6 = np.sqrt(2.0), np.sqrt(6.0)
     E[0, 0, 0], E[0, 1, 1] = 1 / s2, -1 / s2
@@ -412,7 +412,7 @@ def mobility_dense(pos, L, a=1.0, eta=1.0, xi=None):
 
 def body_geometry(pos, body, L):
     """Bead positions unwrapped per body (minimum image about the body's first
-    bead), body centroids X (equal bead masses: the 'centre of mass')
+    bead), body centroids X (equal bead masses: the 'centre of mass', Sec. 2.3.1)
     and lever arms r_b = x_b - X_J."""
     pos = np.asarray(pos, dtype=np.float64)
     body = np.asarray(body)
@@ -431,7 +431,7 @@ def body_geometry(pos, body, L):
 
 
 def shear_flow(gamma):
-    """Simple shear, flow along x, gradient along y: u_inf = gamma y x,
+    """Simple shear, flow along x, gradient along y (Sec. 3.1.1): u_inf = gamma y x,
     E_inf = gamma/2 (xy + yx), Omega_inf = -gamma/2 z."""
     E = np.zeros((3, 3))
     E[0, 1] = E[1, 0] = 0.5 * gamma
@@ -489,7 +489,7 @@ def lub_coefficients(h, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
 def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     """22x22 grand resistance of one inter-body pair acting on
     nu = (U_inf - U, E_inf) per bead (11 each: 6 velocity, 5 strain),
-    returning (F, S) per bead (P:150 convention).
+    returning (F, S) per bead (the grand-resistance convention of Sec. 2.1).
 
     Relative surface velocity of the pair (n from i to j, lever r/2 so that
     a rigid motion of the pair gives zero):
