@@ -86,7 +86,7 @@ typedef struct {
                             k_c = 2 sqrt(-ln xerr) xi + 1 (Sec. 3.2), rounded up
                             to an even 2,3,5-smooth size                           */
   int P;                 /* Gaussian support in grid points per side (even, 4..24);
-                            0: 8                                                   */
+                            0: from xerr (8 for 1e-4, 12 for 1e-6, 16 for 1e-8)    */
   double m_shape;        /* Gaussian shape factor; <= 0: 0.976 sqrt(pi P)          */
   double lub_cutoff;     /* lubrication cut-off r_lub (0: no near field)           */
   double precond_cutoff; /* r_p of the preconditioner (2.1 a, Sec. 2.2.2)          */

@@ -770,3 +770,61 @@ def integrate(X, q, r_body, body, U, dt, comoving_gamma=0.0):
     R = quat_to_matrix(q)
     x = X[body] + np.einsum("bij,bj->bi", R[body], r_body)
     return X, q, x
+
+
+# ---------------------------------------------------------------------------
+# sampled rows (checks at sizes where the dense system does not fit)
+# ---------------------------------------------------------------------------
+
+
+def mobility_real_rows(pos, L, xi, rc, rows, F, a=1.0, eta=1.0):
+    """Rows `rows` of the real-space Ewald part (incl. the self term) applied
+    to F (Nt, 11): the same sum as mobility_real_dense, restricted to the
+    requested target beads.  Returns (len(rows), 11)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    F = np.asarray(F, dtype=np.float64)
+    N = pos.shape[0]
+    nimg = int(np.ceil(rc / L)) + 1
+    shifts = _lattice(nimg).astype(np.float64) * L
+    w0 = wave_blocks_free(np.zeros((1, 3)), xi, a, eta)[0]
+    selfb = self_block(a, eta) - w0
+    out = np.zeros((len(rows), 11))
+    for k, i in enumerate(rows):
+        d = pos[i][None, :] - pos
+        x = (d[:, None, :] + shifts[None, :, :]).reshape(-1, 3)
+        jj = np.repeat(np.arange(N), shifts.shape[0])
+        r = np.linalg.norm(x, axis=1)
+        keep = (r < rc) & (r > 0.0)
+        if keep.any():
+            blk = free_blocks(x[keep], a, eta) - wave_blocks_free(x[keep], xi, a, eta)
+            out[k] = np.einsum("pst,pt->s", blk, F[jj[keep]])
+        out[k] += selfb @ F[i]
+    return out
+
+
+def lubrication_rows(pos, body, L, bodies, dU, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
+    """(RR_FU^nf dU)_J for the aggregates J in `bodies`: the rows of
+    Sigma R_FU Sigma^T, with every inter-body pair of a bead of J found by
+    brute force (minimum image).  Returns (len(bodies), 6)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    body = np.asarray(body)
+    unw, X, r = body_geometry(pos, body, L)
+    dU = np.asarray(dU, dtype=np.float64)
+
+    def rigid(b):
+        J = body[b]
+        return np.concatenate([dU[J, 0:3] + np.cross(dU[J, 3:6], r[b]), dU[J, 3:6]])
+
+    out = np.zeros((len(bodies), 6))
+    for k, J in enumerate(bodies):
+        for b in np.nonzero(body == J)[0]:
+            d = unw - unw[b]
+            d -= L * np.round(d / L)
+            dist = np.linalg.norm(d, axis=1)
+            f = np.zeros(6)
+            for c in np.nonzero((dist < rcut) & (body != J))[0]:
+                R = lub_pair_matrix(np.zeros(3), d[c], a, eta, rcut, hmin)
+                f += R[0:6, 0:6] @ rigid(b) + R[0:6, 11:17] @ rigid(c)
+            out[k, 0:3] += f[0:3]
+            out[k, 3:6] += f[3:6] + np.cross(r[b], f[0:3])
+    return out

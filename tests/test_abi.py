@@ -38,7 +38,7 @@ def test_default_params(lib):
 
     p = pkg.default_params(box=10.0)
     assert p.a == 1.0 and p.eta == 1.0 and p.box == 10.0
-    assert p.P == 8 and p.restart == 30 and abs(p.tol - 1e-6) < 1e-20
+    assert p.P == 0 and p.restart == 30 and abs(p.tol - 1e-6) < 1e-20
     assert abs(p.precond_cutoff - 2.1) < 1e-15 and p.precision == pkg.FSD_FP64
 
 

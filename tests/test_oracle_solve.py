@@ -234,3 +234,29 @@ def test_integrator_rotation_angle():
         X, q, x = O.integrate(X, q, r, np.array([0, 0]), U, 1e-3)
     ang = np.arctan2(x[0, 1], x[0, 0])
     assert abs(ang - 0.5) < 1e-4
+
+
+# ------------------------------------------------------- sampled-row helpers
+
+
+def test_sampled_real_rows_equal_dense_rows():
+    rng = np.random.default_rng(31)
+    pos, body, L = synth.suspension(6, 4, 0.1, 7)
+    xi, rc = 1.0, 2.0 + np.sqrt(46.0) / 1.0
+    rc = min(rc, 0.49 * L)
+    F = rng.normal(size=(len(pos), 11))
+    dense = O.mobility_real_dense(pos, L, xi, rc).reshape(11 * len(pos), -1) @ F.reshape(-1)
+    rows = [0, 5, len(pos) - 1]
+    got = O.mobility_real_rows(pos, L, xi, rc, rows, F)
+    assert np.allclose(got, dense.reshape(-1, 11)[rows], rtol=0, atol=1e-14 * np.abs(dense).max())
+
+
+def test_sampled_lubrication_rows_equal_dense():
+    rng = np.random.default_rng(32)
+    pos, body, L = synth.suspension(12, 4, 0.15, 5)
+    sys_ = O.assemble(pos, body, L, rlub=3.0, M=np.eye(11 * len(pos)))
+    dU = rng.normal(size=(sys_["nb"], 6))
+    dense = (sys_["RRFU"] @ dU.reshape(-1)).reshape(-1, 6)
+    bodies = [0, 3, 11]
+    got = O.lubrication_rows(pos, body, L, bodies, dU)
+    assert np.allclose(got, dense[bodies], rtol=0, atol=1e-12 * np.abs(dense).max())
