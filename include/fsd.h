@@ -66,13 +66,32 @@ enum { FSD_FP64 = 0, FSD_MIXED = 1 };
 /* Flags. */
 enum {
   FSD_FLAG_WARM_START = 1, /* start each solve from the previous solution */
-  FSD_FLAG_COMOVING = 2    /* fsd_step advances the bodies by the disturbance
+  FSD_FLAG_COMOVING = 2,   /* fsd_step advances the bodies by the disturbance
                               motion only: X += (U - U_inf(X)) dt and q by
                               Omega - Omega_inf.  A cubic periodic box has no
                               sheared (Lees-Edwards) images, so the imposed
                               affine motion would drive bodies across the y
                               boundary into each other; each solve is still
                               the full sheared problem */
+  FSD_FLAG_GRAPH = 4,      /* run each solve (and fsd_step's update) as one
+                              captured CUDA graph: the GMRES restart cycles,
+                              Arnoldi steps and refinement sweeps are
+                              conditional graph nodes and the Givens
+                              least-squares update runs on the device, so a
+                              solve makes no host round trip.  The geometry
+                              (neighbour lists, lubrication blocks, LUs) is
+                              still prepared before the launch.  Same
+                              arithmetic as the host-driven loop.  Ignored
+                              while the profiler is on */
+  FSD_FLAG_AUTOTUNE = 8    /* at set-up, when xi, rc and grid are all left
+                              to the rules: time each candidate splitting xi
+                              in {0.30 .. 0.70}/a, and (small boxes) 1.02,
+                              1.25 and 1.6 times the smallest xi whose R_c
+                              stays below L/2 (R_c and the grid from the
+                              accuracy rules of Sec. 3.2, P from xerr) and
+                              each real-space tile on the device, with the
+                              operator the Krylov iterations apply, and keep
+                              the fastest.  Costs about eight set-ups */
 };
 
 typedef struct {
@@ -98,6 +117,8 @@ typedef struct {
   int inner_restart;     /* mixed: FP32-operator GMRES iterations per outer step (30) */
   double inner_tol;      /* mixed: inner relative tolerance (1e-4)                 */
   int flags;             /* FSD_FLAG_*                                             */
+  int tile;              /* real-space lanes per bead (4, 8, 16, 32); 0: from the
+                            mean neighbour count                                   */
 } fsd_params;
 
 typedef struct {
@@ -217,6 +238,62 @@ fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead_pos,
                                   const double *in, double *out, double box,
                                   double xi, int grid, int P, double m_shape,
                                   double a, double eta, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent periodic suspensions (each with its own box,
+ * beads, aggregates and parameters) advanced together.  The paper solves one
+ * suspension per run; batching is this library's way to fill the GPU with
+ * systems that are each too small to.  Each system gets its own context and
+ * stream; each system's solve (or step) is one captured CUDA graph
+ * (FSD_FLAG_GRAPH is forced on), and all systems' graphs are launched before
+ * any is waited for, most expensive first, so they run concurrently.  Results
+ * are those of fsd_solve / fsd_step on each system alone.
+ * ------------------------------------------------------------------------- */
+typedef struct fsd_batch fsd_batch;
+
+/* n_sys >= 1 systems; bead_offsets [n_sys + 1] (host): system s owns beads
+ * bead_offsets[s] .. bead_offsets[s+1]-1 of bead_pos [total][3] and agg_id
+ * [total] (ids dense 0..N_s-1 within each system); params [n_sys] (host), each
+ * as for fsd_setup (FSD_FLAG_AUTOTUNE tunes each system on its own).
+ * cuda_stream: a stream that the batch's work is ordered after and that
+ * waits for it (NULL: none).  On failure *batch is NULL and
+ * fsd_batch_last_error(NULL) names the system. */
+fsd_status fsd_setup_batch(fsd_batch **batch, int n_sys, const int64_t *bead_offsets,
+                           const double *bead_pos, const int32_t *agg_id,
+                           const fsd_params *params, void *cuda_stream);
+
+/* n_sys, agg_offsets [n_sys + 1] (prefix sums of the aggregate counts: the
+ * aggregate arrays below are concatenated in system order) and the
+ * parameters each system uses; any pointer may be NULL. */
+fsd_status fsd_batch_info(const fsd_batch *b, int *n_sys, int64_t *agg_offsets,
+                          fsd_params *params);
+
+/* fsd_solve on every system.  agg_force_torque [A][6] (NULL = 0),
+ * shear_rates [n_sys] (host), agg_velocity [A][6], agg_stresslet [A][9]
+ * (NULL to skip), stats [n_sys] (NULL to skip); A = agg_offsets[n_sys].
+ * Returns when every system is done.  The status is the worst over the
+ * systems (error > FSD_ENOCONV > FSD_EOVERLAP > FSD_OK);
+ * fsd_batch_last_error names the system. */
+fsd_status fsd_solve_batch(fsd_batch *b, const double *agg_force_torque,
+                           const double *shear_rates, double *agg_velocity,
+                           double *agg_stresslet, fsd_stats *stats);
+
+/* fsd_step on every system (same dt). agg_velocity may be NULL. */
+fsd_status fsd_step_batch(fsd_batch *b, const double *agg_force_torque,
+                          const double *shear_rates, double dt,
+                          double *agg_velocity, fsd_stats *stats);
+
+/* Bead positions [total][3] and quaternions [A][4] of every system. */
+fsd_status fsd_batch_get_beads(fsd_batch *b, double *bead_pos, double *agg_quat);
+
+/* System s's context, owned by the batch (operator access, profiler, or
+ * solving it alone); NULL when out of range. */
+fsd_ctx *fsd_batch_system(fsd_batch *b, int s);
+
+/* Message of the last error on b (NULL: of the last failed fsd_setup_batch). */
+const char *fsd_batch_last_error(const fsd_batch *b);
+
+void fsd_destroy_batch(fsd_batch *b);
 
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);

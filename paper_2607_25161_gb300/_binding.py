@@ -17,6 +17,8 @@ FSD_OK, FSD_EINVAL, FSD_ENOMEM, FSD_ECUDA, FSD_ENOCONV, FSD_ENUMERIC, FSD_EOVERL
 FSD_FP64, FSD_MIXED = 0, 1
 FSD_FLAG_WARM_START = 1
 FSD_FLAG_COMOVING = 2
+FSD_FLAG_GRAPH = 4
+FSD_FLAG_AUTOTUNE = 8
 STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",
                 5: "FSD_ENUMERIC", 6: "FSD_EOVERLAP", 7: "FSD_ETIMEOUT"}
 
@@ -26,6 +28,8 @@ EXPORTS = (
     "fsd_apply_mobility", "fsd_apply_saddle", "fsd_apply_precond", "fsd_apply_lubrication",
     "fsd_rhs", "fsd_get_params", "fsd_profile_enable", "fsd_profile_read",
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
+    "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
+    "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch",
 )
 PROF_GROUPS = 10
 
@@ -38,7 +42,7 @@ class FsdParams(ctypes.Structure):
         ("lub_cutoff", ctypes.c_double), ("precond_cutoff", ctypes.c_double),
         ("lub_hmin", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_restart", ctypes.c_int),
-        ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int),
+        ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int), ("tile", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -93,9 +97,21 @@ def load(path=LIB_PATH):
     lib.fsd_last_error.restype = ctypes.c_char_p
     lib.fsd_destroy.argtypes = [P]
     lib.fsd_destroy.restype = None
+    lib.fsd_setup_batch.argtypes = [ctypes.POINTER(P), I, P, P, P, P, P]
+    lib.fsd_batch_info.argtypes = [P, P, P, P]
+    lib.fsd_solve_batch.argtypes = [P, P, P, P, P, P]
+    lib.fsd_step_batch.argtypes = [P, P, P, D, P, P]
+    lib.fsd_batch_get_beads.argtypes = [P, P, P]
+    lib.fsd_batch_system.argtypes = [P, I]
+    lib.fsd_batch_system.restype = P
+    lib.fsd_batch_last_error.argtypes = [P]
+    lib.fsd_batch_last_error.restype = ctypes.c_char_p
+    lib.fsd_destroy_batch.argtypes = [P]
+    lib.fsd_destroy_batch.restype = None
     for name in EXPORTS:
         if name not in ("fsd_default_params", "fsd_last_error", "fsd_destroy",
-                        "fsd_profile_group_name"):
+                        "fsd_profile_group_name", "fsd_batch_system", "fsd_batch_last_error",
+                        "fsd_destroy_batch"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -231,9 +247,109 @@ class Suspension:
         return {self.lib.fsd_profile_group_name(g).decode(): (float(ms[g]), int(cnt[g]))
                 for g in range(PROF_GROUPS)}
 
+    @classmethod
+    def borrowed(cls, ctx, n_beads, n_agg):
+        """A view of a context owned elsewhere (a batch system); close() does
+        not destroy it."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self._keep = []
+        self.ctx = ctypes.c_void_p(ctx)
+        self.n_beads = int(n_beads)
+        self.n_agg = int(n_agg)
+        self._borrowed = True
+        return self
+
+    def close(self):
+        if self.ctx and not getattr(self, "_borrowed", False):
+            self.lib.fsd_destroy(self.ctx)
+        self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent suspensions behind an fsd_batch (fsd_setup_batch ...
+    fsd_destroy_batch).  systems: list of (bead_pos [n,3], agg_id [n], box);
+    params: one dict for all systems or a list of dicts."""
+
+    def __init__(self, systems, params=None, stream=None):
+        self.lib = load()
+        n = len(systems)
+        plist = params if isinstance(params, (list, tuple)) else [params or {}] * n
+        pos = np.ascontiguousarray(np.concatenate([np.asarray(s[0], dtype=np.float64) for s in systems]))
+        ids = np.ascontiguousarray(np.concatenate([np.asarray(s[1], dtype=np.int32) for s in systems]))
+        self.bead_off = np.zeros(n + 1, dtype=np.int64)
+        self.bead_off[1:] = np.cumsum([len(s[0]) for s in systems])
+        arr = (FsdParams * n)()
+        for i, (s, kw) in enumerate(zip(systems, plist)):
+            arr[i] = default_params(box=float(s[2]), **kw)
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.fsd_setup_batch(ctypes.byref(self.ctx), n, _ptr(self.bead_off), _ptr(pos),
+                                      _ptr(ids), ctypes.cast(arr, ctypes.c_void_p), stream)
+        if st != FSD_OK:
+            raise FsdError(st, self.lib.fsd_batch_last_error(None).decode())
+        self.n_sys = n
+        self.agg_off = np.zeros(n + 1, dtype=np.int64)
+        used = (FsdParams * n)()
+        self._check(self.lib.fsd_batch_info(self.ctx, None, _ptr(self.agg_off),
+                                            ctypes.cast(used, ctypes.c_void_p)))
+        self.params = [used[i].as_dict() for i in range(n)]
+        self.n_beads = int(self.bead_off[-1])
+        self.n_agg = int(self.agg_off[-1])
+
+    def _check(self, st, allow=(FSD_OK,)):
+        if st not in allow:
+            raise FsdError(st, self.lib.fsd_batch_last_error(self.ctx).decode())
+        return st
+
+    def _stats(self, arr):
+        return [arr[i].as_dict() for i in range(self.n_sys)]
+
+    def solve(self, ft=None, shear=0.0, allow=(FSD_OK, FSD_EOVERLAP)):
+        """fsd_solve_batch; returns (velocity [A,6], stresslet [A,3,3], [stats], status)."""
+        rates = np.ascontiguousarray(np.broadcast_to(np.asarray(shear, dtype=np.float64), (self.n_sys,)))
+        if ft is not None and not hasattr(ft, "data_ptr"):
+            ft = np.ascontiguousarray(ft, dtype=np.float64)
+        vel = np.zeros((self.n_agg, 6))
+        S = np.zeros((self.n_agg, 3, 3))
+        stats = (FsdStats * self.n_sys)()
+        st = self.lib.fsd_solve_batch(self.ctx, _ptr(ft), _ptr(rates), _ptr(vel), _ptr(S),
+                                      ctypes.cast(stats, ctypes.c_void_p))
+        self._check(st, allow)
+        return vel, S, self._stats(stats), st
+
+    def step(self, ft=None, shear=0.0, dt=1e-3, vel=None, allow=(FSD_OK, FSD_EOVERLAP)):
+        rates = np.ascontiguousarray(np.broadcast_to(np.asarray(shear, dtype=np.float64), (self.n_sys,)))
+        if ft is not None and not hasattr(ft, "data_ptr"):
+            ft = np.ascontiguousarray(ft, dtype=np.float64)
+        stats = (FsdStats * self.n_sys)()
+        st = self.lib.fsd_step_batch(self.ctx, _ptr(ft), _ptr(rates), float(dt), _ptr(vel),
+                                     ctypes.cast(stats, ctypes.c_void_p))
+        self._check(st, allow)
+        return self._stats(stats), st
+
+    def beads(self):
+        pos = np.zeros((self.n_beads, 3))
+        q = np.zeros((self.n_agg, 4))
+        self._check(self.lib.fsd_batch_get_beads(self.ctx, _ptr(pos), _ptr(q)))
+        return pos, q
+
+    def system(self, s):
+        """Suspension view of system s (owned by the batch)."""
+        ctx = self.lib.fsd_batch_system(self.ctx, int(s))
+        if not ctx:
+            raise IndexError(s)
+        return Suspension.borrowed(ctx, self.bead_off[s + 1] - self.bead_off[s],
+                                   self.agg_off[s + 1] - self.agg_off[s])
+
     def close(self):
         if self.ctx:
-            self.lib.fsd_destroy(self.ctx)
+            self.lib.fsd_destroy_batch(self.ctx)
             self.ctx = ctypes.c_void_p()
 
     def __del__(self):

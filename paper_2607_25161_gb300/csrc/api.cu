@@ -15,12 +15,25 @@ struct fsd_ctx {
   fsd::Ctx c;
 };
 
+// Independent suspensions solved together: one context (and stream) per
+// system; every system's step is one captured graph, and all systems' graphs
+// are in flight at once.
+struct fsd_batch {
+  std::vector<fsd_ctx *> sys;
+  std::vector<int64_t> bead_off, agg_off;
+  std::vector<int> order;  // launch order: most expensive system first
+  cudaStream_t user = nullptr;
+  cudaEvent_t ev_user = nullptr;
+  std::vector<cudaEvent_t> ev_done;
+  std::string last_error;
+};
+
 namespace fsd {
 
 bool fft_size_ok(int n);
 void vec_scale_host(Ctx &c, double *y, const double *x, double s);
 
-static std::string g_setup_error;
+static thread_local std::string g_setup_error;
 
 static const char *kProfNames[PG_COUNT] = {"realspace", "spread", "fft_green", "interp",
                                            "body_rows", "precond", "krylov", "neighbors",
@@ -106,6 +119,11 @@ __global__ void k_bodies_out(int N, const int *__restrict__ perm, const double *
   if (J >= N) return;
   for (int k = 0; k < w; ++k) user[(size_t)w * perm[J] + k] = x[(size_t)w * J + k];
 }
+void k_bodies_in_launch(Ctx &c, const double *user, double *internal) {
+  k_bodies_in<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.perm_body.p, user, internal, 6);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
 __global__ void k_bead_pos_out(int Nt, const int *__restrict__ perm,
                                const int *__restrict__ bead_body, const double *__restrict__ X,
                                const double4 *__restrict__ lever, double *user) {
@@ -142,10 +160,6 @@ void apply_saddle(Ctx &c, const double *x, double *y) {
 }
 template void apply_saddle<float>(Ctx &, const double *, double *);
 template void apply_saddle<double>(Ctx &, const double *, double *);
-
-struct KStats {
-  int iters = 0, m64 = 0, m32 = 0, outer = 0;
-};
 
 static double host_norm(Ctx &c, const double *x) {
   double *d = c.hcol.p + 200;
@@ -447,6 +461,8 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.m_in = p.inner_restart > 0 ? std::min(p.inner_restart, 60) : 30;
   c.prm.inner_restart = c.m_in;
   c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-4;
+  if (p.tile != 0 && p.tile != 4 && p.tile != 8 && p.tile != 16 && p.tile != 32)
+    throw Invalid{"tile must be 0, 4, 8, 16 or 32"};
   c.prm.xi = c.xi;
   c.prm.rc = c.rc;
   c.prm.grid = c.n;
@@ -609,6 +625,142 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
   return FSD_OK;
 }
 
+// ---- device-resident step (FSD_FLAG_GRAPH): geometry on the host side,
+//      then the whole solve (+ update) as one graph launch; the end half
+//      waits and turns the device state into a status.
+static bool use_graph(const Ctx &c) { return (c.prm.flags & FSD_FLAG_GRAPH) && !c.prof; }
+
+struct StepMark {
+  std::chrono::steady_clock::time_point t0;
+  int64_t l0 = 0;
+};
+
+static StepMark graph_step_begin(Ctx &c, const double *ft_user, double shear, bool with_str,
+                                 bool integrate, double dt) {
+  StepMark mk;
+  mk.t0 = std::chrono::steady_clock::now();
+  mk.l0 = c.launches;
+  prepare(c);
+  GraphRun o;
+  o.warm = (c.prm.flags & FSD_FLAG_WARM_START) && c.have_prev;
+  o.has_ft = ft_user != nullptr;
+  o.integrate = integrate;
+  o.with_str = with_str;
+  o.shear = shear;
+  o.dt = dt;
+  if (ft_user)
+    FSD_CUDA(cudaMemcpyAsync(graph_ft_buffer(c), ft_user, 6 * (size_t)c.N * sizeof(double),
+                             cudaMemcpyDefault, c.stream));
+  graph_launch(c, o);
+  return mk;
+}
+
+static fsd_status graph_step_end(Ctx &c, const StepMark &mk, fsd_stats *stats) {
+  KStats ks;
+  const double rel = graph_finish(c, ks);
+  c.have_prev = true;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - mk.t0).count();
+  fill_stats(c, stats, ks, rel, ms);
+  if (stats) stats->kernel_launches = c.launches - mk.l0;
+  if (c.h_flags[6]) {
+    c.last_error = "non-finite aggregate velocity";
+    return FSD_ENUMERIC;
+  }
+  if (c.h_flags[3]) {
+    c.last_error = "singular per-aggregate 6x6 preconditioner block";
+    return FSD_ENUMERIC;
+  }
+  if (!(rel <= c.prm.tol)) {
+    c.last_error = "Krylov solve stopped at relative residual " + std::to_string(rel);
+    return FSD_ENOCONV;
+  }
+  if (c.last_warning == FSD_EOVERLAP) {
+    c.last_error = "beads of different aggregates overlap (warning; results written)";
+    return FSD_EOVERLAP;
+  }
+  return FSD_OK;
+}
+
+// ---- autotuner (FSD_FLAG_AUTOTUNE): the splitting xi trades real-space
+//      pairs (R_c falls as 1/xi) against wave-space grid points (the grid
+//      grows as xi); P is the smallest support that meets xerr, which is
+//      always the fastest, so it is not searched.  Each candidate xi (with
+//      R_c and the grid from the accuracy rules) and real-space tile is
+//      timed on the device with the operator the Krylov iterations apply;
+//      the fastest is kept.  The preconditioner and hence the iteration
+//      count do not depend on xi.
+static double time_operator(Ctx &c, int reps) {
+  cudaEvent_t e0, e1;
+  FSD_CUDA(cudaEventCreate(&e0));
+  FSD_CUDA(cudaEventCreate(&e1));
+  double *x = c.t1.p, *y = c.w.p;
+  FSD_CUDA(cudaMemsetAsync(x, 0, c.nunk * sizeof(double), c.stream));
+  const bool f32 = c.prm.precision == FSD_MIXED;
+  auto apply = [&]() {
+    if (f32)
+      apply_saddle<float>(c, x, y);
+    else
+      apply_saddle<double>(c, x, y);
+  };
+  apply();
+  FSD_CUDA(cudaEventRecord(e0, c.stream));
+  for (int r = 0; r < reps; ++r) apply();
+  FSD_CUDA(cudaEventRecord(e1, c.stream));
+  FSD_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  FSD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / reps;
+}
+
+static fsd_params autotune(int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
+                           const fsd_params &p, double *best_ms_out) {
+  static const int kTile[] = {4, 8, 16, 32};
+  // fixed candidates, plus splittings just above the smallest one whose
+  // cut-off 2a + sqrt(-ln xerr)/xi stays below L/2 (small boxes)
+  const double a = p.a > 0 ? p.a : 1.0;
+  const double xerr = p.xerr > 0 ? p.xerr : 1e-6;
+  std::vector<double> xis = {0.30 / a, 0.35 / a, 0.40 / a, 0.45 / a, 0.50 / a,
+                             0.55 / a, 0.60 / a, 0.70 / a};
+  const double room = 0.5 * p.box - 2.0 * a;
+  if (room > 0) {
+    const double xmin = std::sqrt(-std::log(xerr)) / room;
+    for (double f : {1.02, 1.25, 1.6})
+      if (f * xmin > 0.7 / a) xis.push_back(f * xmin);
+  }
+  fsd_params best = p;
+  best.flags &= ~FSD_FLAG_AUTOTUNE;
+  double best_ms = 1e300;
+  for (double xi : xis) {
+    fsd_params q = p;
+    q.flags &= ~(FSD_FLAG_AUTOTUNE | FSD_FLAG_GRAPH);
+    q.xi = xi;
+    fsd_ctx *tmp = new fsd_ctx();
+    try {
+      setup_impl(tmp->c, n_beads, bead_pos, agg_id, q, nullptr);
+      prepare(tmp->c);
+      for (int t : kTile) {
+        tmp->c.prm.tile = t;
+        const double ms = time_operator(tmp->c, 3);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = p;
+          best.flags &= ~FSD_FLAG_AUTOTUNE;
+          best.xi = q.xi;
+          best.tile = t;
+        }
+      }
+    } catch (const Invalid &) {
+      // candidate outside the method's limits (R_c >= L/2, table too large)
+    }
+    fsd_destroy(tmp);
+  }
+  if (best_ms >= 1e300) throw Invalid{"autotune: no admissible splitting for this box"};
+  if (best_ms_out) *best_ms_out = best_ms;
+  return best;
+}
+
 // Write an internal-order device array of N x w to a user pointer (host or device).
 static void bodies_out(Ctx &c, const double *src_int, double *user, int w) {
   if (!user) return;
@@ -673,6 +825,7 @@ void fsd_default_params(fsd_params *p) {
   p->inner_restart = 30;
   p->inner_tol = 1e-4;
   p->flags = 0;
+  p->tile = 0;
 }
 
 fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
@@ -684,8 +837,13 @@ fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos, con
   *ctx = nullptr;
   fsd_ctx *cx = nullptr;
   FSD_API_TRY
+  fsd_params q = *p;
+  double tuned = 0.0;
+  if ((q.flags & FSD_FLAG_AUTOTUNE) && q.xi <= 0 && q.rc <= 0 && q.grid <= 0)
+    q = autotune(n_beads, bead_pos, agg_id, q, &tuned);
   cx = new fsd_ctx();
-  setup_impl(cx->c, n_beads, bead_pos, agg_id, *p, cuda_stream);
+  setup_impl(cx->c, n_beads, bead_pos, agg_id, q, cuda_stream);
+  cx->c.tuned_ms = tuned;
   *ctx = cx;
   return FSD_OK;
   }
@@ -725,7 +883,13 @@ fsd_status fsd_solve(fsd_ctx *ctx, const double *agg_force_torque, double shear_
   // internal outputs live in t1 (velocity) / res (stresslet) after the solve
   double *vel_int = c.t1.p;
   double *str_int = agg_stresslet ? c.res.p : nullptr;
-  fsd_status st = solve_internal(c, agg_force_torque, shear_rate, vel_int, str_int, stats, 0.0);
+  fsd_status st;
+  if (use_graph(c)) {
+    const StepMark mk = graph_step_begin(c, agg_force_torque, shear_rate, str_int != nullptr, false, 0.0);
+    st = graph_step_end(c, mk, stats);
+  } else {
+    st = solve_internal(c, agg_force_torque, shear_rate, vel_int, str_int, stats, 0.0);
+  }
   if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
   (void)vel;
   bodies_out(c, vel_int, agg_velocity, 6);
@@ -747,6 +911,18 @@ fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque, double shear_r
   Ctx &c = ctx->c;
   auto t0 = std::chrono::steady_clock::now();
   double *vel_int = c.t1.p;
+  if (use_graph(c)) {
+    // the update runs inside the graph, after the solve
+    const StepMark mk = graph_step_begin(c, agg_force_torque, shear_rate, false, true, dt);
+    fsd_status st = graph_step_end(c, mk, stats);
+    if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
+    const int64_t l1 = c.launches;
+    if (agg_velocity) bodies_out(c, vel_int, agg_velocity, 6);
+    if (stats) stats->kernel_launches += c.launches - l1;
+    if (stats)
+      stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+  }
   fsd_status st = solve_internal(c, agg_force_torque, shear_rate, vel_int, nullptr, stats, 0.0);
   if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
   const int64_t l1 = c.launches;
@@ -961,6 +1137,7 @@ void fsd_destroy(fsd_ctx *ctx) {
   if (!ctx) return;
   Ctx &c = ctx->c;
   if (c.stream) cudaStreamSynchronize(c.stream);
+  graph_cache_free(c);
   if (c.h_flags) cudaFreeHost(c.h_flags);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
   prof_collect(c);
@@ -970,6 +1147,232 @@ void fsd_destroy(fsd_ctx *ctx) {
   bool own = c.own_stream;
   delete ctx;
   if (own && s) cudaStreamDestroy(s);
+}
+
+// ====================================================== batched suspensions
+
+static int status_rank(fsd_status s) {
+  switch (s) {
+    case FSD_OK: return 0;
+    case FSD_EOVERLAP: return 1;
+    case FSD_ENOCONV: return 2;
+    default: return 3;
+  }
+}
+
+void fsd_destroy_batch(fsd_batch *b) {
+  if (!b) return;
+  for (fsd_ctx *c : b->sys) fsd_destroy(c);
+  for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
+  if (b->ev_user) cudaEventDestroy(b->ev_user);
+  delete b;
+}
+
+fsd_status fsd_setup_batch(fsd_batch **batch, int n_sys, const int64_t *bead_offsets,
+                           const double *bead_pos, const int32_t *agg_id,
+                           const fsd_params *params, void *cuda_stream) {
+  if (!batch || n_sys < 1 || !bead_offsets || !bead_pos || !agg_id || !params) {
+    g_setup_error = "batch, n_sys >= 1, bead_offsets, bead_pos, agg_id and params are required";
+    if (batch) *batch = nullptr;
+    return FSD_EINVAL;
+  }
+  *batch = nullptr;
+  if (bead_offsets[0] != 0) {
+    g_setup_error = "bead_offsets[0] must be 0";
+    return FSD_EINVAL;
+  }
+  for (int s = 0; s < n_sys; ++s)
+    if (bead_offsets[s + 1] <= bead_offsets[s]) {
+      g_setup_error = "system " + std::to_string(s) + " has no beads";
+      return FSD_EINVAL;
+    }
+  fsd_batch *b = nullptr;
+  try {
+    b = new fsd_batch();
+    b->user = (cudaStream_t)cuda_stream;
+    b->bead_off.assign(bead_offsets, bead_offsets + n_sys + 1);
+    b->agg_off.assign(1, 0);
+    std::vector<double> cost(n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+      fsd_params q = params[s];
+      q.flags |= FSD_FLAG_GRAPH;
+      const int64_t o = bead_offsets[s], nb = bead_offsets[s + 1] - o;
+      fsd_ctx *cx = nullptr;
+      const fsd_status st = fsd_setup(&cx, nb, bead_pos + 3 * o, agg_id + o, &q, nullptr);
+      if (st != FSD_OK) {
+        const std::string m = "system " + std::to_string(s) + ": " + g_setup_error;
+        fsd_destroy_batch(b);
+        g_setup_error = m;
+        return st;
+      }
+      b->sys.push_back(cx);
+      const Ctx &c = cx->c;
+      b->agg_off.push_back(b->agg_off.back() + c.N);
+      cost[s] = c.tuned_ms > 0 ? c.tuned_ms : (double)c.Nt + 0.25 * (double)c.n * c.n * c.n;
+      cudaEvent_t e;
+      FSD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      b->ev_done.push_back(e);
+    }
+    if (b->user) FSD_CUDA(cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming));
+    b->order.resize(n_sys);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    *batch = b;
+    return FSD_OK;
+  } catch (const CudaError &e) {
+    g_setup_error = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+    fsd_destroy_batch(b);
+    return e.e == cudaErrorMemoryAllocation ? FSD_ENOMEM : FSD_ECUDA;
+  } catch (const std::bad_alloc &) {
+    g_setup_error = "host allocation failed";
+    fsd_destroy_batch(b);
+    return FSD_ENOMEM;
+  }
+}
+
+fsd_status fsd_batch_info(const fsd_batch *b, int *n_sys, int64_t *agg_offsets,
+                          fsd_params *params) {
+  if (!b) return FSD_EINVAL;
+  const int ns = (int)b->sys.size();
+  if (n_sys) *n_sys = ns;
+  if (agg_offsets)
+    for (int s = 0; s <= ns; ++s) agg_offsets[s] = b->agg_off[s];
+  if (params)
+    for (int s = 0; s < ns; ++s) params[s] = b->sys[s]->c.prm;
+  return FSD_OK;
+}
+
+fsd_ctx *fsd_batch_system(fsd_batch *b, int s) {
+  if (!b || s < 0 || s >= (int)b->sys.size()) return nullptr;
+  return b->sys[s];
+}
+
+// Solve (integrate = false) or step every system: all graphs are launched
+// first (geometry of each system prepared on its own stream just before its
+// launch), then each is waited for and its outputs written.
+static fsd_status batch_run(fsd_batch *b, const double *ft, const double *shear_rates, double dt,
+                            bool integrate, double *vel, double *str, fsd_stats *stats) {
+  const int ns = (int)b->sys.size();
+  std::vector<fsd_status> st(ns, FSD_OK);
+  std::vector<StepMark> mk(ns);
+  std::vector<char> launched(ns, 0);
+  std::vector<std::string> err(ns);
+  if (b->user) {
+    FSD_CUDA(cudaEventRecord(b->ev_user, b->user));
+    for (fsd_ctx *cx : b->sys) FSD_CUDA(cudaStreamWaitEvent(cx->c.stream, b->ev_user, 0));
+  }
+  for (int s : b->order) {
+    Ctx &c = b->sys[s]->c;
+    const double *fts = ft ? ft + 6 * b->agg_off[s] : nullptr;
+    try {
+      if (use_graph(c)) {
+        mk[s] = graph_step_begin(c, fts, shear_rates[s], str != nullptr, integrate, dt);
+        launched[s] = 1;
+      } else {
+        // a system with the profiler on runs the host-driven loop in place
+        double *str_int = str ? c.res.p : nullptr;
+        st[s] = solve_internal(c, fts, shear_rates[s], c.t1.p, str_int, stats ? stats + s : nullptr, 0.0);
+        if (integrate && status_rank(st[s]) < 3) {
+          launch_integrate(c, c.t1.p, dt, shear_rates[s]);
+          launch_wrap_positions(c);
+        }
+      }
+    } catch (const CudaError &e) {
+      err[s] = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+      st[s] = FSD_ECUDA;
+    } catch (const Invalid &e) {
+      err[s] = e.msg;
+      st[s] = FSD_EINVAL;
+    }
+  }
+  for (int s : b->order) {
+    Ctx &c = b->sys[s]->c;
+    try {
+      if (launched[s]) st[s] = graph_step_end(c, mk[s], stats ? stats + s : nullptr);
+      if (status_rank(st[s]) < 3) {
+        if (vel) bodies_out(c, c.t1.p, vel + 6 * b->agg_off[s], 6);
+        if (str) bodies_out(c, c.res.p, str + 9 * b->agg_off[s], 9);
+      }
+      if (b->user) FSD_CUDA(cudaEventRecord(b->ev_done[s], c.stream));
+    } catch (const CudaError &e) {
+      err[s] = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+      st[s] = FSD_ECUDA;
+    } catch (const Invalid &e) {
+      err[s] = e.msg;
+      st[s] = FSD_EINVAL;
+    }
+  }
+  if (b->user)
+    for (int s = 0; s < ns; ++s) FSD_CUDA(cudaStreamWaitEvent(b->user, b->ev_done[s], 0));
+  fsd_status worst = FSD_OK;
+  b->last_error.clear();
+  for (int s = 0; s < ns; ++s) {
+    if (st[s] == FSD_OK) continue;
+    const std::string m = err[s].empty() ? b->sys[s]->c.last_error : err[s];
+    if (status_rank(st[s]) > status_rank(worst)) {
+      worst = st[s];
+      b->last_error = "system " + std::to_string(s) + ": " + m;
+    }
+  }
+  return worst;
+}
+
+fsd_status fsd_solve_batch(fsd_batch *b, const double *agg_force_torque, const double *shear_rates,
+                           double *agg_velocity, double *agg_stresslet, fsd_stats *stats) {
+  if (!b) return FSD_EINVAL;
+  if (!shear_rates || !agg_velocity) {
+    b->last_error = "shear_rates and agg_velocity are required";
+    return FSD_EINVAL;
+  }
+  for (size_t s = 0; s < b->sys.size(); ++s)
+    if (!std::isfinite(shear_rates[s])) {
+      b->last_error = "shear_rates must be finite";
+      return FSD_EINVAL;
+    }
+  try {
+    return batch_run(b, agg_force_torque, shear_rates, 0.0, false, agg_velocity, agg_stresslet, stats);
+  } catch (const CudaError &e) {
+    b->last_error = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+    return FSD_ECUDA;
+  }
+}
+
+fsd_status fsd_step_batch(fsd_batch *b, const double *agg_force_torque, const double *shear_rates,
+                          double dt, double *agg_velocity, fsd_stats *stats) {
+  if (!b) return FSD_EINVAL;
+  if (!shear_rates || !std::isfinite(dt)) {
+    b->last_error = "shear_rates are required and dt must be finite";
+    return FSD_EINVAL;
+  }
+  for (size_t s = 0; s < b->sys.size(); ++s)
+    if (!std::isfinite(shear_rates[s])) {
+      b->last_error = "shear_rates must be finite";
+      return FSD_EINVAL;
+    }
+  try {
+    return batch_run(b, agg_force_torque, shear_rates, dt, true, agg_velocity, nullptr, stats);
+  } catch (const CudaError &e) {
+    b->last_error = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+    return FSD_ECUDA;
+  }
+}
+
+fsd_status fsd_batch_get_beads(fsd_batch *b, double *bead_pos, double *agg_quat) {
+  if (!b) return FSD_EINVAL;
+  for (size_t s = 0; s < b->sys.size(); ++s) {
+    const fsd_status st = fsd_get_beads(b->sys[s], bead_pos ? bead_pos + 3 * b->bead_off[s] : nullptr,
+                                        agg_quat ? agg_quat + 4 * b->agg_off[s] : nullptr);
+    if (st != FSD_OK) {
+      b->last_error = "system " + std::to_string(s) + ": " + b->sys[s]->c.last_error;
+      return st;
+    }
+  }
+  return FSD_OK;
+}
+
+const char *fsd_batch_last_error(const fsd_batch *b) {
+  if (!b) return g_setup_error.c_str();
+  return b->last_error.c_str();
 }
 
 }  // extern "C"

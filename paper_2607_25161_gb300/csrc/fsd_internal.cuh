@@ -93,6 +93,22 @@ enum ProfGroup {
 };
 
 struct Ctx;
+struct GraphCache;  // captured solve graphs of a context (graph.cu)
+
+// Krylov statistics of one solve.
+struct KStats {
+  int iters = 0, m64 = 0, m32 = 0, outer = 0;
+};
+
+// What one captured step does (graph.cu).
+struct GraphRun {
+  int warm = 0;       // start from the previous solution
+  int has_ft = 0;     // applied forces / torques staged in the graph's buffer
+  int integrate = 0;  // advance the rigid bodies by dt after the solve
+  int with_str = 0;   // write the stresslet
+  double shear = 0.0, dt = 0.0;
+};
+
 struct ProfScope {
   Ctx *c;
   int g;
@@ -157,6 +173,10 @@ struct Ctx {
   std::string last_error;
   fsd_status last_warning = FSD_OK;
   int64_t n_pairs = 0, n_lub = 0;
+  // ---- captured solve graphs
+  GraphCache *gcache = nullptr;
+  int64_t graph_pending = -1;
+  double tuned_ms = 0.0;  // operator time measured by the autotuner (0: not tuned)
 };
 
 // ------------------------------------------------------------ launchers
@@ -167,6 +187,7 @@ template <typename T>
 void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint,
                       bool self_only_real);
 void launch_wrap_positions(Ctx &c);  // pos64 / op*.pos / levers from X, q, rbody
+int realspace_group(const Ctx &c);   // lanes per bead of the pair sum
 
 // wavespace.cu
 void build_wave(Ctx &c);
@@ -193,6 +214,11 @@ void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k,
 void vec_scale_host(Ctx &c, double *y, const double *x, double s);  // y = s x
 void cgs_pass(Ctx &c, int mode, const double *V, int64_t ld, int k, double *w,
               const double *coef_dev, double *out_dev);  // fused Gram-Schmidt pass
+void cgs_pass_dev(Ctx &c, int mode, const double *V, int64_t ld, const int *k_dev, int k_add,
+                  int kmax, double *w, const double *coef_dev,
+                  double *out_dev);  // the same with k = *k_dev + k_add read on the device
+void axpy_multi_dev(Ctx &c, double *w, const double *V, int64_t ld, const int *k_dev,
+                    const double *coef_dev, double sign);
 int64_t cgs_partial_size(int64_t nunk, int kmax);
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b,
                int64_t n);                          // y = a x + b y
@@ -201,6 +227,13 @@ void norm2_dev(Ctx &c, const double *x, double *out_dev);
 // api.cu (solver)
 template <typename T>
 void apply_saddle(Ctx &c, const double *x, double *y);
+void k_bodies_in_launch(Ctx &c, const double *user, double *internal);  // [N][6] user -> internal order
+
+// graph.cu (device-resident solve)
+void graph_launch(Ctx &c, const GraphRun &o);  // capture on first use of a key; launch on c.stream
+double graph_finish(Ctx &c, KStats &st);       // wait; statistics; final relative residual
+double *graph_ft_buffer(Ctx &c);               // device buffer [N][6] the graph reads forces from
+void graph_cache_free(Ctx &c);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -43,7 +43,10 @@ __global__ void __launch_bounds__(256) k_dot_partial(const double *__restrict__ 
   }
 }
 
-__global__ void k_dot_final(const double *__restrict__ partial, int nb, int k, double *out) {
+// k_dev (when non-null) gives the count on the device: k = *k_dev + k_add.
+__global__ void k_dot_final(const double *__restrict__ partial, int nb, int k, const int *k_dev,
+                            int k_add, double *out) {
+  if (k_dev) k = *k_dev + k_add;
   const int j = blockIdx.x;
   if (j >= k) return;
   double s = 0.0;
@@ -66,7 +69,7 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, doub
     k_dot_partial<<<kDotBlocks, 256, 0, c.stream>>>(V, ld, k0, kc, w, n, c.partial.p);
     FSD_LAUNCHED(c);
   }
-  k_dot_final<<<k, 256, 0, c.stream>>>(c.partial.p, kDotBlocks, k, out_dev);
+  k_dot_final<<<k, 256, 0, c.stream>>>(c.partial.p, kDotBlocks, k, nullptr, 0, out_dev);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -81,8 +84,10 @@ constexpr int kE = 4;
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64_t ld, int k,
-                                             double *w, const double *__restrict__ coef,
-                                             int64_t n, double *partial) {
+                                             const int *k_dev, int k_add, double *w,
+                                             const double *__restrict__ coef, int64_t n,
+                                             double *partial) {
+  if (k_dev) k = *k_dev + k_add;
   __shared__ double cs[64];
   if (MODE > 0)
     for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = coef[j];
@@ -139,24 +144,38 @@ __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64
 
 static int cgs_blocks(int64_t n) { return std::max(1, ceil_div(n, 256LL * kE)); }
 
-// out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef.
-void cgs_pass(Ctx &c, int mode, const double *V, int64_t ld, int k, double *w,
-              const double *coef_dev, double *out_dev) {
+// out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef.  With k_dev
+// non-null the basis size is read on the device (k = *k_dev + k_add <= kmax),
+// so the pass can sit in a captured loop whose trip count the host never sees.
+static void cgs_launch(Ctx &c, int mode, const double *V, int64_t ld, int k, const int *k_dev,
+                       int k_add, int kmax, double *w, const double *coef_dev, double *out_dev) {
   ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
   const int blocks = cgs_blocks(n);
   const int nwarps = blocks * 8;
   if (mode == 0)
-    k_cgs<0><<<blocks, 256, 0, c.stream>>>(V, ld, k, w, coef_dev, n, c.partial.p);
+    k_cgs<0><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
   else if (mode == 1)
-    k_cgs<1><<<blocks, 256, 0, c.stream>>>(V, ld, k, w, coef_dev, n, c.partial.p);
+    k_cgs<1><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
   else
-    k_cgs<2><<<blocks, 256, 0, c.stream>>>(V, ld, k, w, coef_dev, n, c.partial.p);
+    k_cgs<2><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
   FSD_LAUNCHED(c);
-  const int kk = mode == 2 ? 1 : k;
-  k_dot_final<<<kk, 256, 0, c.stream>>>(c.partial.p, nwarps, kk, out_dev);
+  if (mode == 2)
+    k_dot_final<<<1, 256, 0, c.stream>>>(c.partial.p, nwarps, 1, nullptr, 0, out_dev);
+  else
+    k_dot_final<<<kmax, 256, 0, c.stream>>>(c.partial.p, nwarps, k, k_dev, k_add, out_dev);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
+}
+
+void cgs_pass(Ctx &c, int mode, const double *V, int64_t ld, int k, double *w,
+              const double *coef_dev, double *out_dev) {
+  cgs_launch(c, mode, V, ld, k, nullptr, 0, k, w, coef_dev, out_dev);
+}
+
+void cgs_pass_dev(Ctx &c, int mode, const double *V, int64_t ld, const int *k_dev, int k_add,
+                  int kmax, double *w, const double *coef_dev, double *out_dev) {
+  cgs_launch(c, mode, V, ld, 0, k_dev, k_add, kmax, w, coef_dev, out_dev);
 }
 
 int64_t cgs_partial_size(int64_t nunk, int kmax) {
@@ -165,7 +184,9 @@ int64_t cgs_partial_size(int64_t nunk, int kmax) {
 
 // w[i] += sign * sum_j coef[j] V_j[i]
 __global__ void k_axpy_multi(double *w, const double *__restrict__ V, int64_t ld, int k,
-                             const double *__restrict__ coef, double sign, int64_t n) {
+                             const int *k_dev, const double *__restrict__ coef, double sign,
+                             int64_t n) {
+  if (k_dev) k = *k_dev;
   __shared__ double cs[128];
   for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = sign * coef[j];
   __syncthreads();
@@ -183,7 +204,18 @@ void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k, const dou
   ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
   int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
-  k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, k, coef_dev, sign, n);
+  k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, k, nullptr, coef_dev, sign, n);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+// w += sign * sum_{j < *k_dev} coef[j] V_j (count read on the device)
+void axpy_multi_dev(Ctx &c, double *w, const double *V, int64_t ld, const int *k_dev,
+                    const double *coef_dev, double sign) {
+  ProfScope ps(c, PG_KRYLOV);
+  const int64_t n = c.nunk;
+  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
+  k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, 0, k_dev, coef_dev, sign, n);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }

@@ -9,6 +9,8 @@
 // biharmonic r/(8 pi eta)) minus the wave part (H-filtered, tabulated).
 #include "fsd_internal.cuh"
 
+#include <mutex>
+
 #include <algorithm>
 
 namespace fsd {
@@ -739,6 +741,36 @@ OpData<float> &opdata<float>(Ctx &c) {
   return c.op32;
 }
 
+// Lanes that share one bead's neighbour list, from the mean neighbour count
+// (a tile shape the caller may fix with fsd_params.tile).
+int realspace_group(const Ctx &c) {
+  const int t = c.prm.tile;
+  if (t == 4 || t == 8 || t == 16 || t == 32) return t;
+  const double avg = (double)c.n_pairs / std::max(1, c.Nt);
+  return avg > 96 ? 32 : (avg > 40 ? 16 : (avg > 16 ? 8 : 4));
+}
+
+// Resident blocks per SM of k_realspace<T, GG> at `smem` bytes of dynamic
+// shared memory; sets the kernel's shared-memory limit on first use.
+// Thread-safe: contexts may run on several host threads.
+template <typename T, int GG>
+static int realspace_occupancy(size_t smem, int threads) {
+  static std::mutex mu;
+  static std::vector<std::pair<size_t, int>> seen;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto &e : seen)
+    if (e.first == smem) return e.second;
+  int dev = 0;
+  FSD_CUDA(cudaGetDevice(&dev));
+  (void)dev;
+  FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)std::max<size_t>(smem, 48 * 1024)));
+  int occ = 0;
+  FSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_realspace<T, GG>, threads, smem));
+  seen.emplace_back(smem, occ);
+  return occ;
+}
+
 template <typename T>
 void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, bool) {
   ProfScope ps(c, PG_REAL);
@@ -748,33 +780,22 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, b
   k_pack_sources<T><<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, (const double4 *)c.pos64.p, x,
                                                               op.packed.p);
   FSD_LAUNCHED(c);
-  const double avg = (double)c.n_pairs / std::max(1, c.Nt);
-  int G = avg > 96 ? 32 : (avg > 40 ? 16 : (avg > 16 ? 8 : 4));
+  const int G = realspace_group(c);
   const size_t smem = (size_t)c.tab_nint * TSTRIDE * sizeof(T);
   if (smem > 200 * 1024) throw Invalid{"real-space table too large (reduce rc or raise xi)"};
-  int per_sm = 0;
   const T inv_h = (T)(1.0 / c.tab_h);
   const T c8 = (T)(1.0 / (8.0 * kPi * c.eta));
 #define FSD_RS_LAUNCH(GG)                                                                    \
   {                                                                                          \
-    static size_t set_bytes = 0;                                                             \
-    static int occ = 0;                                                                      \
-    if (set_bytes != smem) {                                                                 \
-      FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>,                                      \
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-      FSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_realspace<T, GG>,       \
-                                                             threads, smem));                \
-      set_bytes = smem;                                                                      \
-    }                                                                                        \
-    per_sm = occ;                                                                            \
-  }                                                                                          \
-  k_realspace<T, GG><<<std::min<int64_t>(ceil_div((int64_t)c.Nt * GG, threads),               \
-                                         (int64_t)std::max(1, per_sm) * c.num_sms),         \
-                       threads, smem, c.stream>>>(                                           \
-      c.Nt, op.packed.p, c.nbr.p, c.ncnt.p, c.cap, x, y, op.table.p, c.tab_nint, inv_h,      \
-      (T)c.L, (T)c.a, c8, op.self_real[0], op.self_real[1], op.self_real[2],               \
-      add_constraint ? 1 : 0, c.bead_body.p, (const double4 *)c.lever64.p,                   \
-      (int)(LDB * (int64_t)c.Nt))
+    const int per_sm = realspace_occupancy<T, GG>(smem, threads);                            \
+    k_realspace<T, GG><<<std::min<int64_t>(ceil_div((int64_t)c.Nt * GG, threads),             \
+                                           (int64_t)std::max(1, per_sm) * c.num_sms),       \
+                         threads, smem, c.stream>>>(                                         \
+        c.Nt, op.packed.p, c.nbr.p, c.ncnt.p, c.cap, x, y, op.table.p, c.tab_nint, inv_h,    \
+        (T)c.L, (T)c.a, c8, op.self_real[0], op.self_real[1], op.self_real[2],             \
+        add_constraint ? 1 : 0, c.bead_body.p, (const double4 *)c.lever64.p,                 \
+        (int)(LDB * (int64_t)c.Nt));                                                         \
+  }
   switch (G) {
     case 32: FSD_RS_LAUNCH(32); FSD_LAUNCHED(c); break;
     case 16: FSD_RS_LAUNCH(16); FSD_LAUNCHED(c); break;

@@ -760,10 +760,13 @@ const float4 *posp<float>(Ctx &c) {
   return (const float4 *)c.op32.pos.p;
 }
 
-// Raise a kernel's dynamic shared-memory limit once per (kernel, size).
+// Raise a kernel's dynamic shared-memory limit once per (kernel, size);
+// thread-safe (contexts may run on several host threads).
 template <typename T>
 static void set_smem(const void *fn, size_t bytes) {
+  static std::mutex mu;
   static std::vector<std::pair<const void *, size_t>> done;
+  std::lock_guard<std::mutex> lock(mu);
   for (auto &d : done)
     if (d.first == fn && d.second >= bytes) return;
   FSD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));

@@ -28,6 +28,9 @@ __all__ = [
     "config_aggregates",
     "random_forces",
     "compress_suspension",
+    "compress_mixed",
+    "mixed_suspension",
+    "batch_workload",
 ]
 
 
@@ -302,3 +305,129 @@ def compress_suspension(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12,
     Pb = beads()
     assert len(_close_pairs(Pb, bodyidx, L, contact)[0]) == 0
     return Pb, bodyidx.astype(np.int32), L
+
+
+# ---------------------------------------------------------------------------
+# batched form: independent suspensions of uneven bead and aggregate counts
+# ---------------------------------------------------------------------------
+
+
+def compress_mixed(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12, step=0.98, max_iter=4000):
+    """compress_suspension for shapes of different bead counts (a list of
+    (n_b, 3) offset arrays): random sequential insertion at phi0, then affine
+    compression of the body centres with soft-repulsion relaxation."""
+    rng = np.random.default_rng(seed)
+    N = len(shapes)
+    nbs = np.array([len(s_) for s_ in shapes])
+    Nt = int(nbs.sum())
+    Lt = box_for_phi(Nt, phi, a)
+    # large bodies first; a looser start when insertion jams
+    phi_start = min(phi0, phi)
+    while True:
+        L = box_for_phi(Nt, phi_start, a)
+        try:
+            pos, body = pack_suspension(list(shapes), L, rng, a, h_gen)
+            break
+        except RuntimeError:
+            phi_start *= 0.7
+    body = body.astype(np.int64)
+    target = 2.0 * a + 1.01 * h_gen
+    push = 2.0 * a + 1.25 * h_gen
+    contact = 2.0 * a + h_gen
+    C = np.zeros((N, 3))
+    np.add.at(C, body, pos)
+    C /= nbs[:, None]
+    off = pos - C[body]
+    inertia = np.zeros(N)
+    np.add.at(inertia, body, np.einsum("nk,nk->n", off, off))
+
+    def rotate(off_, w):
+        wb = w[body]
+        th = np.linalg.norm(wb, axis=1)
+        k = np.where(th[:, None] > 0, wb / np.maximum(th, 1e-300)[:, None], 0.0)
+        ct, st = np.cos(th)[:, None], np.sin(th)[:, None]
+        kx = np.einsum("nj,nj->n", k, off_)[:, None]
+        return off_ * ct + np.cross(k, off_) * st + k * kx * (1 - ct)
+
+    while True:
+        for _ in range(max_iter):
+            Pb = C[body] + off
+            i, j, d = _close_pairs(Pb, body, L, target)
+            if len(i) == 0:
+                break
+            r = np.linalg.norm(d, axis=1)
+            f = ((push - r) / np.maximum(r, 1e-12))[:, None] * d
+            F = np.zeros((N, 3))
+            T = np.zeros((N, 3))
+            np.add.at(F, body[j], 0.5 * f)
+            np.add.at(F, body[i], -0.5 * f)
+            np.add.at(T, body[j], np.cross(off[j], 0.5 * f))
+            np.add.at(T, body[i], np.cross(off[i], -0.5 * f))
+            C = (C + 0.6 * F / np.sqrt(nbs)[:, None]) % L
+            off = rotate(off, 0.6 * T / (inertia[:, None] + a * a))
+        else:
+            raise RuntimeError("relaxation stalled at L=%.3f" % L)
+        if L <= Lt * (1 + 1e-12):
+            break
+        Ln = max(L * step, Lt)
+        C = C * (Ln / L)
+        L = Ln
+    Pb = C[body] + off
+    assert len(_close_pairs(Pb, body, L, contact)[0]) == 0
+    return Pb, body.astype(np.int32), L
+
+
+def _extent(shape):
+    d = shape[:, None, :] - shape[None, :, :]
+    return float(np.sqrt((d * d).sum(-1).max())) if len(shape) > 1 else 0.0
+
+
+def mixed_suspension(n_beads, phi, seed, size_lo=2, size_hi=64, a=1.0, h_gen=0.1):
+    """n_beads beads in random-attachment aggregates whose sizes are drawn
+    uniformly from size_lo..size_hi, at bead volume fraction phi.
+
+    The last aggregate is trimmed so the total is exactly n_beads (a trimmed
+    remainder below size_lo joins the previous aggregate).  An aggregate
+    whose extent (largest bead-centre distance + 2a) exceeds half the box is
+    regrown at half its size: a body larger than that would touch its own
+    periodic images."""
+    rng = np.random.default_rng(seed)
+    L = box_for_phi(n_beads, phi, a)
+    sizes = []
+    while sum(sizes) < n_beads:
+        sizes.append(int(rng.integers(size_lo, size_hi + 1)))
+    sizes[-1] -= sum(sizes) - n_beads
+    if sizes[-1] < size_lo and len(sizes) > 1:
+        sizes[-2] += sizes.pop()
+    shapes = []
+    for nb in sizes:
+        parts = [nb]
+        out = []
+        while parts:
+            k = parts.pop()
+            shp = random_attachment_aggregate(k, rng, a)
+            if k >= 2 * size_lo and _extent(shp) + 2 * a > 0.5 * L:
+                parts += [k // 2, k - k // 2]
+            else:
+                out.append(shp)
+        shapes += out
+    shapes.sort(key=len, reverse=True)  # insert large bodies first
+    if phi > 0.12:
+        return compress_mixed(shapes, phi, seed + 1, a, h_gen)
+    pos, body = pack_suspension(shapes, L, rng, a, h_gen)
+    return pos, body, L
+
+
+def batch_workload(n_sys, seed, n_lo=256, n_hi=8192, phi_lo=0.05, phi_hi=0.3, size_lo=2,
+                   size_hi=64):
+    """Independent suspensions: bead counts round(exp(U[ln n_lo, ln n_hi])),
+    volume fractions U[phi_lo, phi_hi], aggregate sizes U{size_lo..size_hi}.
+    Returns a list of (bead_pos, agg_id, L, phi)."""
+    rng = np.random.default_rng(seed)
+    n = np.rint(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=n_sys))).astype(int)
+    phi = rng.uniform(phi_lo, phi_hi, size=n_sys)
+    out = []
+    for s in range(n_sys):
+        pos, body, L = mixed_suspension(int(n[s]), float(phi[s]), seed * 1000 + s, size_lo, size_hi)
+        out.append((pos, body, L, float(phi[s])))
+    return out
