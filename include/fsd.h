@@ -98,12 +98,15 @@ typedef struct {
   double a;              /* bead radius (1)                                        */
   double eta;            /* viscosity (1)                                          */
   double box;            /* side L of the periodic cube (required, > 0)            */
-  double xi;             /* Ewald splitting (Sec. 3.2); <= 0: 0.5 / a              */
+  double xi;             /* Ewald splitting (Sec. 3.2); <= 0: 0.5 / a, or in a box
+                            too small for that cut-off 1.05 x the smallest xi with
+                            R_c < L/2                                              */
   double xerr;           /* accuracy target of the parameter rules (1e-6)          */
   double rc;             /* real-space cut-off; <= 0: 2a + sqrt(-ln xerr)/xi       */
   int grid;              /* FFT points per side; 0: k_c L / pi with
                             k_c = 2 sqrt(-ln xerr) xi + 1 (Sec. 3.2), rounded up
-                            to an even 2,3,5-smooth size                           */
+                            to a 2,3,5-smooth multiple of 4 (a given grid need
+                            only be even and 2,3,5-smooth)                         */
   int P;                 /* Gaussian support in grid points per side (even, 4..24);
                             0: from xerr (8 for 1e-4, 12 for 1e-6, 16 for 1e-8)    */
   double m_shape;        /* Gaussian shape factor; <= 0: 0.976 sqrt(pi P)          */
@@ -114,8 +117,13 @@ typedef struct {
   int restart;           /* GMRES restart length (30)                              */
   int max_iter;          /* Krylov iteration limit per solve (1000)                */
   int precision;         /* FSD_FP64 or FSD_MIXED                                  */
-  int inner_restart;     /* mixed: FP32-operator GMRES iterations per outer step (30) */
-  double inner_tol;      /* mixed: inner relative tolerance (1e-4)                 */
+  int inner_restart;     /* mixed: FP32-operator GMRES iterations per refinement
+                            sweep (60)                                             */
+  double inner_tol;      /* mixed: floor of the inner relative tolerance; a sweep
+                            aims at max(inner_tol, 0.3 tol / rel), rel the current
+                            FP64 relative residual (1e-7: the FP32 operator's
+                            relative error is ~1e-7, so at tol 1e-6 one sweep
+                            usually suffices)                                      */
   int flags;             /* FSD_FLAG_*                                             */
   int tile;              /* real-space lanes per bead (4, 8, 16, 32); 0: from the
                             mean neighbour count                                   */

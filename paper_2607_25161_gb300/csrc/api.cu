@@ -6,10 +6,13 @@
 #include "fsd_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <thread>
 
 struct fsd_ctx {
   fsd::Ctx c;
@@ -26,6 +29,7 @@ struct fsd_batch {
   cudaEvent_t ev_user = nullptr;
   std::vector<cudaEvent_t> ev_done;
   std::string last_error;
+  int host_threads = 8;  // launch-phase threads
 };
 
 namespace fsd {
@@ -309,10 +313,12 @@ static double solve_system(Ctx &c, const double *b, double *x, KStats &st, bool 
 }
 
 // --------------------------------------------------------------- set-up
-static int round_up_smooth_even(int n) {
+// Smallest 2,3,5-smooth multiple of 4 (>= 8) not below n: multiples of 4
+// let the FP32 spreading add 16-byte aligned quads of grid points.
+static int round_up_smooth4(int n) {
   if (n < 8) n = 8;
   for (int m = n;; ++m)
-    if (fft_size_ok(m)) return m;
+    if (m % 4 == 0 && fft_size_ok(m)) return m;
 }
 
 static uint32_t spread_bits(uint32_t v) {
@@ -416,17 +422,21 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.h_body_start[c.N] = c.Nt;
   // ---- parameters (rules of Sec. 3.2 unless given)
   const double a = c.a;
-  c.xi = p.xi > 0 ? p.xi : 0.5 / a;
   const double xerr = p.xerr > 0 ? p.xerr : 1e-6;
   c.prm.xerr = xerr;
   const double lnx = std::sqrt(-std::log(xerr));
+  // default splitting 0.5/a; in a box too small for its cut-off, 1.05 times
+  // the smallest xi whose R_c = 2a + sqrt(-ln xerr)/xi stays below L/2
+  c.xi = p.xi > 0 ? p.xi : 0.5 / a;
+  if (p.xi <= 0 && p.rc <= 0 && 2.0 * a + lnx / c.xi >= 0.5 * L && 0.5 * L > 2.0 * a)
+    c.xi = 1.05 * lnx / (0.5 * L - 2.0 * a);
   c.rc = p.rc > 0 ? p.rc : 2.0 * a + lnx / c.xi;
   if (p.grid > 0) {
     if (!fft_size_ok(p.grid)) throw Invalid{"grid must be even and 2,3,5-smooth (>= 8)"};
     c.n = p.grid;
   } else {
     const double kc = 2.0 * lnx * c.xi + 1.0;
-    c.n = round_up_smooth_even((int)std::ceil(kc * L / kPi));
+    c.n = round_up_smooth4((int)std::ceil(kc * L / kPi));
   }
   // default support from the accuracy target: the relative error of the
   // wave-space operator against the exact mobility was measured as 8e-5 at
@@ -458,9 +468,9 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.prm.restart = c.m;
   c.prm.max_iter = p.max_iter > 0 ? p.max_iter : 1000;
   if (p.precision != FSD_FP64 && p.precision != FSD_MIXED) throw Invalid{"precision must be 0 or 1"};
-  c.m_in = p.inner_restart > 0 ? std::min(p.inner_restart, 60) : 30;
+  c.m_in = p.inner_restart > 0 ? std::min(p.inner_restart, 60) : 60;
   c.prm.inner_restart = c.m_in;
-  c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-4;
+  c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-7;
   if (p.tile != 0 && p.tile != 4 && p.tile != 8 && p.tile != 16 && p.tile != 32)
     throw Invalid{"tile must be 0, 4, 8, 16 or 32"};
   c.prm.xi = c.xi;
@@ -822,8 +832,8 @@ void fsd_default_params(fsd_params *p) {
   p->restart = 30;
   p->max_iter = 1000;
   p->precision = FSD_FP64;
-  p->inner_restart = 30;
-  p->inner_tol = 1e-4;
+  p->inner_restart = 60;
+  p->inner_tol = 1e-7;
   p->flags = 0;
   p->tile = 0;
 }
@@ -1190,6 +1200,7 @@ fsd_status fsd_setup_batch(fsd_batch **batch, int n_sys, const int64_t *bead_off
   try {
     b = new fsd_batch();
     b->user = (cudaStream_t)cuda_stream;
+    if (const char *e = std::getenv("FSD_BATCH_THREADS")) b->host_threads = std::max(1, std::atoi(e));
     b->bead_off.assign(bead_offsets, bead_offsets + n_sys + 1);
     b->agg_off.assign(1, 0);
     std::vector<double> cost(n_sys);
@@ -1261,30 +1272,46 @@ static fsd_status batch_run(fsd_batch *b, const double *ft, const double *shear_
     FSD_CUDA(cudaEventRecord(b->ev_user, b->user));
     for (fsd_ctx *cx : b->sys) FSD_CUDA(cudaStreamWaitEvent(cx->c.stream, b->ev_user, 0));
   }
-  for (int s : b->order) {
-    Ctx &c = b->sys[s]->c;
-    const double *fts = ft ? ft + 6 * b->agg_off[s] : nullptr;
-    try {
-      if (use_graph(c)) {
-        mk[s] = graph_step_begin(c, fts, shear_rates[s], str != nullptr, integrate, dt);
-        launched[s] = 1;
-      } else {
-        // a system with the profiler on runs the host-driven loop in place
-        double *str_int = str ? c.res.p : nullptr;
-        st[s] = solve_internal(c, fts, shear_rates[s], c.t1.p, str_int, stats ? stats + s : nullptr, 0.0);
-        if (integrate && status_rank(st[s]) < 3) {
-          launch_integrate(c, c.t1.p, dt, shear_rates[s]);
-          launch_wrap_positions(c);
+  // Launch phase on a few host threads: each system's geometry preparation
+  // waits on its own stream (neighbour-list and lubrication sizes), so
+  // systems prepared in parallel keep more graphs in flight.  Systems are
+  // taken most expensive first.
+  int dev = 0;
+  FSD_CUDA(cudaGetDevice(&dev));
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int t; (t = next.fetch_add(1)) < ns;) {
+      const int s = b->order[t];
+      Ctx &c = b->sys[s]->c;
+      const double *fts = ft ? ft + 6 * b->agg_off[s] : nullptr;
+      try {
+        if (use_graph(c)) {
+          mk[s] = graph_step_begin(c, fts, shear_rates[s], str != nullptr, integrate, dt);
+          launched[s] = 1;
+        } else {
+          // a system with the profiler on runs the host-driven loop in place
+          double *str_int = str ? c.res.p : nullptr;
+          st[s] = solve_internal(c, fts, shear_rates[s], c.t1.p, str_int, stats ? stats + s : nullptr, 0.0);
+          if (integrate && status_rank(st[s]) < 3) {
+            launch_integrate(c, c.t1.p, dt, shear_rates[s]);
+            launch_wrap_positions(c);
+          }
         }
+      } catch (const CudaError &e) {
+        err[s] = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+        st[s] = FSD_ECUDA;
+      } catch (const Invalid &e) {
+        err[s] = e.msg;
+        st[s] = FSD_EINVAL;
       }
-    } catch (const CudaError &e) {
-      err[s] = std::string(e.what) + ": " + cudaGetErrorString(e.e);
-      st[s] = FSD_ECUDA;
-    } catch (const Invalid &e) {
-      err[s] = e.msg;
-      st[s] = FSD_EINVAL;
     }
-  }
+  };
+  const int nthreads = std::max(1, std::min({ns, b->host_threads}));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
   for (int s : b->order) {
     Ctx &c = b->sys[s]->c;
     try {

@@ -79,8 +79,26 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, doub
 //   MODE 1:  w -= sum_j coef_j V_j, then partial dots V_j . w
 //   MODE 2:  w -= sum_j coef_j V_j, then partial ||w||^2
 // Each thread owns kE elements spaced by the grid's thread count (coalesced);
-// warp partials go to partial[j * nwarps + warp] (fixed reduction order).
+// basis vectors are taken four at a time so that 4 kE loads are in flight
+// per thread; warp partials go to partial[j * nwarps + warp] (fixed
+// reduction order).
 constexpr int kE = 4;
+
+// Warp sums of four values with six shuffles: after the exchange across
+// lane bit 4 each lane keeps two of the four partial sums, after bit 3 one;
+// bits 2..0 finish it.  Lane 8 q holds the full sum of value q.
+__device__ __forceinline__ double warp_sum4(const double a[4], int lane) {
+  const bool h4 = lane & 16;
+  const double s0 = h4 ? a[0] : a[2], s1 = h4 ? a[1] : a[3];
+  double b0 = (h4 ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
+  double b1 = (h4 ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool h3 = lane & 8;
+  double c = (h3 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h3 ? b0 : b1, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64_t ld, int k,
@@ -94,27 +112,44 @@ __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64
   __syncthreads();
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // a thread whose kE elements are all in range loads without predicates
+  const bool full = t0 + (kE - 1) * T < n;
   double wv[kE];
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
     const int64_t i = t0 + e * T;
     wv[e] = i < n ? w[i] : 0.0;
   }
+  auto ld_col = [&](const double *vj, double *out) {
+    if (full) {
+#pragma unroll
+      for (int e = 0; e < kE; ++e) out[e] = vj[e * T];
+    } else {
+#pragma unroll
+      for (int e = 0; e < kE; ++e) out[e] = t0 + e * T < n ? vj[e * T] : 0.0;
+    }
+  };
   if (MODE > 0) {
-    for (int j = 0; j < k; ++j) {
-      const double c = cs[j];
-      const double *vj = V + (int64_t)j * ld;
+    const double *vj = V + t0;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      double v[4][kE];
 #pragma unroll
-      for (int e = 0; e < kE; ++e) {
-        const int64_t i = t0 + e * T;
-        if (i < n) wv[e] -= c * vj[i];
-      }
+      for (int q = 0; q < 4; ++q) ld_col(vj + q * ld, v[q]);
+      vj += 4 * ld;
+#pragma unroll
+      for (int e = 0; e < kE; ++e)
+        wv[e] -= cs[j] * v[0][e] + cs[j + 1] * v[1][e] + cs[j + 2] * v[2][e] + cs[j + 3] * v[3][e];
+    }
+    for (; j < k; ++j, vj += ld) {
+      double v[kE];
+      ld_col(vj, v);
+#pragma unroll
+      for (int e = 0; e < kE; ++e) wv[e] -= cs[j] * v[e];
     }
 #pragma unroll
-    for (int e = 0; e < kE; ++e) {
-      const int64_t i = t0 + e * T;
-      if (i < n) w[i] = wv[e];
-    }
+    for (int e = 0; e < kE; ++e)
+      if (t0 + e * T < n) w[t0 + e * T] = wv[e];
   }
   const int lane = threadIdx.x & 31;
   const int64_t gw = t0 >> 5;
@@ -128,14 +163,28 @@ __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64
     if (lane == 0) partial[gw] = acc;
     return;
   }
-  for (int j = 0; j < k; ++j) {
-    const double *vj = V + (int64_t)j * ld;
+  const double *vj = V + t0;
+  int j = 0;
+  for (; j + 4 <= k; j += 4) {
+    double v[4][kE], acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ld_col(vj + q * ld, v[q]);
+    vj += 4 * ld;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc[q] = 0.0;
+#pragma unroll
+      for (int e = 0; e < kE; ++e) acc[q] += v[q][e] * wv[e];
+    }
+    const double r = warp_sum4(acc, lane);
+    if ((lane & 7) == 0) partial[(int64_t)(j + (lane >> 3)) * nwarps + gw] = r;
+  }
+  for (; j < k; ++j, vj += ld) {
+    double v[kE];
+    ld_col(vj, v);
     double acc = 0.0;
 #pragma unroll
-    for (int e = 0; e < kE; ++e) {
-      const int64_t i = t0 + e * T;
-      if (i < n) acc += vj[i] * wv[e];
-    }
+    for (int e = 0; e < kE; ++e) acc += v[e] * wv[e];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) partial[(int64_t)j * nwarps + gw] = acc;

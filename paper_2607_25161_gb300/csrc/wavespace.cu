@@ -431,6 +431,119 @@ __global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int
   }
 }
 
+// ------------------------------------------------ fused x + y passes (FP32)
+// One block per (component, z) plane, both transforms in shared memory
+// (FP32 planes up to n = 160 fit next to their ping-pong copy).
+// Forward: rows y = 2r and 2r + 1 of the real plane form the complex line
+// z_r = g_2r + i g_2r+1; after the x DFT the half spectra of the two rows are
+// A_k = (Z_k + conj Z_{n-k})/2 and B_k = (Z_k - conj Z_{n-k})/(2i), k <= n/2.
+// They are transposed into nh = n/2 + 1 lines along y, transformed, and
+// written as spec[comp][z][y][kx].
+template <typename T>
+__global__ void __launch_bounds__(512) k_fft_xy_fwd(const T *__restrict__ grid, Cx<T> *spec,
+                                                    FftPlan plan, const T *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = n + 1, nh = n / 2 + 1, nr = n / 2;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + plan.ntw;  // nh lines of ls
+  Cx<T> *B = A + nh * ls;
+  load_twiddles(tw_s, tw, plan.ntw);
+  const int64_t cz = blockIdx.x;  // comp * n + z
+  const T *g = grid + cz * n * n;
+  {
+    // eight loads in flight per thread: the plane load is latency-bound
+    constexpr int U = 8;
+    const int total = nr * n;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+      T va[U], vb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int r = (int)fdiv((uint32_t)e, plan.fn), x = e - r * n;
+        va[u] = e < total ? g[(2 * r) * n + x] : T(0);
+        vb[u] = e < total ? g[(2 * r + 1) * n + x] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= total) continue;
+        const int r = (int)fdiv((uint32_t)e, plan.fn), x = e - r * n;
+        A[r * ls + x] = {va[u], vb[u]};
+      }
+    }
+  }
+  __syncthreads();
+  Cx<T> *Z = fft_lines<T>(A, B, nr, n, ls, plan, tw_s, T(-1));
+  Cx<T> *Y = (Z == A) ? B : A;
+  for (int e = threadIdx.x; e < nr * nh; e += blockDim.x) {
+    const int r = (int)fdiv((uint32_t)e, plan.fnh), k = e - r * nh;
+    const Cx<T> zk = Z[r * ls + k];
+    const Cx<T> zm = Z[r * ls + (k == 0 ? 0 : n - k)];
+    Y[k * ls + 2 * r] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    Y[k * ls + 2 * r + 1] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
+  }
+  __syncthreads();
+  Cx<T> *R = fft_lines<T>(Y, Z, nh, n, ls, plan, tw_s, T(-1));
+  Cx<T> *out = spec + cz * n * nh;
+  for (int e = threadIdx.x; e < n * nh; e += blockDim.x) {
+    const int y = (int)fdiv((uint32_t)e, plan.fnh), k = e - y * nh;
+    out[e] = R[k * ls + y];
+  }
+}
+
+// Inverse of k_fft_xy_fwd: the y lines are transformed back, rows 2r and
+// 2r + 1 are packed as Z_k = A_k + i B_k (k <= n/2; conj(A_{n-k}) +
+// i conj(B_{n-k}) beyond), and the inverse x DFT gives the two real rows as
+// its real and imaginary parts, written to a planar field [comp][z][y][x].
+template <typename T>
+__global__ void __launch_bounds__(512) k_fft_xy_inv(T *field, const Cx<T> *__restrict__ spec,
+                                                    FftPlan plan, const T *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = n + 1, nh = n / 2 + 1, nr = n / 2;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + plan.ntw;
+  Cx<T> *B = A + nh * ls;
+  load_twiddles(tw_s, tw, plan.ntw);
+  const int64_t cz = blockIdx.x;
+  const Cx<T> *in = spec + cz * n * nh;
+  {
+    constexpr int U = 8;
+    const int total = n * nh;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+      Cx<T> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < total ? in[e] : Cx<T>{T(0), T(0)};
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= total) continue;
+        const int y = (int)fdiv((uint32_t)e, plan.fnh), k = e - y * nh;
+        A[k * ls + y] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  Cx<T> *Y = fft_lines<T>(A, B, nh, n, ls, plan, tw_s, T(1));
+  Cx<T> *Z = (Y == A) ? B : A;
+  for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+    const int r = (int)fdiv((uint32_t)e, plan.fn), k = e - r * n;
+    const int kk = k <= n / 2 ? k : n - k;
+    const Cx<T> a = Y[kk * ls + 2 * r], b = Y[kk * ls + 2 * r + 1];
+    Z[r * ls + k] = k <= n / 2 ? Cx<T>{a.x - b.y, a.y + b.x} : Cx<T>{a.x + b.y, -a.y + b.x};
+  }
+  __syncthreads();
+  Cx<T> *X = fft_lines<T>(Z, Y, nr, n, ls, plan, tw_s, T(1));
+  T *o = field + cz * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int y = (int)fdiv((uint32_t)e, plan.fn), x = e - y * n;
+    const Cx<T> v = X[(y >> 1) * ls + x];
+    o[e] = (y & 1) ? v.y : v.x;
+  }
+}
+
 // ------------------------------------------------------- z pass + Green
 // Lines along z for fixed y, TX = 2^LTX consecutive kx, all six components:
 // forward DFT, Green's function, inverse DFT.
@@ -610,9 +723,97 @@ __global__ void __launch_bounds__(256) k_spread(int Nt, const typename V4Of<T>::
   }
 }
 
+// FP32 spreading with 16-byte vector reductions (grids whose side n is a
+// multiple of 4): the same sums as k_spread, but each lane owns an aligned
+// quad of four x points of one grid row and adds its six components with
+// one red.global.add.v4.f32 each, so a bead issues a quarter of the atomic
+// operations.  The bead's x window [g0, g0 + P) is covered by the aligned
+// quads from a0 = 4 floor(g0 / 4); slots outside the window carry weight 0.
+constexpr int kMaxQ = (kMaxP + 6) / 4;
+
+__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(256) k_spread_v4(int Nt, const float4 *__restrict__ pos,
+                                                   const double *__restrict__ x, float *grid, int n,
+                                                   int P, float h, float alpha, float cnorm) {
+  __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
+  __shared__ int si[8][2][kMaxP];
+  __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
+  __shared__ int sxq[8][kMaxQ];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= Nt) return;
+  const float4 p = pos[i];
+  const int g0x = (int)floorf(p.x / h) - P / 2 + 1;
+  const int a0 = g0x >= 0 ? (g0x & ~3) : -((-g0x + 3) & ~3);  // 4 floor(g0x / 4)
+  const int nq = (g0x - a0 + P + 3) >> 2;                      // quads covering the window
+  for (int e = lane; e < 2 * P; e += 32) {
+    const int d = e / P, k = e - d * P;
+    const float pc = d == 0 ? p.y : p.z;
+    const int g = (int)floorf(pc / h) - P / 2 + 1 + k;
+    const float yv = float(g) * h - pc;
+    sw[warp][d][k] = expf(-alpha * yv * yv);
+    sy[warp][d][k] = yv;
+    si[warp][d][k] = ((g % n) + n) % n;
+  }
+  for (int sl = lane; sl < 4 * nq; sl += 32) {
+    const int g = a0 + sl, k = g - g0x;
+    const float yv = float(g) * h - p.x;
+    sxw[warp][sl] = (k >= 0 && k < P) ? expf(-alpha * yv * yv) : 0.f;
+    sxy[warp][sl] = yv;
+  }
+  for (int q = lane; q < nq; q += 32) sxq[warp][q] = (((a0 + 4 * q) % n) + n) % n;
+  __syncwarp();
+  const double *xr = x + (size_t)i * LDB;
+  const float F0 = (float)xr[0], F1 = (float)xr[1], F2 = (float)xr[2];
+  const float L0 = (float)xr[3], L1 = (float)xr[4], L2 = (float)xr[5];
+  const float r2i = 0.70710678118654752440f, r6i = 0.40824829046386301637f;
+  const float s0 = (float)xr[6], s1 = (float)xr[7], s2 = (float)xr[8], s3 = (float)xr[9],
+              s4 = (float)xr[10];
+  const float Sxx = r2i * s0 - r6i * s1, Syy = -r2i * s0 - r6i * s1, Szz = 2.f * r6i * s1;
+  const float Sxy = r2i * s2, Sxz = r2i * s3, Syz = r2i * s4;
+  const float D00 = Sxx, D01 = Sxy - 0.5f * L2, D02 = Sxz + 0.5f * L1;
+  const float D10 = Sxy + 0.5f * L2, D11 = Syy, D12 = Syz - 0.5f * L0;
+  const float D20 = Sxz - 0.5f * L1, D21 = Syz + 0.5f * L0, D22 = Szz;
+  const float ta = 2.f * alpha;
+  const int64_t n3 = (int64_t)n * n * n;
+  const int T = P * P * nq;
+  for (int t = lane; t < T; t += 32) {
+    const int q = t % nq, r = t / nq;
+    const int iy = r % P, iz = r / P;
+    const float wyz = cnorm * sw[warp][0][iy] * sw[warp][1][iz];
+    const float y1 = sy[warp][0][iy], y2 = sy[warp][1][iz];
+    const float b0 = D01 * y1 + D02 * y2, b1 = D11 * y1 + D12 * y2, b2 = D21 * y1 + D22 * y2;
+    float W[4], d0[4], d1[4], d2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float w = wyz * sxw[warp][4 * q + j];
+      const float y0 = sxy[warp][4 * q + j];
+      const float wd = ta * w;
+      W[j] = w;
+      d0[j] = wd * (D00 * y0 + b0);
+      d1[j] = wd * (D10 * y0 + b1);
+      d2[j] = wd * (D20 * y0 + b2);
+    }
+    float *g = grid + (((int64_t)si[warp][1][iz] * n + si[warp][0][iy]) * n + sxq[warp][q]);
+    red_add_v4(g, W[0] * F0, W[1] * F0, W[2] * F0, W[3] * F0);
+    red_add_v4(g + n3, W[0] * F1, W[1] * F1, W[2] * F1, W[3] * F1);
+    red_add_v4(g + 2 * n3, W[0] * F2, W[1] * F2, W[2] * F2, W[3] * F2);
+    red_add_v4(g + 3 * n3, d0[0], d0[1], d0[2], d0[3]);
+    red_add_v4(g + 4 * n3, d1[0], d1[1], d1[2], d1[3]);
+    red_add_v4(g + 5 * n3, d2[0], d2[1], d2[2], d2[3]);
+  }
+}
+
 // One warp per bead: u = h^3 sum W u_M, G_ab = h^3 sum 2 alpha W y_b u_D,a;
 // omega = (1/2) curl, e = sym G projected; added to the bead row of y.
-template <typename T>
+// PL: the six fields are planar [6][n^3] (from the fused FFT) instead of
+// interleaved [n^3][8].
+template <typename T, bool PL>
 __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::type *__restrict__ pos,
                                                 const T *__restrict__ grid, double *y, int n, int P,
                                                 T h, T alpha, T cnorm_h3) {
@@ -643,7 +844,14 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
     const T W = sw[warp][0][ix] * sw[warp][1][iy] * sw[warp][2][iz];
     const T y0 = sy[warp][0][ix], y1 = sy[warp][1][iy], y2 = sy[warp][2][iz];
     T g6[6];
-    load6<T>(grid + ((((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * n + si[warp][0][ix]) << 3), g6);
+    const int64_t gi = ((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * n + si[warp][0][ix];
+    if (PL) {
+      const int64_t n3 = (int64_t)n * n * n;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) g6[c] = grid[c * n3 + gi];
+    } else {
+      load6<T>(grid + (gi << 3), g6);
+    }
     const T u0 = g6[0], u1 = g6[1], u2 = g6[2], d0 = g6[3], d1 = g6[4], d2 = g6[5];
     acc[0] += W * u0;
     acc[1] += W * u1;
@@ -659,6 +867,102 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
     acc[9] += d2 * w0;  // G_20
     acc[10] += d2 * w1; // G_21
     acc[11] += d2 * w2; // G_22
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  if (lane != 0) return;
+  double a_[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a_[k] = (double)acc[k] * (double)cnorm_h3;
+  const double G00 = a_[3], G01 = a_[4], G02 = a_[5], G10 = a_[6], G11 = a_[7], G12 = a_[8],
+               G20 = a_[9], G21 = a_[10], G22 = a_[11];
+  const double r2i = 0.70710678118654752440, r6i = 0.40824829046386301637,
+               s2 = 1.41421356237309504880;
+  double *yr = y + (size_t)i * LDB;
+  yr[0] += a_[0];
+  yr[1] += a_[1];
+  yr[2] += a_[2];
+  yr[3] += 0.5 * (G21 - G12);
+  yr[4] += 0.5 * (G02 - G20);
+  yr[5] += 0.5 * (G10 - G01);
+  yr[6] += r2i * (G00 - G11);
+  yr[7] += r6i * (2.0 * G22 - G00 - G11);
+  yr[8] += s2 * 0.5 * (G01 + G10);
+  yr[9] += s2 * 0.5 * (G02 + G20);
+  yr[10] += s2 * 0.5 * (G12 + G21);
+}
+
+// FP32 interpolation from planar fields [6][n^3] (n a multiple of 4): the
+// sums of k_interp, with each lane reading an aligned quad of four x points
+// of one grid row per field (six 16-byte loads); slots outside the bead's x
+// window carry weight 0 (the quads of k_spread_v4).
+__global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restrict__ pos,
+                                                   const float *__restrict__ field, double *y, int n,
+                                                   int P, float h, float alpha, float cnorm_h3) {
+  __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
+  __shared__ int si[8][2][kMaxP];
+  __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
+  __shared__ int sxq[8][kMaxQ];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= Nt) return;
+  const float4 p = pos[i];
+  const int g0x = (int)floorf(p.x / h) - P / 2 + 1;
+  const int a0 = g0x >= 0 ? (g0x & ~3) : -((-g0x + 3) & ~3);
+  const int nq = (g0x - a0 + P + 3) >> 2;
+  for (int e = lane; e < 2 * P; e += 32) {
+    const int d = e / P, k = e - d * P;
+    const float pc = d == 0 ? p.y : p.z;
+    const int g = (int)floorf(pc / h) - P / 2 + 1 + k;
+    const float yv = float(g) * h - pc;
+    sw[warp][d][k] = expf(-alpha * yv * yv);
+    sy[warp][d][k] = yv;
+    si[warp][d][k] = ((g % n) + n) % n;
+  }
+  for (int sl = lane; sl < 4 * nq; sl += 32) {
+    const int g = a0 + sl, k = g - g0x;
+    const float yv = float(g) * h - p.x;
+    sxw[warp][sl] = (k >= 0 && k < P) ? expf(-alpha * yv * yv) : 0.f;
+    sxy[warp][sl] = yv;
+  }
+  for (int q = lane; q < nq; q += 32) sxq[warp][q] = (((a0 + 4 * q) % n) + n) % n;
+  __syncwarp();
+  const float ta = 2.f * alpha;
+  const int64_t n3 = (int64_t)n * n * n;
+  float acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+  const int T = P * P * nq;
+  for (int t = lane; t < T; t += 32) {
+    const int q = t % nq, r = t / nq;
+    const int iy = r % P, iz = r / P;
+    const float wyz = sw[warp][0][iy] * sw[warp][1][iz];
+    const float y1 = sy[warp][0][iy], y2 = sy[warp][1][iz];
+    const float *g = field + (((int64_t)si[warp][1][iz] * n + si[warp][0][iy]) * n + sxq[warp][q]);
+    float4 f[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) f[c] = *(const float4 *)(g + c * n3);
+    float W[4], Y0[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      W[j] = wyz * sxw[warp][4 * q + j];
+      Y0[j] = sxy[warp][4 * q + j];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      acc[c] += W[0] * f[c].x + W[1] * f[c].y + W[2] * f[c].z + W[3] * f[c].w;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float4 d = f[3 + a];
+      const float s = ta * (W[0] * d.x + W[1] * d.y + W[2] * d.z + W[3] * d.w);
+      const float s0 = ta * (W[0] * Y0[0] * d.x + W[1] * Y0[1] * d.y + W[2] * Y0[2] * d.z +
+                             W[3] * Y0[3] * d.w);
+      acc[3 + 3 * a] += s0;      // G_a0
+      acc[4 + 3 * a] += s * y1;  // G_a1
+      acc[5 + 3 * a] += s * y2;  // G_a2
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
@@ -783,8 +1087,13 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   {
   ProfScope ps(c, PG_SPREAD);
   FSD_CUDA(cudaMemsetAsync(op.grid.p, 0, gbytes, c.stream));
-  k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
-                                                      alpha, (T)cn);
+  if (sizeof(T) == 4 && n % 4 == 0)
+    k_spread_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p, x,
+                                                         (float *)op.grid.p, n, P, (float)h,
+                                                         (float)alpha, (float)cn);
+  else
+    k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
+                                                        alpha, (T)cn);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   }
@@ -795,8 +1104,21 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const int threads = 256;
   const int ntw = plan.ntw;
   Cx<T> *spec = (Cx<T> *)op.spec.p;
-  // x forward
-  {
+  // FP32 planes that fit in shared memory with their ping-pong copy take the
+  // fused x + y kernels (interpolation then reads planar fields); otherwise
+  // separate x and y passes (interleaved fields).
+  const size_t sm_xy = (size_t)(ntw + 2 * nh * (n + 1)) * sizeof(Cx<T>);
+  const bool fused = sizeof(T) == 4 && sm_xy <= (size_t)227 * 1024;
+  const int LTXy = sizeof(T) == 8 ? 3 : 4;
+  const int TXy = 1 << LTXy;
+  const size_t smy = (size_t)(ntw + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
+  const int blocks_y = 6 * n * ceil_div(nh, TXy);
+  if (fused) {
+    set_smem<T>((const void *)k_fft_xy_fwd<T>, sm_xy);
+    k_fft_xy_fwd<T><<<6 * n, 512, sm_xy, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+  } else {
     const int NL = 4;
     size_t sm = (size_t)(ntw + 2 * 3 * NL * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_fwd<T>, sm);
@@ -804,15 +1126,11 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     k_fft_x_fwd<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p, NL);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
+    set_smem<T>((const void *)k_fft_y<T>, smy);
+    k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(-1));
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
   }
-  const int LTXy = sizeof(T) == 8 ? 3 : 4;
-  const int TXy = 1 << LTXy;
-  const size_t smy = (size_t)(ntw + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
-  set_smem<T>((const void *)k_fft_y<T>, smy);
-  const int blocks_y = 6 * n * ceil_div(nh, TXy);
-  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(-1));
-  FSD_LAUNCHED(c);
-  FSD_CUDA(cudaGetLastError());
   {
     const int LTX = 2;  // four kx columns: 6 x 4 lines keep 4 CTAs per SM (FP32)
     const int TX = 1 << LTX;
@@ -824,10 +1142,15 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
-  k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
-  FSD_LAUNCHED(c);
-  FSD_CUDA(cudaGetLastError());
-  {
+  if (fused) {
+    set_smem<T>((const void *)k_fft_xy_inv<T>, sm_xy);
+    k_fft_xy_inv<T><<<6 * n, 512, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+  } else {
+    k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
     const int NL = 4;
     size_t sm = (size_t)(ntw + 2 * 3 * NL * (n + 1)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_inv<T>, sm);
@@ -839,8 +1162,19 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   }
   ProfScope ps(c, PG_INTERP);
   const double h3 = c.h * c.h * c.h;
-  k_interp<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P, h,
-                                                      alpha, (T)(cn * h3));
+  const bool planar = sizeof(T) == 4 &&
+                      (size_t)(make_plan(n, nullptr).ntw + 2 * (n / 2 + 1) * (n + 1)) * sizeof(Cx<T>) <=
+                          (size_t)227 * 1024;
+  if (planar && n % 4 == 0)
+    k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p,
+                                                         (const float *)op.gout.p, y, n, P,
+                                                         (float)h, (float)alpha, (float)(cn * h3));
+  else if (planar)
+    k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
+                                                              h, alpha, (T)(cn * h3));
+  else
+    k_interp<T, false><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
+                                                               P, h, alpha, (T)(cn * h3));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -1075,7 +1409,7 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, 1.f);
   k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * (n + 1)) * sizeof(Cx<float>),
                        st>>>(gout, spec, plan, tw, 4);
-  k_interp<float><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, gout, y, n, P, (float)h, (float)alpha,
+  k_interp<float, false><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, gout, y, n, P, (float)h, (float)alpha,
                                                (float)(cn * h * h * h));
   k_na_stage_out<<<(nb + 127) / 128, 128, 0, st>>>(nb, y, out);
   if (cudaGetLastError() != cudaSuccess) return FSD_ECUDA;

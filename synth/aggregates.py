@@ -312,10 +312,12 @@ def compress_suspension(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12,
 # ---------------------------------------------------------------------------
 
 
-def compress_mixed(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12, step=0.98, max_iter=4000):
+def compress_mixed(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12, step=0.98, max_iter=400):
     """compress_suspension for shapes of different bead counts (a list of
     (n_b, 3) offset arrays): random sequential insertion at phi0, then affine
-    compression of the body centres with soft-repulsion relaxation."""
+    compression of the body centres with soft-repulsion relaxation.  Large
+    branched aggregates can jam below the requested phi; the densest packing
+    reached is then returned (its box L gives the actual phi)."""
     rng = np.random.default_rng(seed)
     N = len(shapes)
     nbs = np.array([len(s_) for s_ in shapes])
@@ -349,12 +351,12 @@ def compress_mixed(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12, step=0.98, ma
         kx = np.einsum("nj,nj->n", k, off_)[:, None]
         return off_ * ct + np.cross(k, off_) * st + k * kx * (1 - ct)
 
-    while True:
+    def relax(C, off):
         for _ in range(max_iter):
             Pb = C[body] + off
             i, j, d = _close_pairs(Pb, body, L, target)
             if len(i) == 0:
-                break
+                return C, off, True
             r = np.linalg.norm(d, axis=1)
             f = ((push - r) / np.maximum(r, 1e-12))[:, None] * d
             F = np.zeros((N, 3))
@@ -365,13 +367,24 @@ def compress_mixed(shapes, phi, seed, a=1.0, h_gen=0.1, phi0=0.12, step=0.98, ma
             np.add.at(T, body[i], np.cross(off[i], -0.5 * f))
             C = (C + 0.6 * F / np.sqrt(nbs)[:, None]) % L
             off = rotate(off, 0.6 * T / (inertia[:, None] + a * a))
-        else:
-            raise RuntimeError("relaxation stalled at L=%.3f" % L)
-        if L <= Lt * (1 + 1e-12):
-            break
+        return C, off, False
+
+    # a compression whose relaxation stalls is undone and retried with half
+    # the strain
+    C, off, ok = relax(C, off)
+    if not ok:
+        raise RuntimeError("relaxation stalled at L=%.3f" % L)
+    while L > Lt * (1 + 1e-12):
         Ln = max(L * step, Lt)
+        C0, off0, L0 = C.copy(), off.copy(), L
         C = C * (Ln / L)
         L = Ln
+        C, off, ok = relax(C, off)
+        if not ok:
+            C, off, L = C0, off0, L0
+            step = 1.0 - 0.5 * (1.0 - step)
+            if step > 1.0 - 1e-3:
+                break  # jammed: keep the densest packing reached
     Pb = C[body] + off
     assert len(_close_pairs(Pb, body, L, contact)[0]) == 0
     return Pb, body.astype(np.int32), L
@@ -422,12 +435,13 @@ def batch_workload(n_sys, seed, n_lo=256, n_hi=8192, phi_lo=0.05, phi_hi=0.3, si
                    size_hi=64):
     """Independent suspensions: bead counts round(exp(U[ln n_lo, ln n_hi])),
     volume fractions U[phi_lo, phi_hi], aggregate sizes U{size_lo..size_hi}.
-    Returns a list of (bead_pos, agg_id, L, phi)."""
+    Returns a list of (bead_pos, agg_id, L, phi), phi the volume fraction
+    reached (below the drawn one where the aggregates jammed first)."""
     rng = np.random.default_rng(seed)
     n = np.rint(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=n_sys))).astype(int)
     phi = rng.uniform(phi_lo, phi_hi, size=n_sys)
     out = []
     for s in range(n_sys):
         pos, body, L = mixed_suspension(int(n[s]), float(phi[s]), seed * 1000 + s, size_lo, size_hi)
-        out.append((pos, body, L, float(phi[s])))
+        out.append((pos, body, L, len(pos) * 4.0 / 3.0 * math.pi / L ** 3))
     return out
