@@ -87,15 +87,25 @@ struct FftPlan {
   FftStage st[kMaxStages];
 };
 
-// Stages 4^a 2^b 3^c 5^d; per stage the twiddles exp(-2 pi i r k / (Ns R)),
-// r = 1..R-1, k < Ns, stored contiguously (complex) from toff.
-static FftPlan make_plan(int n, std::vector<double> *tw) {
+// Stages 16^a 9^b 8^c 4^d 2^e 3^f 5^g with big_radix (FP32: the largest
+// register DFTs first, fewer passes through shared memory), else
+// 4^d 2^e 3^f 5^g (FP64: the register cost of a 16-point DFT in doubles
+// costs more occupancy than the saved passes gain); per stage the twiddles
+// exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns, stored contiguously
+// (complex) from toff.
+static FftPlan make_plan(int n, std::vector<double> *tw, bool big_radix) {
   FftPlan p{};
   p.n = n;
   p.fn = make_fastdiv(n);
   p.fnh = make_fastdiv(n / 2 + 1);
   int m = n, k = 0;
   std::vector<int> radices;
+  if (big_radix)
+    for (int f : {16, 9, 8})
+      while (m % f == 0) {
+        radices.push_back(f);
+        m /= f;
+      }
   while (m % 4 == 0) {
     radices.push_back(4);
     m /= 4;
@@ -138,10 +148,19 @@ bool fft_size_ok(int n) {
   return m == 1;
 }
 
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void dft_two_level(Cx<T> *v, T sg);
+
 // Small DFT of size R in registers, sign sg (-1 forward, +1 inverse).
 template <typename T, int R>
 __device__ __forceinline__ void dft_small(Cx<T> *v, T sg) {
-  if (R == 2) {
+  if constexpr (R == 16) {
+    dft_two_level<T, 4, 4>(v, sg);
+  } else if constexpr (R == 9) {
+    dft_two_level<T, 3, 3>(v, sg);
+  } else if constexpr (R == 8) {
+    dft_two_level<T, 2, 4>(v, sg);
+  } else if (R == 2) {
     Cx<T> a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
@@ -178,6 +197,71 @@ __device__ __forceinline__ void dft_small(Cx<T> *v, T sg) {
   }
 }
 
+// exp(sg 2 pi i m / R) for R in {8, 9, 16}; m is a compile-time constant
+// after unrolling, so the table reads fold away.
+template <typename T, int R>
+__device__ __forceinline__ Cx<T> root_of_unity(int m, T sg) {
+  constexpr double c16[16] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
+                              0.38268343236508977173, 0.0, -0.38268343236508977173,
+                              -0.70710678118654752440, -0.92387953251128675613, -1.0,
+                              -0.92387953251128675613, -0.70710678118654752440,
+                              -0.38268343236508977173, 0.0, 0.38268343236508977173,
+                              0.70710678118654752440, 0.92387953251128675613};
+  constexpr double s16[16] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
+                              0.92387953251128675613, 1.0, 0.92387953251128675613,
+                              0.70710678118654752440, 0.38268343236508977173, 0.0,
+                              -0.38268343236508977173, -0.70710678118654752440,
+                              -0.92387953251128675613, -1.0, -0.92387953251128675613,
+                              -0.70710678118654752440, -0.38268343236508977173};
+  constexpr double c9[9] = {1.0, 0.76604444311897803520, 0.17364817766693034885, -0.5,
+                            -0.93969262078590838405, -0.93969262078590838405, -0.5,
+                            0.17364817766693034885, 0.76604444311897803520};
+  constexpr double s9[9] = {0.0, 0.64278760968653932632, 0.98480775301220805936,
+                            0.86602540378443864676, 0.34202014332566873304,
+                            -0.34202014332566873304, -0.86602540378443864676,
+                            -0.98480775301220805936, -0.64278760968653932632};
+  m %= R;
+  if (R == 9) return {T(c9[m]), sg * T(s9[m])};
+  const int q = m * (16 / R);  // R = 8 or 16
+  return {T(c16[q]), sg * T(s16[q])};
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(Cx<T> *v, T sg);
+
+// DFT of size R1 R2 in registers (Cooley-Tukey): with n = R2 n1 + n2 and
+// k = k1 + R1 k2, X_k = sum_n2 w_R^(n2 k1) w_R2^(n2 k2) [DFT_R1 over n1 of
+// x_(R2 n1 + n2)]_k1.
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void dft_two_level(Cx<T> *v, T sg) {
+  constexpr int R = R1 * R2;
+  Cx<T> y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    Cx<T> t[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
+    dft_small<T, R1>(t, sg);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) y[n2 * R1 + k1] = cmul(t[k1], root_of_unity<T, R>(n2 * k1, sg));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    Cx<T> t[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
+    dft_small<T, R2>(t, sg);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[k2];
+  }
+}
+
+// Line buffers in shared memory store element i of a line at i + i/16: a
+// radix-16 stage writes with a stride of 16 elements, which the padding
+// spreads over distinct banks.  fft_ls(n) is the padded line length.
+__host__ __device__ __forceinline__ int fft_ls(int n) { return n + (n - 1) / 16 + 1; }
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
 // One Stockham stage of radix R over nl lines stored with stride ls:
 //   for butterfly j < n/R, k = j mod Ns, g = j div Ns:
 //   v_r = in[j + r n/R] w_(r,k),  DFT_R,  out[g Ns R + k + r Ns] = v_r.
@@ -193,19 +277,20 @@ __device__ __forceinline__ void stockham_stage(const Cx<T> *in, Cx<T> *out, int 
     const int j = b - line * nb;
     const int g = (int)fdiv((uint32_t)j, st.ns);
     const int k = j - g * Ns;
-    const Cx<T> *src = in + line * ls + j;
+    const Cx<T> *src = in + line * ls;
     Cx<T> v[R];
-    v[0] = src[0];
+    v[0] = src[fpad(j)];
 #pragma unroll
     for (int r = 1; r < R; ++r) {
       Cx<T> w = tw[(r - 1) * Ns + k];
       w.y *= -sg;  // tables hold the forward twiddles
-      v[r] = cmul(src[r * nb], w);
+      v[r] = cmul(src[fpad(j + r * nb)], w);
     }
     dft_small<T, R>(v, sg);
-    Cx<T> *dst = out + line * ls + g * Ns * R + k;
+    Cx<T> *dst = out + line * ls;
+    const int d0 = g * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst[fpad(d0 + r * Ns)] = v[r];
   }
 }
 
@@ -217,7 +302,21 @@ __device__ Cx<T> *fft_lines(Cx<T> *A, Cx<T> *B, int nl, int n, int ls, const Fft
   Cx<T> *in = A, *out = B;
   for (int s = 0; s < plan.nst; ++s) {
     const FftStage &st = plan.st[s];
-    if (st.R == 4)
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {  // FP32 plans use the register DFTs
+      done = true;
+      if (st.R == 16)
+        stockham_stage<T, 16>(in, out, nl, n, ls, st, tws, sg);
+      else if (st.R == 9)
+        stockham_stage<T, 9>(in, out, nl, n, ls, st, tws, sg);
+      else if (st.R == 8)
+        stockham_stage<T, 8>(in, out, nl, n, ls, st, tws, sg);
+      else
+        done = false;
+    }
+    if (done)
+      ;
+    else if (st.R == 4)
       stockham_stage<T, 4>(in, out, nl, n, ls, st, tws, sg);
     else if (st.R == 2)
       stockham_stage<T, 2>(in, out, nl, n, ls, st, tws, sg);
@@ -275,7 +374,7 @@ __global__ void k_fft_x_fwd(const T *__restrict__ grid, Cx<T> *spec, FftPlan pla
                             const T *__restrict__ tw, int NL) {
   // grid: planar [6][n^3]
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int NLL = 3 * NL;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
@@ -304,7 +403,7 @@ __global__ void k_fft_x_fwd(const T *__restrict__ grid, Cx<T> *spec, FftPlan pla
         if (e >= total) continue;
         const int l = (int)fdiv((uint32_t)e, plan.fn), xx = e - l * n;
 #pragma unroll
-        for (int p = 0; p < 3; ++p) A[(l * 3 + p) * ls + xx] = {v[u][p], v[u][p + 3]};
+        for (int p = 0; p < 3; ++p) A[(l * 3 + p) * ls + fpad(xx)] = {v[u][p], v[u][p + 3]};
       }
     }
   }
@@ -316,8 +415,8 @@ __global__ void k_fft_x_fwd(const T *__restrict__ grid, Cx<T> *spec, FftPlan pla
     const int l = lp / 3, p = lp - 3 * l;
     const int64_t row = row0 + l;
     if (row >= nrows) continue;
-    const Cx<T> zk = Z[lp * ls + k];
-    const Cx<T> zm = Z[lp * ls + (k == 0 ? 0 : n - k)];
+    const Cx<T> zk = Z[lp * ls + fpad(k)];
+    const Cx<T> zm = Z[lp * ls + fpad(k == 0 ? 0 : n - k)];
     // (Z_k - conj Z_{n-k}) / (2i): (p + iq)/(2i) = (q - ip)/2
     spec[p * cs + row * nh + k] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
     spec[(p + 3) * cs + row * nh + k] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
@@ -330,7 +429,7 @@ template <typename T>
 __global__ void k_fft_x_inv(T *grid, const Cx<T> *__restrict__ spec, FftPlan plan,
                             const T *__restrict__ tw, int NL) {
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int NLL = 3 * NL;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
@@ -365,7 +464,7 @@ __global__ void k_fft_x_inv(T *grid, const Cx<T> *__restrict__ spec, FftPlan pla
         if (e >= total) continue;
         const int lp = (int)fdiv((uint32_t)e, plan.fn), k = e - lp * n;
         // k <= n/2: a + i b;  beyond: conj(a) + i conj(b) of the mirrored bin
-        A[lp * ls + k] = k <= n / 2 ? Cx<T>{a[u].x - b[u].y, a[u].y + b[u].x}
+        A[lp * ls + fpad(k)] = k <= n / 2 ? Cx<T>{a[u].x - b[u].y, a[u].y + b[u].x}
                                     : Cx<T>{a[u].x + b[u].y, -a[u].y + b[u].x};
       }
     }
@@ -379,7 +478,7 @@ __global__ void k_fft_x_inv(T *grid, const Cx<T> *__restrict__ spec, FftPlan pla
     T v[6];
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      const Cx<T> z = Z[(l * 3 + p) * ls + xx];
+      const Cx<T> z = Z[(l * 3 + p) * ls + fpad(xx)];
       v[p] = z.x;
       v[p + 3] = z.y;
     }
@@ -392,7 +491,7 @@ __global__ void k_fft_x_inv(T *grid, const Cx<T> *__restrict__ spec, FftPlan pla
 template <typename T>
 __global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int LTX, T sg) {
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int TX = 1 << LTX;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
@@ -418,7 +517,7 @@ __global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int e = e0 + u * blockDim.x;
-        if (e < total) A[(e & (TX - 1)) * ls + (e >> LTX)] = v[u];
+        if (e < total) A[(e & (TX - 1)) * ls + fpad(e >> LTX)] = v[u];
       }
     }
   }
@@ -427,7 +526,7 @@ __global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int
   for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
     const int yy = e >> LTX, t = e & (TX - 1);
     const int kx = kx0 + t;
-    if (kx < nh) base[(int64_t)yy * nh + kx] = Z[t * ls + yy];
+    if (kx < nh) base[(int64_t)yy * nh + kx] = Z[t * ls + fpad(yy)];
   }
 }
 
@@ -443,7 +542,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_fft_xy_fwd(const T *__restrict__ grid, Cx<T> *spec,
                                                     FftPlan plan, const T *__restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, nh = n / 2 + 1, nr = n / 2;
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1, nr = n / 2;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;  // nh lines of ls
   Cx<T> *B = A + nh * ls;
@@ -468,7 +567,7 @@ __global__ void __launch_bounds__(512) k_fft_xy_fwd(const T *__restrict__ grid, 
         const int e = e0 + u * blockDim.x;
         if (e >= total) continue;
         const int r = (int)fdiv((uint32_t)e, plan.fn), x = e - r * n;
-        A[r * ls + x] = {va[u], vb[u]};
+        A[r * ls + fpad(x)] = {va[u], vb[u]};
       }
     }
   }
@@ -477,17 +576,17 @@ __global__ void __launch_bounds__(512) k_fft_xy_fwd(const T *__restrict__ grid, 
   Cx<T> *Y = (Z == A) ? B : A;
   for (int e = threadIdx.x; e < nr * nh; e += blockDim.x) {
     const int r = (int)fdiv((uint32_t)e, plan.fnh), k = e - r * nh;
-    const Cx<T> zk = Z[r * ls + k];
-    const Cx<T> zm = Z[r * ls + (k == 0 ? 0 : n - k)];
-    Y[k * ls + 2 * r] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
-    Y[k * ls + 2 * r + 1] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
+    const Cx<T> zk = Z[r * ls + fpad(k)];
+    const Cx<T> zm = Z[r * ls + fpad(k == 0 ? 0 : n - k)];
+    Y[k * ls + fpad(2 * r)] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    Y[k * ls + fpad(2 * r + 1)] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
   }
   __syncthreads();
   Cx<T> *R = fft_lines<T>(Y, Z, nh, n, ls, plan, tw_s, T(-1));
   Cx<T> *out = spec + cz * n * nh;
   for (int e = threadIdx.x; e < n * nh; e += blockDim.x) {
     const int y = (int)fdiv((uint32_t)e, plan.fnh), k = e - y * nh;
-    out[e] = R[k * ls + y];
+    out[e] = R[k * ls + fpad(y)];
   }
 }
 
@@ -499,7 +598,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_fft_xy_inv(T *field, const Cx<T> *__restrict__ spec,
                                                     FftPlan plan, const T *__restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, nh = n / 2 + 1, nr = n / 2;
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1, nr = n / 2;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + nh * ls;
@@ -521,7 +620,7 @@ __global__ void __launch_bounds__(512) k_fft_xy_inv(T *field, const Cx<T> *__res
         const int e = e0 + u * blockDim.x;
         if (e >= total) continue;
         const int y = (int)fdiv((uint32_t)e, plan.fnh), k = e - y * nh;
-        A[k * ls + y] = v[u];
+        A[k * ls + fpad(y)] = v[u];
       }
     }
   }
@@ -531,15 +630,15 @@ __global__ void __launch_bounds__(512) k_fft_xy_inv(T *field, const Cx<T> *__res
   for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
     const int r = (int)fdiv((uint32_t)e, plan.fn), k = e - r * n;
     const int kk = k <= n / 2 ? k : n - k;
-    const Cx<T> a = Y[kk * ls + 2 * r], b = Y[kk * ls + 2 * r + 1];
-    Z[r * ls + k] = k <= n / 2 ? Cx<T>{a.x - b.y, a.y + b.x} : Cx<T>{a.x + b.y, -a.y + b.x};
+    const Cx<T> a = Y[kk * ls + fpad(2 * r)], b = Y[kk * ls + fpad(2 * r + 1)];
+    Z[r * ls + fpad(k)] = k <= n / 2 ? Cx<T>{a.x - b.y, a.y + b.x} : Cx<T>{a.x + b.y, -a.y + b.x};
   }
   __syncthreads();
   Cx<T> *X = fft_lines<T>(Z, Y, nr, n, ls, plan, tw_s, T(1));
   T *o = field + cz * n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int y = (int)fdiv((uint32_t)e, plan.fn), x = e - y * n;
-    const Cx<T> v = X[(y >> 1) * ls + x];
+    const Cx<T> v = X[(y >> 1) * ls + fpad(x)];
     o[e] = (y & 1) ? v.y : v.x;
   }
 }
@@ -551,7 +650,7 @@ template <typename T>
 __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
                               const T *__restrict__ green, int LTX) {
   extern __shared__ unsigned char smem_raw[];
-  const int n = plan.n, ls = n + 1, nh = n / 2 + 1;
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int TX = 1 << LTX;
   const int NLn = 6 * TX;
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
@@ -584,7 +683,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
         if (e >= total) continue;
         const int t = e & (TX - 1), rest = e >> LTX;
         const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
-        A[(comp * TX + t) * ls + zz] = v[u];
+        A[(comp * TX + t) * ls + fpad(zz)] = v[u];
       }
     }
   }
@@ -600,8 +699,8 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     Cx<T> gF[3], gD[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      gF[d] = Z[(d * TX + t) * ls + zz];
-      gD[d] = Z[((d + 3) * TX + t) * ls + zz];
+      gF[d] = Z[(d * TX + t) * ls + fpad(zz)];
+      gD[d] = Z[((d + 3) * TX + t) * ls + fpad(zz)];
     }
     Cx<T> oM[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     Cx<T> oD[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
@@ -627,8 +726,8 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      Z[(d * TX + t) * ls + zz] = oM[d];
-      Z[((d + 3) * TX + t) * ls + zz] = oD[d];
+      Z[(d * TX + t) * ls + fpad(zz)] = oM[d];
+      Z[((d + 3) * TX + t) * ls + fpad(zz)] = oD[d];
     }
   }
   __syncthreads();
@@ -639,7 +738,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     const int t = e & (TX - 1), rest = e >> LTX;
     const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
     const int kx = kx0 + t;
-    if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + zz];
+    if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + fpad(zz)];
   }
 }
 
@@ -935,6 +1034,7 @@ __global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restr
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = 0.f;
   const int T = P * P * nq;
+#pragma unroll 2
   for (int t = lane; t < T; t += 32) {
     const int q = t % nq, r = t / nq;
     const int iy = r % P, iz = r / P;
@@ -943,7 +1043,7 @@ __global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restr
     const float *g = field + (((int64_t)si[warp][1][iz] * n + si[warp][0][iy]) * n + sxq[warp][q]);
     float4 f[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) f[c] = *(const float4 *)(g + c * n3);
+    for (int c = 0; c < 6; ++c) f[c] = __ldg((const float4 *)(g + c * n3));
     float W[4], Y0[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1021,8 +1121,9 @@ void build_wave(Ctx &c) {
   c.op32.spec.alloc(ssize);
   // per-stage twiddle tables of the plan
   std::vector<double> tw;
-  make_plan(n, &tw);
+  make_plan(n, &tw, false);
   upload(c.op64.twiddle, tw);
+  make_plan(n, &tw, true);
   upload(c.op32.twiddle, tw);
   // Green table by m = kx^2 + ky^2 + kz^2
   const int hm = n / 2;
@@ -1099,7 +1200,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   }
   {
   ProfScope ps(c, PG_FFT);
-  FftPlan plan = make_plan(n, nullptr);
+  FftPlan plan = make_plan(n, nullptr, sizeof(T) == 4);
   const int nh = n / 2 + 1;
   const int threads = 256;
   const int ntw = plan.ntw;
@@ -1107,11 +1208,11 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   // FP32 planes that fit in shared memory with their ping-pong copy take the
   // fused x + y kernels (interpolation then reads planar fields); otherwise
   // separate x and y passes (interleaved fields).
-  const size_t sm_xy = (size_t)(ntw + 2 * nh * (n + 1)) * sizeof(Cx<T>);
+  const size_t sm_xy = (size_t)(ntw + 2 * nh * fft_ls(n)) * sizeof(Cx<T>);
   const bool fused = sizeof(T) == 4 && sm_xy <= (size_t)227 * 1024;
   const int LTXy = sizeof(T) == 8 ? 3 : 4;
   const int TXy = 1 << LTXy;
-  const size_t smy = (size_t)(ntw + 2 * TXy * (n + 1)) * sizeof(Cx<T>);
+  const size_t smy = (size_t)(ntw + 2 * TXy * fft_ls(n)) * sizeof(Cx<T>);
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
   if (fused) {
     set_smem<T>((const void *)k_fft_xy_fwd<T>, sm_xy);
@@ -1120,7 +1221,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     FSD_CUDA(cudaGetLastError());
   } else {
     const int NL = 4;
-    size_t sm = (size_t)(ntw + 2 * 3 * NL * (n + 1)) * sizeof(Cx<T>);
+    size_t sm = (size_t)(ntw + 2 * 3 * NL * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_fwd<T>, sm);
     int blocks = ceil_div((int64_t)n * n, NL);
     k_fft_x_fwd<T><<<blocks, threads, sm, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p, NL);
@@ -1134,7 +1235,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   {
     const int LTX = 2;  // four kx columns: 6 x 4 lines keep 4 CTAs per SM (FP32)
     const int TX = 1 << LTX;
-    size_t sm = (size_t)(ntw + 2 * 6 * TX * (n + 1)) * sizeof(Cx<T>);
+    size_t sm = (size_t)(ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_z_green<T>, sm);
     int blocks = n * ceil_div(nh, TX);
     k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p, op.green.p,
@@ -1152,7 +1253,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     const int NL = 4;
-    size_t sm = (size_t)(ntw + 2 * 3 * NL * (n + 1)) * sizeof(Cx<T>);
+    size_t sm = (size_t)(ntw + 2 * 3 * NL * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_inv<T>, sm);
     int blocks = ceil_div((int64_t)n * n, NL);
     k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p, NL);
@@ -1163,7 +1264,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   ProfScope ps(c, PG_INTERP);
   const double h3 = c.h * c.h * c.h;
   const bool planar = sizeof(T) == 4 &&
-                      (size_t)(make_plan(n, nullptr).ntw + 2 * (n / 2 + 1) * (n + 1)) * sizeof(Cx<T>) <=
+                      (size_t)(make_plan(n, nullptr, true).ntw + 2 * (n / 2 + 1) * fft_ls(n)) * sizeof(Cx<T>) <=
                           (size_t)227 * 1024;
   if (planar && n % 4 == 0)
     k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p,
@@ -1398,16 +1499,16 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   k_spread<float><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, x, gridp, n, P, (float)h, (float)alpha,
                                                (float)cn);
   const int ntw = plan.ntw;
-  k_fft_x_fwd<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * (n + 1)) * sizeof(Cx<float>),
+  k_fft_x_fwd<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gridp, spec, plan, tw, 4);
   const int blocks_y = 6 * n * ((nh + 15) / 16);
-  const size_t smy = (size_t)(ntw + 2 * 16 * (n + 1)) * sizeof(Cx<float>);
+  const size_t smy = (size_t)(ntw + 2 * 16 * fft_ls(n)) * sizeof(Cx<float>);
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, -1.f);
   k_fft_z_green<float><<<n * ((nh + 3) / 4), threads,
-                         (ntw + 2 * 6 * 4 * (n + 1)) * sizeof(Cx<float>), st>>>(spec, plan, tw,
+                         (ntw + 2 * 6 * 4 * fft_ls(n)) * sizeof(Cx<float>), st>>>(spec, plan, tw,
                                                                                 green, 2);
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, 1.f);
-  k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * (n + 1)) * sizeof(Cx<float>),
+  k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gout, spec, plan, tw, 4);
   k_interp<float, false><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, gout, y, n, P, (float)h, (float)alpha,
                                                (float)(cn * h * h * h));
