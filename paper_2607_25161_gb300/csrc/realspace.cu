@@ -615,7 +615,7 @@ __device__ __forceinline__ void load_packed<double>(const double *__restrict__ p
 // shuffles and its first lane writes the bead row:
 //   y_i = sum_j M_r(x_i - x_j) x_j + M_self,r x_i [+ (dU + dOm x r_i, dOm, 0)]
 template <typename T, int G>
-__global__ void __launch_bounds__(256, 3) k_realspace(
+__global__ void __launch_bounds__(256, 4) k_realspace(
     int Nt, const T *__restrict__ packed, const int *__restrict__ nbr,
     const int *__restrict__ ncnt, int cap, const double *__restrict__ x, double *__restrict__ y,
     const T *__restrict__ tab_g, int nint, T inv_h, T L, T a, T c8, T self_t, T self_r,

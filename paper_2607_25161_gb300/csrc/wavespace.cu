@@ -539,7 +539,7 @@ __global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int
 // They are transposed into nh = n/2 + 1 lines along y, transformed, and
 // written as spec[comp][z][y][kx].
 template <typename T>
-__global__ void __launch_bounds__(512) k_fft_xy_fwd(const T *__restrict__ grid, Cx<T> *spec,
+__global__ void __launch_bounds__(1024) k_fft_xy_fwd(const T *__restrict__ grid, Cx<T> *spec,
                                                     FftPlan plan, const T *__restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1, nr = n / 2;
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(512) k_fft_xy_fwd(const T *__restrict__ grid, 
 // i conj(B_{n-k}) beyond), and the inverse x DFT gives the two real rows as
 // its real and imaginary parts, written to a planar field [comp][z][y][x].
 template <typename T>
-__global__ void __launch_bounds__(512) k_fft_xy_inv(T *field, const Cx<T> *__restrict__ spec,
+__global__ void __launch_bounds__(1024) k_fft_xy_inv(T *field, const Cx<T> *__restrict__ spec,
                                                     FftPlan plan, const T *__restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1, nr = n / 2;
@@ -1216,7 +1216,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
   if (fused) {
     set_smem<T>((const void *)k_fft_xy_fwd<T>, sm_xy);
-    k_fft_xy_fwd<T><<<6 * n, 512, sm_xy, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p);
+    k_fft_xy_fwd<T><<<6 * n, 1024, sm_xy, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
@@ -1245,7 +1245,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   }
   if (fused) {
     set_smem<T>((const void *)k_fft_xy_inv<T>, sm_xy);
-    k_fft_xy_inv<T><<<6 * n, 512, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
+    k_fft_xy_inv<T><<<6 * n, 1024, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
