@@ -50,11 +50,15 @@ WORKLOAD = dict(n_agg=4096, n_b=8, phi=0.2, seed=1, shear=1.0, lub=3.0, xi=0.5, 
 SAMPLE_AGG = 4  # oracle sample: 4 aggregates x 8 beads at the same phi / generator
 
 
-def workload_name(w, L, prm):
+def workload_name(w):
+    """The workload, from its defining constants only (both arms print it)."""
+    import synth
+
+    L = synth.box_for_phi(w["n_agg"] * w["n_b"], w["phi"])
     return ("%d beads: %d rigid %d-bead random-attachment aggregates, phi %.2f, L %.2f, "
-            "shear %g, lubrication %ga, xi %.2f, grid %d^3, P %d (operator error ~7e-7), rc %.2f, GMRES %g"
+            "shear %g, lubrication %ga, xi %.2f, GMRES %g"
             % (w["n_agg"] * w["n_b"], w["n_agg"], w["n_b"], w["phi"], L, w["shear"], w["lub"],
-               prm["xi"], prm["grid"], prm["P"], prm["rc"], w["tol"]))
+               w["xi"], w["tol"]))
 
 
 # ----------------------------------------------------------------- clocks
@@ -208,10 +212,12 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "oracle sample per step: %d-bead sub-box of the 32768-bead "
-                                   "phi 0.2 workload" % (SAMPLE_AGG * WORKLOAD["n_b"])},
+            "config": {"workload": workload_name(WORKLOAD), "beads": WORKLOAD["n_agg"] * WORKLOAD["n_b"],
+                       "aggregates": WORKLOAD["n_agg"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "one %d-bead oracle solve per step" % (SAMPLE_AGG * WORKLOAD["n_b"])},
+                             "sample": "each step one dense oracle solve of a %d-bead sub-box (%d x %d-bead "
+                                       "aggregates, same phi, generator, shear and lubrication)"
+                                       % (SAMPLE_AGG * WORKLOAD["n_b"], SAMPLE_AGG, WORKLOAD["n_b"])},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -380,7 +386,9 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_name(w, L, prm), "beads": Nt, "aggregates": w["n_agg"],
+        "config": {"workload": workload_name(w), "beads": Nt, "aggregates": w["n_agg"],
+                   "method": "grid %d^3, P %d (wave-space operator error ~7e-7), rc %.2f"
+                             % (prm["grid"], prm["P"], prm["rc"]),
                    "precision": "mixed: FP32 operator in FP64 iterative refinement; FP64 Arnoldi, LU, residual",
                    "l2": "working set per step > L2 (grids, Krylov basis, neighbour lists ~0.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",

@@ -1,0 +1,116 @@
+"""Pins of the Brownian oracle (oracle/brownian_oracle.py) against what the
+definitions and the paper fix (Sec. 2.2 stochastic sampling, Eq. SP2,
+Eq. UBff):
+
+* Philox4x32-10 reproduces the published known-answer vectors of its
+  authors' reference implementation;
+* the analytic wave-space sample has covariance exactly M_w: the sample is
+  linear in the random field, so summing the outer products of its response
+  to each independent field component gives the covariance, which must equal
+  the wave-vector sum M_w of fsd_oracle (pinned elsewhere against closed forms
+  and xi-independence);
+* the dense square root applied twice is the operator;
+* a near-field Brownian force enters the body rows exactly like an applied
+  aggregate force and torque (the same Sigma projection, the same sign);
+* Box-Muller normals from Philox have zero mean, unit variance, no
+  correlation between components.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import brownian_oracle as B
+
+
+def test_philox_known_answers():
+    assert B.philox4x32_10((0, 0, 0, 0), (0, 0)) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    f = 0xFFFFFFFF
+    assert B.philox4x32_10((f, f, f, f), (f, f)) == [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert B.philox4x32_10((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344),
+                           (0xA4093822, 0x299F31D0)) == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_box_muller_moments():
+    z = np.array([B._normals(7, 3, 2, i, 1) for i in range(20000)]).reshape(-1, 4)
+    assert abs(z.mean()) < 0.02
+    assert abs(z.var() - 1.0) < 0.03
+    c = np.corrcoef(z.T)
+    assert np.abs(c - np.eye(4)).max() < 0.03
+
+
+def test_wave_sample_covariance_is_the_wave_mobility():
+    # two beads, a grid whose k-cube contains the sphere the wave sum needs
+    L, n, xi = 10.0, 12, 0.22
+    pos = np.array([[1.0, 2.0, 3.0], [4.5, 2.5, 6.0]])
+    nh = n // 2 + 1
+    cov = np.zeros((22, 22))
+    for c in range(3):
+        for kz in range(n):
+            for ky in range(n):
+                for kx in range(nh):
+                    if kx == n // 2 or ky == n // 2 or kz == n // 2 or (kx == ky == kz == 0):
+                        continue
+                    mz, my = (n - kz) % n, (n - ky) % n
+                    if kx == 0 and (mz, my) < (kz, ky):
+                        continue  # the mirror of a canonical point carries no new variable
+                    for val in (1.0 / np.sqrt(2.0), 1j / np.sqrt(2.0)):
+                        f = np.zeros((3, n, n, nh), dtype=np.complex128)
+                        f[c, kz, ky, kx] = val
+                        if kx == 0:
+                            f[c, mz, my, 0] = np.conj(val)
+                        u = B.brownian_wave_slip(pos, L, xi, n, f).reshape(-1)
+                        cov += np.outer(u, u)
+    kmax = 2.0 * xi * np.sqrt(46.0)
+    assert kmax < 2 * np.pi * (n // 2 - 1) / L
+    Mw = O.mobility_wave_dense(pos, L, xi, kmax).reshape(22, 22)
+    assert np.abs(cov - Mw).max() < 1e-10 * np.abs(Mw).max()
+
+
+def test_hermitian_field_gives_real_slip():
+    rng = np.random.default_rng(3)
+    n = 10
+    f = B.hermitian_field(n, rng)
+    pos = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 1.0]])
+    u = B.brownian_wave_slip(pos, 9.0, 0.4, n, f)
+    assert u.shape == (2, 11) and np.all(np.isfinite(u)) and np.abs(u).max() > 0
+    # the library's generator fills the same layout with the same symmetry
+    g = B.philox_wave_field(n, seed=5, step=2)
+    for kz in range(n):
+        for ky in range(n):
+            mz, my = (n - kz) % n, (n - ky) % n
+            assert np.allclose(g[:, kz, ky, 0], np.conj(g[:, mz, my, 0]))
+
+
+def test_sqrtm_apply():
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(9, 9))
+    A = A @ A.T
+    v = rng.normal(size=9)
+    assert np.allclose(B.sqrtm_apply(A, B.sqrtm_apply(A, v)), A @ v, rtol=1e-10, atol=1e-10)
+
+
+def test_near_field_noise_acts_like_an_aggregate_force():
+    import synth
+
+    pos, body, L = synth.config_doublets(3, 12.0, seed=4)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(len(pos), 6))
+    M = O.mobility_dense(pos, L)
+    out = B.solve_brownian(pos, body, L, np.zeros((len(pos), 11)), f, gamma=0.5, rlub=0.0, M=M)
+    unw, X, r = O.body_geometry(pos, body, L)
+    FT = O.sigma_T(r, body, body.max() + 1).T @ f.reshape(-1)
+    ref = O.solve(pos, body, L, gamma=0.5, FT=FT, rlub=0.0, M=M)
+    assert np.allclose(out["U"], ref["U"], rtol=1e-12, atol=1e-14)
+
+
+def test_zero_noise_is_the_deterministic_solve():
+    import synth
+
+    pos, body, L = synth.config_doublets(2, 12.0, seed=6)
+    M = O.mobility_dense(pos, L)
+    z = np.zeros((len(pos), 11))
+    out = B.solve_brownian(pos, body, L, z, np.zeros((len(pos), 6)), gamma=1.0, rlub=0.0, M=M)
+    ref = O.solve(pos, body, L, gamma=1.0, rlub=0.0, M=M)
+    assert np.allclose(out["U"], ref["U"], rtol=1e-13, atol=1e-15)
+    assert np.allclose(out["S"], ref["S"], rtol=1e-13, atol=1e-15)
