@@ -303,6 +303,34 @@ const char *fsd_batch_last_error(const fsd_batch *b);
 
 void fsd_destroy_batch(fsd_batch *b);
 
+/* Brownian forcing of the NEXT solve (Sec. 2.2 stochastic sampling, Eq. SP2,
+ * Eq. UBff; Algorithm 1 step 3).  Samples, at the current configuration,
+ *   far-field slip   u^B  = sqrt(2 kT/dt) (M_w^(1/2) psi_w + M_r^(1/2) psi_r)
+ *   near-field force F^B  = sqrt(2 kT/dt) (R_FU^nf)^(1/2) psi_nf
+ * with the wave part analytic (a random field scaled in k space, inverse FFT,
+ * interpolation), the real-space and near-field square roots by Lanczos
+ * iterations on the real-space operator (in the context's operator
+ * precision) and the bead-level lubrication blocks (FP64).  The next
+ * fsd_solve / fsd_step adds u^B to the bead rows (velocity, rotation and
+ * strain) and -Sigma F^B to the body rows of Eq. spm_agg, then forgets them.
+ * The Brownian drift and stresslet are not included.
+ * Random inputs (host or device; NULL: drawn from Philox4x32-10 with key
+ * `seed` and counter (index, stream * 256 + call, step): stream 1 the wave
+ * field at the canonical point of each Hermitian pair, stream 2 psi_real,
+ * stream 3 psi_nf, index = bead position in the setup arrays):
+ *   wave_field [3][n][n][n/2+1] complex (re, im) doubles, layout [c][kz][ky][kx]
+ *     (k = 2 pi m / L, m_i = index, or index - n past n/2): standard complex
+ *     Gaussians, Hermitian in the kx = 0 plane; Nyquist points and k = 0 are
+ *     ignored;
+ *   psi_real [n_beads][11], psi_nf [n_beads][6]: standard normals.
+ * Outputs (NULL to skip): slip [n_beads][11] = u^B, force_nf [n_beads][6] =
+ * F^B.  stats: iters = real-space Lanczos steps, outer_iters = near-field
+ * Lanczos steps. */
+fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint64_t step,
+                        const double *wave_field, const double *psi_real,
+                        const double *psi_nf, double *slip, double *force_nf,
+                        fsd_stats *stats);
+
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);
 

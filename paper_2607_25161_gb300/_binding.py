@@ -29,7 +29,7 @@ EXPORTS = (
     "fsd_rhs", "fsd_get_params", "fsd_profile_enable", "fsd_profile_read",
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
     "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
-    "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch",
+    "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian",
 )
 PROF_GROUPS = 10
 
@@ -106,6 +106,8 @@ def load(path=LIB_PATH):
     lib.fsd_batch_system.restype = P
     lib.fsd_batch_last_error.argtypes = [P]
     lib.fsd_batch_last_error.restype = ctypes.c_char_p
+    lib.fsd_brownian.argtypes = [P, D, D, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P, P,
+                                 ctypes.POINTER(FsdStats)]
     lib.fsd_destroy_batch.argtypes = [P]
     lib.fsd_destroy_batch.restype = None
     for name in EXPORTS:
@@ -235,6 +237,24 @@ class Suspension:
             out = np.zeros(11 * self.n_beads + 6 * self.n_agg)
         self._check(self.lib.fsd_rhs(self.ctx, _ptr(ft), float(shear), _ptr(out)))
         return out
+
+    def brownian(self, kT, dt, seed=0, step=0, wave_field=None, psi_real=None, psi_nf=None):
+        """fsd_brownian: Brownian terms of the next solve; returns (slip
+        [Nt, 11], near-field force [Nt, 6], stats)."""
+        def prep(a):
+            if a is None or hasattr(a, "data_ptr"):
+                return a
+            return np.ascontiguousarray(a, dtype=np.float64)
+        if wave_field is not None and not hasattr(wave_field, "data_ptr"):
+            wave_field = np.ascontiguousarray(np.stack([np.asarray(wave_field).real,
+                                                        np.asarray(wave_field).imag], -1))
+        slip = np.zeros((self.n_beads, 11))
+        fnf = np.zeros((self.n_beads, 6))
+        st_ = FsdStats()
+        self._check(self.lib.fsd_brownian(self.ctx, float(kT), float(dt), int(seed), int(step),
+                                          _ptr(wave_field), _ptr(prep(psi_real)), _ptr(prep(psi_nf)),
+                                          _ptr(slip), _ptr(fnf), ctypes.byref(st_)))
+        return slip, fnf, st_.as_dict()
 
     def profile(self, on=True):
         self._check(self.lib.fsd_profile_enable(self.ctx, 1 if on else 0))

@@ -605,6 +605,8 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
     ft_int = c.t2.p;
   }
   launch_rhs(c, ft_int, shear, c.rhs.p);
+  launch_brownian_rhs(c, c.rhs.p);
+  c.brown_pending = false;  // consumed by this solve
   KStats ks;
   const bool warm = (c.prm.flags & FSD_FLAG_WARM_START) && c.have_prev;
   double rel = solve_system(c, c.rhs.p, c.xsol.p, ks, warm);
@@ -658,10 +660,13 @@ static StepMark graph_step_begin(Ctx &c, const double *ft_user, double shear, bo
   o.with_str = with_str;
   o.shear = shear;
   o.dt = dt;
+  o.brown = c.brown_pending ? 1 : 0;
+  o.brown_scale = c.brown_scale;
   if (ft_user)
     FSD_CUDA(cudaMemcpyAsync(graph_ft_buffer(c), ft_user, 6 * (size_t)c.N * sizeof(double),
                              cudaMemcpyDefault, c.stream));
   graph_launch(c, o);
+  c.brown_pending = false;  // consumed by this solve
   return mk;
 }
 
@@ -1093,6 +1098,57 @@ fsd_status fsd_rhs(fsd_ctx *ctx, const double *agg_force_torque, double shear_ra
   }
   launch_rhs(c, ft_int, shear_rate, c.t1.p);
   vec_out(c, c.t1.p, b, true, true);
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint64_t step,
+                        const double *wave_field, const double *psi_real, const double *psi_nf,
+                        double *slip, double *force_nf, fsd_stats *stats) {
+  if (!ctx) return FSD_EINVAL;
+  if (!(kT >= 0.0) || !(dt > 0.0) || !std::isfinite(kT) || !std::isfinite(dt)) {
+    ctx->c.last_error = "kT must be >= 0 and dt > 0 (finite)";
+    return FSD_EINVAL;
+  }
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = c.launches;
+  prepare(c);
+  const size_t nh = (size_t)c.n / 2 + 1;
+  DBuf<double> sf, sr, sn;
+  const double *fd = wave_field ? dev_in(c, wave_field, 6 * (size_t)c.n * c.n * nh, sf) : nullptr;
+  const double *rd = psi_real ? dev_in(c, psi_real, 11 * (size_t)c.Nt, sr) : nullptr;
+  const double *nd = psi_nf ? dev_in(c, psi_nf, 6 * (size_t)c.Nt, sn) : nullptr;
+  int ir = 0, inf = 0;
+  brownian_sample(c, kT, dt, seed, step, fd, rd, nd, &ir, &inf);
+  for (int q = 0; q < 2; ++q) {
+    double *user = q == 0 ? slip : force_nf;
+    const int w = q == 0 ? 11 : 6;
+    if (!user) continue;
+    if (is_device_ptr(user)) {
+      brownian_outputs(c, q == 0 ? user : nullptr, q == 1 ? user : nullptr);
+    } else {
+      DBuf<double> tmp;
+      tmp.alloc((size_t)w * c.Nt);
+      brownian_outputs(c, q == 0 ? tmp.p : nullptr, q == 1 ? tmp.p : nullptr);
+      FSD_CUDA(cudaMemcpyAsync(user, tmp.p, (size_t)w * c.Nt * sizeof(double), cudaMemcpyDeviceToHost,
+                               c.stream));
+      FSD_CUDA(cudaStreamSynchronize(c.stream));
+    }
+  }
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iters = ir;
+    stats->outer_iters = inf;
+    stats->kernel_launches = c.launches - l0;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->grid = c.n;
+    stats->P = c.P;
+    stats->xi = c.xi;
+    stats->rc = c.rc;
+  }
   return FSD_OK;
   FSD_API_CATCH(ctx)
 }

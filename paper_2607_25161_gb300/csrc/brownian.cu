@@ -1,0 +1,326 @@
+// Brownian forcing of the saddle-point solve (Sec. 2.2 "stochastic
+// sampling", Eq. SP2, Eq. UBff; Algorithm 1 step 3):
+//   far-field slip      u^B  = sqrt(2 kT/dt) (M_w^(1/2) psi_w + M_r^(1/2) psi_r)
+//   near-field force    F^B  = sqrt(2 kT/dt) (R_FU^nf)^(1/2) psi_nf
+// The wave part is analytic (wavespace.cu: a random field scaled in k space,
+// inverse FFT, interpolation); the real-space and near-field square roots come
+// from Lanczos iterations (Krylov approximation of f(A) b, f = sqrt) on the
+// library's real-space operator and bead-level lubrication blocks.  The next
+// solve adds u^B to the bead rows (all 11 components) and -Sigma F^B to the
+// body rows of its right-hand side.
+//
+// Random numbers: given by the caller, or drawn from Philox4x32-10 with the
+// counter layout (index, stream * 256 + call, step): stream 1 the wave field
+// (wavespace.cu), stream 2 psi_r (11 per bead), stream 3 psi_nf (6 per bead),
+// the index of a bead being its position in the caller's bead array.
+#include "fsd_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace fsd {
+
+// ---------------------------------------------------------------- kernels
+// y = R_FU^nf x, bead rows, R the bead-level near-field FU blocks (BSR,
+// diagonal separate); components 6..11 of y are zero.
+__global__ void k_bsr_bead(int Nt, const int *__restrict__ brow, const int *__restrict__ bcol,
+                           const double *__restrict__ bval, const double *__restrict__ bdiag,
+                           const double *__restrict__ x, double *y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Nt) return;
+  double g[6];
+  const double *xb = x + (size_t)b * LDB;
+  const double *D = bdiag + (size_t)b * 36;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s += D[6 * a + q] * xb[q];
+    g[a] = s;
+  }
+  for (int k = brow[b]; k < brow[b + 1]; ++k) {
+    const double *xc = x + (size_t)bcol[k] * LDB;
+    const double *Bk = bval + (size_t)k * 36;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s += Bk[6 * a + q] * xc[q];
+      g[a] += s;
+    }
+  }
+  double *yb = y + (size_t)b * LDB;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) yb[a] = g[a];
+#pragma unroll
+  for (int a = 6; a < LDB; ++a) yb[a] = 0.0;
+}
+
+// caller's psi [Nt][w] (bead order of the caller) -> solution layout
+__global__ void k_psi_in(int Nt, const int *__restrict__ perm, const double *__restrict__ user, int w,
+                         double *x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const double *u = user + (size_t)perm[i] * w;
+  double *o = x + (size_t)i * LDB;
+  for (int k = 0; k < LDB; ++k) o[k] = k < w ? u[k] : 0.0;
+}
+
+// psi from Philox: bead i draws with the index of its caller position
+__global__ void k_psi_philox(int Nt, const int *__restrict__ perm, uint64_t seed, uint64_t step,
+                             uint32_t stream, int w, double *x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  double z[12];
+  const int calls = (w + 3) / 4;
+  for (int q = 0; q < calls; ++q) philox_normals4(seed, step, stream, (uint32_t)q, (uint32_t)perm[i], z + 4 * q);
+  double *o = x + (size_t)i * LDB;
+  for (int k = 0; k < LDB; ++k) o[k] = k < w ? z[k] : 0.0;
+}
+
+// user[perm[i]][k] = s x[i][k], k < w
+__global__ void k_brown_out(int Nt, const int *__restrict__ perm, const double *__restrict__ x, int w,
+                            double s, double *user) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const double *v = x + (size_t)i * LDB;
+  double *u = user + (size_t)perm[i] * w;
+  for (int k = 0; k < w; ++k) u[k] = s * v[k];
+}
+
+// bead rows of b += s u^B (velocity, rotation, strain)
+__global__ void k_brown_rhs_bead(int Nt, const double *__restrict__ slip, double s, double *b) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Nt * LDB) return;
+  if (e % LDB < 11) b[e] += s * slip[e];
+}
+
+// body rows of b -= s Sigma F^B: per body the summed force and the torque
+// about X (L_b + r_b x F_b)
+__global__ void k_brown_rhs_body(int N, const int *__restrict__ body_start,
+                                 const double4 *__restrict__ lever, const double *__restrict__ fnf,
+                                 double s, double *b, int64_t off) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= N) return;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = body_start[J]; i < body_start[J + 1]; ++i) {
+    const double *f = fnf + (size_t)i * LDB;
+    const double4 r = lever[i];
+    acc[0] += f[0];
+    acc[1] += f[1];
+    acc[2] += f[2];
+    acc[3] += f[3] + r.y * f[2] - r.z * f[1];
+    acc[4] += f[4] + r.z * f[0] - r.x * f[2];
+    acc[5] += f[5] + r.x * f[1] - r.y * f[0];
+  }
+  double *o = b + off + 6 * (size_t)J;
+  for (int a = 0; a < 6; ++a) o[a] -= s * acc[a];
+}
+
+// ------------------------------------------------------------- Lanczos
+// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi
+// rotations: A = Q diag(lam) Q^T (Q column-major, m x m).
+static void jacobi_eigen(int m, std::vector<double> A, std::vector<double> &lam,
+                         std::vector<double> &Q) {
+  Q.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+  auto a = [&](int i, int j) -> double & { return A[(size_t)i * m + j]; };
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) (i == j ? tot : off) += a(i, j) * a(i, j);
+    if (off <= 1e-30 * (tot + off) || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a(p, q);
+        if (apq == 0.0) continue;
+        // rotation angle zeroing a(p, q): tan(2 theta) = 2 a_pq / (a_qq - a_pp)
+        const double tau = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = a(k, p), akq = a(k, q);
+          a(k, p) = cs * akp - sn * akq;
+          a(k, q) = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = a(p, k), aqk = a(q, k);
+          a(p, k) = cs * apk - sn * aqk;
+          a(q, k) = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double qkp = Q[(size_t)p * m + k], qkq = Q[(size_t)q * m + k];
+          Q[(size_t)p * m + k] = cs * qkp - sn * qkq;
+          Q[(size_t)q * m + k] = sn * qkp + cs * qkq;
+        }
+      }
+  }
+  lam.resize(m);
+  for (int i = 0; i < m; ++i) lam[i] = a(i, i);
+}
+
+// ||b|| T^(1/2) e_1 for the Lanczos tridiagonal T (alpha, beta)
+static std::vector<double> sqrt_coeffs(int m, const std::vector<double> &al,
+                                       const std::vector<double> &be, double bnorm) {
+  std::vector<double> T((size_t)m * m, 0.0), lam, Q;
+  for (int i = 0; i < m; ++i) {
+    T[(size_t)i * m + i] = al[i];
+    if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = be[i];
+  }
+  jacobi_eigen(m, T, lam, Q);
+  std::vector<double> cf(m, 0.0);
+  for (int k = 0; k < m; ++k) {
+    const double w = std::sqrt(std::max(0.0, lam[k])) * Q[(size_t)k * m + 0];  // sqrt(l) (Q^T e1)_k
+    for (int i = 0; i < m; ++i) cf[i] += Q[(size_t)k * m + i] * w;
+  }
+  for (double &v : cf) v *= bnorm;
+  return cf;
+}
+
+static double dev_norm(Ctx &c, const double *x) {
+  double *d = c.hcol.p + 200;
+  norm2_dev(c, x, d);
+  FSD_CUDA(cudaMemcpyAsync(c.h_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  return std::sqrt(std::max(0.0, c.h_pinned[0]));
+}
+
+// out = A^(1/2) b by Lanczos with full re-orthogonalisation: V_m T_m^(1/2)
+// (||b|| e_1), stopped when the coefficients change by less than tol
+// (relative).  apply(x, y) sets y = A x (bead rows; body rows must stay 0).
+template <class Apply>
+static int lanczos_sqrt(Ctx &c, Apply apply, const double *b, double *out, double tol, int maxit) {
+  const int64_t ld = c.nunk, n = c.nunk;
+  double *V = c.V.p, *w = c.w.p;
+  const double bnorm = dev_norm(c, b);
+  FSD_CUDA(cudaMemsetAsync(out, 0, n * sizeof(double), c.stream));
+  if (!(bnorm > 0.0)) return 0;
+  vec_scale_host(c, V, b, 1.0 / bnorm);
+  std::vector<double> al, be, cf, prev;
+  double *h1 = c.hcol.p, *hn = c.hcol.p + 128;
+  int m = 0;
+  for (int j = 0; j < maxit; ++j) {
+    apply(V + (int64_t)j * ld, w);
+    FSD_CUDA(cudaMemsetAsync(w + (int64_t)LDB * c.Nt, 0, 6 * (size_t)c.N * sizeof(double), c.stream));
+    cgs_pass(c, 0, V, ld, j + 1, w, nullptr, h1);
+    cgs_pass(c, 2, V, ld, j + 1, w, h1, hn);
+    FSD_CUDA(cudaMemcpyAsync(c.h_pinned, c.hcol.p, 192 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c.stream));
+    FSD_CUDA(cudaStreamSynchronize(c.stream));
+    al.push_back(c.h_pinned[j]);
+    const double beta = std::sqrt(std::max(0.0, c.h_pinned[128]));
+    if (!(beta == beta)) throw Invalid{"NaN in the Lanczos process"};
+    m = j + 1;
+    cf = sqrt_coeffs(m, al, be, bnorm);
+    double dn = 0.0, cn = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double d = cf[i] - (i < (int)prev.size() ? prev[i] : 0.0);
+      dn += d * d;
+      cn += cf[i] * cf[i];
+    }
+    prev = cf;
+    if (j > 0 && dn <= tol * tol * cn) break;
+    if (beta <= 1e-14 * bnorm || j + 1 == maxit) break;
+    be.push_back(beta);
+    vec_scale_host(c, V + (int64_t)(j + 1) * ld, w, 1.0 / beta);
+  }
+  std::memcpy(c.h_pinned + 256, cf.data(), m * sizeof(double));
+  FSD_CUDA(cudaMemcpyAsync(c.hcol.p + 256, c.h_pinned + 256, m * sizeof(double),
+                           cudaMemcpyHostToDevice, c.stream));
+  axpy_multi(c, out, V, ld, m, c.hcol.p + 256, 1.0);
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  return m;
+}
+
+// ------------------------------------------------------------- sampling
+void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
+                     const double *field_dev, const double *psi_r_dev, const double *psi_nf_dev,
+                     int *iters_real, int *iters_nf) {
+  if (!(kT >= 0.0) || !(dt > 0.0)) throw Invalid{"kT must be >= 0 and dt > 0"};
+  const int64_t n = c.nunk;
+  if (c.bslip.n < (size_t)n) c.bslip.alloc(n);
+  if (c.bfnf.n < (size_t)n) c.bfnf.alloc(n);
+  if (c.bwork.n < (size_t)n) c.bwork.alloc(n);
+  const bool f32 = c.prm.precision == FSD_MIXED;
+  const int maxit = std::min(std::max(c.m, c.m_in), 60);
+  const double tol = 1e-7;
+  // wave part: u_w = M_w^(1/2) psi_w
+  if (f32)
+    launch_brownian_wave<float>(c, field_dev, seed, step, c.bslip.p);
+  else
+    launch_brownian_wave<double>(c, field_dev, seed, step, c.bslip.p);
+  // real-space part: u_r = M_r^(1/2) psi_r (Lanczos on the real-space operator)
+  FSD_CUDA(cudaMemsetAsync(c.bwork.p, 0, n * sizeof(double), c.stream));
+  if (psi_r_dev)
+    k_psi_in<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, psi_r_dev, 11, c.bwork.p);
+  else
+    k_psi_philox<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, seed, step, 2u, 11,
+                                                           c.bwork.p);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+  auto real_op = [&](const double *x, double *y) {
+    if (f32)
+      launch_realspace<float>(c, x, y, false, false);
+    else
+      launch_realspace<double>(c, x, y, false, false);
+  };
+  const int ir = lanczos_sqrt(c, real_op, c.bwork.p, c.t2.p, tol, maxit);
+  vec_axpby(c, c.bslip.p, 1.0, c.t2.p, 1.0, n);
+  // near-field part: F^B = R_FU^(1/2) psi_nf (Lanczos on the bead-level blocks)
+  int inf = 0;
+  if (c.n_lub > 0) {
+    FSD_CUDA(cudaMemsetAsync(c.bwork.p, 0, n * sizeof(double), c.stream));
+    if (psi_nf_dev)
+      k_psi_in<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, psi_nf_dev, 6, c.bwork.p);
+    else
+      k_psi_philox<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, seed, step, 3u, 6,
+                                                             c.bwork.p);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+    auto nf_op = [&](const double *x, double *y) {
+      k_bsr_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.brow.p, c.bcol.p, c.op64.bval.p,
+                                                            c.op64.bdiag.p, x, y);
+      FSD_LAUNCHED(c);
+      FSD_CUDA(cudaGetLastError());
+    };
+    inf = lanczos_sqrt(c, nf_op, c.bwork.p, c.bfnf.p, tol, maxit);
+  } else {
+    FSD_CUDA(cudaMemsetAsync(c.bfnf.p, 0, n * sizeof(double), c.stream));
+  }
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  c.brown_scale = std::sqrt(2.0 * kT / dt);
+  c.brown_pending = true;
+  if (iters_real) *iters_real = ir;
+  if (iters_nf) *iters_nf = inf;
+}
+
+void launch_brownian_rhs(Ctx &c, double *b) {
+  if (!c.brown_pending) return;
+  ProfScope ps(c, PG_MISC);
+  k_brown_rhs_bead<<<ceil_div((int64_t)c.Nt * LDB, 256), 256, 0, c.stream>>>(c.Nt, c.bslip.p,
+                                                                           c.brown_scale, b);
+  FSD_LAUNCHED(c);
+  k_brown_rhs_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(
+      c.N, c.body_start.p, (const double4 *)c.lever64.p, c.bfnf.p, c.brown_scale, b,
+      (int64_t)LDB * c.Nt);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void brownian_outputs(Ctx &c, double *slip_user_dev, double *fnf_user_dev) {
+  if (slip_user_dev) {
+    k_brown_out<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, c.bslip.p, 11,
+                                                           c.brown_scale, slip_user_dev);
+    FSD_LAUNCHED(c);
+  }
+  if (fnf_user_dev) {
+    k_brown_out<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, c.bfnf.p, 6,
+                                                           c.brown_scale, fnf_user_dev);
+    FSD_LAUNCHED(c);
+  }
+  FSD_CUDA(cudaGetLastError());
+}
+
+}  // namespace fsd

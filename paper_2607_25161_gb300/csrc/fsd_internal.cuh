@@ -75,6 +75,7 @@ struct OpData {
   DBuf<T> pos;        // wrapped positions [Nt][4] (x, y, z, 0)
   DBuf<T> lever;      // r_b = x_b - X_J [Nt][4]
   DBuf<T> packed;     // per bead (x, y, z, F, L, S6, 0) in the operator precision [Nt][16]
+  DBuf<T> btab;       // Brownian wave-field scales [m = kx^2+ky^2+kz^2][2]: (c fM, c fD)
 };
 
 // Kernel groups timed by the opt-in profiler (CUDA events on the stream).
@@ -106,7 +107,8 @@ struct GraphRun {
   int has_ft = 0;     // applied forces / torques staged in the graph's buffer
   int integrate = 0;  // advance the rigid bodies by dt after the solve
   int with_str = 0;   // write the stresslet
-  double shear = 0.0, dt = 0.0;
+  int brown = 0;      // add the pending Brownian terms to the right-hand side
+  double shear = 0.0, dt = 0.0, brown_scale = 0.0;
 };
 
 struct ProfScope {
@@ -173,11 +175,57 @@ struct Ctx {
   std::string last_error;
   fsd_status last_warning = FSD_OK;
   int64_t n_pairs = 0, n_lub = 0;
+  // ---- Brownian forcing of the next solve (brownian.cu)
+  DBuf<double> bslip, bfnf, bwork;  // slip u_w + u_r and near-field force (solution layout), scratch
+  bool brown_pending = false;       // the next solve adds them to its right-hand side
+  double brown_scale = 0.0;         // sqrt(2 kT / dt)
   // ---- captured solve graphs
   GraphCache *gcache = nullptr;
   int64_t graph_pending = -1;
   double tuned_ms = 0.0;  // operator time measured by the autotuner (0: not tuned)
 };
+
+// ------------------------------------------------- counter-based normals
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two
+// 32x32 -> 64-bit multiplications with the Weyl key schedule; the Brownian
+// sampler draws every random number from (counter, key), so any element can
+// be generated independently and reproducibly.
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Four standard normals for counter (index, stream * 256 + call, step) and
+// key seed: Box-Muller on u_j = (x_j + 1) 2^-32.
+__device__ inline void philox_normals4(uint64_t seed, uint64_t step, uint32_t stream, uint32_t call,
+                                       uint32_t index, double z[4]) {
+  uint32_t c[4] = {index, (stream << 8) | call, (uint32_t)step, (uint32_t)(step >> 32)};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double s = 2.3283064365386963e-10;  // 2^-32
+  const double u0 = ((double)c[0] + 1.0) * s, u1 = ((double)c[1] + 1.0) * s;
+  const double u2 = ((double)c[2] + 1.0) * s, u3 = ((double)c[3] + 1.0) * s;
+  const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+  double s0, c0, s1, c1;
+  sincospi(2.0 * u1, &s0, &c0);
+  sincospi(2.0 * u3, &s1, &c1);
+  z[0] = r0 * c0;
+  z[1] = r0 * s0;
+  z[2] = r1 * c1;
+  z[3] = r1 * s1;
+}
 
 // ------------------------------------------------------------ launchers
 // realspace.cu
@@ -228,6 +276,19 @@ void norm2_dev(Ctx &c, const double *x, double *out_dev);
 template <typename T>
 void apply_saddle(Ctx &c, const double *x, double *y);
 void k_bodies_in_launch(Ctx &c, const double *user, double *internal);  // [N][6] user -> internal order
+
+// wavespace.cu (Brownian wave part): out (solution layout, bead rows) =
+// M_w^(1/2) xi for the random field xi (field: complex [3][n][n][n/2+1] on the
+// device, or null for the counter-based generator)
+template <typename T>
+void launch_brownian_wave(Ctx &c, const double *field, uint64_t seed, uint64_t step, double *out);
+
+// brownian.cu
+void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
+                     const double *field_dev, const double *psi_r_dev, const double *psi_nf_dev,
+                     int *iters_real, int *iters_nf);   // fills bslip, bfnf; sets pending
+void launch_brownian_rhs(Ctx &c, double *b);               // b += the pending Brownian terms
+void brownian_outputs(Ctx &c, double *slip_user_dev, double *fnf_user_dev);  // scaled, user order
 
 // graph.cu (device-resident solve)
 void graph_launch(Ctx &c, const GraphRun &o);  // capture on first use of a key; launch on c.stream

@@ -43,8 +43,8 @@ struct GState {
 };
 
 struct GraphKey {
-  int mixed, warm, has_ft, integrate, with_str, group, lub;
-  double shear, dt;
+  int mixed, warm, has_ft, integrate, with_str, group, lub, brown;
+  double shear, dt, brown_scale;
   const void *nbr, *lnbr, *bcol, *bval64, *bval32, *packed64, *packed32;
   int cap, lcap;
   int64_t nunk;
@@ -524,6 +524,8 @@ static GraphKey make_key(Ctx &c, const GraphRun &o) {
   k.lub = c.n_lub > 0;
   k.shear = o.shear;
   k.dt = o.integrate ? o.dt : 0.0;
+  k.brown = o.brown;
+  k.brown_scale = o.brown ? o.brown_scale : 0.0;
   k.nbr = c.nbr.p;
   k.lnbr = c.lnbr.p;
   k.bcol = c.bcol.p;
@@ -578,6 +580,7 @@ static GraphEntry &build_entry(Ctx &c, const GraphRun &o, const GraphKey &k) {
       k_bodies_in_launch(c, gc.ft.p, c.t2.p);
     }
     launch_rhs(c, o.has_ft ? c.t2.p : nullptr, o.shear, c.rhs.p);
+    if (o.brown) launch_brownian_rhs(c, c.rhs.p);
     e.l_top += c.launches - l0;
     deps = cap_end(c);
     deps = capture_solve(c, e, e.graph, deps, o.warm);

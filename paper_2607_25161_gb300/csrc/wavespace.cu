@@ -742,6 +742,105 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
   }
 }
 
+// ----------------------------------------------- Brownian z pass (PSE)
+// Lines along z for fixed ky, TX = 2^LTX consecutive kx: the random field
+// xi(k) (three complex components; from `field`, or from Philox stream 1 at
+// the canonical point of a Hermitian pair), projected by (I - k k) and scaled
+// by btab = (c fM, c fD), gives the velocity field (components 0-2) and the
+// dipole read-out field (3-5) in k space; the inverse z transform leaves them
+// in the state the operator's z pass leaves its output in.  Nyquist points
+// and k = 0 carry no noise.
+template <typename T>
+__global__ void k_brown_z(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
+                          const T *__restrict__ btab, const double *__restrict__ field,
+                          uint64_t seed, uint64_t step, int LTX) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
+  const int TX = 1 << LTX;
+  const int NLn = 6 * TX;
+  Cx<T> *tw_s = (Cx<T> *)smem_raw;
+  Cx<T> *A = tw_s + plan.ntw;
+  Cx<T> *B = A + NLn * ls;
+  load_twiddles(tw_s, tw, plan.ntw);
+  const int ntile = (nh + TX - 1) >> LTX;
+  const int yy = blockIdx.x / ntile;
+  const int tile = blockIdx.x - yy * ntile;
+  const int kx0 = tile << LTX;
+  const int ky = yy <= n / 2 ? yy : yy - n;
+  for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
+    const int t = e & (TX - 1), zz = e >> LTX;
+    const int kx = kx0 + t;
+    const int kz = zz <= n / 2 ? zz : zz - n;
+    Cx<T> oM[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
+    Cx<T> oD[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
+    const bool nyq = kx == n / 2 || yy == n / 2 || zz == n / 2;
+    if (kx < nh && !nyq && (kx | yy | zz) != 0) {
+      double xr[3], xim[3];
+      if (field) {
+        const int64_t cs = (int64_t)n * n * nh;
+        const int64_t o = ((int64_t)zz * n + yy) * nh + kx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          xr[c] = field[2 * (c * cs + o)];
+          xim[c] = field[2 * (c * cs + o) + 1];
+        }
+      } else {
+        int cz = zz, cy = yy;
+        bool conj = false;
+        if (kx == 0) {
+          const int mz = (n - zz) % n, my = (n - yy) % n;
+          if (mz < zz || (mz == zz && my < yy)) {
+            cz = mz;
+            cy = my;
+            conj = true;
+          }
+        }
+        const uint32_t idx = (uint32_t)(((int64_t)cz * n + cy) * nh + kx);
+        double z0[4], z1[4];
+        philox_normals4(seed, step, 1u, 0u, idx, z0);
+        philox_normals4(seed, step, 1u, 1u, idx, z1);
+        const double s = 0.70710678118654752440;
+        xr[0] = s * z0[0]; xim[0] = s * z0[1];
+        xr[1] = s * z0[2]; xim[1] = s * z0[3];
+        xr[2] = s * z1[0]; xim[2] = s * z1[1];
+        if (conj)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) xim[c] = -xim[c];
+      }
+      const double kk[3] = {(double)kx, (double)ky, (double)kz};
+      const double m = kk[0] * kk[0] + kk[1] * kk[1] + kk[2] * kk[2];
+      double pr = 0.0, pi = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pr += kk[c] * xr[c];
+        pi += kk[c] * xim[c];
+      }
+      const int mi = (int)m;
+      const T bm = btab[2 * mi], bd = btab[2 * mi + 1];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T vr = (T)(xr[c] - kk[c] * pr / m), vi = (T)(xim[c] - kk[c] * pi / m);
+        oM[c] = {bm * vr, bm * vi};
+        oD[c] = {bd * vr, bd * vi};
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      A[(d * TX + t) * ls + fpad(zz)] = oM[d];
+      A[((d + 3) * TX + t) * ls + fpad(zz)] = oD[d];
+    }
+  }
+  __syncthreads();
+  Cx<T> *R = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(1));
+  const int64_t zstride = (int64_t)n * nh, cstride = (int64_t)n * zstride;
+  for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
+    const int t = e & (TX - 1), rest = e >> LTX;
+    const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+    const int kx = kx0 + t;
+    if (kx < nh) spec[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + fpad(zz)];
+  }
+}
+
 // ------------------------------------------------------------ spreading
 template <typename T>
 struct V4Of;
@@ -1142,6 +1241,22 @@ void build_wave(Ctx &c) {
   }
   upload(c.op64.green, gr);
   upload(c.op32.green, gr);
+  // Brownian wave-field scales (Sec. 2.2, Eq. UBff): the random field xi(k)
+  // becomes f(k) sqrt(H(k)/(eta k^2)) / (sqrt(V) W^(k)) (I - k k) xi(k), the
+  // analytic square root of the wave part once the interpolation's Gaussian
+  // W^(k) = exp(-k^2/(4 alpha)) is divided out
+  std::vector<double> bt(2 * (size_t)(mmax + 1), 0.0);
+  const double isv = 1.0 / std::sqrt(c.L * c.L * c.L);
+  for (int m = 1; m <= mmax; ++m) {
+    double k = 2.0 * kPi * std::sqrt((double)m) / c.L;
+    double k2 = k * k;
+    double H = (1.0 + k2 / (4.0 * c.xi * c.xi)) * std::exp(-k2 / (4.0 * c.xi * c.xi));
+    double sc = std::sqrt(H / (c.eta * k2)) * std::exp(k2 / (4.0 * c.alpha)) * isv;
+    bt[2 * m] = sc * j0h(k * c.a);
+    bt[2 * m + 1] = sc * fDh(k * c.a);
+  }
+  upload(c.op64.btab, bt);
+  upload(c.op32.btab, bt);
 }
 
 template <typename T>
@@ -1178,6 +1293,62 @@ static void set_smem(const void *fn, size_t bytes) {
   done.push_back({fn, bytes});
 }
 
+// Inverse y and x transforms of the six fields held in spec (after the z
+// pass), then interpolation: y += h^3 sum W (fields) per bead.
+template <typename T>
+static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, double *y) {
+  const int n = c.n, P = c.P;
+  const T h = (T)c.h, alpha = (T)c.alpha;
+  const double cn = std::pow(c.alpha / kPi, 1.5);
+  const int nh = n / 2 + 1;
+  const int threads = 256;
+  const int ntw = plan.ntw;
+  const size_t sm_xy = (size_t)(ntw + 2 * nh * fft_ls(n)) * sizeof(Cx<T>);
+  const bool fused = sizeof(T) == 4 && sm_xy <= (size_t)227 * 1024;
+  const int LTXy = sizeof(T) == 8 ? 3 : 4;
+  const int TXy = 1 << LTXy;
+  const size_t smy = (size_t)(ntw + 2 * TXy * fft_ls(n)) * sizeof(Cx<T>);
+  const int blocks_y = 6 * n * ceil_div(nh, TXy);
+  {
+  ProfScope ps(c, PG_FFT);
+  if (fused) {
+    set_smem<T>((const void *)k_fft_xy_inv<T>, sm_xy);
+    k_fft_xy_inv<T><<<6 * n, 1024, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+  } else {
+    k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+    const int NL = 4;
+    size_t sm = (size_t)(ntw + 2 * 3 * NL * fft_ls(n)) * sizeof(Cx<T>);
+    set_smem<T>((const void *)k_fft_x_inv<T>, sm);
+    int blocks = ceil_div((int64_t)n * n, NL);
+    k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p, NL);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+  }
+  }
+  ProfScope ps2(c, PG_INTERP);
+  const double h3 = c.h * c.h * c.h;
+  const bool planar = sizeof(T) == 4 &&
+                      (size_t)(make_plan(n, nullptr, true).ntw + 2 * (n / 2 + 1) * fft_ls(n)) * sizeof(Cx<T>) <=
+                          (size_t)227 * 1024;
+  if (planar && n % 4 == 0)
+    k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p,
+                                                         (const float *)op.gout.p, y, n, P,
+                                                         (float)h, (float)alpha, (float)(cn * h3));
+  else if (planar)
+    k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
+                                                              h, alpha, (T)(cn * h3));
+  else
+    k_interp<T, false><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
+                                                               P, h, alpha, (T)(cn * h3));
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+
 template <typename T>
 void launch_wavespace(Ctx &c, const double *x, double *y) {
   OpData<T> &op = opd<T>(c);
@@ -1198,13 +1369,13 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   }
+  const FftPlan plan = make_plan(n, nullptr, sizeof(T) == 4);
+  Cx<T> *spec = (Cx<T> *)op.spec.p;
   {
   ProfScope ps(c, PG_FFT);
-  FftPlan plan = make_plan(n, nullptr, sizeof(T) == 4);
   const int nh = n / 2 + 1;
   const int threads = 256;
   const int ntw = plan.ntw;
-  Cx<T> *spec = (Cx<T> *)op.spec.p;
   // FP32 planes that fit in shared memory with their ping-pong copy take the
   // fused x + y kernels (interpolation then reads planar fields); otherwise
   // separate x and y passes (interleaved fields).
@@ -1243,45 +1414,35 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
-  if (fused) {
-    set_smem<T>((const void *)k_fft_xy_inv<T>, sm_xy);
-    k_fft_xy_inv<T><<<6 * n, 1024, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
-    FSD_LAUNCHED(c);
-    FSD_CUDA(cudaGetLastError());
-  } else {
-    k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
-    FSD_LAUNCHED(c);
-    FSD_CUDA(cudaGetLastError());
-    const int NL = 4;
-    size_t sm = (size_t)(ntw + 2 * 3 * NL * fft_ls(n)) * sizeof(Cx<T>);
-    set_smem<T>((const void *)k_fft_x_inv<T>, sm);
-    int blocks = ceil_div((int64_t)n * n, NL);
-    k_fft_x_inv<T><<<blocks, threads, sm, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p, NL);
-    FSD_LAUNCHED(c);
-    FSD_CUDA(cudaGetLastError());
   }
-  }
-  ProfScope ps(c, PG_INTERP);
-  const double h3 = c.h * c.h * c.h;
-  const bool planar = sizeof(T) == 4 &&
-                      (size_t)(make_plan(n, nullptr, true).ntw + 2 * (n / 2 + 1) * fft_ls(n)) * sizeof(Cx<T>) <=
-                          (size_t)227 * 1024;
-  if (planar && n % 4 == 0)
-    k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p,
-                                                         (const float *)op.gout.p, y, n, P,
-                                                         (float)h, (float)alpha, (float)(cn * h3));
-  else if (planar)
-    k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
-                                                              h, alpha, (T)(cn * h3));
-  else
-    k_interp<T, false><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
-                                                               P, h, alpha, (T)(cn * h3));
-  FSD_LAUNCHED(c);
-  FSD_CUDA(cudaGetLastError());
+  wave_tail<T>(c, op, plan, spec, y);
 }
 
 template void launch_wavespace<float>(Ctx &, const double *, double *);
 template void launch_wavespace<double>(Ctx &, const double *, double *);
+
+template <typename T>
+void launch_brownian_wave(Ctx &c, const double *field, uint64_t seed, uint64_t step, double *out) {
+  OpData<T> &op = opd<T>(c);
+  const int n = c.n, nh = n / 2 + 1;
+  const FftPlan plan = make_plan(n, nullptr, sizeof(T) == 4);
+  Cx<T> *spec = (Cx<T> *)op.spec.p;
+  {
+    ProfScope ps(c, PG_FFT);
+    const int LTX = 2;
+    const int TX = 1 << LTX;
+    const size_t sm = (size_t)(plan.ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
+    set_smem<T>((const void *)k_brown_z<T>, sm);
+    k_brown_z<T><<<n * ceil_div(nh, TX), 256, sm, c.stream>>>(spec, plan, op.twiddle.p, op.btab.p,
+                                                               field, seed, step, LTX);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
+  }
+  FSD_CUDA(cudaMemsetAsync(out, 0, (size_t)c.nunk * sizeof(double), c.stream));
+  wave_tail<T>(c, op, plan, spec, out);
+}
+template void launch_brownian_wave<float>(Ctx &, const double *, uint64_t, uint64_t, double *);
+template void launch_brownian_wave<double>(Ctx &, const double *, uint64_t, uint64_t, double *);
 
 }  // namespace fsd
 

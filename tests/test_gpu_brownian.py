@@ -1,0 +1,158 @@
+"""GPU parity of the Brownian forcing (fsd_brownian; Sec. 2.2 stochastic
+sampling, Eq. SP2, Eq. UBff, Algorithm 1 step 3) against the Brownian oracle,
+through the C ABI, on the same random inputs.
+
+Tolerances (relative L2):
+  wave part (analytic PSE sample, grid rule x_err = 1e-8, P = 16: the
+    interpolation's truncation error is ~1.5e-6 at P = 12, ~1e-8 at P = 16):
+    1e-6 FP64, 1e-5 with the FP32 operator;
+  real-space square root (Lanczos, coefficient change < 1e-7 on the
+    real-space operator): 1e-6 FP64, 1e-5 FP32;
+  near-field square root (Lanczos on the FP64 bead blocks): 1e-6;
+  Brownian solve at GMRES 1e-10: 1e-6 FP64, 1e-5 mixed.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import brownian_oracle as BO
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+HI = dict(xi=1.2, P=16, xerr=1e-8, tol=1e-10, lub_cutoff=3.0)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2607_25161_gb300 as p
+
+    return p
+
+
+def ragged_system(seed=3):
+    rng = np.random.default_rng(seed)
+    sizes = [1, 2, 3, 5, 8, 4, 6, 7]
+    shapes = [synth.random_attachment_aggregate(n, rng) for n in sizes]
+    L = synth.box_for_phi(sum(sizes), 0.1)
+    pos, body = synth.pack_suspension(shapes, L, rng, h_gen=0.05)
+    return pos, body, L
+
+
+@pytest.fixture(scope="module")
+def sysB(pkg):
+    pos, body, L = ragged_system()
+    s = pkg.Suspension(pos, body, L, **HI)
+    prm = s.params
+    s.close()
+    n, xi = prm["grid"], prm["xi"]
+    rng = np.random.default_rng(11)
+    field = BO.hermitian_field(n, rng)
+    psi_r = rng.normal(size=(len(pos), 11))
+    psi_nf = rng.normal(size=(len(pos), 6))
+    unw, X, r = O.body_geometry(pos, body, L)
+    uw = BO.brownian_wave_slip(unw, L, xi, n, field)
+    rc = 2.0 + np.sqrt(46.0) / xi
+    Mr = O.mobility_real_dense(unw, L, xi, rc).reshape(11 * len(pos), -1)
+    ur = BO.sqrtm_apply(Mr, psi_r.reshape(-1)).reshape(-1, 11)
+    RFU = O.split_grand(O.lubrication_dense(unw, body, L, rcut=3.0), len(pos))[0]
+    fnf = BO.sqrtm_apply(RFU, psi_nf.reshape(-1)).reshape(-1, 6)
+    return dict(pos=pos, body=body, L=L, n=n, xi=xi, field=field, psi_r=psi_r, psi_nf=psi_nf,
+                uw=uw, ur=ur, fnf=fnf)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-6), (MIXED, 1e-5)])
+def test_wave_slip_matches_oracle(pkg, sysB, prec, tol):
+    d = sysB
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], precision=prec, **HI)
+    z = np.zeros_like(d["psi_r"])
+    slip, fnf, st = s.brownian(1.0, 1.0, wave_field=d["field"], psi_real=z,
+                               psi_nf=np.zeros_like(d["psi_nf"]))
+    s.close()
+    assert rel(slip / np.sqrt(2.0), d["uw"]) < tol
+    assert np.all(fnf == 0.0)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-6), (MIXED, 1e-5)])
+def test_real_space_lanczos_matches_dense_square_root(pkg, sysB, prec, tol):
+    d = sysB
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], precision=prec, **HI)
+    slip, fnf, st = s.brownian(2.0, 0.5, wave_field=np.zeros_like(d["field"]), psi_real=d["psi_r"],
+                               psi_nf=np.zeros_like(d["psi_nf"]))
+    s.close()
+    assert 2 <= st["iters"] <= 60
+    assert rel(slip / np.sqrt(2.0 * 2.0 / 0.5), d["ur"]) < tol
+
+
+def test_near_field_lanczos_matches_dense_square_root(pkg, sysB):
+    d = sysB
+    assert np.abs(d["fnf"]).max() > 0
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], **HI)
+    slip, fnf, st = s.brownian(1.0, 1.0, wave_field=np.zeros_like(d["field"]),
+                               psi_real=np.zeros_like(d["psi_r"]), psi_nf=d["psi_nf"])
+    s.close()
+    assert st["outer_iters"] >= 2
+    assert rel(fnf / np.sqrt(2.0), d["fnf"]) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol,flags", [(FP64, 1e-6, 0), (MIXED, 1e-5, 0), (MIXED, 1e-5, 4)])
+def test_brownian_solve_matches_oracle(pkg, sysB, prec, tol, flags):
+    d = sysB
+    kT, dt = 0.7, 0.01
+    sc = np.sqrt(2.0 * kT / dt)
+    uB = sc * (d["uw"] + d["ur"])
+    fB = sc * d["fnf"]
+    ft = synth.random_forces(d["body"].max() + 1, 12)
+    ref = BO.solve_brownian(d["pos"], d["body"], d["L"], uB, fB, gamma=1.0, FT=ft, rlub=3.0)
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], precision=prec, flags=flags, **HI)
+    slip, fnf, _ = s.brownian(kT, dt, wave_field=d["field"], psi_real=d["psi_r"], psi_nf=d["psi_nf"])
+    assert rel(slip, uB) < tol and rel(fnf, fB) < 1e-6
+    vel, S, st, status = s.solve(ft, 1.0)
+    assert status == pkg.FSD_OK
+    assert rel(vel, ref["U"]) < tol
+    assert rel(S, ref["S"]) < tol
+    # the terms are used once: the next solve is the deterministic one
+    vel2, S2, _, _ = s.solve(ft, 1.0)
+    s.close()
+    det = O.solve(d["pos"], d["body"], d["L"], gamma=1.0, FT=ft, rlub=3.0)
+    assert rel(vel2, det["U"]) < tol
+
+
+def test_internal_generator_matches_oracle_philox(pkg, sysB):
+    d = sysB
+    seed, step = 123456789012345, 42
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], **HI)
+    slip, fnf, st = s.brownian(1.0, 1.0, seed=seed, step=step)
+    s.close()
+    n, N = d["n"], len(d["pos"])
+    field = BO.philox_wave_field(n, seed, step)
+    psi_r = BO.philox_psi(N, seed, step, 2, 11)
+    psi_nf = BO.philox_psi(N, seed, step, 3, 6)
+    unw, X, r = O.body_geometry(d["pos"], d["body"], d["L"])
+    uw = BO.brownian_wave_slip(unw, d["L"], d["xi"], n, field)
+    rc = 2.0 + np.sqrt(46.0) / d["xi"]
+    Mr = O.mobility_real_dense(unw, d["L"], d["xi"], rc).reshape(11 * N, -1)
+    ur = BO.sqrtm_apply(Mr, psi_r.reshape(-1)).reshape(-1, 11)
+    RFU = O.split_grand(O.lubrication_dense(unw, d["body"], d["L"], rcut=3.0), N)[0]
+    f = BO.sqrtm_apply(RFU, psi_nf.reshape(-1)).reshape(-1, 6)
+    assert rel(slip / np.sqrt(2.0), uw + ur) < 1e-6
+    assert rel(fnf / np.sqrt(2.0), f) < 1e-6
+
+
+def test_invalid_brownian_arguments(pkg, sysB):
+    d = sysB
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], **HI)
+    with pytest.raises(pkg.FsdError):
+        s.brownian(-1.0, 1.0)
+    with pytest.raises(pkg.FsdError):
+        s.brownian(1.0, 0.0)
+    s.close()
