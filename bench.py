@@ -340,6 +340,35 @@ def run_ours(args, rank, world, local_rank):
             "iters_per_step": itw / args.steps,
             "note": "same workload and tolerance; GMRES starts from the previous step's solution"}
 
+    # ---- Brownian step: fsd_brownian (PSE far-field slip, near-field force,
+    #      Lanczos square roots) before each step, kT = 1 (same workload)
+    s = make(pkg.FSD_MIXED)
+    for k in range(args.warmup):
+        s.brownian(1.0, w["dt"], seed=11, step=k, outputs=False)
+        s.step(None, w["shear"], w["dt"])
+    barrier()
+    torch.cuda.synchronize()
+    eb0 = torch.cuda.Event(enable_timing=True)
+    eb1 = torch.cuda.Event(enable_timing=True)
+    eb0.record(stream)
+    lz_r = lz_n = itb = 0
+    for k in range(args.steps):
+        _, _, stb = s.brownian(1.0, w["dt"], seed=11, step=1000 + k, outputs=False)
+        lz_r += stb["iters"]
+        lz_n += stb["outer_iters"]
+        stb2, _ = s.step(None, w["shear"], w["dt"])
+        itb += stb2["iters"]
+    eb1.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    msb = max_over_ranks(eb0.elapsed_time(eb1))
+    brown = {"value": Nt * args.steps * world / (msb / 1e3), "ms_per_step": msb / args.steps,
+             "kT": 1.0, "dt": w["dt"], "iters_per_step": itb / args.steps,
+             "lanczos_real_per_step": lz_r / args.steps, "lanczos_near_per_step": lz_n / args.steps,
+             "note": "each step: PSE far-field slip (analytic wave part + Lanczos real-space square root, "
+                     "FP32 operator) and near-field Brownian force (Lanczos, FP64), then the mixed solve "
+                     "with them; drift not included"}
+
     # ---- plain FP64 path on the same initial configuration
     s64 = make(pkg.FSD_FP64)
     for _ in range(max(1, min(args.warmup, 2))):
@@ -405,6 +434,7 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms_per_step": {g: round(v[0] / PS, 4) for g, v in prof.items()},
         "profile_iters_per_step": prof_iters / PS,
         "warm_start": warm,
+        "brownian": brown,
         "roofline": roof,
         "cpu_baseline": base,
         "e2e": e2e,

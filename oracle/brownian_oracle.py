@@ -19,8 +19,12 @@ Algorithm 1 step 3):
         u_w(x_i) = V^(-1/2) sum_k e^(i k.x_i) Q(k)^H sqrt(H(k)/(eta k^2)) (I - k k) xi(k),
     whose covariance over the field is exactly the wave-vector sum M_w
     (pinned in tests/test_oracle_brownian.py);
-* near-field Brownian force  F^B_nf = sqrt(2 kT/dt) (R_FU^nf)^(1/2) psi_nf,
-  R_FU^nf the bead-level near-field resistance (dense eigendecomposition);
+* near-field Brownian force  F^B_nf = sqrt(2 kT/dt) R_FU^nf^(1/2) psi_nf with
+  the preconditioned square root of the "fast preconditioned Krylov" sampling
+  (Sec. 2.2): G = blockdiag(D_b^(-1/2)), D_b the 6x6 diagonal block of bead b
+  (eigenvalues below 1e-12 of the block's largest count as zero and get
+  scale 1), and R^(1/2) psi := G^-1 (G R G)^(1/2) psi, whose covariance is R
+  for any such G (pinned); R_FU^nf is the bead-level near-field resistance;
 * the saddle-point right-hand side with them (Eq. spm_agg): bead rows + u^B,
   body rows - Sigma F^B_nf.
 
@@ -182,6 +186,25 @@ def sqrtm_apply(A, v):
     return U @ (np.sqrt(np.clip(lam, 0.0, None)) * (U.T @ v))
 
 
+def block_precond_sqrt_apply(R, v, bs=6):
+    """G^-1 (G R G)^(1/2) v with G = blockdiag(D_b^(-1/2)) over bs x bs
+    diagonal blocks D_b of the symmetric positive semidefinite R."""
+    nb = R.shape[0] // bs
+    G = np.zeros_like(R)
+    Gi = np.zeros_like(R)
+    for b in range(nb):
+        sl = slice(b * bs, (b + 1) * bs)
+        D = 0.5 * (R[sl, sl] + R[sl, sl].T)
+        lam, U = np.linalg.eigh(D)
+        lmax = max(lam.max(), 0.0)
+        pos = (lam > 1e-12 * lmax) & (lam > 0.0)
+        fs = np.where(pos, 1.0 / np.sqrt(np.where(pos, lam, 1.0)), 1.0)
+        fi = np.where(pos, np.sqrt(np.where(pos, lam, 1.0)), 1.0)
+        G[sl, sl] = (U * fs) @ U.T
+        Gi[sl, sl] = (U * fi) @ U.T
+    return Gi @ sqrtm_apply(G @ R @ G, v)
+
+
 def brownian_terms(pos, body, L, xi, n, field, psi_r, psi_nf, kT, dt, rlub=3.0, a=1.0, eta=1.0,
                    hmin=1e-3):
     """(u^B (N, 11), F^B_nf (N, 6)) of Eq. SP2 / Eq. UBff for the given random
@@ -200,7 +223,7 @@ def brownian_terms(pos, body, L, xi, n, field, psi_r, psi_nf, kT, dt, rlub=3.0, 
     else:
         Rg = np.zeros((11 * N, 11 * N))
     RFU = F.split_grand(Rg, N)[0]
-    fnf = sqrtm_apply(RFU, np.asarray(psi_nf).reshape(-1)).reshape(N, 6)
+    fnf = block_precond_sqrt_apply(RFU, np.asarray(psi_nf).reshape(-1)).reshape(N, 6)
     return s * (uw + ur), s * fnf
 
 

@@ -238,9 +238,11 @@ class Suspension:
         self._check(self.lib.fsd_rhs(self.ctx, _ptr(ft), float(shear), _ptr(out)))
         return out
 
-    def brownian(self, kT, dt, seed=0, step=0, wave_field=None, psi_real=None, psi_nf=None):
+    def brownian(self, kT, dt, seed=0, step=0, wave_field=None, psi_real=None, psi_nf=None,
+                 outputs=True):
         """fsd_brownian: Brownian terms of the next solve; returns (slip
-        [Nt, 11], near-field force [Nt, 6], stats)."""
+        [Nt, 11], near-field force [Nt, 6], stats) (None, None, stats when
+        outputs is false)."""
         def prep(a):
             if a is None or hasattr(a, "data_ptr"):
                 return a
@@ -248,8 +250,8 @@ class Suspension:
         if wave_field is not None and not hasattr(wave_field, "data_ptr"):
             wave_field = np.ascontiguousarray(np.stack([np.asarray(wave_field).real,
                                                         np.asarray(wave_field).imag], -1))
-        slip = np.zeros((self.n_beads, 11))
-        fnf = np.zeros((self.n_beads, 6))
+        slip = np.zeros((self.n_beads, 11)) if outputs else None
+        fnf = np.zeros((self.n_beads, 6)) if outputs else None
         st_ = FsdStats()
         self._check(self.lib.fsd_brownian(self.ctx, float(kT), float(dt), int(seed), int(step),
                                           _ptr(wave_field), _ptr(prep(psi_real)), _ptr(prep(psi_nf)),

@@ -593,7 +593,8 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
                                  double *str_int, fsd_stats *stats, double t0_ms) {
   auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = c.launches;
-  prepare(c);
+  if (!c.geom_fresh) prepare(c);
+  c.geom_fresh = false;
   fsd_status fl = check_flags(c);
   const double *ft_int = nullptr;
   if (ft_user) {
@@ -652,7 +653,8 @@ static StepMark graph_step_begin(Ctx &c, const double *ft_user, double shear, bo
   StepMark mk;
   mk.t0 = std::chrono::steady_clock::now();
   mk.l0 = c.launches;
-  prepare(c);
+  if (!c.geom_fresh) prepare(c);
+  c.geom_fresh = false;
   GraphRun o;
   o.warm = (c.prm.flags & FSD_FLAG_WARM_START) && c.have_prev;
   o.has_ft = ft_user != nullptr;
@@ -1115,6 +1117,7 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
   auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = c.launches;
   prepare(c);
+  c.geom_fresh = true;  // the next solve reuses this preparation
   const size_t nh = (size_t)c.n / 2 + 1;
   DBuf<double> sf, sr, sn;
   const double *fd = wave_field ? dev_in(c, wave_field, 6 * (size_t)c.n * c.n * nh, sf) : nullptr;

@@ -58,6 +58,88 @@ __global__ void k_bsr_bead(int Nt, const int *__restrict__ brow, const int *__re
   for (int a = 6; a < LDB; ++a) yb[a] = 0.0;
 }
 
+// Per bead: the near-field diagonal block D (6x6, symmetric positive
+// semidefinite) -> G = D^(-1/2) and its inverse D^(1/2) (cyclic Jacobi in
+// registers; eigenvalues below 1e-12 of the largest are treated as zero:
+// their directions get G = 1, D^(1/2) = 1, and carry no near-field coupling).
+__global__ void k_block_isqrt(int Nt, const double *__restrict__ bdiag, double *G, double *Gi) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Nt) return;
+  double a[6][6], v[6][6];
+  const double *D = bdiag + (size_t)b * 36;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      a[i][j] = 0.5 * (D[6 * i + j] + D[6 * j + i]);
+      v[i][j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j) off += a[i][j] * a[i][j];
+    if (off < 1e-40) break;
+    for (int p = 0; p < 5; ++p)
+      for (int q = p + 1; q < 6; ++q) {
+        const double apq = a[p][q];
+        if (fabs(apq) < 1e-300) continue;
+        const double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < 6; ++k) {
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = cs * akp - sn * akq;
+          a[k][q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < 6; ++k) {
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = cs * apk - sn * aqk;
+          a[q][k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < 6; ++k) {
+          const double vkp = v[k][p], vkq = v[k][q];
+          v[k][p] = cs * vkp - sn * vkq;
+          v[k][q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int i = 0; i < 6; ++i) lmax = fmax(lmax, a[i][i]);
+  double fs[6], fi[6];
+  for (int i = 0; i < 6; ++i) {
+    const bool pos = a[i][i] > 1e-12 * lmax && a[i][i] > 0.0;
+    fs[i] = pos ? 1.0 / sqrt(a[i][i]) : 1.0;
+    fi[i] = pos ? sqrt(a[i][i]) : 1.0;
+  }
+  double *g = G + (size_t)b * 36, *gi = Gi + (size_t)b * 36;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int k = 0; k < 6; ++k) {
+        s1 += v[i][k] * fs[k] * v[j][k];
+        s2 += v[i][k] * fi[k] * v[j][k];
+      }
+      g[6 * i + j] = s1;
+      gi[6 * i + j] = s2;
+    }
+}
+
+// y_b = B_b x_b (6x6 per bead, components 0..5; 6..11 zero)
+// (may run in place: every input of a bead is read before its output is written)
+__global__ void k_block_apply(int Nt, const double *__restrict__ Bm, const double *x, double *y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Nt) return;
+  const double *B = Bm + (size_t)b * 36;
+  const double *xb = x + (size_t)b * LDB;
+  double o[6];
+  for (int a = 0; a < 6; ++a) {
+    double s = 0.0;
+    for (int q = 0; q < 6; ++q) s += B[6 * a + q] * xb[q];
+    o[a] = s;
+  }
+  double *yb = y + (size_t)b * LDB;
+  for (int a = 0; a < 6; ++a) yb[a] = o[a];
+  for (int a = 6; a < LDB; ++a) yb[a] = 0.0;
+}
+
 // caller's psi [Nt][w] (bead order of the caller) -> solution layout
 __global__ void k_psi_in(int Nt, const int *__restrict__ perm, const double *__restrict__ user, int w,
                          double *x) {
@@ -279,13 +361,30 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
                                                              c.bwork.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
+    // preconditioned sampling: with G = blockdiag(D_b^(-1/2)), D_b the
+    // bead's diagonal block, F = G^-1 (G R G^T)^(1/2) psi has covariance R and
+    // the Lanczos iteration runs on the well-scaled G R G^T
+    if (c.bgain.n < (size_t)c.Nt * 72) c.bgain.alloc((size_t)c.Nt * 72);
+    double *G = c.bgain.p, *Gi = c.bgain.p + (size_t)c.Nt * 36;
+    k_block_isqrt<<<ceil_div(c.Nt, 64), 64, 0, c.stream>>>(c.Nt, c.op64.bdiag.p, G, Gi);
+    FSD_LAUNCHED(c);
+    if (c.bwork2.n < (size_t)n) c.bwork2.alloc(n);
+    double *tmp = c.bwork2.p;
+    FSD_CUDA(cudaMemsetAsync(tmp, 0, n * sizeof(double), c.stream));
     auto nf_op = [&](const double *x, double *y) {
+      k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, G, x, tmp);
+      FSD_LAUNCHED(c);
       k_bsr_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.brow.p, c.bcol.p, c.op64.bval.p,
-                                                            c.op64.bdiag.p, x, y);
+                                                            c.op64.bdiag.p, tmp, y);
+      FSD_LAUNCHED(c);
+      k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, G, y, y);
       FSD_LAUNCHED(c);
       FSD_CUDA(cudaGetLastError());
     };
-    inf = lanczos_sqrt(c, nf_op, c.bwork.p, c.bfnf.p, tol, maxit);
+    inf = lanczos_sqrt(c, nf_op, c.bwork.p, c.t2.p, tol, maxit);
+    k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, Gi, c.t2.p, c.bfnf.p);
+    FSD_LAUNCHED(c);
+    FSD_CUDA(cudaGetLastError());
   } else {
     FSD_CUDA(cudaMemsetAsync(c.bfnf.p, 0, n * sizeof(double), c.stream));
   }

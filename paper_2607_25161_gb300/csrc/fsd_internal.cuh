@@ -176,8 +176,11 @@ struct Ctx {
   fsd_status last_warning = FSD_OK;
   int64_t n_pairs = 0, n_lub = 0;
   // ---- Brownian forcing of the next solve (brownian.cu)
-  DBuf<double> bslip, bfnf, bwork;  // slip u_w + u_r and near-field force (solution layout), scratch
+  DBuf<double> bslip, bfnf, bwork, bwork2;  // slip u_w + u_r, near-field force (solution layout), scratch
+  DBuf<double> bgain;               // per bead D^(-1/2) and D^(1/2) of the near-field diagonal block
   bool brown_pending = false;       // the next solve adds them to its right-hand side
+  bool geom_fresh = false;          // geometry prepared at the current positions (the next
+                                    // solve may skip its own preparation)
   double brown_scale = 0.0;         // sqrt(2 kT / dt)
   // ---- captured solve graphs
   GraphCache *gcache = nullptr;

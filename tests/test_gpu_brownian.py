@@ -8,7 +8,8 @@ Tolerances (relative L2):
     1e-6 FP64, 1e-5 with the FP32 operator;
   real-space square root (Lanczos, coefficient change < 1e-7 on the
     real-space operator): 1e-6 FP64, 1e-5 FP32;
-  near-field square root (Lanczos on the FP64 bead blocks): 1e-6;
+  near-field square root (block-Jacobi preconditioned Lanczos on the FP64
+    bead blocks, against the oracle's preconditioned square root): 1e-6;
   Brownian solve at GMRES 1e-10: 1e-6 FP64, 1e-5 mixed.
 """
 
@@ -65,7 +66,7 @@ def sysB(pkg):
     Mr = O.mobility_real_dense(unw, L, xi, rc).reshape(11 * len(pos), -1)
     ur = BO.sqrtm_apply(Mr, psi_r.reshape(-1)).reshape(-1, 11)
     RFU = O.split_grand(O.lubrication_dense(unw, body, L, rcut=3.0), len(pos))[0]
-    fnf = BO.sqrtm_apply(RFU, psi_nf.reshape(-1)).reshape(-1, 6)
+    fnf = BO.block_precond_sqrt_apply(RFU, psi_nf.reshape(-1)).reshape(-1, 6)
     return dict(pos=pos, body=body, L=L, n=n, xi=xi, field=field, psi_r=psi_r, psi_nf=psi_nf,
                 uw=uw, ur=ur, fnf=fnf)
 
@@ -143,7 +144,7 @@ def test_internal_generator_matches_oracle_philox(pkg, sysB):
     Mr = O.mobility_real_dense(unw, d["L"], d["xi"], rc).reshape(11 * N, -1)
     ur = BO.sqrtm_apply(Mr, psi_r.reshape(-1)).reshape(-1, 11)
     RFU = O.split_grand(O.lubrication_dense(unw, d["body"], d["L"], rcut=3.0), N)[0]
-    f = BO.sqrtm_apply(RFU, psi_nf.reshape(-1)).reshape(-1, 6)
+    f = BO.block_precond_sqrt_apply(RFU, psi_nf.reshape(-1)).reshape(-1, 6)
     assert rel(slip / np.sqrt(2.0), uw + ur) < 1e-6
     assert rel(fnf / np.sqrt(2.0), f) < 1e-6
 

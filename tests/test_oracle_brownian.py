@@ -9,7 +9,8 @@ Eq. UBff):
   to each independent field component gives the covariance, which must equal
   the wave-vector sum M_w of fsd_oracle (pinned elsewhere against closed forms
   and xi-independence);
-* the dense square root applied twice is the operator;
+* the dense square root applied twice is the operator; the block-Jacobi
+  preconditioned square root G^-1 (G R G)^(1/2) has covariance exactly R;
 * a near-field Brownian force enters the body rows exactly like an applied
   aggregate force and torque (the same Sigma projection, the same sign);
 * Box-Muller normals from Philox have zero mean, unit variance, no
@@ -114,3 +115,17 @@ def test_zero_noise_is_the_deterministic_solve():
     ref = O.solve(pos, body, L, gamma=1.0, rlub=0.0, M=M)
     assert np.allclose(out["U"], ref["U"], rtol=1e-13, atol=1e-15)
     assert np.allclose(out["S"], ref["S"], rtol=1e-13, atol=1e-15)
+
+
+def test_preconditioned_square_root_has_covariance_R():
+    import synth
+
+    rng = np.random.default_rng(3)
+    shapes = [synth.random_attachment_aggregate(k, rng) for k in (2, 3, 4, 2, 3)]
+    L = synth.box_for_phi(14, 0.15)
+    pos, body = synth.pack_suspension(shapes, L, rng, h_gen=0.05)
+    R = O.split_grand(O.lubrication_dense(pos, body, L, rcut=3.0), len(pos))[0]
+    assert np.abs(R).max() > 0
+    n = R.shape[0]
+    S = np.column_stack([B.block_precond_sqrt_apply(R, e) for e in np.eye(n)])
+    assert np.abs(S @ S.T - R).max() < 1e-9 * np.abs(R).max()
