@@ -352,10 +352,12 @@ def run_ours(args, rank, world, local_rank):
     eb1 = torch.cuda.Event(enable_timing=True)
     eb0.record(stream)
     lz_r = lz_n = itb = 0
+    lz_ch = 0.0
     for k in range(args.steps):
         _, _, stb = s.brownian(1.0, w["dt"], seed=11, step=1000 + k, outputs=False)
         lz_r += stb["iters"]
         lz_n += stb["outer_iters"]
+        lz_ch = max(lz_ch, stb["rel_residual"])
         stb2, _ = s.step(None, w["shear"], w["dt"])
         itb += stb2["iters"]
     eb1.record(stream)
@@ -365,6 +367,7 @@ def run_ours(args, rank, world, local_rank):
     brown = {"value": Nt * args.steps * world / (msb / 1e3), "ms_per_step": msb / args.steps,
              "kT": 1.0, "dt": w["dt"], "iters_per_step": itb / args.steps,
              "lanczos_real_per_step": lz_r / args.steps, "lanczos_near_per_step": lz_n / args.steps,
+             "lanczos_last_change_max": lz_ch,
              "note": "each step: PSE far-field slip (analytic wave part + Lanczos real-space square root, "
                      "FP32 operator) and near-field Brownian force (Lanczos, FP64), then the mixed solve "
                      "with them; drift not included"}

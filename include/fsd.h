@@ -325,7 +325,9 @@ void fsd_destroy_batch(fsd_batch *b);
  *   psi_real [n_beads][11], psi_nf [n_beads][6]: standard normals.
  * Outputs (NULL to skip): slip [n_beads][11] = u^B, force_nf [n_beads][6] =
  * F^B.  stats: iters = real-space Lanczos steps, outer_iters = near-field
- * Lanczos steps. */
+ * Lanczos steps (each stops when its coefficients change by less than 1e-7
+ * relative, or after 60 steps), rel_residual = the larger last relative
+ * change of the two. */
 fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint64_t step,
                         const double *wave_field, const double *psi_real,
                         const double *psi_nf, double *slip, double *force_nf,

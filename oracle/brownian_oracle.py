@@ -21,10 +21,11 @@ Algorithm 1 step 3):
     (pinned in tests/test_oracle_brownian.py);
 * near-field Brownian force  F^B_nf = sqrt(2 kT/dt) R_FU^nf^(1/2) psi_nf with
   the preconditioned square root of the "fast preconditioned Krylov" sampling
-  (Sec. 2.2): G = blockdiag(D_b^(-1/2)), D_b the 6x6 diagonal block of bead b
-  (eigenvalues below 1e-12 of the block's largest count as zero and get
-  scale 1), and R^(1/2) psi := G^-1 (G R G)^(1/2) psi, whose covariance is R
-  for any such G (pinned); R_FU^nf is the bead-level near-field resistance;
+  (Sec. 2.2): per bead b, L_b L_b^T = D_b + 1e-6 (tr D_b / 6) I (Cholesky;
+  D_b the 6x6 diagonal block of R; L_b = I when tr D_b = 0), G = blockdiag
+  (L_b^-1), and R^(1/2) psi := L (G R G^T)^(1/2) psi, whose covariance is R
+  for any invertible G (pinned); R_FU^nf is the bead-level near-field
+  resistance;
 * the saddle-point right-hand side with them (Eq. spm_agg): bead rows + u^B,
   body rows - Sigma F^B_nf.
 
@@ -187,22 +188,23 @@ def sqrtm_apply(A, v):
 
 
 def block_precond_sqrt_apply(R, v, bs=6):
-    """G^-1 (G R G)^(1/2) v with G = blockdiag(D_b^(-1/2)) over bs x bs
-    diagonal blocks D_b of the symmetric positive semidefinite R."""
+    """L (G R G^T)^(1/2) v with L = blockdiag(chol(D_b + 1e-6 tr(D_b)/6 I))
+    over the bs x bs diagonal blocks D_b of the symmetric positive
+    semidefinite R (L_b = I where tr D_b = 0) and G = L^-1."""
     nb = R.shape[0] // bs
+    Lm = np.zeros_like(R)
     G = np.zeros_like(R)
-    Gi = np.zeros_like(R)
     for b in range(nb):
         sl = slice(b * bs, (b + 1) * bs)
         D = 0.5 * (R[sl, sl] + R[sl, sl].T)
-        lam, U = np.linalg.eigh(D)
-        lmax = max(lam.max(), 0.0)
-        pos = (lam > 1e-12 * lmax) & (lam > 0.0)
-        fs = np.where(pos, 1.0 / np.sqrt(np.where(pos, lam, 1.0)), 1.0)
-        fi = np.where(pos, np.sqrt(np.where(pos, lam, 1.0)), 1.0)
-        G[sl, sl] = (U * fs) @ U.T
-        Gi[sl, sl] = (U * fi) @ U.T
-    return Gi @ sqrtm_apply(G @ R @ G, v)
+        tr = np.trace(D)
+        if tr > 0:
+            Lb = np.linalg.cholesky(D + 1e-6 * tr / bs * np.eye(bs))
+        else:
+            Lb = np.eye(bs)
+        Lm[sl, sl] = Lb
+        G[sl, sl] = np.linalg.inv(Lb)
+    return Lm @ sqrtm_apply(G @ R @ G.T, v)
 
 
 def brownian_terms(pos, body, L, xi, n, field, psi_r, psi_nf, kT, dt, rlub=3.0, a=1.0, eta=1.0,

@@ -1124,7 +1124,8 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
   const double *rd = psi_real ? dev_in(c, psi_real, 11 * (size_t)c.Nt, sr) : nullptr;
   const double *nd = psi_nf ? dev_in(c, psi_nf, 6 * (size_t)c.Nt, sn) : nullptr;
   int ir = 0, inf = 0;
-  brownian_sample(c, kT, dt, seed, step, fd, rd, nd, &ir, &inf);
+  double change = 0.0;
+  brownian_sample(c, kT, dt, seed, step, fd, rd, nd, &ir, &inf, &change);
   for (int q = 0; q < 2; ++q) {
     double *user = q == 0 ? slip : force_nf;
     const int w = q == 0 ? 11 : 6;
@@ -1145,6 +1146,7 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
     std::memset(stats, 0, sizeof(*stats));
     stats->iters = ir;
     stats->outer_iters = inf;
+    stats->rel_residual = change;
     stats->kernel_launches = c.launches - l0;
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     stats->grid = c.n;

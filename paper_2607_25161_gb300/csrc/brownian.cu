@@ -58,73 +58,59 @@ __global__ void k_bsr_bead(int Nt, const int *__restrict__ brow, const int *__re
   for (int a = 6; a < LDB; ++a) yb[a] = 0.0;
 }
 
-// Per bead: the near-field diagonal block D (6x6, symmetric positive
-// semidefinite) -> G = D^(-1/2) and its inverse D^(1/2) (cyclic Jacobi in
-// registers; eigenvalues below 1e-12 of the largest are treated as zero:
-// their directions get G = 1, D^(1/2) = 1, and carry no near-field coupling).
-__global__ void k_block_isqrt(int Nt, const double *__restrict__ bdiag, double *G, double *Gi) {
+// Per bead: Cholesky factor L of the near-field diagonal block D (6x6,
+// symmetric positive semidefinite), regularised as D + 1e-6 (tr D / 6) I so
+// that null directions (which carry no near-field coupling) stay
+// invertible, and G = L^-1 (forward substitution).  A bead without
+// near-field pairs (tr D = 0) gets L = G = I.  Row-major 6x6 each.
+__global__ void k_block_chol(int Nt, const double *__restrict__ bdiag, double *Lm, double *Gm) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Nt) return;
-  double a[6][6], v[6][6];
   const double *D = bdiag + (size_t)b * 36;
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) {
-      a[i][j] = 0.5 * (D[6 * i + j] + D[6 * j + i]);
-      v[i][j] = i == j ? 1.0 : 0.0;
-    }
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < 6; ++i)
-      for (int j = i + 1; j < 6; ++j) off += a[i][j] * a[i][j];
-    if (off < 1e-40) break;
-    for (int p = 0; p < 5; ++p)
-      for (int q = p + 1; q < 6; ++q) {
-        const double apq = a[p][q];
-        if (fabs(apq) < 1e-300) continue;
-        const double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
-        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
-        for (int k = 0; k < 6; ++k) {
-          const double akp = a[k][p], akq = a[k][q];
-          a[k][p] = cs * akp - sn * akq;
-          a[k][q] = sn * akp + cs * akq;
-        }
-        for (int k = 0; k < 6; ++k) {
-          const double apk = a[p][k], aqk = a[q][k];
-          a[p][k] = cs * apk - sn * aqk;
-          a[q][k] = sn * apk + cs * aqk;
-        }
-        for (int k = 0; k < 6; ++k) {
-          const double vkp = v[k][p], vkq = v[k][q];
-          v[k][p] = cs * vkp - sn * vkq;
-          v[k][q] = sn * vkp + cs * vkq;
-        }
-      }
-  }
-  double lmax = 0.0;
-  for (int i = 0; i < 6; ++i) lmax = fmax(lmax, a[i][i]);
-  double fs[6], fi[6];
+  double A[6][6], L[6][6], G[6][6];
+  double tr = 0.0;
   for (int i = 0; i < 6; ++i) {
-    const bool pos = a[i][i] > 1e-12 * lmax && a[i][i] > 0.0;
-    fs[i] = pos ? 1.0 / sqrt(a[i][i]) : 1.0;
-    fi[i] = pos ? sqrt(a[i][i]) : 1.0;
+    for (int j = 0; j < 6; ++j) {
+      A[i][j] = 0.5 * (D[6 * i + j] + D[6 * j + i]);
+      L[i][j] = G[i][j] = 0.0;
+    }
+    tr += A[i][i];
   }
-  double *g = G + (size_t)b * 36, *gi = Gi + (size_t)b * 36;
+  if (tr > 0.0) {
+    const double reg = 1e-6 * tr / 6.0;
+    for (int i = 0; i < 6; ++i) A[i][i] += reg;
+    for (int j = 0; j < 6; ++j) {
+      double s = A[j][j];
+      for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+      L[j][j] = sqrt(s > 0.0 ? s : reg);
+      for (int i = j + 1; i < 6; ++i) {
+        double t = A[i][j];
+        for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+        L[i][j] = t / L[j][j];
+      }
+    }
+    for (int c = 0; c < 6; ++c)
+      for (int i = c; i < 6; ++i) {
+        double t = i == c ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) t -= L[i][k] * G[k][c];
+        G[i][c] = t / L[i][i];
+      }
+  } else {
+    for (int i = 0; i < 6; ++i) L[i][i] = G[i][i] = 1.0;
+  }
+  double *lo = Lm + (size_t)b * 36, *go = Gm + (size_t)b * 36;
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) {
-      double s1 = 0.0, s2 = 0.0;
-      for (int k = 0; k < 6; ++k) {
-        s1 += v[i][k] * fs[k] * v[j][k];
-        s2 += v[i][k] * fi[k] * v[j][k];
-      }
-      g[6 * i + j] = s1;
-      gi[6 * i + j] = s2;
+      lo[6 * i + j] = L[i][j];
+      go[6 * i + j] = G[i][j];
     }
 }
 
-// y_b = B_b x_b (6x6 per bead, components 0..5; 6..11 zero)
-// (may run in place: every input of a bead is read before its output is written)
-__global__ void k_block_apply(int Nt, const double *__restrict__ Bm, const double *x, double *y) {
+// y_b = B_b x_b, or B_b^T x_b with tr (6x6 per bead, components 0..5;
+// 6..11 zero).  May run in place: every input of a bead is read before its
+// output is written.
+__global__ void k_block_apply(int Nt, const double *__restrict__ Bm, int tr, const double *x,
+                              double *y) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Nt) return;
   const double *B = Bm + (size_t)b * 36;
@@ -132,7 +118,7 @@ __global__ void k_block_apply(int Nt, const double *__restrict__ Bm, const doubl
   double o[6];
   for (int a = 0; a < 6; ++a) {
     double s = 0.0;
-    for (int q = 0; q < 6; ++q) s += B[6 * a + q] * xb[q];
+    for (int q = 0; q < 6; ++q) s += (tr ? B[6 * q + a] : B[6 * a + q]) * xb[q];
     o[a] = s;
   }
   double *yb = y + (size_t)b * LDB;
@@ -218,20 +204,21 @@ static void jacobi_eigen(int m, std::vector<double> A, std::vector<double> &lam,
       for (int q = p + 1; q < m; ++q) {
         const double apq = a(p, q);
         if (apq == 0.0) continue;
-        // rotation angle zeroing a(p, q): tan(2 theta) = 2 a_pq / (a_qq - a_pp)
-        const double tau = (a(q, q) - a(p, p)) / (2.0 * apq);
-        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        // rotation zeroing a(p, q): cot(2 theta) = (a_qq - a_pp) / (2 a_pq),
+        // t = tan(theta); the update keeps the matrix exactly symmetric
+        const double th = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(1.0 + th * th));
         const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
-        for (int k = 0; k < m; ++k) {  // columns p, q
-          const double akp = a(k, p), akq = a(k, q);
-          a(k, p) = cs * akp - sn * akq;
-          a(k, q) = sn * akp + cs * akq;
+        const double app = a(p, p) - t * apq, aqq = a(q, q) + t * apq;
+        for (int r = 0; r < m; ++r) {
+          if (r == p || r == q) continue;
+          const double arp = a(r, p), arq = a(r, q);
+          a(r, p) = a(p, r) = cs * arp - sn * arq;
+          a(r, q) = a(q, r) = sn * arp + cs * arq;
         }
-        for (int k = 0; k < m; ++k) {  // rows p, q
-          const double apk = a(p, k), aqk = a(q, k);
-          a(p, k) = cs * apk - sn * aqk;
-          a(q, k) = sn * apk + cs * aqk;
-        }
+        a(p, p) = app;
+        a(q, q) = aqq;
+        a(p, q) = a(q, p) = 0.0;
         for (int k = 0; k < m; ++k) {
           const double qkp = Q[(size_t)p * m + k], qkq = Q[(size_t)q * m + k];
           Q[(size_t)p * m + k] = cs * qkp - sn * qkq;
@@ -273,11 +260,13 @@ static double dev_norm(Ctx &c, const double *x) {
 // (||b|| e_1), stopped when the coefficients change by less than tol
 // (relative).  apply(x, y) sets y = A x (bead rows; body rows must stay 0).
 template <class Apply>
-static int lanczos_sqrt(Ctx &c, Apply apply, const double *b, double *out, double tol, int maxit) {
+static int lanczos_sqrt(Ctx &c, Apply apply, const double *b, double *out, double tol, int maxit,
+                        double *change) {
   const int64_t ld = c.nunk, n = c.nunk;
   double *V = c.V.p, *w = c.w.p;
   const double bnorm = dev_norm(c, b);
   FSD_CUDA(cudaMemsetAsync(out, 0, n * sizeof(double), c.stream));
+  if (change) *change = 0.0;
   if (!(bnorm > 0.0)) return 0;
   vec_scale_host(c, V, b, 1.0 / bnorm);
   std::vector<double> al, be, cf, prev;
@@ -303,6 +292,7 @@ static int lanczos_sqrt(Ctx &c, Apply apply, const double *b, double *out, doubl
       cn += cf[i] * cf[i];
     }
     prev = cf;
+    if (change) *change = j > 0 && cn > 0 ? std::sqrt(dn / cn) : 1.0;
     if (j > 0 && dn <= tol * tol * cn) break;
     if (beta <= 1e-14 * bnorm || j + 1 == maxit) break;
     be.push_back(beta);
@@ -319,7 +309,7 @@ static int lanczos_sqrt(Ctx &c, Apply apply, const double *b, double *out, doubl
 // ------------------------------------------------------------- sampling
 void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
                      const double *field_dev, const double *psi_r_dev, const double *psi_nf_dev,
-                     int *iters_real, int *iters_nf) {
+                     int *iters_real, int *iters_nf, double *change) {
   if (!(kT >= 0.0) || !(dt > 0.0)) throw Invalid{"kT must be >= 0 and dt > 0"};
   const int64_t n = c.nunk;
   if (c.bslip.n < (size_t)n) c.bslip.alloc(n);
@@ -348,7 +338,8 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
     else
       launch_realspace<double>(c, x, y, false, false);
   };
-  const int ir = lanczos_sqrt(c, real_op, c.bwork.p, c.t2.p, tol, maxit);
+  double ch_r = 0.0, ch_n = 0.0;
+  const int ir = lanczos_sqrt(c, real_op, c.bwork.p, c.t2.p, tol, maxit, &ch_r);
   vec_axpby(c, c.bslip.p, 1.0, c.t2.p, 1.0, n);
   // near-field part: F^B = R_FU^(1/2) psi_nf (Lanczos on the bead-level blocks)
   int inf = 0;
@@ -361,28 +352,29 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
                                                              c.bwork.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
-    // preconditioned sampling: with G = blockdiag(D_b^(-1/2)), D_b the
-    // bead's diagonal block, F = G^-1 (G R G^T)^(1/2) psi has covariance R and
-    // the Lanczos iteration runs on the well-scaled G R G^T
+    // preconditioned sampling: with L L^T the bead's regularised diagonal
+    // block and G = L^-1, F = L (G R G^T)^(1/2) psi has covariance R
+    // (L G = I) and the Lanczos iteration runs on G R G^T, whose diagonal
+    // blocks are (nearly) the identity
     if (c.bgain.n < (size_t)c.Nt * 72) c.bgain.alloc((size_t)c.Nt * 72);
-    double *G = c.bgain.p, *Gi = c.bgain.p + (size_t)c.Nt * 36;
-    k_block_isqrt<<<ceil_div(c.Nt, 64), 64, 0, c.stream>>>(c.Nt, c.op64.bdiag.p, G, Gi);
+    double *Lb = c.bgain.p, *G = c.bgain.p + (size_t)c.Nt * 36;
+    k_block_chol<<<ceil_div(c.Nt, 64), 64, 0, c.stream>>>(c.Nt, c.op64.bdiag.p, Lb, G);
     FSD_LAUNCHED(c);
     if (c.bwork2.n < (size_t)n) c.bwork2.alloc(n);
     double *tmp = c.bwork2.p;
     FSD_CUDA(cudaMemsetAsync(tmp, 0, n * sizeof(double), c.stream));
     auto nf_op = [&](const double *x, double *y) {
-      k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, G, x, tmp);
+      k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, G, 1, x, tmp);
       FSD_LAUNCHED(c);
       k_bsr_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.brow.p, c.bcol.p, c.op64.bval.p,
                                                             c.op64.bdiag.p, tmp, y);
       FSD_LAUNCHED(c);
-      k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, G, y, y);
+      k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, G, 0, y, y);
       FSD_LAUNCHED(c);
       FSD_CUDA(cudaGetLastError());
     };
-    inf = lanczos_sqrt(c, nf_op, c.bwork.p, c.t2.p, tol, maxit);
-    k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, Gi, c.t2.p, c.bfnf.p);
+    inf = lanczos_sqrt(c, nf_op, c.bwork.p, c.t2.p, tol, maxit, &ch_n);
+    k_block_apply<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, Lb, 0, c.t2.p, c.bfnf.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
@@ -393,6 +385,7 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
   c.brown_pending = true;
   if (iters_real) *iters_real = ir;
   if (iters_nf) *iters_nf = inf;
+  if (change) *change = std::max(ch_r, ch_n);
 }
 
 void launch_brownian_rhs(Ctx &c, double *b) {

@@ -177,7 +177,7 @@ struct Ctx {
   int64_t n_pairs = 0, n_lub = 0;
   // ---- Brownian forcing of the next solve (brownian.cu)
   DBuf<double> bslip, bfnf, bwork, bwork2;  // slip u_w + u_r, near-field force (solution layout), scratch
-  DBuf<double> bgain;               // per bead D^(-1/2) and D^(1/2) of the near-field diagonal block
+  DBuf<double> bgain;               // per bead Cholesky factor L of the near-field diagonal block and L^-1
   bool brown_pending = false;       // the next solve adds them to its right-hand side
   bool geom_fresh = false;          // geometry prepared at the current positions (the next
                                     // solve may skip its own preparation)
@@ -289,7 +289,8 @@ void launch_brownian_wave(Ctx &c, const double *field, uint64_t seed, uint64_t s
 // brownian.cu
 void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
                      const double *field_dev, const double *psi_r_dev, const double *psi_nf_dev,
-                     int *iters_real, int *iters_nf);   // fills bslip, bfnf; sets pending
+                     int *iters_real, int *iters_nf,
+                     double *change);  // fills bslip, bfnf; sets pending; change: last Lanczos step
 void launch_brownian_rhs(Ctx &c, double *b);               // b += the pending Brownian terms
 void brownian_outputs(Ctx &c, double *slip_user_dev, double *fnf_user_dev);  // scaled, user order
 

@@ -8,7 +8,7 @@ Tolerances (relative L2):
     1e-6 FP64, 1e-5 with the FP32 operator;
   real-space square root (Lanczos, coefficient change < 1e-7 on the
     real-space operator): 1e-6 FP64, 1e-5 FP32;
-  near-field square root (block-Jacobi preconditioned Lanczos on the FP64
+  near-field square root (block-Cholesky preconditioned Lanczos on the FP64
     bead blocks, against the oracle's preconditioned square root): 1e-6;
   Brownian solve at GMRES 1e-10: 1e-6 FP64, 1e-5 mixed.
 """

@@ -9,8 +9,9 @@ Eq. UBff):
   to each independent field component gives the covariance, which must equal
   the wave-vector sum M_w of fsd_oracle (pinned elsewhere against closed forms
   and xi-independence);
-* the dense square root applied twice is the operator; the block-Jacobi
-  preconditioned square root G^-1 (G R G)^(1/2) has covariance exactly R;
+* the dense square root applied twice is the operator; the block-Cholesky
+  preconditioned square root L (G R G^T)^(1/2), G = L^-1, has covariance
+  exactly R;
 * a near-field Brownian force enters the body rows exactly like an applied
   aggregate force and torque (the same Sigma projection, the same sign);
 * Box-Muller normals from Philox have zero mean, unit variance, no
