@@ -127,6 +127,11 @@ typedef struct {
   int flags;             /* FSD_FLAG_*                                             */
   int tile;              /* real-space lanes per bead (4, 8, 16, 32); 0: from the
                             mean neighbour count                                   */
+  double lanczos_tol;    /* fsd_brownian: a Lanczos square root stops when its
+                            coefficients change by less than this, relative;
+                            <= 0: 1e-7                                             */
+  int lanczos_max_iter;  /* fsd_brownian: Lanczos step limit; <= 0: 60; at most
+                            the Krylov basis length max(restart, inner_restart)   */
 } fsd_params;
 
 typedef struct {

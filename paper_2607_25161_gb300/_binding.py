@@ -43,6 +43,7 @@ class FsdParams(ctypes.Structure):
         ("lub_hmin", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_restart", ctypes.c_int),
         ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int), ("tile", ctypes.c_int),
+        ("lanczos_tol", ctypes.c_double), ("lanczos_max_iter", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -471,6 +471,8 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.m_in = p.inner_restart > 0 ? std::min(p.inner_restart, 60) : 60;
   c.prm.inner_restart = c.m_in;
   c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-7;
+  c.prm.lanczos_tol = p.lanczos_tol > 0 ? p.lanczos_tol : 1e-7;
+  c.prm.lanczos_max_iter = p.lanczos_max_iter > 0 ? std::max(p.lanczos_max_iter, 2) : 60;
   if (p.tile != 0 && p.tile != 4 && p.tile != 8 && p.tile != 16 && p.tile != 32)
     throw Invalid{"tile must be 0, 4, 8, 16 or 32"};
   c.prm.xi = c.xi;
@@ -843,6 +845,8 @@ void fsd_default_params(fsd_params *p) {
   p->inner_tol = 1e-7;
   p->flags = 0;
   p->tile = 0;
+  p->lanczos_tol = 1e-7;
+  p->lanczos_max_iter = 60;
 }
 
 fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,

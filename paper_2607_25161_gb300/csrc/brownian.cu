@@ -316,8 +316,8 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
   if (c.bfnf.n < (size_t)n) c.bfnf.alloc(n);
   if (c.bwork.n < (size_t)n) c.bwork.alloc(n);
   const bool f32 = c.prm.precision == FSD_MIXED;
-  const int maxit = std::min(std::max(c.m, c.m_in), 60);
-  const double tol = 1e-7;
+  const int maxit = std::min(std::max(c.m, c.m_in), c.prm.lanczos_max_iter);
+  const double tol = c.prm.lanczos_tol;
   // wave part: u_w = M_w^(1/2) psi_w
   if (f32)
     launch_brownian_wave<float>(c, field_dev, seed, step, c.bslip.p);
