@@ -370,7 +370,37 @@ def run_ours(args, rank, world, local_rank):
              "lanczos_last_change_max": lz_ch,
              "note": "each step: PSE far-field slip (analytic wave part + Lanczos real-space square root, "
                      "FP32 operator) and near-field Brownian force (Lanczos, FP64), then the mixed solve "
-                     "with them; drift not included"}
+                     "with them; drift not included (see brownian_drift)"}
+
+    # ---- Brownian step with the drift (Sec. 2.4; appendix on the drift):
+    #      fsd_brownian, fsd_drift (two solves at displaced configurations),
+    #      then the step's solve: three solves per step either way
+    drift_lines = {}
+    for dname, meth in (("rfd", pkg.FSD_DRIFT_RFD), ("fixman", pkg.FSD_DRIFT_FIXMAN)):
+        s = make(pkg.FSD_MIXED)
+
+        def one(k):
+            s.brownian(1.0, w["dt"], seed=11, step=k, outputs=False)
+            _, _, _, std, _ = s.drift(meth, 1.0, dt=w["dt"], seed=11, step=k, outputs=False)
+            st2, _ = s.step(None, w["shear"], w["dt"])
+            return std["iters"] + st2["iters"]
+        for k in range(min(args.warmup, 3)):
+            one(k)
+        KD = max(3, args.steps // 2)
+        barrier()
+        torch.cuda.synchronize()
+        ed0 = torch.cuda.Event(enable_timing=True)
+        ed1 = torch.cuda.Event(enable_timing=True)
+        ed0.record(stream)
+        itd = sum(one(2000 + k) for k in range(KD))
+        ed1.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        msd = max_over_ranks(ed0.elapsed_time(ed1))
+        drift_lines[dname] = {"value": Nt * KD * world / (msd / 1e3), "ms_per_step": msd / KD,
+                              "steps": KD, "iters_per_step": itd / KD, "solves_per_step": 3}
+    drift_lines["note"] = ("kT = 1: Brownian terms, the drift by RFD (eps = tol^(1/3) a) or the modified "
+                           "Fixman midpoint (m = 100), then the step's mixed solve and update")
 
     # ---- plain FP64 path on the same initial configuration
     s64 = make(pkg.FSD_FP64)
@@ -438,6 +468,7 @@ def run_ours(args, rank, world, local_rank):
         "profile_iters_per_step": prof_iters / PS,
         "warm_start": warm,
         "brownian": brown,
+        "brownian_drift": drift_lines,
         "roofline": roof,
         "cpu_baseline": base,
         "e2e": e2e,

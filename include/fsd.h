@@ -330,13 +330,46 @@ void fsd_destroy_batch(fsd_batch *b);
  *   psi_real [n_beads][11], psi_nf [n_beads][6]: standard normals.
  * Outputs (NULL to skip): slip [n_beads][11] = u^B, force_nf [n_beads][6] =
  * F^B.  stats: iters = real-space Lanczos steps, outer_iters = near-field
- * Lanczos steps (each stops when its coefficients change by less than 1e-7
- * relative, or after 60 steps), rel_residual = the larger last relative
- * change of the two. */
+ * Lanczos steps (each stops when its coefficients change by less than
+ * lanczos_tol relative, or after lanczos_max_iter steps), rel_residual = the
+ * larger last relative change of the two. */
 fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint64_t step,
                         const double *wave_field, const double *psi_real,
                         const double *psi_nf, double *slip, double *force_nf,
                         fsd_stats *stats);
+
+/* Methods of fsd_drift. */
+enum { FSD_DRIFT_RFD = 0, FSD_DRIFT_FIXMAN = 1 };
+
+/* Brownian drift kT div(R_FU^-1) and Brownian stresslet S^B (Sec. 2.4; the
+ * appendix on the drift), added to the velocity of the NEXT fsd_solve /
+ * fsd_step (and so to its update), then forgotten.  A displacement of the
+ * configuration by h v (v [N][6]) moves X by h v_t and rotates the lever
+ * arms by the unit quaternion normalise(1, (h/2) v_w) (the Euler step of
+ * Eq. EM2); each solve below has no background flow, and the stresslets
+ * differenced are the hydrodynamic ones (S^ff - R_SU^nf Sigma^T U).
+ *   FSD_DRIFT_RFD (Eq. rfd): U+- = the solve at x +- (eps/2) dq with body
+ *     forcing dq; drift = kT (U+ - U-)/eps, S^B = kT (S+ - S-)/eps.
+ *     param = eps (<= 0: a tol^(1/3), the error balance eps ~ tol^(1/3));
+ *     dq [N][6] (host or device) or NULL: standard normals from Philox
+ *     stream 4, index = aggregate id, calls 0 and 1, first 6 of the 8.
+ *     Two solves; pending Brownian terms (fsd_brownian) stay pending; dt is
+ *     not used.
+ *   FSD_DRIFT_FIXMAN (modified Fixman midpoint): needs pending Brownian
+ *     terms.  U0, S0 = the solve with them at x; x' = x + (dt/m) U0;
+ *     U', S' = the solve with the same terms at x'; drift = (m/2)(U' - U0),
+ *     S^B = -(m/2)(S' - S0).  param = m (<= 0: 100).  Two solves; the
+ *     Brownian terms are spent: the next solve gets U0 + drift added instead.
+ * The configuration, the warm-start vector and the flags are as before on
+ * return; the solves run host-driven or as graphs like fsd_solve.  Outputs
+ * (NULL to skip): drift [N][6], brownian_velocity [N][6] (Fixman: U0),
+ * brownian_stresslet [N][9].  stats sum the two solves (rel_residual: the
+ * larger).  FSD_ENOCONV from a solve is returned after the outputs are
+ * written. */
+fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double param,
+                     uint64_t seed, uint64_t step, const double *dq, double *drift,
+                     double *brownian_velocity, double *brownian_stresslet,
+                     fsd_stats *stats);
 
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);

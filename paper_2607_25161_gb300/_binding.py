@@ -19,6 +19,7 @@ FSD_FLAG_WARM_START = 1
 FSD_FLAG_COMOVING = 2
 FSD_FLAG_GRAPH = 4
 FSD_FLAG_AUTOTUNE = 8
+FSD_DRIFT_RFD, FSD_DRIFT_FIXMAN = 0, 1
 STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",
                 5: "FSD_ENUMERIC", 6: "FSD_EOVERLAP", 7: "FSD_ETIMEOUT"}
 
@@ -29,7 +30,7 @@ EXPORTS = (
     "fsd_rhs", "fsd_get_params", "fsd_profile_enable", "fsd_profile_read",
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
     "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
-    "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian",
+    "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian", "fsd_drift",
 )
 PROF_GROUPS = 10
 
@@ -109,6 +110,8 @@ def load(path=LIB_PATH):
     lib.fsd_batch_last_error.restype = ctypes.c_char_p
     lib.fsd_brownian.argtypes = [P, D, D, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P, P,
                                  ctypes.POINTER(FsdStats)]
+    lib.fsd_drift.argtypes = [P, I, D, D, D, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P,
+                              ctypes.POINTER(FsdStats)]
     lib.fsd_destroy_batch.argtypes = [P]
     lib.fsd_destroy_batch.restype = None
     for name in EXPORTS:
@@ -258,6 +261,22 @@ class Suspension:
                                           _ptr(wave_field), _ptr(prep(psi_real)), _ptr(prep(psi_nf)),
                                           _ptr(slip), _ptr(fnf), ctypes.byref(st_)))
         return slip, fnf, st_.as_dict()
+
+    def drift(self, method, kT, dt=0.0, param=0.0, seed=0, step=0, dq=None, outputs=True,
+              allow=(FSD_OK, FSD_EOVERLAP)):
+        """fsd_drift: Brownian drift added to the next solve; returns (drift
+        [N, 6], Brownian velocity [N, 6] (Fixman), Brownian stresslet
+        [N, 3, 3], stats, status) (None for the arrays when outputs is false)."""
+        if dq is not None and not hasattr(dq, "data_ptr"):
+            dq = np.ascontiguousarray(dq, dtype=np.float64)
+        d = np.zeros((self.n_agg, 6)) if outputs else None
+        ub = np.zeros((self.n_agg, 6)) if outputs else None
+        sb = np.zeros((self.n_agg, 3, 3)) if outputs else None
+        st_ = FsdStats()
+        st = self.lib.fsd_drift(self.ctx, int(method), float(kT), float(dt), float(param), int(seed),
+                                int(step), _ptr(dq), _ptr(d), _ptr(ub), _ptr(sb), ctypes.byref(st_))
+        self._check(st, allow)
+        return d, ub, sb, st_.as_dict(), st
 
     def profile(self, on=True):
         self._check(self.lib.fsd_profile_enable(self.ctx, 1 if on else 0))

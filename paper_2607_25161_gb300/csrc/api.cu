@@ -616,6 +616,8 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
   FSD_CUDA(cudaMemcpyAsync(c.xprev.p, c.xsol.p, c.nunk * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
   c.have_prev = true;
   launch_outputs(c, c.xsol.p, shear, vel_int, str_int);
+  if (c.vextra_pending) launch_add_velocity(c, vel_int);
+  c.vextra_pending = false;  // consumed by this solve
   FSD_CUDA(cudaMemsetAsync(c.flags.p + 6, 0, sizeof(int), c.stream));
   k_nan_check<<<152, 256, 0, c.stream>>>(vel_int, 6 * (int64_t)c.N, c.flags.p + 6);
   FSD_LAUNCHED(c);
@@ -666,11 +668,14 @@ static StepMark graph_step_begin(Ctx &c, const double *ft_user, double shear, bo
   o.dt = dt;
   o.brown = c.brown_pending ? 1 : 0;
   o.brown_scale = c.brown_scale;
+  o.add_vel = c.vextra_pending ? 1 : 0;
+  o.str_hydro = c.str_hydro ? 1 : 0;
   if (ft_user)
     FSD_CUDA(cudaMemcpyAsync(graph_ft_buffer(c), ft_user, 6 * (size_t)c.N * sizeof(double),
                              cudaMemcpyDefault, c.stream));
   graph_launch(c, o);
   c.brown_pending = false;  // consumed by this solve
+  c.vextra_pending = false;
   return mk;
 }
 
@@ -698,6 +703,168 @@ static fsd_status graph_step_end(Ctx &c, const StepMark &mk, fsd_stats *stats) {
     return FSD_EOVERLAP;
   }
   return FSD_OK;
+}
+
+// ---- Brownian drift (Sec. 2.4; appendix on the drift): solves at displaced
+//      rigid configurations, differenced.
+
+// One solve of the current configuration with the pending terms, host-driven
+// or as the captured graph; velocity in t1, stresslet (when wanted) in res.
+static fsd_status solve_any(Ctx &c, const double *ft_user, bool with_str, fsd_stats *stats) {
+  if (use_graph(c)) {
+    const StepMark mk = graph_step_begin(c, ft_user, 0.0, with_str, false, 0.0);
+    return graph_step_end(c, mk, stats);
+  }
+  return solve_internal(c, ft_user, 0.0, c.t1.p, with_str ? c.res.p : nullptr, stats, 0.0);
+}
+
+static bool status_fatal(fsd_status s) { return s != FSD_OK && s != FSD_ENOCONV && s != FSD_EOVERLAP; }
+
+// Saves what the drift solves change (body positions and orientations, the
+// warm-start vector, flags, pending terms) and puts it back on every exit.
+struct DriftState {
+  Ctx &c;
+  int flags;
+  bool have_prev, brown, vx, done = false;
+  explicit DriftState(Ctx &cx) : c(cx) {
+    flags = c.prm.flags;
+    have_prev = c.have_prev;
+    brown = c.brown_pending;
+    vx = c.vextra_pending;
+    if (c.dsave.n < 7 * (size_t)c.N) c.dsave.alloc(7 * (size_t)c.N);
+    if (c.dxprev.n < (size_t)c.nunk) c.dxprev.alloc(c.nunk);
+    FSD_CUDA(cudaMemcpyAsync(c.dsave.p, c.X.p, 3 * (size_t)c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    FSD_CUDA(cudaMemcpyAsync(c.dsave.p + 3 * (size_t)c.N, c.q.p, 4 * (size_t)c.N * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c.stream));
+    FSD_CUDA(cudaMemcpyAsync(c.dxprev.p, c.xprev.p, c.nunk * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    c.prm.flags &= ~FSD_FLAG_WARM_START;
+    c.vextra_pending = false;
+    c.str_hydro = true;
+  }
+  void restore_geometry() {
+    FSD_CUDA(cudaMemcpyAsync(c.X.p, c.dsave.p, 3 * (size_t)c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    FSD_CUDA(cudaMemcpyAsync(c.q.p, c.dsave.p + 3 * (size_t)c.N, 4 * (size_t)c.N * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c.stream));
+    launch_wrap_positions(c);
+    c.geom_fresh = false;
+  }
+  ~DriftState() {
+    // best effort on the error path: the context is then reported broken by
+    // the status already returned
+    cudaMemcpyAsync(c.X.p, c.dsave.p, 3 * (size_t)c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    cudaMemcpyAsync(c.q.p, c.dsave.p + 3 * (size_t)c.N, 4 * (size_t)c.N * sizeof(double),
+                    cudaMemcpyDeviceToDevice, c.stream);
+    cudaMemcpyAsync(c.xprev.p, c.dxprev.p, c.nunk * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    try {
+      launch_wrap_positions(c);
+    } catch (...) {
+    }
+    cudaStreamSynchronize(c.stream);
+    c.geom_fresh = false;
+    c.prm.flags = flags;
+    c.have_prev = have_prev;
+    c.str_hydro = false;
+    if (!done) {
+      c.vextra_pending = vx;
+      c.brown_pending = brown;
+    }
+  }
+};
+
+static void add_stats(fsd_stats &acc, const fsd_stats &s) {
+  acc.iters += s.iters;
+  acc.outer_iters += s.outer_iters;
+  acc.matvec64 += s.matvec64;
+  acc.matvec32 += s.matvec32;
+  acc.rel_residual = std::max(acc.rel_residual, s.rel_residual);
+  acc.n_pairs = s.n_pairs;
+  acc.n_lub = s.n_lub;
+  acc.grid = s.grid;
+  acc.P = s.P;
+  acc.xi = s.xi;
+  acc.rc = s.rc;
+}
+
+// Work vectors in dwork (internal order except the first): dq in user order,
+// dq, U_a, S_a, drift, stresslet.
+static fsd_status drift_impl(Ctx &c, int method, double kT, double dt, double param, uint64_t seed,
+                             uint64_t step, const double *dq_user_in, fsd_stats &acc) {
+  const size_t N6 = 6 * (size_t)c.N, N9 = 9 * (size_t)c.N;
+  if (c.dwork.n < 4 * N6 + 2 * N9) c.dwork.alloc(4 * N6 + 2 * N9);
+  double *dq_user = c.dwork.p, *dq = dq_user + N6, *Ua = dq + N6, *Sa = Ua + N6, *vout = Sa + N9,
+         *sout = vout + N6;
+  if (c.vextra.n < N6) c.vextra.alloc(N6);
+  if (c.t1.n < N6 || c.res.n < N9) throw Invalid{"internal: output buffers too small"};
+  fsd_status worst = FSD_OK;
+  auto take = [&](fsd_status st) {
+    if (status_fatal(st)) return true;
+    if (st == FSD_ENOCONV || (st == FSD_EOVERLAP && worst == FSD_OK)) worst = st;
+    return false;
+  };
+  DriftState ds(c);
+  fsd_stats sub;
+  if (method == FSD_DRIFT_RFD) {
+    // U+- = N(x +- eps/2 dq) dq (body forcing dq, no flow); drift = kT (U+ - U-)/eps,
+    // S^B = kT (S+ - S-)/eps
+    const double eps = param > 0 ? param : c.a * std::cbrt(c.prm.tol);
+    if (dq_user_in)
+      FSD_CUDA(cudaMemcpyAsync(dq_user, dq_user_in, N6 * sizeof(double), cudaMemcpyDefault, c.stream));
+    else
+      launch_dq_philox(c, seed, step, dq_user);
+    k_bodies_in_launch(c, dq_user, dq);
+    c.brown_pending = false;  // the drift solves carry no Brownian terms
+    for (int sgn = 1; sgn >= -1; sgn -= 2) {
+      ds.restore_geometry();
+      launch_integrate(c, dq, 0.5 * sgn * eps, 0.0);
+      launch_wrap_positions(c);
+      std::memset(&sub, 0, sizeof(sub));
+      const fsd_status st = solve_any(c, dq_user, true, &sub);
+      add_stats(acc, sub);
+      if (take(st)) return st;
+      FSD_CUDA(cudaMemcpyAsync(sgn > 0 ? Ua : vout, c.t1.p, N6 * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c.stream));
+      FSD_CUDA(cudaMemcpyAsync(sgn > 0 ? Sa : sout, c.res.p, N9 * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c.stream));
+    }
+    launch_scaled_diff(c, Ua, vout, kT / eps, vout, (int64_t)N6);
+    launch_scaled_diff(c, Sa, sout, kT / eps, sout, (int64_t)N9);
+    if (ds.vx)
+      launch_axpy(c, vout, c.vextra.p, (int64_t)N6);
+    else
+      FSD_CUDA(cudaMemcpyAsync(c.vextra.p, vout, N6 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    c.brown_pending = ds.brown;  // still for the next solve
+  } else {
+    // modified Fixman: U0 = solve with the Brownian terms at x; x' = x + (dt/m) U0;
+    // U' = the same solve at x'; drift = (m/2)(U' - U0), S^B = -(m/2)(S' - S0)
+    if (!ds.brown) throw Invalid{"the Fixman drift needs Brownian terms: call fsd_brownian first"};
+    const double m = param > 0 ? param : 100.0;
+    std::memset(&sub, 0, sizeof(sub));
+    fsd_status st = solve_any(c, nullptr, true, &sub);
+    add_stats(acc, sub);
+    if (take(st)) return st;
+    FSD_CUDA(cudaMemcpyAsync(Ua, c.t1.p, N6 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    FSD_CUDA(cudaMemcpyAsync(Sa, c.res.p, N9 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    launch_integrate(c, Ua, dt / m, 0.0);
+    launch_wrap_positions(c);
+    c.geom_fresh = false;
+    c.brown_pending = true;  // the same u^B, E^B and F^B_nf at x'
+    std::memset(&sub, 0, sizeof(sub));
+    st = solve_any(c, nullptr, true, &sub);
+    add_stats(acc, sub);
+    if (take(st)) return st;
+    launch_scaled_diff(c, c.t1.p, Ua, 0.5 * m, vout, (int64_t)N6);
+    launch_scaled_diff(c, c.res.p, Sa, -0.5 * m, sout, (int64_t)N9);
+    // the next solve gets U0 + drift; its own Brownian terms are spent
+    if (!ds.vx) FSD_CUDA(cudaMemsetAsync(c.vextra.p, 0, N6 * sizeof(double), c.stream));
+    launch_axpy(c, Ua, c.vextra.p, (int64_t)N6);
+    launch_axpy(c, vout, c.vextra.p, (int64_t)N6);
+    c.brown_pending = false;
+  }
+  ds.restore_geometry();
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  c.vextra_pending = true;
+  ds.done = true;
+  return worst;
 }
 
 // ---- autotuner (FSD_FLAG_AUTOTUNE): the splitting xi trades real-space
@@ -1159,6 +1326,43 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
     stats->rc = c.rc;
   }
   return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double param, uint64_t seed,
+                     uint64_t step, const double *dq, double *drift, double *brownian_velocity,
+                     double *brownian_stresslet, fsd_stats *stats) {
+  if (!ctx) return FSD_EINVAL;
+  Ctx &c0 = ctx->c;
+  if (method != FSD_DRIFT_RFD && method != FSD_DRIFT_FIXMAN) {
+    c0.last_error = "method must be FSD_DRIFT_RFD or FSD_DRIFT_FIXMAN";
+    return FSD_EINVAL;
+  }
+  if (!(kT >= 0.0) || !std::isfinite(kT) || !std::isfinite(param) ||
+      (method == FSD_DRIFT_FIXMAN && !(dt > 0.0 && std::isfinite(dt)))) {
+    c0.last_error = "kT must be >= 0, param finite, and dt > 0 for the Fixman drift";
+    return FSD_EINVAL;
+  }
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = c.launches;
+  fsd_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  const fsd_status st = drift_impl(c, method, kT, dt, param, seed, step, dq, acc);
+  if (!status_fatal(st)) {
+    const size_t N6 = 6 * (size_t)c.N, N9 = 9 * (size_t)c.N;
+    double *Ua = c.dwork.p + 2 * N6, *vout = Ua + N6 + N9, *sout = vout + N6;
+    bodies_out(c, vout, drift, 6);
+    if (method == FSD_DRIFT_FIXMAN) bodies_out(c, Ua, brownian_velocity, 6);
+    bodies_out(c, sout, brownian_stresslet, 9);
+  }
+  if (stats) {
+    *stats = acc;
+    stats->kernel_launches = c.launches - l0;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
   FSD_API_CATCH(ctx)
 }
 

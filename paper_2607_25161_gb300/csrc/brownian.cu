@@ -415,4 +415,52 @@ void brownian_outputs(Ctx &c, double *slip_user_dev, double *fnf_user_dev) {
   FSD_CUDA(cudaGetLastError());
 }
 
+// ---------------------------------------------------------- drift helpers
+// Random body vector dq of the random finite differences (appendix on the
+// Brownian drift, Eq. rfd): Philox stream 4, index = user body id, calls 0
+// and 1 give 8 normals of which the first 6 are used.
+__global__ void k_dq_philox(int N, uint64_t seed, uint64_t step, double *user) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= N) return;
+  double z[8];
+  philox_normals4(seed, step, 4u, 0u, (uint32_t)J, z);
+  philox_normals4(seed, step, 4u, 1u, (uint32_t)J, z + 4);
+  for (int k = 0; k < 6; ++k) user[6 * (size_t)J + k] = z[k];
+}
+
+__global__ void k_scaled_diff(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                              double s, double *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = s * (a[i] - b[i]);
+}
+
+__global__ void k_axpy1(int64_t n, const double *__restrict__ x, double *y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+static int small_grid(int64_t n) { return (int)std::min<int64_t>(ceil_div(n, 256), 4 * 152); }
+
+void launch_dq_philox(Ctx &c, uint64_t seed, uint64_t step, double *user) {
+  k_dq_philox<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, seed, step, user);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void launch_scaled_diff(Ctx &c, const double *a, const double *b, double s, double *out, int64_t n) {
+  k_scaled_diff<<<small_grid(n), 256, 0, c.stream>>>(n, a, b, s, out);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void launch_axpy(Ctx &c, const double *x, double *y, int64_t n) {
+  k_axpy1<<<small_grid(n), 256, 0, c.stream>>>(n, x, y);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void launch_add_velocity(Ctx &c, double *vel_int) { launch_axpy(c, c.vextra.p, vel_int, 6 * (int64_t)c.N); }
+
 }  // namespace fsd

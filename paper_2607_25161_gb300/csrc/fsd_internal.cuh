@@ -108,6 +108,8 @@ struct GraphRun {
   int integrate = 0;  // advance the rigid bodies by dt after the solve
   int with_str = 0;   // write the stresslet
   int brown = 0;      // add the pending Brownian terms to the right-hand side
+  int add_vel = 0;    // add the pending drift velocity to the velocity output
+  int str_hydro = 0;  // stresslet output without the constraint part
   double shear = 0.0, dt = 0.0, brown_scale = 0.0;
 };
 
@@ -182,6 +184,11 @@ struct Ctx {
   bool geom_fresh = false;          // geometry prepared at the current positions (the next
                                     // solve may skip its own preparation)
   double brown_scale = 0.0;         // sqrt(2 kT / dt)
+  // ---- Brownian drift (brownian.cu, api.cu)
+  DBuf<double> vextra;              // [N][6] velocity added to the next solve's output
+  bool vextra_pending = false;
+  bool str_hydro = false;           // outputs write the hydrodynamic stresslet only
+  DBuf<double> dsave, dwork, dxprev;  // saved X, q; drift vectors; saved previous solution
   // ---- captured solve graphs
   GraphCache *gcache = nullptr;
   int64_t graph_pending = -1;
@@ -256,6 +263,11 @@ void launch_rhs(Ctx &c, const double *ft_internal, double shear, double *b);
 void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int,
                     double *str_int);
 void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear);
+// brownian.cu: drift helpers
+void launch_add_velocity(Ctx &c, double *vel_int);  // vel_int += vextra
+void launch_dq_philox(Ctx &c, uint64_t seed, uint64_t step, double *user);  // [N][6], stream 4
+void launch_scaled_diff(Ctx &c, const double *a, const double *b, double s, double *out, int64_t n);
+void launch_axpy(Ctx &c, const double *x, double *y, int64_t n);  // y += x
 
 // krylov.cu
 void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w,

@@ -43,7 +43,7 @@ struct GState {
 };
 
 struct GraphKey {
-  int mixed, warm, has_ft, integrate, with_str, group, lub, brown;
+  int mixed, warm, has_ft, integrate, with_str, group, lub, brown, add_vel, str_hydro;
   double shear, dt, brown_scale;
   const void *nbr, *lnbr, *bcol, *bval64, *bval32, *packed64, *packed32;
   int cap, lcap;
@@ -526,6 +526,8 @@ static GraphKey make_key(Ctx &c, const GraphRun &o) {
   k.dt = o.integrate ? o.dt : 0.0;
   k.brown = o.brown;
   k.brown_scale = o.brown ? o.brown_scale : 0.0;
+  k.add_vel = o.add_vel;
+  k.str_hydro = o.str_hydro;
   k.nbr = c.nbr.p;
   k.lnbr = c.lnbr.p;
   k.bcol = c.bcol.p;
@@ -589,6 +591,7 @@ static GraphEntry &build_entry(Ctx &c, const GraphRun &o, const GraphKey &k) {
     FSD_CUDA(cudaMemcpyAsync(c.xprev.p, c.xsol.p, c.nunk * sizeof(double), cudaMemcpyDeviceToDevice,
                              c.stream));
     launch_outputs(c, c.xsol.p, o.shear, c.t1.p, o.with_str ? c.res.p : nullptr);
+    if (o.add_vel) launch_add_velocity(c, c.t1.p);
     FSD_CUDA(cudaMemsetAsync(c.flags.p + 6, 0, sizeof(int), c.stream));
     k_g_nan_check<<<152, 256, 0, c.stream>>>(c.t1.p, 6 * (int64_t)c.N, c.flags.p + 6);
     FSD_LAUNCHED(c);

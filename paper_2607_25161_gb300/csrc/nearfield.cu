@@ -484,12 +484,13 @@ __global__ void k_rhs_body(int N, const int *__restrict__ body_start,
 }
 
 // ---------------------------------------------------------------- outputs
-// Thread per aggregate: lab-frame velocity and S^H + S^C.
+// Thread per aggregate: lab-frame velocity and S^H + S^C (S^H alone when
+// with_constraint is 0).
 __global__ void k_outputs(int N, const int *__restrict__ body_start,
                           const double4 *__restrict__ lever, const double *__restrict__ X,
                           const double *__restrict__ x, const double *__restrict__ fnf,
                           const double *__restrict__ snf, int have_nf, double gamma,
-                          double *vel, double *str, int64_t off) {
+                          double *vel, double *str, int64_t off, int with_constraint) {
   int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= N) return;
   const double *u = x + off + 6 * (size_t)J;
@@ -517,7 +518,8 @@ __global__ void k_outputs(int N, const int *__restrict__ body_start,
     const double r[3] = {rv.x, rv.y, rv.z};
     const double Sh[9] = {Sxx, Sxy, Sxz, Sxy, Syy, Syz, Sxz, Syz, Szz};
     for (int p = 0; p < 3; ++p)
-      for (int qq = 0; qq < 3; ++qq) S[3 * p + qq] += Sh[3 * p + qq] + 0.5 * (r[p] * F[qq] + F[p] * r[qq]);
+      for (int qq = 0; qq < 3; ++qq)
+        S[3 * p + qq] += Sh[3 * p + qq] + (with_constraint ? 0.5 * (r[p] * F[qq] + F[p] * r[qq]) : 0.0);
   }
   for (int k = 0; k < 9; ++k) str[9 * (size_t)J + k] = S[k];
 }
@@ -693,7 +695,7 @@ void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int, doub
   k_outputs<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
                                                      (const double4 *)c.lever64.p, c.X.p, x,
                                                      c.fnf.p, c.snf.p, nf ? 1 : 0, shear, vel_int,
-                                                     str_int, off);
+                                                     str_int, off, c.str_hydro ? 0 : 1);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
