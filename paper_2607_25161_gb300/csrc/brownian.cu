@@ -188,64 +188,66 @@ __global__ void k_brown_rhs_body(int N, const int *__restrict__ body_start,
 }
 
 // ------------------------------------------------------------- Lanczos
-// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi
-// rotations: A = Q diag(lam) Q^T (Q column-major, m x m).
-static void jacobi_eigen(int m, std::vector<double> A, std::vector<double> &lam,
-                         std::vector<double> &Q) {
-  Q.assign((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
-  auto a = [&](int i, int j) -> double & { return A[(size_t)i * m + j]; };
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) (i == j ? tot : off) += a(i, j) * a(i, j);
-    if (off <= 1e-30 * (tot + off) || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = a(p, q);
-        if (apq == 0.0) continue;
-        // rotation zeroing a(p, q): cot(2 theta) = (a_qq - a_pp) / (2 a_pq),
-        // t = tan(theta); the update keeps the matrix exactly symmetric
-        const double th = (a(q, q) - a(p, p)) / (2.0 * apq);
-        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(1.0 + th * th));
-        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
-        const double app = a(p, p) - t * apq, aqq = a(q, q) + t * apq;
-        for (int r = 0; r < m; ++r) {
-          if (r == p || r == q) continue;
-          const double arp = a(r, p), arq = a(r, q);
-          a(r, p) = a(p, r) = cs * arp - sn * arq;
-          a(r, q) = a(q, r) = sn * arp + cs * arq;
-        }
-        a(p, p) = app;
-        a(q, q) = aqq;
-        a(p, q) = a(q, p) = 0.0;
-        for (int k = 0; k < m; ++k) {
-          const double qkp = Q[(size_t)p * m + k], qkq = Q[(size_t)q * m + k];
-          Q[(size_t)p * m + k] = cs * qkp - sn * qkq;
-          Q[(size_t)q * m + k] = sn * qkp + cs * qkq;
-        }
-      }
-  }
-  lam.resize(m);
-  for (int i = 0; i < m; ++i) lam[i] = a(i, i);
-}
-
-// ||b|| T^(1/2) e_1 for the Lanczos tridiagonal T (alpha, beta)
+// ||b|| f(T) e_1, f = sqrt, for the symmetric tridiagonal T (diagonal al,
+// off-diagonal be): implicit QR steps with the Wilkinson shift (Golub & Van
+// Loan, the implicit symmetric QR step) diagonalise T = Z diag(lam) Z^T with
+// Z the product of the Givens rotations G_1 G_2 ...; only the first row of Z
+// is kept during the sweep, and Z y is formed at the end by applying the
+// recorded rotations to y in reverse.
+struct Rot {
+  int k;
+  double c, s;
+};
 static std::vector<double> sqrt_coeffs(int m, const std::vector<double> &al,
                                        const std::vector<double> &be, double bnorm) {
-  std::vector<double> T((size_t)m * m, 0.0), lam, Q;
-  for (int i = 0; i < m; ++i) {
-    T[(size_t)i * m + i] = al[i];
-    if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = be[i];
+  std::vector<double> d(al.begin(), al.begin() + m), e(std::max(m, 1), 0.0);
+  for (int i = 0; i + 1 < m; ++i) e[i] = be[i];
+  std::vector<double> z0(m, 0.0);
+  if (m > 0) z0[0] = 1.0;
+  std::vector<Rot> rots;
+  rots.reserve((size_t)4 * m * m + 16);
+  int q = m - 1, guard = 0;
+  while (q > 0 && guard < 60 * m) {
+    for (int i = 0; i < q; ++i)
+      if (std::fabs(e[i]) <= 1e-16 * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
+    while (q > 0 && e[q - 1] == 0.0) --q;
+    if (q == 0) break;
+    int p = q - 1;
+    while (p > 0 && e[p - 1] != 0.0) --p;
+    ++guard;
+    const double a = d[q - 1], b = e[q - 1], c = d[q];
+    const double dl = 0.5 * (a - c);
+    const double mu = c - b * b / (dl + (dl >= 0.0 ? 1.0 : -1.0) * std::hypot(dl, b));
+    double x = d[p] - mu, z = e[p];
+    for (int k = p; k < q; ++k) {
+      const double r = std::hypot(x, z);
+      const double cs = r > 0 ? x / r : 1.0, sn = r > 0 ? z / r : 0.0;
+      if (k > p) e[k - 1] = r;
+      const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+      d[k] = cs * cs * dk + 2.0 * cs * sn * ek + sn * sn * dk1;
+      d[k + 1] = sn * sn * dk - 2.0 * cs * sn * ek + cs * cs * dk1;
+      e[k] = cs * sn * (dk1 - dk) + (cs * cs - sn * sn) * ek;
+      if (k + 1 < q) {
+        z = sn * e[k + 1];
+        e[k + 1] = cs * e[k + 1];
+        x = e[k];
+      }
+      const double a0 = z0[k], a1 = z0[k + 1];
+      z0[k] = cs * a0 + sn * a1;
+      z0[k + 1] = -sn * a0 + cs * a1;
+      rots.push_back({k, cs, sn});
+    }
   }
-  jacobi_eigen(m, T, lam, Q);
-  std::vector<double> cf(m, 0.0);
-  for (int k = 0; k < m; ++k) {
-    const double w = std::sqrt(std::max(0.0, lam[k])) * Q[(size_t)k * m + 0];  // sqrt(l) (Q^T e1)_k
-    for (int i = 0; i < m; ++i) cf[i] += Q[(size_t)k * m + i] * w;
+  std::vector<double> y(m);
+  for (int k = 0; k < m; ++k) y[k] = std::sqrt(std::max(0.0, d[k])) * z0[k];
+  for (size_t j = rots.size(); j-- > 0;) {
+    const Rot &g = rots[j];
+    const double a0 = y[g.k], a1 = y[g.k + 1];
+    y[g.k] = g.c * a0 - g.s * a1;
+    y[g.k + 1] = g.s * a0 + g.c * a1;
   }
-  for (double &v : cf) v *= bnorm;
-  return cf;
+  for (double &v : y) v *= bnorm;
+  return y;
 }
 
 static double dev_norm(Ctx &c, const double *x) {
