@@ -31,6 +31,8 @@ __all__ = [
     "compress_mixed",
     "mixed_suspension",
     "batch_workload",
+    "rod",
+    "rod_suspension",
 ]
 
 
@@ -145,6 +147,26 @@ def suspension(n_agg, n_b, phi, seed, a=1.0, h_gen=0.1):
         return compress_suspension(np.array(shapes), phi, seed + 1, a, h_gen)
     L = box_for_phi(n_agg * n_b, phi, a)
     pos, body = pack_suspension(shapes, L, rng, a, h_gen)
+    return pos, body, L
+
+
+def rod(n_b, a=1.0):
+    """A straight rigid rod of n_b touching beads (centre spacing 2a) along x,
+    centred on its bead centroid."""
+    x = (np.arange(n_b) - 0.5 * (n_b - 1)) * 2.0 * a
+    return np.stack([x, np.zeros(n_b), np.zeros(n_b)], axis=1)
+
+
+def rod_suspension(n_rods, n_b, phi, seed, a=1.0, h_gen=0.1):
+    """n_rods straight n_b-bead rods at bead volume fraction phi, uniform
+    centres and orientations, no inter-rod gap below h_gen (the rod workload
+    of the scaling study, Sec. 3.3).  A rod must be shorter than half the
+    box (it would otherwise reach its own periodic image)."""
+    rng = np.random.default_rng(seed)
+    L = box_for_phi(n_rods * n_b, phi, a)
+    if 2.0 * a * n_b >= 0.5 * L:
+        raise ValueError("rod of %d beads does not fit half of the box L = %.1f" % (n_b, L))
+    pos, body = pack_suspension([rod(n_b, a)] * n_rods, L, rng, a, h_gen, max_tries=200000)
     return pos, body, L
 
 
