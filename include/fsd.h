@@ -371,6 +371,17 @@ fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double para
                      double *brownian_velocity, double *brownian_stresslet,
                      fsd_stats *stats);
 
+/* Hertz normal contact between beads of different aggregates at the current
+ * configuration (Sec. 4: F_N = k_n delta^1.5 n, delta = 2a - r the overlap,
+ * n the unit vector along the line of centres; the rod benchmark of
+ * Sec. 3.3 uses normal contact between rods): each overlapping pair pushes
+ * its two beads apart with kn delta^1.5; the bead forces are summed per
+ * aggregate into a force and a torque about the centroid X.  Writes
+ * agg_force_torque [N][6] (host or device; pass it to fsd_step / fsd_solve as
+ * the applied force).  kn in units of force / length^1.5.  The neighbour
+ * lists built here are reused by the next solve. */
+fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque);
+
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);
 

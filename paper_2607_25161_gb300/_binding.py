@@ -31,6 +31,7 @@ EXPORTS = (
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
     "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
     "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian", "fsd_drift",
+    "fsd_contact_forces",
 )
 PROF_GROUPS = 10
 
@@ -112,6 +113,7 @@ def load(path=LIB_PATH):
                                  ctypes.POINTER(FsdStats)]
     lib.fsd_drift.argtypes = [P, I, D, D, D, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P,
                               ctypes.POINTER(FsdStats)]
+    lib.fsd_contact_forces.argtypes = [P, D, P]
     lib.fsd_destroy_batch.argtypes = [P]
     lib.fsd_destroy_batch.restype = None
     for name in EXPORTS:
@@ -277,6 +279,13 @@ class Suspension:
                                 int(step), _ptr(dq), _ptr(d), _ptr(ub), _ptr(sb), ctypes.byref(st_))
         self._check(st, allow)
         return d, ub, sb, st_.as_dict(), st
+
+    def contact(self, kn, out=None):
+        """fsd_contact_forces: Hertz contact force / torque per aggregate [N, 6]."""
+        if out is None:
+            out = np.zeros((self.n_agg, 6))
+        self._check(self.lib.fsd_contact_forces(self.ctx, float(kn), _ptr(out)))
+        return out
 
     def profile(self, on=True):
         self._check(self.lib.fsd_profile_enable(self.ctx, 1 if on else 0))

@@ -1287,7 +1287,7 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
   Ctx &c = ctx->c;
   auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = c.launches;
-  prepare(c);
+  if (!c.geom_fresh) prepare(c);
   c.geom_fresh = true;  // the next solve reuses this preparation
   const size_t nh = (size_t)c.n / 2 + 1;
   DBuf<double> sf, sr, sn;
@@ -1363,6 +1363,25 @@ fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double para
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return st;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque) {
+  if (!ctx) return FSD_EINVAL;
+  if (!(kn >= 0.0) || !std::isfinite(kn) || !agg_force_torque) {
+    ctx->c.last_error = "kn must be finite and >= 0, agg_force_torque is required";
+    return FSD_EINVAL;
+  }
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  if (!c.geom_fresh) prepare(c);
+  c.geom_fresh = true;  // the next solve reuses this preparation
+  const size_t need = 3 * (size_t)c.Nt + 6 * (size_t)c.N;
+  if (c.cwork.n < need) c.cwork.alloc(need);
+  double *ft_int = c.cwork.p + 3 * (size_t)c.Nt;
+  launch_contact(c, kn, c.cwork.p, ft_int);
+  bodies_out(c, ft_int, agg_force_torque, 6);
+  return FSD_OK;
   FSD_API_CATCH(ctx)
 }
 

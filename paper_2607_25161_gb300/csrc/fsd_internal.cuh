@@ -189,6 +189,7 @@ struct Ctx {
   bool vextra_pending = false;
   bool str_hydro = false;           // outputs write the hydrodynamic stresslet only
   DBuf<double> dsave, dwork, dxprev;  // saved X, q; drift vectors; saved previous solution
+  DBuf<double> cwork;                 // contact forces: per bead [Nt][3], then [N][6]
   // ---- captured solve graphs
   GraphCache *gcache = nullptr;
   int64_t graph_pending = -1;
@@ -263,6 +264,9 @@ void launch_rhs(Ctx &c, const double *ft_internal, double shear, double *b);
 void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int,
                     double *str_int);
 void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear);
+// Hertz contact: per-bead forces into fb_scratch [Nt][3], aggregate force and
+// torque into ft_int [N][6] (internal order); needs the neighbour lists
+void launch_contact(Ctx &c, double kn, double *fb_scratch, double *ft_int);
 // brownian.cu: drift helpers
 void launch_add_velocity(Ctx &c, double *vel_int);  // vel_int += vextra
 void launch_dq_philox(Ctx &c, uint64_t seed, uint64_t step, double *user);  // [N][6], stream 4

@@ -552,6 +552,64 @@ __global__ void k_integrate(int N, const double *__restrict__ vel, double dt, do
   qq[3] = nz * inv;
 }
 
+// ------------------------------------------------------------ Hertz contact
+// Normal contact between beads of different aggregates (Sec. 4: F_N =
+// k_n delta^1.5 n, delta = 2a - r, n along the line of centres; the rod
+// benchmark of Sec. 3.3): bead i receives kn delta^1.5 (x_i - x_j)/r from
+// each such neighbour j.  The mobility neighbour list (r < R_c, R_c > 2a)
+// holds every pair that can touch.
+__global__ void k_contact_bead(int Nt, const double4 *__restrict__ pos, const int *__restrict__ nbr,
+                               const int *__restrict__ ncnt, int cap,
+                               const int *__restrict__ bead_body, double L, double two_a,
+                               double kn, double *fb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const double4 p = pos[i];
+  const int bi = bead_body[i];
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  const int n = ncnt[i];
+  for (int k = 0; k < n; ++k) {
+    const int j = nbr[(size_t)i * cap + k];
+    if (bead_body[j] == bi) continue;
+    const double4 q = pos[j];
+    double d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z;
+    d0 -= L * rint(d0 / L);
+    d1 -= L * rint(d1 / L);
+    d2 -= L * rint(d2 / L);
+    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    if (r2 >= two_a * two_a || r2 == 0.0) continue;
+    const double r = sqrt(r2), delta = two_a - r;
+    const double s = kn * delta * sqrt(delta) / r;
+    f0 += s * d0;
+    f1 += s * d1;
+    f2 += s * d2;
+  }
+  fb[3 * (size_t)i] = f0;
+  fb[3 * (size_t)i + 1] = f1;
+  fb[3 * (size_t)i + 2] = f2;
+}
+
+// Aggregate force and torque about the centroid: F_J = sum_b F_b,
+// T_J = sum_b r_b x F_b.
+__global__ void k_contact_body(int N, const int *__restrict__ body_start,
+                               const double4 *__restrict__ lever, const double *__restrict__ fb,
+                               double *ft) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= N) return;
+  double o[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = body_start[J]; b < body_start[J + 1]; ++b) {
+    const double f0 = fb[3 * (size_t)b], f1 = fb[3 * (size_t)b + 1], f2 = fb[3 * (size_t)b + 2];
+    const double4 r = lever[b];
+    o[0] += f0;
+    o[1] += f1;
+    o[2] += f2;
+    o[3] += r.y * f2 - r.z * f1;
+    o[4] += r.z * f0 - r.x * f2;
+    o[5] += r.x * f1 - r.y * f0;
+  }
+  for (int k = 0; k < 6; ++k) ft[6 * (size_t)J + k] = o[k];
+}
+
 // ============================================================ host side
 
 static void strain6(double shear, double *e) {
@@ -704,6 +762,18 @@ void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear) {
   ProfScope ps(c, PG_MISC);
   const double ag = (c.prm.flags & FSD_FLAG_COMOVING) ? shear : 0.0;
   k_integrate<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, vel_int, dt, c.X.p, c.q.p, ag);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void launch_contact(Ctx &c, double kn, double *fb_scratch, double *ft_int) {
+  ProfScope ps(c, PG_MISC);
+  k_contact_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
+      c.Nt, (const double4 *)c.pos64.p, c.nbr.p, c.ncnt.p, c.cap, c.bead_body.p, c.L, 2.0 * c.a, kn,
+      fb_scratch);
+  FSD_LAUNCHED(c);
+  k_contact_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
+                                                          (const double4 *)c.lever64.p, fb_scratch, ft_int);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
