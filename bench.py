@@ -10,7 +10,7 @@ FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path is
 reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload step|batch]
+                  [--workload step|batch|rods]
 
 With N > 1 (torchrun) every rank steps its own replica of the suspension (the
 single-suspension solve does not shard); value = beads x steps x ranks / the
@@ -26,7 +26,12 @@ captures under profiles/ are taken on.
 volume fractions uniform in [0.05, 0.3]) advanced together by
 fsd_step_batch (one graph per system and step, all in flight), next to the
 same suspensions stepped one at a time; mixed precision, GMRES 1e-6,
-autotuned splitting."""
+autotuned splitting.
+
+--workload rods runs the rod scaling study of Sec. 3.3: Brownian rigid rods
+(8 and 27 beads) with Hertz contact at phi 0.01, 0.05, 0.10 and 8192 / 32768
+beads, xi = 0.5 and xi = 25/L; it reports t_s (wall time per step per bead)
+for every point."""
 
 import argparse
 import hashlib
@@ -644,13 +649,123 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ rod scaling study
+# Sec. 3.3: N Brownian rigid rods of n_b beads in a periodic cube with normal
+# contact between rods; t_s = wall time per step per bead at phi in {0.01,
+# 0.05, 0.10}, n_b in {8, 27}, xi = 0.5 and xi = 25/L.
+RODS = dict(n_b=(8, 27), phi=(0.01, 0.05, 0.10), n_tot=(8192, 32768), kT=1.0, dt=1e-3, kn=1e4,
+            lub=3.0, rp=2.0, tol=1e-6, seed=7)
+
+
+def _rod_system(args_):
+    import synth
+
+    nb, phi, n_tot = args_
+    return synth.rod_suspension(n_tot // nb, nb, phi, RODS["seed"])
+
+
+def rod_points():
+    import synth
+
+    pts = []
+    for nb in RODS["n_b"]:
+        for phi in RODS["phi"]:
+            for n in RODS["n_tot"]:
+                L = synth.box_for_phi((n // nb) * nb, phi)
+                if 2.0 * nb < 0.5 * L:  # a rod must be shorter than half the box
+                    pts.append((nb, phi, n))
+    return pts
+
+
+def run_rods(args, local_rank):
+    import multiprocessing as mp
+
+    pts = rod_points()
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        systems = pool.map(_rod_system, pts)
+    t_gen = time.perf_counter() - t0
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import paper_2607_25161_gb300 as pkg
+    from __graft_entry__ import build
+
+    build()
+    r = RODS
+    stream = torch.cuda.Stream()
+    dev_id = local_rank
+    if os.environ.get("CUDA_VISIBLE_DEVICES"):
+        ids = os.environ["CUDA_VISIBLE_DEVICES"].split(",")
+        if local_rank < len(ids):
+            dev_id = ids[local_rank]
+    clk = ClockSampler(dev_id)
+    clk.start()
+    K = max(3, min(args.steps, 5))
+    out = []
+    launches = 0
+    for (nb, phi, n), (pos, body, L) in zip(pts, systems):
+        for xi_mode in ("0.5", "25/L"):
+            xi = 0.5 if xi_mode == "0.5" else 25.0 / L
+            s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED, xi=xi,
+                               lub_cutoff=r["lub"], precond_cutoff=r["rp"], tol=r["tol"],
+                               flags=pkg.FSD_FLAG_GRAPH)
+            prm = s.params
+            ft = torch.zeros((s.n_agg, 6), dtype=torch.float64, device="cuda")
+            ok = (pkg.FSD_OK, pkg.FSD_EOVERLAP)
+
+            def one(k):
+                s.brownian(r["kT"], r["dt"], seed=r["seed"], step=k, outputs=False)
+                s.contact(r["kn"], out=ft)
+                st, _ = s.step(ft, 0.0, r["dt"], allow=ok)
+                return st
+            for k in range(min(args.warmup, 3)):
+                one(k)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its = 0
+            for k in range(K):
+                st = one(100 + k)
+                its += st["iters"]
+                launches += st["kernel_launches"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            s.close()
+            out.append({"n_b": nb, "phi": phi, "beads": len(pos), "L": round(L, 2), "xi": xi_mode,
+                        "xi_value": round(xi, 4), "rc": round(prm["rc"], 2), "grid": prm["grid"],
+                        "ms_per_step": round(ms, 3), "t_s_us": round(1e3 * ms / len(pos), 4),
+                        "bead_steps_per_s": round(len(pos) / (ms / 1e3), 1), "iters_per_step": its / K})
+            print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    clocks = clk.stop()
+    head = next(p for p in out if p["n_b"] == 8 and p["phi"] == 0.10 and p["beads"] == 32768
+                and p["xi"] == "0.5")
+    line = {
+        "metric": "t_s: wall time per step per bead of Brownian rigid rods (Sec. 3.3 scaling study)",
+        "value": head["bead_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "rods: n_b %s, phi %s, N_tot %s, xi 0.5 and 25/L; value = the 8-bead, "
+                               "phi 0.10, 32768-bead, xi 0.5 point" % (r["n_b"], r["phi"], r["n_tot"]),
+                   "step": "fsd_brownian (kT 1) + fsd_contact_forces (Hertz, kn 1e4 kT/a^1.5) + fsd_step "
+                           "(mixed, GMRES 1e-6, lubrication 3a, one graph), dt 1e-3, no shear, no drift",
+                   "generation_s": round(t_gen, 1)},
+        "points": out,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="step", choices=("step", "batch"))
+    ap.add_argument("--workload", default="step", choices=("step", "batch", "rods"))
     ap.add_argument("--profile-run", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -667,6 +782,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             run_batch(args, rank, world, local_rank)
+        return
+    if args.workload == "rods":
+        if rank == 0:
+            run_rods(args, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -1317,6 +1317,9 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
+    // the Brownian wave sample can reach this before any forward pass has
+    // raised the kernel's shared-memory limit
+    set_smem<T>((const void *)k_fft_y<T>, smy);
     k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());

@@ -166,6 +166,11 @@ def rod_suspension(n_rods, n_b, phi, seed, a=1.0, h_gen=0.1):
     L = box_for_phi(n_rods * n_b, phi, a)
     if 2.0 * a * n_b >= 0.5 * L:
         raise ValueError("rod of %d beads does not fit half of the box L = %.1f" % (n_b, L))
+    # random sequential insertion of long rods saturates early (27-bead rods
+    # jam near phi 0.1): above phi0 = 1.5 / n_b insert at phi0 and compress
+    phi0 = 1.5 / n_b
+    if phi > phi0:
+        return compress_suspension(np.array([rod(n_b, a)] * n_rods), phi, seed + 1, a, h_gen, phi0=phi0)
     pos, body = pack_suspension([rod(n_b, a)] * n_rods, L, rng, a, h_gen, max_tries=200000)
     return pos, body, L
 

@@ -157,3 +157,23 @@ def test_invalid_brownian_arguments(pkg, sysB):
     with pytest.raises(pkg.FsdError):
         s.brownian(1.0, 0.0)
     s.close()
+
+
+def test_wave_sample_on_a_grid_too_large_for_the_fused_fft(pkg):
+    # n = 180: FP32 planes no longer fit shared memory, so the FP32 sample
+    # takes the separate x and y passes (like FP64); the sample is the first
+    # thing each fresh context runs
+    rng = np.random.default_rng(21)
+    pos = rng.uniform(0.0, 30.0, size=(6, 3))
+    pos[:, 0] = np.arange(6) * 5.0 + 1.0
+    body = np.arange(6)
+    out = []
+    for prec in (FP64, MIXED):
+        s = pkg.Suspension(pos, body, 30.0, precision=prec, xi=0.5, grid=180)
+        assert s.params["grid"] == 180
+        z = np.zeros((6, 11))
+        slip, _, _ = s.brownian(1.0, 1.0, seed=3, step=9, psi_real=z, psi_nf=np.zeros((6, 6)))
+        s.close()
+        out.append(slip)
+    assert np.abs(out[0]).max() > 0
+    assert rel(out[1], out[0]) < 1e-5
