@@ -751,20 +751,23 @@ int realspace_group(const Ctx &c) {
 }
 
 // Resident blocks per SM of k_realspace<T, GG> at `smem` bytes of dynamic
-// shared memory; sets the kernel's shared-memory limit on first use.
+// shared memory.  The kernel's shared-memory limit is only ever raised (to
+// the largest table any context has used): contexts with different tables
+// share the kernel, and a lower limit would fail the larger ones' launches.
 // Thread-safe: contexts may run on several host threads.
 template <typename T, int GG>
 static int realspace_occupancy(size_t smem, int threads) {
   static std::mutex mu;
   static std::vector<std::pair<size_t, int>> seen;
+  static size_t limit = 0;
   std::lock_guard<std::mutex> lock(mu);
+  if (smem > limit) {
+    FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)std::max<size_t>(smem, 48 * 1024)));
+    limit = smem;
+  }
   for (auto &e : seen)
     if (e.first == smem) return e.second;
-  int dev = 0;
-  FSD_CUDA(cudaGetDevice(&dev));
-  (void)dev;
-  FSD_CUDA(cudaFuncSetAttribute(k_realspace<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)std::max<size_t>(smem, 48 * 1024)));
   int occ = 0;
   FSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_realspace<T, GG>, threads, smem));
   seen.emplace_back(smem, occ);

@@ -1293,6 +1293,18 @@ static void set_smem(const void *fn, size_t bytes) {
   done.push_back({fn, bytes});
 }
 
+// Largest log2 line count <= want whose two line buffers (lines_per_unit
+// lines each of the padded length) and the twiddles fit one block's shared
+// memory; large grids (FP64 above n ~ 270) take fewer lines per block.
+template <typename T>
+static int fit_log2_lines(int want, int lines_per_unit, int n, int ntw) {
+  for (int l = want; l >= 0; --l) {
+    const size_t b = (size_t)(ntw + 2 * (size_t)lines_per_unit * (1 << l) * fft_ls(n)) * sizeof(Cx<T>);
+    if (b <= (size_t)227 * 1024) return l;
+  }
+  throw Invalid{"FFT grid too large for one line per block in shared memory"};
+}
+
 // Inverse y and x transforms of the six fields held in spec (after the z
 // pass), then interpolation: y += h^3 sum W (fields) per bead.
 template <typename T>
@@ -1305,7 +1317,7 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
   const int ntw = plan.ntw;
   const size_t sm_xy = (size_t)(ntw + 2 * nh * fft_ls(n)) * sizeof(Cx<T>);
   const bool fused = sizeof(T) == 4 && sm_xy <= (size_t)227 * 1024;
-  const int LTXy = sizeof(T) == 8 ? 3 : 4;
+  const int LTXy = fit_log2_lines<T>(sizeof(T) == 8 ? 3 : 4, 1, n, ntw);
   const int TXy = 1 << LTXy;
   const size_t smy = (size_t)(ntw + 2 * TXy * fft_ls(n)) * sizeof(Cx<T>);
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
@@ -1323,7 +1335,7 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
     k_fft_y<T><<<blocks_y, threads, smy, c.stream>>>(spec, plan, op.twiddle.p, LTXy, T(1));
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
-    const int NL = 4;
+    const int NL = 1 << fit_log2_lines<T>(2, 3, n, ntw);
     size_t sm = (size_t)(ntw + 2 * 3 * NL * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_inv<T>, sm);
     int blocks = ceil_div((int64_t)n * n, NL);
@@ -1384,7 +1396,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   // separate x and y passes (interleaved fields).
   const size_t sm_xy = (size_t)(ntw + 2 * nh * fft_ls(n)) * sizeof(Cx<T>);
   const bool fused = sizeof(T) == 4 && sm_xy <= (size_t)227 * 1024;
-  const int LTXy = sizeof(T) == 8 ? 3 : 4;
+  const int LTXy = fit_log2_lines<T>(sizeof(T) == 8 ? 3 : 4, 1, n, ntw);
   const int TXy = 1 << LTXy;
   const size_t smy = (size_t)(ntw + 2 * TXy * fft_ls(n)) * sizeof(Cx<T>);
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
@@ -1394,7 +1406,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
-    const int NL = 4;
+    const int NL = 1 << fit_log2_lines<T>(2, 3, n, ntw);
     size_t sm = (size_t)(ntw + 2 * 3 * NL * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_x_fwd<T>, sm);
     int blocks = ceil_div((int64_t)n * n, NL);
@@ -1407,7 +1419,8 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     FSD_CUDA(cudaGetLastError());
   }
   {
-    const int LTX = 2;  // four kx columns: 6 x 4 lines keep 4 CTAs per SM (FP32)
+    // four kx columns: 6 x 4 lines keep 4 CTAs per SM (FP32)
+    const int LTX = fit_log2_lines<T>(2, 6, n, ntw);
     const int TX = 1 << LTX;
     size_t sm = (size_t)(ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_z_green<T>, sm);
@@ -1432,7 +1445,7 @@ void launch_brownian_wave(Ctx &c, const double *field, uint64_t seed, uint64_t s
   Cx<T> *spec = (Cx<T> *)op.spec.p;
   {
     ProfScope ps(c, PG_FFT);
-    const int LTX = 2;
+    const int LTX = fit_log2_lines<T>(2, 6, n, plan.ntw);
     const int TX = 1 << LTX;
     const size_t sm = (size_t)(plan.ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_brown_z<T>, sm);

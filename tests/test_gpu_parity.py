@@ -241,3 +241,19 @@ def test_invalid_parameters(pkg):
         pkg.Suspension(pos, body, L, xi=0.05)  # real-space cut-off beyond L/2
     with pytest.raises(pkg.FsdError):
         pkg.Suspension(pos, body, L, P=7)
+
+
+def test_contexts_with_different_real_space_tables_interleave(pkg):
+    # a larger table (smaller xi) then a smaller one, then the larger again:
+    # the shared kernel's shared-memory limit must stay high enough for both
+    pos, body, L = synth.config_doublets(24, 40.0, seed=8)
+    rng = np.random.default_rng(2)
+    F = rng.normal(size=(len(pos), 11))
+    big = pkg.Suspension(pos, body, L, xi=0.3)
+    small = pkg.Suspension(pos, body, L, xi=1.0)
+    u1 = big.apply_mobility(F, part=1, precision=pkg.FSD_MIXED)
+    small.apply_mobility(F, part=1, precision=pkg.FSD_MIXED)
+    u2 = big.apply_mobility(F, part=1, precision=pkg.FSD_MIXED)
+    big.close()
+    small.close()
+    assert np.allclose(u1, u2, rtol=1e-6, atol=0.0)

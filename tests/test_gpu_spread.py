@@ -60,3 +60,22 @@ def test_fused_and_separate_fft_passes_agree(pkg):
         w32 = s.apply_mobility(F, part=2, precision=MIXED).reshape(-1)
         s.close()
         assert rel(w32, w64) < 1e-5
+
+
+def test_wave_operator_on_grids_beyond_the_default_line_counts(pkg):
+    # n = 300: the FP64 z pass no longer fits four kx columns of six lines in
+    # shared memory and takes fewer per block; FP32 at n = 300 takes the
+    # separate x and y passes.  Both precisions must agree.
+    import numpy as np
+
+    rng = np.random.default_rng(31)
+    pos = rng.uniform(0.0, 40.0, size=(16, 3))
+    pos[:, 0] = np.arange(16) * 2.5 + 0.5
+    s = pkg.Suspension(pos, np.arange(16), 40.0, xi=0.5, grid=300)
+    assert s.params["grid"] == 300
+    F = rng.normal(size=(16, 11))
+    u64 = s.apply_mobility(F, part=2, precision=pkg.FSD_FP64)
+    u32 = s.apply_mobility(F, part=2, precision=pkg.FSD_MIXED)
+    s.close()
+    assert np.abs(u64).max() > 0
+    assert np.linalg.norm(u32 - u64) < 1e-5 * np.linalg.norm(u64)
