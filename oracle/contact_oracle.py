@@ -26,19 +26,19 @@ import numpy as np
 from . import fsd_oracle as F
 
 
-def hertz_contact(pos, body, L, kn, a=1.0):
+def hertz_contact(pos, body, L, kn, a=1.0, tilt=0.0):
     """(N, 6) aggregate force and torque (about X_J) from Hertz contacts;
-    also returns the per-bead forces (N_tot, 3)."""
+    also returns the per-bead forces (N_tot, 3).  tilt: the Lees-Edwards
+    offset of the box (0: cubic)."""
     body = np.asarray(body)
-    unw, X, r = F.body_geometry(pos, body, L)
+    unw, X, r = F.body_geometry(pos, body, L, tilt)
     Nt = len(unw)
     fb = np.zeros((Nt, 3))
     for i in range(Nt):
         for j in range(i + 1, Nt):
             if body[i] == body[j]:
                 continue
-            d = unw[i] - unw[j]
-            d -= L * np.round(d / L)
+            d = F.min_image(unw[i] - unw[j], L, tilt)
             dist = np.linalg.norm(d)
             delta = 2.0 * a - dist
             if delta > 0.0:

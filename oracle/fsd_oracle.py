@@ -324,18 +324,35 @@ def oracle_split(L):
     return xi, rc, kmax
 
 
+def min_image(d, L, tilt=0.0):
+    """Nearest periodic image of displacements d (..., 3) in a Lees-Edwards
+    box of side L whose image across y is offset by `tilt` along x (tilt 0:
+    the cubic box): wrap y first (shifting x by the offset), then x and z."""
+    d = np.array(d, dtype=np.float64, copy=True)
+    ny = np.round(d[..., 1] / L)
+    d[..., 0] -= ny * tilt
+    d[..., 1] -= ny * L
+    d[..., 0] -= L * np.round(d[..., 0] / L)
+    d[..., 2] -= L * np.round(d[..., 2] / L)
+    return d
+
+
 def _lattice(nmax):
     g = np.arange(-nmax, nmax + 1)
     return np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
 
 
-def mobility_real_dense(pos, L, xi, rc, a=1.0, eta=1.0):
-    """Real-space Ewald part + self term, dense (N, 11, N, 11)."""
+def mobility_real_dense(pos, L, xi, rc, a=1.0, eta=1.0, tilt=0.0):
+    """Real-space Ewald part + self term, dense (N, 11, N, 11).  Images at
+    n1 e1 + n2 e2 + n3 e3 with e1 = (L, 0, 0), e2 = (tilt, L, 0), e3 = (0, 0, L)
+    (a Lees-Edwards box; tilt 0 the cube)."""
     pos = np.asarray(pos, dtype=np.float64)
     N = pos.shape[0]
     M = np.zeros((N, 11, N, 11))
-    nimg = int(np.ceil(rc / L)) + 1
-    shifts = _lattice(nimg).astype(np.float64) * L
+    nimg = int(np.ceil(rc / L)) + 2
+    lat = _lattice(nimg).astype(np.float64)
+    shifts = lat * L
+    shifts[:, 0] += lat[:, 1] * tilt
     for i in range(N):
         d = pos[i][None, :] - pos  # x_i - x_j
         x = (d[:, None, :] + shifts[None, :, :]).reshape(-1, 3)
@@ -356,24 +373,29 @@ def mobility_real_dense(pos, L, xi, rc, a=1.0, eta=1.0):
     return M
 
 
-def wave_vectors(L, kmax):
-    nmax = int(np.ceil(kmax * L / (2 * PI)))
+def wave_vectors(L, kmax, tilt=0.0):
+    """Half of the reciprocal lattice within kmax.  For the Lees-Edwards box
+    (lattice e1 = (L, 0, 0), e2 = (tilt, L, 0), e3 = (0, 0, L)) the
+    reciprocal vectors are k = (2 pi / L) (n1, n2 - (tilt/L) n1, n3)."""
+    tau = tilt / L
+    nmax = int(np.ceil(kmax * L / (2 * PI) * (1.0 + abs(tau)))) + 1
     n = _lattice(nmax)
     # half space: first nonzero component positive
     first = np.where(n[:, 0] != 0, n[:, 0], np.where(n[:, 1] != 0, n[:, 1], n[:, 2]))
-    n = n[first > 0]
+    n = n[first > 0].astype(np.float64)
+    n[:, 1] -= tau * n[:, 0]
     k = 2 * PI * n / L
     kn = np.linalg.norm(k, axis=1)
     return k[kn <= kmax]
 
 
-def mobility_wave_dense(pos, L, xi, kmax, a=1.0, eta=1.0):
+def mobility_wave_dense(pos, L, xi, kmax, a=1.0, eta=1.0, tilt=0.0):
     """Wave-space Ewald part, dense: (1/V) sum_{k != 0} e^{ik.(x_i-x_j)}
     Q^H (I - kk) Q H(k,xi)/(eta k^2).  The k = 0 mode is excluded (mean force
     balanced by the mean pressure gradient)."""
     pos = np.asarray(pos, dtype=np.float64)
     N = pos.shape[0]
-    k = wave_vectors(L, kmax)
+    k = wave_vectors(L, kmax, tilt)
     kn = np.linalg.norm(k, axis=1)
     kh = k / kn[:, None]
     Q = source_operator(k, a)
@@ -393,15 +415,17 @@ def mobility_wave_dense(pos, L, xi, kmax, a=1.0, eta=1.0):
     return M
 
 
-def mobility_dense(pos, L, a=1.0, eta=1.0, xi=None):
-    """Periodic FTS mobility M_inf, dense (11N x 11N), bead-major."""
+def mobility_dense(pos, L, a=1.0, eta=1.0, xi=None, tilt=0.0):
+    """Periodic FTS mobility M_inf, dense (11N x 11N), bead-major (a
+    Lees-Edwards box when tilt != 0)."""
     xo, rc, kmax = oracle_split(L)
     if xi is not None:
         xo = xi
         rc = 2.0 + np.sqrt(46.0) / xo
         kmax = 2.0 * xo * np.sqrt(46.0)
     N = len(pos)
-    M = mobility_real_dense(pos, L, xo, rc, a, eta) + mobility_wave_dense(pos, L, xo, kmax, a, eta)
+    M = (mobility_real_dense(pos, L, xo, rc, a, eta, tilt)
+         + mobility_wave_dense(pos, L, xo, kmax, a, eta, tilt))
     return M.reshape(11 * N, 11 * N)
 
 
@@ -410,7 +434,7 @@ def mobility_dense(pos, L, a=1.0, eta=1.0, xi=None):
 # ---------------------------------------------------------------------------
 
 
-def body_geometry(pos, body, L):
+def body_geometry(pos, body, L, tilt=0.0):
     """Bead positions unwrapped per body (minimum image about the body's first
     bead), body centroids X (equal bead masses: the 'centre of mass', Sec. 2.3.1)
     and lever arms r_b = x_b - X_J."""
@@ -422,8 +446,7 @@ def body_geometry(pos, body, L):
     for J in range(nb):
         idx = np.nonzero(body == J)[0]
         ref = pos[idx[0]]
-        d = pos[idx] - ref
-        d -= L * np.round(d / L)
+        d = min_image(pos[idx] - ref, L, tilt)
         unw[idx] = ref + d
         X[J] = unw[idx].mean(axis=0)
     r = unw - X[body]
@@ -518,7 +541,7 @@ def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     return Ls.T @ G @ Ls + Lt.T @ Gt @ Lt
 
 
-def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
+def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, tilt=0.0):
     """Bead-level grand near-field resistance (11 Nt x 11 Nt), per bead
     ordering (6 velocity, 5 strain), summed over inter-body pairs with
     r < rcut (minimum image).  Intra-body pairs are excluded (Alg. 1 step 1)."""
@@ -532,7 +555,7 @@ def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
             if body[i] == body[j]:
                 continue
             d = pos[j] - pos[i]
-            d -= L * np.round(d / L)
+            d = min_image(d, L, tilt)
             if np.linalg.norm(d) >= rcut:
                 continue
             Rp = lub_pair_matrix(np.zeros(3), d, a, eta, rcut, hmin)
@@ -557,7 +580,7 @@ def split_grand(R, Nt):
 
 
 def assemble(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None,
-             hmin=1e-3):
+             hmin=1e-3, tilt=0.0):
     """Dense saddle-point matrix and right-hand side of Eq. spm_agg.
 
     Unknowns: (F (11 per bead), U - U_inf (6 per body)).  Returns a dict with
@@ -565,16 +588,16 @@ def assemble(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None,
     body = np.asarray(body)
     Nt = len(pos)
     nb = int(body.max()) + 1
-    unw, X, r = body_geometry(pos, body, L)
+    unw, X, r = body_geometry(pos, body, L, tilt)
     if M is None:
-        M = mobility_dense(unw, L, a, eta)
+        M = mobility_dense(unw, L, a, eta, tilt=tilt)
     E, Om = shear_flow(gamma)
     e5 = sym_to_vec5(E)
     ST = sigma_T(r, body, nb)
     Bm = B_op(Nt)
     BST = Bm @ ST
     if rlub > 2.0 * a:
-        Rg = lubrication_dense(unw, body, L, a, eta, rlub, hmin)
+        Rg = lubrication_dense(unw, body, L, a, eta, rlub, hmin, tilt)
     else:
         Rg = np.zeros((11 * Nt, 11 * Nt))
     RFU, RFE, RSU, RSE = split_grand(Rg, Nt)
@@ -639,10 +662,11 @@ def outputs(sys_, sol):
     return dict(U=U, dU=dU, S=S, SH=SH, SC=SC, F=Fm, Fnf=Fnf, Snf=Snf)
 
 
-def solve(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None, hmin=1e-3):
+def solve(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None, hmin=1e-3, tilt=0.0):
     """Dense direct solve of Eq. spm_agg (LAPACK gesv).  Returns outputs plus
-    the relative residual ||A x - b|| / ||b||."""
-    sys_ = assemble(pos, body, L, gamma, FT, a, eta, rlub, M, hmin)
+    the relative residual ||A x - b|| / ||b||.  tilt != 0: the Lees-Edwards
+    box (images across y offset by tilt along x)."""
+    sys_ = assemble(pos, body, L, gamma, FT, a, eta, rlub, M, hmin, tilt)
     sys_["body"] = np.asarray(body)
     x = np.linalg.solve(sys_["A"], sys_["b"])
     res = np.linalg.norm(sys_["A"] @ x - sys_["b"]) / max(np.linalg.norm(sys_["b"]), 1e-300)
@@ -707,7 +731,7 @@ def preconditioner_dense(sys_, pos, body, L, a=1.0, eta=1.0, rp=2.1, hmin=1e-3, 
     return Upper @ Mid @ Lower
 
 
-def lubrication_dense_cut(pos, body, L, a, eta, rpair, rlub, hmin=1e-3):
+def lubrication_dense_cut(pos, body, L, a, eta, rpair, rlub, hmin=1e-3, tilt=0.0):
     """R_nf with the pair functions of cut-off rlub, restricted to pairs r < rpair."""
     pos = np.asarray(pos, dtype=np.float64)
     Nt = pos.shape[0]
@@ -717,7 +741,7 @@ def lubrication_dense_cut(pos, body, L, a, eta, rpair, rlub, hmin=1e-3):
             if body[i] == body[j]:
                 continue
             d = pos[j] - pos[i]
-            d -= L * np.round(d / L)
+            d = min_image(d, L, tilt)
             if np.linalg.norm(d) >= min(rpair, rlub):
                 continue
             Rp = lub_pair_matrix(np.zeros(3), d, a, eta, rlub, hmin)
