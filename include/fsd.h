@@ -83,7 +83,7 @@ enum {
                               still prepared before the launch.  Same
                               arithmetic as the host-driven loop.  Ignored
                               while the profiler is on */
-  FSD_FLAG_AUTOTUNE = 8    /* at set-up, when xi, rc and grid are all left
+  FSD_FLAG_AUTOTUNE = 8,   /* at set-up, when xi, rc and grid are all left
                               to the rules: time each candidate splitting xi
                               in {0.30 .. 0.70}/a, and (small boxes) 1.02,
                               1.25 and 1.6 times the smallest xi whose R_c
@@ -92,6 +92,13 @@ enum {
                               each real-space tile on the device, with the
                               operator the Krylov iterations apply, and keep
                               the fastest.  Costs about eight set-ups */
+  FSD_FLAG_LEES_EDWARDS = 16 /* sheared periodic box for shear runs: fsd_step
+                              moves the bodies by their full velocity and
+                              advances the box offset `tilt` by shear_rate L dt
+                              (wrapped to [-L/2, L/2)), so each body's images
+                              across y move with the imposed flow.  Excludes
+                              FSD_FLAG_COMOVING; steps run host-driven (the
+                              offset changes every step) */
 };
 
 typedef struct {
@@ -132,6 +139,12 @@ typedef struct {
                             <= 0: 1e-7                                             */
   int lanczos_max_iter;  /* fsd_brownian: Lanczos step limit; <= 0: 60; at most
                             the Krylov basis length max(restart, inner_restart)   */
+  double tilt;           /* Lees-Edwards offset of the box: the periodic image
+                            across y sits at (x + tilt, y + L, z); lattice
+                            e1 = (L,0,0), e2 = (tilt,L,0), e3 = (0,0,L).  Taken
+                            modulo L into [-L/2, L/2) (0: the cube).  With a
+                            non-zero tilt (or FSD_FLAG_LEES_EDWARDS) R_c and
+                            the lubrication cut-off must stay below 0.447 L    */
 } fsd_params;
 
 typedef struct {
@@ -381,6 +394,11 @@ fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double para
  * the applied force).  kn in units of force / length^1.5.  The neighbour
  * lists built here are reused by the next solve. */
 fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque);
+
+/* Sets the Lees-Edwards offset of the box (see fsd_params.tilt; taken
+ * modulo L).  fsd_get_params reports the current offset.  Brownian sampling
+ * (fsd_brownian) needs tilt 0. */
+fsd_status fsd_set_tilt(fsd_ctx *ctx, double tilt);
 
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);

@@ -19,6 +19,7 @@ FSD_FLAG_WARM_START = 1
 FSD_FLAG_COMOVING = 2
 FSD_FLAG_GRAPH = 4
 FSD_FLAG_AUTOTUNE = 8
+FSD_FLAG_LEES_EDWARDS = 16
 FSD_DRIFT_RFD, FSD_DRIFT_FIXMAN = 0, 1
 STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",
                 5: "FSD_ENUMERIC", 6: "FSD_EOVERLAP", 7: "FSD_ETIMEOUT"}
@@ -31,7 +32,7 @@ EXPORTS = (
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
     "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
     "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian", "fsd_drift",
-    "fsd_contact_forces",
+    "fsd_contact_forces", "fsd_set_tilt",
 )
 PROF_GROUPS = 10
 
@@ -46,6 +47,7 @@ class FsdParams(ctypes.Structure):
         ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_restart", ctypes.c_int),
         ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int), ("tile", ctypes.c_int),
         ("lanczos_tol", ctypes.c_double), ("lanczos_max_iter", ctypes.c_int),
+        ("tilt", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -114,6 +116,7 @@ def load(path=LIB_PATH):
     lib.fsd_drift.argtypes = [P, I, D, D, D, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P,
                               ctypes.POINTER(FsdStats)]
     lib.fsd_contact_forces.argtypes = [P, D, P]
+    lib.fsd_set_tilt.argtypes = [P, D]
     lib.fsd_destroy_batch.argtypes = [P]
     lib.fsd_destroy_batch.restype = None
     for name in EXPORTS:
@@ -279,6 +282,10 @@ class Suspension:
                                 int(step), _ptr(dq), _ptr(d), _ptr(ub), _ptr(sb), ctypes.byref(st_))
         self._check(st, allow)
         return d, ub, sb, st_.as_dict(), st
+
+    def set_tilt(self, tilt):
+        """fsd_set_tilt: Lees-Edwards offset of the box."""
+        self._check(self.lib.fsd_set_tilt(self.ctx, float(tilt)))
 
     def contact(self, kn, out=None):
         """fsd_contact_forces: Hertz contact force / torque per aggregate [N, 6]."""

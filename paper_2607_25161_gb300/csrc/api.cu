@@ -330,6 +330,12 @@ static uint32_t spread_bits(uint32_t v) {
   return v;
 }
 
+// Lees-Edwards offset modulo L, in [-L/2, L/2)
+static double wrap_tilt(double t, double L) {
+  t -= L * std::floor(t / L + 0.5);
+  return t;
+}
+
 static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
                        const fsd_params &p, void *stream) {
   if (n_beads < 1) throw Invalid{"n_beads must be >= 1"};
@@ -372,20 +378,30 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   for (int i = 0; i < c.Nt; ++i) members[ids[i]].push_back(i);
   for (int J = 0; J < c.N; ++J)
     if (members[J].empty()) throw Invalid{"agg_id values must be dense 0..N-1"};
-  // ---- per body: unwrap about the first bead, centroid, body frame
+  // ---- per body: unwrap about the first bead (nearest image, Lees-Edwards
+  //      box when tilted), centroid, body frame
   const double L = c.L;
+  if (!(L > 0) || !std::isfinite(p.tilt)) throw Invalid{"box must be > 0 and tilt finite"};
+  c.tilt = wrap_tilt(p.tilt, L);
+  c.prm.tilt = c.tilt;
   std::vector<double> X(3 * (size_t)c.N), rb(3 * (size_t)c.Nt);
   std::vector<double> unw(3 * (size_t)c.Nt);
   for (int J = 0; J < c.N; ++J) {
     const int f = members[J][0];
     double s[3] = {0, 0, 0};
-    for (int i : members[J])
+    for (int i : members[J]) {
+      double dd[3] = {pos[3 * i] - pos[3 * f], pos[3 * i + 1] - pos[3 * f + 1],
+                      pos[3 * i + 2] - pos[3 * f + 2]};
+      const double ny = std::nearbyint(dd[1] / L);
+      dd[0] -= ny * c.tilt;
+      dd[1] -= ny * L;
+      dd[0] -= L * std::nearbyint(dd[0] / L);
+      dd[2] -= L * std::nearbyint(dd[2] / L);
       for (int d = 0; d < 3; ++d) {
-        double dd = pos[3 * i + d] - pos[3 * f + d];
-        dd -= L * std::nearbyint(dd / L);
-        unw[3 * i + d] = pos[3 * f + d] + dd;
+        unw[3 * i + d] = pos[3 * f + d] + dd[d];
         s[d] += unw[3 * i + d];
       }
+    }
     for (int d = 0; d < 3; ++d) X[3 * J + d] = s[d] / members[J].size();
   }
   // ---- spatial order of bodies (Morton code of the wrapped centroid)
@@ -457,6 +473,11 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.h = L / c.n;
   c.alpha = 2.0 * c.m_shape * c.m_shape / ((c.P * c.h) * (c.P * c.h));
   if (c.rc >= 0.5 * L) throw Invalid{"real-space cut-off must be below L/2 (raise xi or the box)"};
+  const bool le = (p.flags & FSD_FLAG_LEES_EDWARDS) || c.tilt != 0.0;
+  if (le && (c.rc >= 0.447 * L || p.lub_cutoff >= 0.447 * L))
+    throw Invalid{"in a Lees-Edwards box R_c and the lubrication cut-off must be below 0.447 L"};
+  if ((p.flags & FSD_FLAG_LEES_EDWARDS) && (p.flags & FSD_FLAG_COMOVING))
+    throw Invalid{"FSD_FLAG_LEES_EDWARDS and FSD_FLAG_COMOVING exclude each other"};
   if (p.lub_cutoff < 0) throw Invalid{"lub_cutoff must be >= 0"};
   if (p.lub_cutoff >= 0.5 * L) throw Invalid{"lub_cutoff must be below L/2"};
   c.prm.lub_cutoff = p.lub_cutoff > 2.0 * a ? p.lub_cutoff : 0.0;
@@ -499,6 +520,8 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.lever64.alloc(4 * (size_t)Nt);
   c.op32.pos.alloc(4 * (size_t)Nt);
   c.op32.lever.alloc(4 * (size_t)Nt);
+  c.wpos64.alloc(4 * (size_t)Nt);
+  c.wpos32.alloc(4 * (size_t)Nt);
   FSD_CUDA(cudaMemcpy(c.body_start.p, c.h_body_start.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice));
   FSD_CUDA(cudaMemcpy(c.bead_body.p, bead_body.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
   FSD_CUDA(cudaMemcpy(c.perm_bead.p, c.h_perm_bead.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
@@ -645,7 +668,11 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
 // ---- device-resident step (FSD_FLAG_GRAPH): geometry on the host side,
 //      then the whole solve (+ update) as one graph launch; the end half
 //      waits and turns the device state into a status.
-static bool use_graph(const Ctx &c) { return (c.prm.flags & FSD_FLAG_GRAPH) && !c.prof; }
+static bool use_graph(const Ctx &c) {
+  // a Lees-Edwards step changes the box offset, which the kernels take as an
+  // argument: those steps run host-driven
+  return (c.prm.flags & FSD_FLAG_GRAPH) && !c.prof && !(c.prm.flags & FSD_FLAG_LEES_EDWARDS);
+}
 
 struct StepMark {
   std::chrono::steady_clock::time_point t0;
@@ -1116,6 +1143,11 @@ fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque, double shear_r
   const int64_t l1 = c.launches;
   if (agg_velocity) bodies_out(c, vel_int, agg_velocity, 6);
   launch_integrate(c, vel_int, dt, shear_rate);
+  if (c.prm.flags & FSD_FLAG_LEES_EDWARDS) {
+    // the images across y move with the imposed flow: offset += shear L dt
+    c.tilt = wrap_tilt(c.tilt + shear_rate * c.L * dt, c.L);
+    c.prm.tilt = c.tilt;
+  }
   launch_wrap_positions(c);
   FSD_CUDA(cudaStreamSynchronize(c.stream));
   if (stats) stats->kernel_launches += c.launches - l1;
@@ -1283,6 +1315,10 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
     ctx->c.last_error = "kT must be >= 0 and dt > 0 (finite)";
     return FSD_EINVAL;
   }
+  if (ctx->c.tilt != 0.0) {
+    ctx->c.last_error = "Brownian sampling needs a cubic box (tilt 0)";
+    return FSD_EINVAL;
+  }
   FSD_API_TRY
   Ctx &c = ctx->c;
   auto t0 = std::chrono::steady_clock::now();
@@ -1363,6 +1399,26 @@ fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double para
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return st;
+  FSD_API_CATCH(ctx)
+}
+
+fsd_status fsd_set_tilt(fsd_ctx *ctx, double tilt) {
+  if (!ctx) return FSD_EINVAL;
+  if (!std::isfinite(tilt)) {
+    ctx->c.last_error = "tilt must be finite";
+    return FSD_EINVAL;
+  }
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  const double t = wrap_tilt(tilt, c.L);
+  if (t != 0.0 && (c.rc >= 0.447 * c.L || c.prm.lub_cutoff >= 0.447 * c.L))
+    throw Invalid{"in a Lees-Edwards box R_c and the lubrication cut-off must be below 0.447 L"};
+  c.tilt = t;
+  c.prm.tilt = t;
+  launch_wrap_positions(c);
+  FSD_CUDA(cudaStreamSynchronize(c.stream));
+  c.geom_fresh = false;
+  return FSD_OK;
   FSD_API_CATCH(ctx)
 }
 
@@ -1583,6 +1639,10 @@ static fsd_status batch_run(fsd_batch *b, const double *ft, const double *shear_
           st[s] = solve_internal(c, fts, shear_rates[s], c.t1.p, str_int, stats ? stats + s : nullptr, 0.0);
           if (integrate && status_rank(st[s]) < 3) {
             launch_integrate(c, c.t1.p, dt, shear_rates[s]);
+            if (c.prm.flags & FSD_FLAG_LEES_EDWARDS) {
+              c.tilt = wrap_tilt(c.tilt + shear_rates[s] * c.L * dt, c.L);
+              c.prm.tilt = c.tilt;
+            }
             launch_wrap_positions(c);
           }
         }

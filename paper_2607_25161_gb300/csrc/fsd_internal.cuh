@@ -150,6 +150,11 @@ struct Ctx {
   std::vector<int> h_body_start;
   DBuf<int> body_start, bead_body, perm_bead, perm_body;
   DBuf<double> X, q, rbody, pos64, lever64;
+  // Lees-Edwards box: offset of the image across y (0: cube); wave-space
+  // positions in sheared coordinates s = (x - (tilt/L) y, y, z), wrapped
+  double tilt = 0.0;
+  DBuf<double> wpos64;
+  DBuf<float> wpos32;
   // ---- neighbour lists
   int cap = 0, lcap = 0, ncell = 1;
   DBuf<int> nbr, ncnt, lnbr, lcnt;
@@ -195,6 +200,18 @@ struct Ctx {
   int64_t graph_pending = -1;
   double tuned_ms = 0.0;  // operator time measured by the autotuner (0: not tuned)
 };
+
+// ------------------------------------------------------ Lees-Edwards box
+// Nearest image of a displacement in the sheared periodic box (lattice
+// (L,0,0), (tilt,L,0), (0,0,L)): wrap y first, shifting x by the offset, then
+// x and z.  tilt = 0 is the cube.
+__device__ __forceinline__ void le_image(double &d0, double &d1, double &d2, double L, double tilt) {
+  const double ny = rint(d1 / L);
+  d0 -= ny * tilt;
+  d1 -= ny * L;
+  d0 -= L * rint(d0 / L);
+  d2 -= L * rint(d2 / L);
+}
 
 // ------------------------------------------------- counter-based normals
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two

@@ -44,7 +44,7 @@ struct GState {
 
 struct GraphKey {
   int mixed, warm, has_ft, integrate, with_str, group, lub, brown, add_vel, str_hydro;
-  double shear, dt, brown_scale;
+  double shear, dt, brown_scale, tilt;
   const void *nbr, *lnbr, *bcol, *bval64, *bval32, *packed64, *packed32;
   int cap, lcap;
   int64_t nunk;
@@ -527,6 +527,7 @@ static GraphKey make_key(Ctx &c, const GraphRun &o) {
   k.brown = o.brown;
   k.brown_scale = o.brown ? o.brown_scale : 0.0;
   k.add_vel = o.add_vel;
+  k.tilt = c.tilt;
   k.str_hydro = o.str_hydro;
   k.nbr = c.nbr.p;
   k.lnbr = c.lnbr.p;

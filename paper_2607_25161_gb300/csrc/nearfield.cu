@@ -79,10 +79,9 @@ __device__ __forceinline__ void pair_blocks(const double n[3], double r, PairCoe
     }
 }
 
-__device__ __forceinline__ void min_image(double &d0, double &d1, double &d2, double L) {
-  d0 -= L * rint(d0 / L);
-  d1 -= L * rint(d1 / L);
-  d2 -= L * rint(d2 / L);
+__device__ __forceinline__ void min_image(double &d0, double &d1, double &d2, double L,
+                                          double tilt) {
+  le_image(d0, d1, d2, L, tilt);
 }
 
 // Thread per bead row: off-diagonal blocks in CSR order, the diagonal block,
@@ -91,8 +90,8 @@ __global__ void k_lub_assemble(int Nt, const double4 *__restrict__ pos,
                                const int *__restrict__ lnbr, const int *__restrict__ lcnt,
                                int lcap, const int *__restrict__ brow, int *bcol, double *bval64,
                                float *bval32, double *bdiag64, float *bdiag32, double *pdiag,
-                               double L, double a, double eta, double rcut, double rp,
-                               double hmin) {
+                               double L, double tilt, double a, double eta, double rcut,
+                               double rp, double hmin) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   double Dg[36], Pg[36];
@@ -103,7 +102,7 @@ __global__ void k_lub_assemble(int Nt, const double4 *__restrict__ pos,
     const int j = lnbr[(size_t)i * lcap + k];
     const double4 pj = pos[j];
     double d0 = pj.x - pi.x, d1 = pj.y - pi.y, d2 = pj.z - pi.z;
-    min_image(d0, d1, d2, L);
+    min_image(d0, d1, d2, L, tilt);
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     const double n[3] = {d0 / r, d1 / r, d2 / r};
     PairCoef p = lub_coef(r, a, eta, rcut, hmin);
@@ -371,7 +370,7 @@ __global__ void k_nf_bead(int Nt, const double4 *__restrict__ pos,
                           const int *__restrict__ lnbr, const int *__restrict__ lcnt, int lcap,
                           const double *__restrict__ dU, double e00, double e11, double e22,
                           double e01, double e02, double e12, double *fnf, double *snf, double L,
-                          double a, double eta, double rcut, double hmin) {
+                          double tilt, double a, double eta, double rcut, double hmin) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   const double E[9] = {e00, e01, e02, e01, e11, e12, e02, e12, e22};
@@ -398,7 +397,7 @@ __global__ void k_nf_bead(int Nt, const double4 *__restrict__ pos,
     const int j = lnbr[(size_t)i * lcap + k];
     const double4 pj = pos[j];
     double d0 = pj.x - pi.x, d1 = pj.y - pi.y, d2 = pj.z - pi.z;
-    min_image(d0, d1, d2, L);
+    min_image(d0, d1, d2, L, tilt);
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     const double n[3] = {d0 / r, d1 / r, d2 / r};
     PairCoef p = lub_coef(r, a, eta, rcut, hmin);
@@ -560,8 +559,8 @@ __global__ void k_integrate(int N, const double *__restrict__ vel, double dt, do
 // holds every pair that can touch.
 __global__ void k_contact_bead(int Nt, const double4 *__restrict__ pos, const int *__restrict__ nbr,
                                const int *__restrict__ ncnt, int cap,
-                               const int *__restrict__ bead_body, double L, double two_a,
-                               double kn, double *fb) {
+                               const int *__restrict__ bead_body, double L, double tilt,
+                               double two_a, double kn, double *fb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   const double4 p = pos[i];
@@ -573,9 +572,7 @@ __global__ void k_contact_bead(int Nt, const double4 *__restrict__ pos, const in
     if (bead_body[j] == bi) continue;
     const double4 q = pos[j];
     double d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z;
-    d0 -= L * rint(d0 / L);
-    d1 -= L * rint(d1 / L);
-    d2 -= L * rint(d2 / L);
+    le_image(d0, d1, d2, L, tilt);
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
     if (r2 >= two_a * two_a || r2 == 0.0) continue;
     const double r = sqrt(r2), delta = two_a - r;
@@ -641,7 +638,7 @@ void build_lubrication(Ctx &c) {
   const double rl = c.prm.lub_cutoff > 2.0 * c.a ? c.prm.lub_cutoff : 2.0 * c.a;
   k_lub_assemble<<<ceil_div(Nt, 128), 128, 0, c.stream>>>(
       Nt, (const double4 *)c.pos64.p, c.lnbr.p, c.lcnt.p, c.lcap, c.brow.p, c.bcol.p,
-      c.op64.bval.p, c.op32.bval.p, c.op64.bdiag.p, c.op32.bdiag.p, c.pdiag.p, c.L, c.a, c.eta, rl,
+      c.op64.bval.p, c.op32.bval.p, c.op64.bdiag.p, c.op32.bdiag.p, c.pdiag.p, c.L, c.tilt, c.a, c.eta, rl,
       c.prm.precond_cutoff, c.prm.lub_hmin);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
@@ -726,7 +723,7 @@ void launch_rhs(Ctx &c, const double *ft_int, double shear, double *b) {
     const double rl = c.prm.lub_cutoff;
     k_nf_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
         c.Nt, (const double4 *)c.pos64.p, (const double4 *)c.lever64.p, c.bead_body.p, c.lnbr.p,
-        c.lcnt.p, c.lcap, nullptr, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.a,
+        c.lcnt.p, c.lcap, nullptr, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.tilt, c.a,
         c.eta, rl, c.prm.lub_hmin);
     FSD_LAUNCHED(c);
   }
@@ -746,7 +743,7 @@ void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int, doub
   if (nf) {
     k_nf_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
         c.Nt, (const double4 *)c.pos64.p, (const double4 *)c.lever64.p, c.bead_body.p, c.lnbr.p,
-        c.lcnt.p, c.lcap, x + off, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.a,
+        c.lcnt.p, c.lcap, x + off, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.tilt, c.a,
         c.eta, c.prm.lub_cutoff, c.prm.lub_hmin);
     FSD_LAUNCHED(c);
   }
@@ -769,7 +766,7 @@ void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear) {
 void launch_contact(Ctx &c, double kn, double *fb_scratch, double *ft_int) {
   ProfScope ps(c, PG_MISC);
   k_contact_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
-      c.Nt, (const double4 *)c.pos64.p, c.nbr.p, c.ncnt.p, c.cap, c.bead_body.p, c.L, 2.0 * c.a, kn,
+      c.Nt, (const double4 *)c.pos64.p, c.nbr.p, c.ncnt.p, c.cap, c.bead_body.p, c.L, c.tilt, 2.0 * c.a, kn,
       fb_scratch);
   FSD_LAUNCHED(c);
   k_contact_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,

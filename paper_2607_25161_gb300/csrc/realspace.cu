@@ -186,34 +186,51 @@ __device__ __forceinline__ void quat_rot(const double *q, const double *v, doubl
   o[2] = R20 * v[0] + R21 * v[1] + R22 * v[2];
 }
 
-__global__ void k_wrap_positions(int Nt, double L, const int *__restrict__ bead_body,
+__device__ __forceinline__ double wrap_box(double x, double L) {
+  x -= L * floor(x / L);
+  if (x >= L) x -= L;
+  if (x < 0) x = 0;
+  return x;
+}
+
+// Bead positions from the rigid-body state, wrapped into the periodic box:
+// in a Lees-Edwards box (offset tilt) a bead wrapped across y moves by the
+// offset along x.  wpos holds the wave-space (sheared) coordinates
+// s = (x - (tilt/L) y, y, z) wrapped into [0, L): the box is a plain cube in
+// them, so spreading and interpolation run on a regular grid (equal to pos
+// for tilt 0).
+__global__ void k_wrap_positions(int Nt, double L, double tilt, const int *__restrict__ bead_body,
                                  const double *__restrict__ X, const double *__restrict__ q,
                                  const double *__restrict__ rbody, double4 *pos64,
-                                 double4 *lever64, float4 *pos32, float4 *lever32) {
+                                 double4 *lever64, float4 *pos32, float4 *lever32,
+                                 double4 *wpos64, float4 *wpos32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   int J = bead_body[i];
   double rb[3] = {rbody[3 * i], rbody[3 * i + 1], rbody[3 * i + 2]};
   double lv[3];
   quat_rot(q + 4 * J, rb, lv);
-  double p[3];
-  for (int d = 0; d < 3; ++d) {
-    double x = X[3 * J + d] + lv[d];
-    x -= L * floor(x / L);
-    if (x >= L) x -= L;
-    if (x < 0) x = 0;
-    p[d] = x;
-  }
-  pos64[i] = make_double4(p[0], p[1], p[2], 0.0);
+  double x = X[3 * J] + lv[0], y = X[3 * J + 1] + lv[1], z = X[3 * J + 2] + lv[2];
+  const double ny = floor(y / L);
+  y -= ny * L;
+  x -= ny * tilt;
+  x = wrap_box(x, L);
+  y = wrap_box(y, L);
+  z = wrap_box(z, L);
+  const double sx = tilt != 0.0 ? wrap_box(x - (tilt / L) * y, L) : x;
+  pos64[i] = make_double4(x, y, z, 0.0);
   lever64[i] = make_double4(lv[0], lv[1], lv[2], 0.0);
-  pos32[i] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
+  pos32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
   lever32[i] = make_float4((float)lv[0], (float)lv[1], (float)lv[2], 0.f);
+  wpos64[i] = make_double4(sx, y, z, 0.0);
+  wpos32[i] = make_float4((float)sx, (float)y, (float)z, 0.f);
 }
 
 void launch_wrap_positions(Ctx &c) {
   k_wrap_positions<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(
-      c.Nt, c.L, c.bead_body.p, c.X.p, c.q.p, c.rbody.p, (double4 *)c.pos64.p,
-      (double4 *)c.lever64.p, (float4 *)c.op32.pos.p, (float4 *)c.op32.lever.p);
+      c.Nt, c.L, c.tilt, c.bead_body.p, c.X.p, c.q.p, c.rbody.p, (double4 *)c.pos64.p,
+      (double4 *)c.lever64.p, (float4 *)c.op32.pos.p, (float4 *)c.op32.lever.p,
+      (double4 *)c.wpos64.p, (float4 *)c.wpos32.p);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -288,7 +305,8 @@ __global__ void k_sort_cells(int ncells, const int *__restrict__ cell_start, int
 
 // One thread per bead: mobility neighbours (r < rc, any body, j != i) and
 // lubrication neighbours (r < rlub, different body).
-__global__ void k_neighbors(int Nt, const double4 *__restrict__ pos, double L, int nc,
+__global__ void k_neighbors(int Nt, const double4 *__restrict__ pos,
+                            const double4 *__restrict__ spos, double L, double tilt, int nc,
                             const int *__restrict__ cell_start,
                             const int *__restrict__ cell_beads,
                             const int *__restrict__ bead_body, double rc2, double rl2,
@@ -297,8 +315,9 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos, double L, i
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   double4 p = pos[i];
+  const double4 sp = spos[i];
   int bi = bead_body[i];
-  int cx = cell_of(p.x, L, nc), cy = cell_of(p.y, L, nc), cz = cell_of(p.z, L, nc);
+  int cx = cell_of(sp.x, L, nc), cy = cell_of(sp.y, L, nc), cz = cell_of(sp.z, L, nc);
   int cnt = 0, lc = 0;
   int span = nc >= 3 ? 1 : 0;
   int *row = nbr + (size_t)i * cap;
@@ -313,9 +332,7 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos, double L, i
           if (j == i) continue;
           double4 q = pos[j];
           double d0 = q.x - p.x, d1 = q.y - p.y, d2 = q.z - p.z;
-          d0 -= L * rint(d0 / L);
-          d1 -= L * rint(d1 / L);
-          d2 -= L * rint(d2 / L);
+          le_image(d0, d1, d2, L, tilt);
           double r2 = d0 * d0 + d1 * d1 + d2 * d2;
           if (r2 < rc2) {
             if (cnt < cap) row[cnt] = j;
@@ -340,7 +357,10 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos, double L, i
 
 void build_neighbors(Ctx &c) {
   ProfScope ps(c, PG_NEIGHBOR);
-  int nc = (int)std::floor(c.L / std::max(c.rc, c.prm.lub_cutoff));
+  // cells in sheared coordinates: a pair at distance r differs by up to
+  // r sqrt(1 + (tilt/L)^2) in s_x, so the cells widen by that factor
+  const double shear_f = std::sqrt(1.0 + (c.tilt / c.L) * (c.tilt / c.L));
+  int nc = (int)std::floor(c.L / (shear_f * std::max(c.rc, c.prm.lub_cutoff)));
   if (nc < 3) nc = 1;
   if (nc > 128) nc = 128;
   int ncells = nc * nc * nc;
@@ -352,15 +372,16 @@ void build_neighbors(Ctx &c) {
     c.cell_beads.alloc(c.Nt);
   }
   const double4 *pos = (const double4 *)c.pos64.p;
+  const double4 *spos = (const double4 *)c.wpos64.p;
   for (int attempt = 0; attempt < 4; ++attempt) {
     FSD_CUDA(cudaMemsetAsync(c.cell_count.p, 0, ncells * sizeof(int), c.stream));
     FSD_CUDA(cudaMemsetAsync(c.flags.p, 0, 8 * sizeof(int), c.stream));
-    k_cell_count<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, pos, c.L, nc, c.cell_count.p);
+    k_cell_count<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, spos, c.L, nc, c.cell_count.p);
     FSD_LAUNCHED(c);
     k_exclusive_scan<<<1, 1024, 0, c.stream>>>(ncells, c.cell_count.p, c.cell_start.p,
                                                c.cell_cursor.p);
     FSD_LAUNCHED(c);
-    k_cell_fill<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, pos, c.L, nc, c.cell_cursor.p,
+    k_cell_fill<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, spos, c.L, nc, c.cell_cursor.p,
                                                            c.cell_beads.p);
     FSD_LAUNCHED(c);
     k_sort_cells<<<ceil_div(ncells, 128), 128, 0, c.stream>>>(ncells, c.cell_start.p,
@@ -369,7 +390,7 @@ void build_neighbors(Ctx &c) {
     double rl = c.prm.lub_cutoff > 2.0 * c.a ? c.prm.lub_cutoff : 0.0;
     double ov = 2.0 * c.a * (1.0 - 1e-6);
     k_neighbors<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
-        c.Nt, pos, c.L, nc, c.cell_start.p, c.cell_beads.p, c.bead_body.p, c.rc * c.rc,
+        c.Nt, pos, spos, c.L, c.tilt, nc, c.cell_start.p, c.cell_beads.p, c.bead_body.p, c.rc * c.rc,
         rl * rl, ov * ov, c.cap, c.lcap, c.nbr.p, c.ncnt.p, c.lnbr.p, c.lcnt.p, c.flags.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
@@ -618,7 +639,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(256, 4) k_realspace(
     int Nt, const T *__restrict__ packed, const int *__restrict__ nbr,
     const int *__restrict__ ncnt, int cap, const double *__restrict__ x, double *__restrict__ y,
-    const T *__restrict__ tab_g, int nint, T inv_h, T L, T a, T c8, T self_t, T self_r,
+    const T *__restrict__ tab_g, int nint, T inv_h, T L, T tilt, T a, T c8, T self_t, T self_r,
     T self_s, int add_constraint, const int *__restrict__ bead_body,
     const double4 *__restrict__ lever, int Nt_off) {
   // the radial table is staged once per (persistent) CTA in shared memory
@@ -652,8 +673,13 @@ __global__ void __launch_bounds__(256, 4) k_realspace(
     T pj[3], F[3], Lm[3], S6[6];
     load_packed<T>(packed, j, pj, F, Lm, S6);
     T d0 = pi0 - pj[0], d1 = pi1 - pj[1], d2 = pi2 - pj[2];
+    {
+      // Lees-Edwards image: across y the box is offset by tilt along x
+      const T ny = rint_t<T>(d1 * invL);
+      d0 -= ny * tilt;
+      d1 -= L * ny;
+    }
     d0 -= L * rint_t<T>(d0 * invL);
-    d1 -= L * rint_t<T>(d1 * invL);
     d2 -= L * rint_t<T>(d2 * invL);
     const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
     const T r = sqrt_t<T>(r2);
@@ -795,7 +821,7 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, b
                                            (int64_t)std::max(1, per_sm) * c.num_sms),       \
                          threads, smem, c.stream>>>(                                         \
         c.Nt, op.packed.p, c.nbr.p, c.ncnt.p, c.cap, x, y, op.table.p, c.tab_nint, inv_h,    \
-        (T)c.L, (T)c.a, c8, op.self_real[0], op.self_real[1], op.self_real[2],             \
+        (T)c.L, (T)c.tilt, (T)c.a, c8, op.self_real[0], op.self_real[1], op.self_real[2],  \
         add_constraint ? 1 : 0, c.bead_body.p, (const double4 *)c.lever64.p,                 \
         (int)(LDB * (int64_t)c.Nt));                                                         \
   }

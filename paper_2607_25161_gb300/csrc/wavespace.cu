@@ -646,9 +646,31 @@ __global__ void __launch_bounds__(1024) k_fft_xy_inv(T *field, const Cx<T> *__re
 // ------------------------------------------------------- z pass + Green
 // Lines along z for fixed y, TX = 2^LTX consecutive kx, all six components:
 // forward DFT, Green's function, inverse DFT.
+// Green's function factors for the Lees-Edwards box (tau = tilt / L):
+// A(k) f_s(ka) f_t(ka) with A = (1 + k^2/(4 xi^2)) e^(-k^2/(4 xi^2)) e^(k_s^2/(2 alpha))
+// / (eta k^2 n^3), k the physical and k_s the sheared-grid wave vector
+// (the same expression the cubic table holds, with k_s = k there).
+struct GreenLE {
+  double tau = 0.0, ks2 = 0.0, xi = 0.0, alpha = 0.0, a = 0.0, eta = 0.0, inv_n3 = 0.0;
+};
+
+__device__ __forceinline__ void green_le(const GreenLE &g, double mp, double ms, double &t1,
+                                         double &t2, double &t3) {
+  const double k2 = g.ks2 * mp;
+  const double e = -k2 / (4.0 * g.xi * g.xi) + g.ks2 * ms / (2.0 * g.alpha);
+  const double A = (1.0 + k2 / (4.0 * g.xi * g.xi)) * exp(e) / (g.eta * k2) * g.inv_n3;
+  const double z = sqrt(k2) * g.a;
+  const double fm = z < 1e-3 ? 1.0 - z * z / 6.0 + z * z * z * z / 120.0 : sin(z) / z;
+  const double fd = z < 1e-2 ? 1.0 - z * z / 10.0 + z * z * z * z / 280.0
+                             : 3.0 * (sin(z) - z * cos(z)) / (z * z * z);
+  t1 = A * fm * fm;
+  t2 = A * fm * fd;
+  t3 = A * fd * fd;
+}
+
 template <typename T>
 __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
-                              const T *__restrict__ green, int LTX) {
+                              const T *__restrict__ green, int LTX, GreenLE le) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int TX = 1 << LTX;
@@ -705,9 +727,33 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     Cx<T> oM[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     Cx<T> oD[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     if (m > 0 && kx < nh) {
-      const T t1 = green[3 * m], t2 = green[3 * m + 1], t3 = green[3 * m + 2];
-      const T kk[3] = {(T)kx, (T)ky, (T)kz};
-      const T im = T(1) / (T)m;
+      T t1, t2, t3, kk[3], im;
+      if (le.tau == 0.0) {
+        t1 = green[3 * m];
+        t2 = green[3 * m + 1];
+        t3 = green[3 * m + 2];
+        kk[0] = (T)kx;
+        kk[1] = (T)ky;
+        kk[2] = (T)kz;
+        im = T(1) / (T)m;
+      } else {
+        // Lees-Edwards box: the grid index k_s = (kx, ky, kz) is the wave
+        // vector of the sheared coordinates; the physical one is
+        // (kx, ky - tau kx, kz) (in 2 pi / L).  The window factor stays on
+        // |k_s|^2; H(k), 1/k^2, the form factors and the projection take
+        // the physical k (evaluated here in FP64)
+        const double kyp = (double)ky - le.tau * (double)kx;
+        const double mp = (double)kx * kx + kyp * kyp + (double)kz * kz;
+        double g1, g2, g3;
+        green_le(le, mp, (double)m, g1, g2, g3);
+        t1 = (T)g1;
+        t2 = (T)g2;
+        t3 = (T)g3;
+        kk[0] = (T)kx;
+        kk[1] = (T)kyp;
+        kk[2] = (T)kz;
+        im = (T)(1.0 / mp);
+      }
       Cx<T> sF = {T(0), T(0)}, sD = {T(0), T(0)};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -874,7 +920,7 @@ constexpr int kMaxP = 24;
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread(int Nt, const typename V4Of<T>::type *__restrict__ pos,
                                                 const double *__restrict__ x, T *grid, int n, int P,
-                                                T h, T alpha, T cnorm) {
+                                                T h, T alpha, T cnorm, T tau) {
   __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP];
   __shared__ int si[8][3][kMaxP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -899,10 +945,13 @@ __global__ void __launch_bounds__(256) k_spread(int Nt, const typename V4Of<T>::
   const T s0 = (T)xr[6], s1 = (T)xr[7], s2 = (T)xr[8], s3 = (T)xr[9], s4 = (T)xr[10];
   const T Sxx = r2i * s0 - r6i * s1, Syy = -r2i * s0 - r6i * s1, Szz = T(2) * r6i * s1;
   const T Sxy = r2i * s2, Sxz = r2i * s3, Syz = r2i * s4;
-  // D = S + A with A y = (1/2) L x y
-  const T D00 = Sxx, D01 = Sxy - T(0.5) * L2, D02 = Sxz + T(0.5) * L1;
-  const T D10 = Sxy + T(0.5) * L2, D11 = Syy, D12 = Syz - T(0.5) * L0;
-  const T D20 = Sxz - T(0.5) * L1, D21 = Syz + T(0.5) * L0, D22 = Szz;
+  // D = S + A with A y = (1/2) L x y; in a Lees-Edwards box the window is a
+  // Gaussian of the sheared coordinates, whose x-gradient is the s-gradient
+  // transformed by A^-T: column 0 of D takes -tau column 1
+  const T D01 = Sxy - T(0.5) * L2, D11 = Syy, D21 = Syz + T(0.5) * L0;
+  const T D00 = Sxx - tau * D01, D02 = Sxz + T(0.5) * L1;
+  const T D10 = Sxy + T(0.5) * L2 - tau * D11, D12 = Syz - T(0.5) * L0;
+  const T D20 = Sxz - T(0.5) * L1 - tau * D21, D22 = Szz;
   const int P3 = P * P * P;
   const T ta = T(2) * alpha;
   for (int t = lane; t < P3; t += 32) {
@@ -937,7 +986,7 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
 
 __global__ void __launch_bounds__(256) k_spread_v4(int Nt, const float4 *__restrict__ pos,
                                                    const double *__restrict__ x, float *grid, int n,
-                                                   int P, float h, float alpha, float cnorm) {
+                                                   int P, float h, float alpha, float cnorm, float tau) {
   __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
   __shared__ int si[8][2][kMaxP];
   __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
@@ -974,9 +1023,10 @@ __global__ void __launch_bounds__(256) k_spread_v4(int Nt, const float4 *__restr
               s4 = (float)xr[10];
   const float Sxx = r2i * s0 - r6i * s1, Syy = -r2i * s0 - r6i * s1, Szz = 2.f * r6i * s1;
   const float Sxy = r2i * s2, Sxz = r2i * s3, Syz = r2i * s4;
-  const float D00 = Sxx, D01 = Sxy - 0.5f * L2, D02 = Sxz + 0.5f * L1;
-  const float D10 = Sxy + 0.5f * L2, D11 = Syy, D12 = Syz - 0.5f * L0;
-  const float D20 = Sxz - 0.5f * L1, D21 = Syz + 0.5f * L0, D22 = Szz;
+  const float D01 = Sxy - 0.5f * L2, D11 = Syy, D21 = Syz + 0.5f * L0;
+  const float D00 = Sxx - tau * D01, D02 = Sxz + 0.5f * L1;
+  const float D10 = Sxy + 0.5f * L2 - tau * D11, D12 = Syz - 0.5f * L0;
+  const float D20 = Sxz - 0.5f * L1 - tau * D21, D22 = Szz;
   const float ta = 2.f * alpha;
   const int64_t n3 = (int64_t)n * n * n;
   const int T = P * P * nq;
@@ -1014,7 +1064,7 @@ __global__ void __launch_bounds__(256) k_spread_v4(int Nt, const float4 *__restr
 template <typename T, bool PL>
 __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::type *__restrict__ pos,
                                                 const T *__restrict__ grid, double *y, int n, int P,
-                                                T h, T alpha, T cnorm_h3) {
+                                                T h, T alpha, T cnorm_h3, double tau) {
   __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP];
   __shared__ int si[8][3][kMaxP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1074,8 +1124,10 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
   double a_[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) a_[k] = (double)acc[k] * (double)cnorm_h3;
-  const double G00 = a_[3], G01 = a_[4], G02 = a_[5], G10 = a_[6], G11 = a_[7], G12 = a_[8],
-               G20 = a_[9], G21 = a_[10], G22 = a_[11];
+  // Lees-Edwards box: d/dy = d/ds_y - tau d/ds_x on the sheared window
+  const double G00 = a_[3], G01 = a_[4] - tau * a_[3], G02 = a_[5], G10 = a_[6],
+               G11 = a_[7] - tau * a_[6], G12 = a_[8], G20 = a_[9], G21 = a_[10] - tau * a_[9],
+               G22 = a_[11];
   const double r2i = 0.70710678118654752440, r6i = 0.40824829046386301637,
                s2 = 1.41421356237309504880;
   double *yr = y + (size_t)i * LDB;
@@ -1098,7 +1150,8 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
 // window carry weight 0 (the quads of k_spread_v4).
 __global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restrict__ pos,
                                                    const float *__restrict__ field, double *y, int n,
-                                                   int P, float h, float alpha, float cnorm_h3) {
+                                                   int P, float h, float alpha, float cnorm_h3,
+                                                   double tau) {
   __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
   __shared__ int si[8][2][kMaxP];
   __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
@@ -1171,8 +1224,10 @@ __global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restr
   double a_[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) a_[k] = (double)acc[k] * (double)cnorm_h3;
-  const double G00 = a_[3], G01 = a_[4], G02 = a_[5], G10 = a_[6], G11 = a_[7], G12 = a_[8],
-               G20 = a_[9], G21 = a_[10], G22 = a_[11];
+  // Lees-Edwards box: d/dy = d/ds_y - tau d/ds_x on the sheared window
+  const double G00 = a_[3], G01 = a_[4] - tau * a_[3], G02 = a_[5], G10 = a_[6],
+               G11 = a_[7] - tau * a_[6], G12 = a_[8], G20 = a_[9], G21 = a_[10] - tau * a_[9],
+               G22 = a_[11];
   const double r2i = 0.70710678118654752440, r6i = 0.40824829046386301637,
                s2 = 1.41421356237309504880;
   double *yr = y + (size_t)i * LDB;
@@ -1271,13 +1326,15 @@ OpData<float> &opd<float>(Ctx &c) {
 }
 template <typename T>
 static const typename V4Of<T>::type *posp(Ctx &c);
+// wave-space bead positions: the sheared coordinates of a Lees-Edwards box
+// (the ordinary wrapped positions for tilt 0)
 template <>
 const double4 *posp<double>(Ctx &c) {
-  return (const double4 *)c.pos64.p;
+  return (const double4 *)c.wpos64.p;
 }
 template <>
 const float4 *posp<float>(Ctx &c) {
-  return (const float4 *)c.op32.pos.p;
+  return (const float4 *)c.wpos32.p;
 }
 
 // Raise a kernel's dynamic shared-memory limit once per (kernel, size);
@@ -1350,15 +1407,17 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
                       (size_t)(make_plan(n, nullptr, true).ntw + 2 * (n / 2 + 1) * fft_ls(n)) * sizeof(Cx<T>) <=
                           (size_t)227 * 1024;
   if (planar && n % 4 == 0)
-    k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p,
+    k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p,
                                                          (const float *)op.gout.p, y, n, P,
-                                                         (float)h, (float)alpha, (float)(cn * h3));
+                                                         (float)h, (float)alpha, (float)(cn * h3),
+                                                         c.tilt / c.L);
   else if (planar)
     k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
-                                                              h, alpha, (T)(cn * h3));
+                                                              h, alpha, (T)(cn * h3), c.tilt / c.L);
   else
     k_interp<T, false><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
-                                                               P, h, alpha, (T)(cn * h3));
+                                                               P, h, alpha, (T)(cn * h3),
+                                                               c.tilt / c.L);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -1375,12 +1434,13 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   ProfScope ps(c, PG_SPREAD);
   FSD_CUDA(cudaMemsetAsync(op.grid.p, 0, gbytes, c.stream));
   if (sizeof(T) == 4 && n % 4 == 0)
-    k_spread_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.op32.pos.p, x,
+    k_spread_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p, x,
                                                          (float *)op.grid.p, n, P, (float)h,
-                                                         (float)alpha, (float)cn);
+                                                         (float)alpha, (float)cn,
+                                                         (float)(c.tilt / c.L));
   else
     k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
-                                                        alpha, (T)cn);
+                                                        alpha, (T)cn, (T)(c.tilt / c.L));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   }
@@ -1425,8 +1485,18 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     size_t sm = (size_t)(ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_fft_z_green<T>, sm);
     int blocks = n * ceil_div(nh, TX);
+    GreenLE le;
+    if (c.tilt != 0.0) {
+      le.tau = c.tilt / c.L;
+      le.ks2 = (2.0 * kPi / c.L) * (2.0 * kPi / c.L);
+      le.xi = c.xi;
+      le.alpha = c.alpha;
+      le.a = c.a;
+      le.eta = c.eta;
+      le.inv_n3 = 1.0 / ((double)n * n * n);
+    }
     k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p, op.green.p,
-                                                        LTX);
+                                                        LTX, le);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
@@ -1674,7 +1744,7 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
     return FSD_ECUDA;
   const double cn = std::pow(alpha / kPi, 1.5);
   k_spread<float><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, x, gridp, n, P, (float)h, (float)alpha,
-                                               (float)cn);
+                                               (float)cn, 0.f);
   const int ntw = plan.ntw;
   k_fft_x_fwd<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gridp, spec, plan, tw, 4);
@@ -1683,12 +1753,12 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, -1.f);
   k_fft_z_green<float><<<n * ((nh + 3) / 4), threads,
                          (ntw + 2 * 6 * 4 * fft_ls(n)) * sizeof(Cx<float>), st>>>(spec, plan, tw,
-                                                                                green, 2);
+                                                                                green, 2, GreenLE());
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, 1.f);
   k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gout, spec, plan, tw, 4);
   k_interp<float, false><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, gout, y, n, P, (float)h, (float)alpha,
-                                               (float)(cn * h * h * h));
+                                               (float)(cn * h * h * h), 0.0);
   k_na_stage_out<<<(nb + 127) / 128, 128, 0, st>>>(nb, y, out);
   if (cudaGetLastError() != cudaSuccess) return FSD_ECUDA;
   return FSD_OK;

@@ -1,0 +1,137 @@
+"""GPU parity of the Lees-Edwards (sheared periodic) box against the oracle's
+sheared lattice (images at n1 e1 + n2 e2 + n3 e3, e2 = (tilt, L, 0);
+reciprocal vectors (2 pi/L)(n1, n2 - tilt/L n1, n3)), through the C ABI.
+
+Tolerances (relative L2) as for the cubic box: FP64 1e-6 at x_err = 1e-8,
+P = 16, GMRES 1e-10; the FP32 operator (mixed) 1e-5."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import contact_oracle as C
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+HI = dict(xi=1.2, P=16, xerr=1e-8, tol=1e-10)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2607_25161_gb300 as p
+
+    return p
+
+
+@pytest.fixture(scope="module")
+def sysLE():
+    rng = np.random.default_rng(12)
+    sizes = [1, 2, 3, 4, 2, 3]
+    shapes = [synth.random_attachment_aggregate(n, rng) for n in sizes]
+    L = 14.0
+    pos, body = synth.pack_suspension(shapes, L, rng, h_gen=0.05)
+    return pos, body, L
+
+
+@pytest.mark.parametrize("tilt_frac", [0.3, -0.45])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-6), (MIXED, 1e-5)])
+def test_mobility_matches_oracle_with_tilt(pkg, sysLE, tilt_frac, prec, tol):
+    pos, body, L = sysLE
+    tilt = tilt_frac * L
+    rng = np.random.default_rng(3)
+    F = rng.normal(size=(len(pos), 11))
+    unw, X, r = O.body_geometry(pos, body, L, tilt)
+    ref = O.mobility_dense(unw, L, tilt=tilt) @ F.reshape(-1)
+    s = pkg.Suspension(pos, body, L, tilt=tilt, **HI)
+    assert abs(s.params["tilt"] - tilt) < 1e-12
+    u = s.apply_mobility(F, part=3, precision=prec)
+    s.close()
+    assert rel(u.reshape(-1), ref) < tol
+
+
+def test_tilt_modulo_L_and_set_tilt(pkg, sysLE):
+    pos, body, L = sysLE
+    rng = np.random.default_rng(4)
+    F = rng.normal(size=(len(pos), 11))
+    a = pkg.Suspension(pos, body, L, tilt=0.3 * L, **HI)
+    ua = a.apply_mobility(F, part=3)
+    a.close()
+    b = pkg.Suspension(pos, body, L, **HI)
+    u0 = b.apply_mobility(F, part=3)
+    b.set_tilt(-0.7 * L)
+    assert abs(b.params["tilt"] - 0.3 * L) < 1e-12
+    ub = b.apply_mobility(F, part=3)
+    b.close()
+    assert rel(ub, ua) < 1e-12
+    assert rel(ua, u0) > 1e-4
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-6), (MIXED, 1e-5)])
+def test_solve_matches_oracle_with_tilt(pkg, sysLE, prec, tol):
+    pos, body, L = sysLE
+    tilt = -0.37 * L
+    ft = synth.random_forces(body.max() + 1, 5)
+    ref = O.solve(pos, body, L, gamma=0.7, FT=ft, rlub=3.0, tilt=tilt)
+    s = pkg.Suspension(pos, body, L, tilt=tilt, precision=prec, lub_cutoff=3.0, **HI)
+    vel, S, st, status = s.solve(ft, 0.7)
+    s.close()
+    assert status == pkg.FSD_OK
+    assert rel(vel, ref["U"]) < tol
+    assert rel(S, ref["S"]) < tol
+
+
+def test_lees_edwards_step_advances_the_box(pkg, sysLE):
+    pos, body, L = sysLE
+    gamma, dt = 0.8, 0.05
+    s = pkg.Suspension(pos, body, L, flags=pkg.FSD_FLAG_LEES_EDWARDS, lub_cutoff=3.0, **HI)
+    vel, _, _, _ = s.solve(None, gamma)
+    p0, q0 = s.beads()
+    s.step(None, gamma, dt)
+    p1, q1 = s.beads()
+    tilt1 = s.params["tilt"]
+    for _ in range(9):
+        s.step(None, gamma, dt)
+    tilt10 = s.params["tilt"]
+    s.close()
+    wrap = lambda t: t - L * np.floor(t / L + 0.5)  # noqa: E731
+    assert abs(tilt1 - wrap(gamma * L * dt)) < 1e-12
+    assert abs(tilt10 - wrap(10 * gamma * L * dt)) < 1e-10
+    # one step: every body moved rigidly by its full (lab-frame) velocity;
+    # the centroids are those the library took from the set-up positions
+    # (U_inf = gamma X_y depends on which periodic image X is)
+    unw, X, r = O.body_geometry(pos, body, L, 0.0)
+    N = body.max() + 1
+    q = np.tile([1.0, 0.0, 0.0, 0.0], (N, 1))
+    _, _, x1 = O.integrate(X, q, r, body, vel, dt)
+    d = O.min_image(p1 - x1, L, tilt1)
+    assert np.abs(d).max() < 1e-10
+
+
+def test_contact_with_tilt(pkg):
+    L, tilt = 20.0, 0.31 * 20.0
+    # bead 1 is bead 0's neighbour through the sheared y boundary
+    pos = np.array([[3.0, 0.4, 5.0], [3.0 + tilt - 0.5, L - 1.3, 5.0], [12.0, 10.0, 12.0]])
+    body = np.array([0, 1, 2])
+    ref, fb = C.hertz_contact(pos, body, L, 50.0, tilt=tilt)
+    assert np.abs(fb).max() > 0
+    s = pkg.Suspension(pos, body, L, xi=0.8, tilt=tilt)
+    ft = s.contact(50.0)
+    s.close()
+    assert rel(ft, ref) < 1e-12
+
+
+def test_brownian_needs_a_cubic_box(pkg, sysLE):
+    pos, body, L = sysLE
+    s = pkg.Suspension(pos, body, L, tilt=0.2 * L, **HI)
+    with pytest.raises(pkg.FsdError):
+        s.brownian(1.0, 1e-3)
+    s.close()
