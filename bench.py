@@ -377,6 +377,31 @@ def run_ours(args, rank, world, local_rank):
                      "FP32 operator) and near-field Brownian force (Lanczos, FP64), then the mixed solve "
                      "with them; drift not included (see brownian_drift)"}
 
+    # ---- sheared periodic box: the same workload stepped with
+    #      FSD_FLAG_LEES_EDWARDS (bodies move by their full velocity, the box
+    #      offset by shear L dt; host-driven steps)
+    s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED,
+                       **dict(common, flags=pkg.FSD_FLAG_LEES_EDWARDS))
+    for _ in range(min(args.warmup, 3)):
+        s.step(None, w["shear"], w["dt"])
+    barrier()
+    torch.cuda.synchronize()
+    el0 = torch.cuda.Event(enable_timing=True)
+    el1 = torch.cuda.Event(enable_timing=True)
+    el0.record(stream)
+    its_le = []
+    for _ in range(args.steps):
+        stl, _ = s.step(None, w["shear"], w["dt"])
+        its_le.append(stl["iters"])
+    el1.record(stream)
+    torch.cuda.synchronize()
+    tilt_end = s.params["tilt"]
+    s.close()
+    msl = max_over_ranks(el0.elapsed_time(el1))
+    lees = {"value": Nt * args.steps * world / (msl / 1e3), "ms_per_step": msl / args.steps,
+            "iters_first_last": [its_le[0], its_le[-1]], "tilt_end": tilt_end,
+            "note": "Lees-Edwards box (sheared images), full velocity, host-driven steps"}
+
     # ---- Brownian step with the drift (Sec. 2.4; appendix on the drift):
     #      fsd_brownian, fsd_drift (two solves at displaced configurations),
     #      then the step's solve: three solves per step either way
@@ -474,6 +499,7 @@ def run_ours(args, rank, world, local_rank):
         "warm_start": warm,
         "brownian": brown,
         "brownian_drift": drift_lines,
+        "lees_edwards": lees,
         "roofline": roof,
         "cpu_baseline": base,
         "e2e": e2e,
