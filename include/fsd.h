@@ -396,8 +396,7 @@ fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double para
 fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque);
 
 /* Sets the Lees-Edwards offset of the box (see fsd_params.tilt; taken
- * modulo L).  fsd_get_params reports the current offset.  Brownian sampling
- * (fsd_brownian) needs tilt 0. */
+ * modulo L).  fsd_get_params reports the current offset. */
 fsd_status fsd_set_tilt(fsd_ctx *ctx, double tilt);
 
 /* Parameters actually used (after the defaulting rules). */

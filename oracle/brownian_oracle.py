@@ -150,10 +150,12 @@ def _k_int(i, n):
     return i if i < n // 2 else i - n
 
 
-def brownian_wave_slip(pos, L, xi, n, field, a=1.0, eta=1.0):
+def brownian_wave_slip(pos, L, xi, n, field, a=1.0, eta=1.0, tilt=0.0):
     """u_w per bead (N, 11) for the half-spectrum field [3][n][n][n/2+1]:
     V^-1/2 sum over k = 2 pi m / L, |m_i| < n/2, k != 0 (kx < 0 by
-    conjugation) of e^(ik.x) Q(k)^H sqrt(H/(eta k^2)) (I - kk) xi(k)."""
+    conjugation) of e^(ik.x) Q(k)^H sqrt(H/(eta k^2)) (I - kk) xi(k).  In a
+    Lees-Edwards box (tilt != 0) the field index m labels the reciprocal
+    vector k = (2 pi / L)(m1, m2 - (tilt/L) m1, m3) of the sheared lattice."""
     pos = np.asarray(pos, dtype=np.float64)
     nh = n // 2 + 1
     ms, vals, wts = [], [], []
@@ -166,6 +168,7 @@ def brownian_wave_slip(pos, L, xi, n, field, a=1.0, eta=1.0):
                 vals.append(field[:, kz, ky, kx])
                 wts.append(1.0 if kx == 0 else 2.0)  # kx > 0 also stands for -k
     m = np.array(ms, dtype=np.float64)
+    m[:, 1] -= (tilt / L) * m[:, 0]
     v = np.array(vals)
     w = np.array(wts)
     k = 2.0 * np.pi * m / L

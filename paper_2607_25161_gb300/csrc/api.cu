@@ -1315,10 +1315,6 @@ fsd_status fsd_brownian(fsd_ctx *ctx, double kT, double dt, uint64_t seed, uint6
     ctx->c.last_error = "kT must be >= 0 and dt > 0 (finite)";
     return FSD_EINVAL;
   }
-  if (ctx->c.tilt != 0.0) {
-    ctx->c.last_error = "Brownian sampling needs a cubic box (tilt 0)";
-    return FSD_EINVAL;
-  }
   FSD_API_TRY
   Ctx &c = ctx->c;
   auto t0 = std::chrono::steady_clock::now();

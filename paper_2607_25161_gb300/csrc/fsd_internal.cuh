@@ -76,6 +76,8 @@ struct OpData {
   DBuf<T> lever;      // r_b = x_b - X_J [Nt][4]
   DBuf<T> packed;     // per bead (x, y, z, F, L, S6, 0) in the operator precision [Nt][16]
   DBuf<T> btab;       // Brownian wave-field scales [m = kx^2+ky^2+kz^2][2]: (c fM, c fD)
+  DBuf<T> green_le;   // Lees-Edwards box: Green factors per wave vector [ky][kx][kz][3]
+  double green_le_tilt = 0.0;  // box offset the table was built for (0: none)
 };
 
 // Kernel groups timed by the opt-in profiler (CUDA events on the stream).

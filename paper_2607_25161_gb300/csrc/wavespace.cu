@@ -652,6 +652,7 @@ __global__ void __launch_bounds__(1024) k_fft_xy_inv(T *field, const Cx<T> *__re
 // (the same expression the cubic table holds, with k_s = k there).
 struct GreenLE {
   double tau = 0.0, ks2 = 0.0, xi = 0.0, alpha = 0.0, a = 0.0, eta = 0.0, inv_n3 = 0.0;
+  double isv = 0.0;  // 1 / sqrt(V): the Brownian wave-field scale
 };
 
 __device__ __forceinline__ void green_le(const GreenLE &g, double mp, double ms, double &t1,
@@ -668,9 +669,35 @@ __device__ __forceinline__ void green_le(const GreenLE &g, double mp, double ms,
   t3 = A * fd * fd;
 }
 
+// Lees-Edwards Green factors for every half-spectrum point, laid out as the
+// z pass visits them: [ky index][kx][kz index][3].
+template <typename T>
+__global__ void k_green_le_table(int n, GreenLE le, T *gle) {
+  const int nh = n / 2 + 1;
+  const int64_t total = (int64_t)n * nh * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int zz = (int)(e % n);
+    const int kx = (int)((e / n) % nh);
+    const int yy = (int)(e / ((int64_t)n * nh));
+    const int ky = yy <= n / 2 ? yy : yy - n, kz = zz <= n / 2 ? zz : zz - n;
+    const int m = kx * kx + ky * ky + kz * kz;
+    double g1 = 0.0, g2 = 0.0, g3 = 0.0;
+    if (m > 0) {
+      const double kyp = (double)ky - le.tau * (double)kx;
+      const double mp = (double)kx * kx + kyp * kyp + (double)kz * kz;
+      green_le(le, mp, (double)m, g1, g2, g3);
+    }
+    gle[3 * e] = (T)g1;
+    gle[3 * e + 1] = (T)g2;
+    gle[3 * e + 2] = (T)g3;
+  }
+}
+
 template <typename T>
 __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
-                              const T *__restrict__ green, int LTX, GreenLE le) {
+                              const T *__restrict__ green, int LTX, GreenLE le,
+                              const T *__restrict__ gle) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int TX = 1 << LTX;
@@ -744,11 +771,11 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
         // the physical k (evaluated here in FP64)
         const double kyp = (double)ky - le.tau * (double)kx;
         const double mp = (double)kx * kx + kyp * kyp + (double)kz * kz;
-        double g1, g2, g3;
-        green_le(le, mp, (double)m, g1, g2, g3);
-        t1 = (T)g1;
-        t2 = (T)g2;
-        t3 = (T)g3;
+        // factors of this box offset, tabulated once per offset
+        const T *gq = gle + 3 * (((size_t)yy * nh + kx) * n + zz);
+        t1 = gq[0];
+        t2 = gq[1];
+        t3 = gq[2];
         kk[0] = (T)kx;
         kk[1] = (T)kyp;
         kk[2] = (T)kz;
@@ -799,7 +826,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
 template <typename T>
 __global__ void k_brown_z(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
                           const T *__restrict__ btab, const double *__restrict__ field,
-                          uint64_t seed, uint64_t step, int LTX) {
+                          uint64_t seed, uint64_t step, int LTX, GreenLE le) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int TX = 1 << LTX;
@@ -853,7 +880,11 @@ __global__ void k_brown_z(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
 #pragma unroll
           for (int c = 0; c < 3; ++c) xim[c] = -xim[c];
       }
-      const double kk[3] = {(double)kx, (double)ky, (double)kz};
+      // physical wave vector (the grid's in a cube; (kx, ky - tau kx, kz) in a
+      // Lees-Edwards box, whose window factor stays on the grid index)
+      const double ms = (double)kx * kx + (double)ky * ky + (double)kz * kz;
+      const double kyp = (double)ky - le.tau * (double)kx;
+      const double kk[3] = {(double)kx, kyp, (double)kz};
       const double m = kk[0] * kk[0] + kk[1] * kk[1] + kk[2] * kk[2];
       double pr = 0.0, pi = 0.0;
 #pragma unroll
@@ -861,8 +892,22 @@ __global__ void k_brown_z(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
         pr += kk[c] * xr[c];
         pi += kk[c] * xim[c];
       }
-      const int mi = (int)m;
-      const T bm = btab[2 * mi], bd = btab[2 * mi + 1];
+      T bm, bd;
+      if (le.tau == 0.0) {
+        const int mi = (int)ms;
+        bm = btab[2 * mi];
+        bd = btab[2 * mi + 1];
+      } else {
+        const double k2 = le.ks2 * m;
+        const double H = (1.0 + k2 / (4.0 * le.xi * le.xi)) * exp(-k2 / (4.0 * le.xi * le.xi));
+        const double sc = sqrt(H / (le.eta * k2)) * exp(le.ks2 * ms / (4.0 * le.alpha)) * le.isv;
+        const double z = sqrt(k2) * le.a;
+        const double fm = z < 1e-3 ? 1.0 - z * z / 6.0 + z * z * z * z / 120.0 : sin(z) / z;
+        const double fd = z < 1e-2 ? 1.0 - z * z / 10.0 + z * z * z * z / 280.0
+                                   : 3.0 * (sin(z) - z * cos(z)) / (z * z * z);
+        bm = (T)(sc * fm);
+        bd = (T)(sc * fd);
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const T vr = (T)(xr[c] - kk[c] * pr / m), vi = (T)(xim[c] - kk[c] * pi / m);
@@ -1494,9 +1539,18 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
       le.a = c.a;
       le.eta = c.eta;
       le.inv_n3 = 1.0 / ((double)n * n * n);
+      if (op.green_le_tilt != c.tilt || !op.green_le.p) {
+        // once per box offset (a Lees-Edwards step changes it once)
+        const size_t cnt = (size_t)3 * n * nh * n;
+        if (op.green_le.n < cnt) op.green_le.alloc(cnt);
+        k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(n, le, op.green_le.p);
+        FSD_LAUNCHED(c);
+        FSD_CUDA(cudaGetLastError());
+        op.green_le_tilt = c.tilt;
+      }
     }
     k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p, op.green.p,
-                                                        LTX, le);
+                                                        LTX, le, op.green_le.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
@@ -1519,8 +1573,18 @@ void launch_brownian_wave(Ctx &c, const double *field, uint64_t seed, uint64_t s
     const int TX = 1 << LTX;
     const size_t sm = (size_t)(plan.ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
     set_smem<T>((const void *)k_brown_z<T>, sm);
+    GreenLE le;
+    if (c.tilt != 0.0) {
+      le.tau = c.tilt / c.L;
+      le.ks2 = (2.0 * kPi / c.L) * (2.0 * kPi / c.L);
+      le.xi = c.xi;
+      le.alpha = c.alpha;
+      le.a = c.a;
+      le.eta = c.eta;
+      le.isv = 1.0 / std::sqrt(c.L * c.L * c.L);
+    }
     k_brown_z<T><<<n * ceil_div(nh, TX), 256, sm, c.stream>>>(spec, plan, op.twiddle.p, op.btab.p,
-                                                               field, seed, step, LTX);
+                                                               field, seed, step, LTX, le);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
@@ -1753,7 +1817,8 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, -1.f);
   k_fft_z_green<float><<<n * ((nh + 3) / 4), threads,
                          (ntw + 2 * 6 * 4 * fft_ls(n)) * sizeof(Cx<float>), st>>>(spec, plan, tw,
-                                                                                green, 2, GreenLE());
+                                                                                green, 2, GreenLE(),
+                                                                                nullptr);
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, 1.f);
   k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gout, spec, plan, tw, 4);

@@ -10,6 +10,7 @@ import pytest
 
 import oracle as O
 import synth
+from oracle import brownian_oracle as BO
 from oracle import contact_oracle as C
 
 pytestmark = pytest.mark.gpu
@@ -129,9 +130,27 @@ def test_contact_with_tilt(pkg):
     assert rel(ft, ref) < 1e-12
 
 
-def test_brownian_needs_a_cubic_box(pkg, sysLE):
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-6), (MIXED, 1e-5)])
+def test_brownian_slip_with_tilt(pkg, sysLE, prec, tol):
+    # analytic wave part on the sheared reciprocal lattice + Lanczos square
+    # root of the sheared real-space part, against the dense oracle
     pos, body, L = sysLE
-    s = pkg.Suspension(pos, body, L, tilt=0.2 * L, **HI)
-    with pytest.raises(pkg.FsdError):
-        s.brownian(1.0, 1e-3)
+    tilt = 0.27 * L
+    s = pkg.Suspension(pos, body, L, tilt=tilt, precision=prec, **HI)
+    prm = s.params
+    n, xi = prm["grid"], prm["xi"]
+    rng = np.random.default_rng(17)
+    field = BO.hermitian_field(n, rng)
+    psi_r = rng.normal(size=(len(pos), 11))
+    slip, _, st = s.brownian(1.0, 1.0, wave_field=field, psi_real=psi_r,
+                             psi_nf=np.zeros((len(pos), 6)))
     s.close()
+    unw, X, r = O.body_geometry(pos, body, L, tilt)
+    uw = BO.brownian_wave_slip(unw, L, xi, n, field, tilt=tilt)
+    rc = 2.0 + np.sqrt(46.0) / xi
+    Mr = O.mobility_real_dense(unw, L, xi, rc, tilt=tilt).reshape(11 * len(pos), -1)
+    ur = BO.sqrtm_apply(Mr, psi_r.reshape(-1)).reshape(-1, 11)
+    assert rel(slip / np.sqrt(2.0), uw + ur) < tol
+    # the tilt matters for the sample
+    uw0 = BO.brownian_wave_slip(unw, L, xi, n, field)
+    assert rel(uw0, uw) > 1e-3

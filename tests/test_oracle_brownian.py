@@ -130,3 +130,35 @@ def test_preconditioned_square_root_has_covariance_R():
     n = R.shape[0]
     S = np.column_stack([B.block_precond_sqrt_apply(R, e) for e in np.eye(n)])
     assert np.abs(S @ S.T - R).max() < 1e-9 * np.abs(R).max()
+
+
+def test_wave_sample_covariance_with_tilt():
+    # the same identity in a Lees-Edwards box: the index m of the field
+    # labels the sheared reciprocal vector (2 pi/L)(m1, m2 - tau m1, m3)
+    L, n, xi, tilt = 10.0, 12, 0.15, 3.0
+    pos = np.array([[1.0, 2.0, 3.0], [4.5, 9.5, 6.0]])
+    nh = n // 2 + 1
+    cov = np.zeros((22, 22))
+    for c in range(3):
+        for kz in range(n):
+            for ky in range(n):
+                for kx in range(nh):
+                    if kx == n // 2 or ky == n // 2 or kz == n // 2 or (kx == ky == kz == 0):
+                        continue
+                    mz, my = (n - kz) % n, (n - ky) % n
+                    if kx == 0 and (mz, my) < (kz, ky):
+                        continue
+                    for val in (1.0 / np.sqrt(2.0), 1j / np.sqrt(2.0)):
+                        f = np.zeros((3, n, n, nh), dtype=np.complex128)
+                        f[c, kz, ky, kx] = val
+                        if kx == 0:
+                            f[c, mz, my, 0] = np.conj(val)
+                        u = B.brownian_wave_slip(pos, L, xi, n, f, tilt=tilt).reshape(-1)
+                        cov += np.outer(u, u)
+    kmax = 2.0 * xi * np.sqrt(46.0)
+    # every sheared reciprocal vector inside kmax has indices below Nyquist
+    assert kmax * L / (2 * np.pi) * (1 + tilt / L) < n // 2 - 1
+    Mw = O.mobility_wave_dense(pos, L, xi, kmax, tilt=tilt).reshape(22, 22)
+    assert np.abs(cov - Mw).max() < 1e-10 * np.abs(Mw).max()
+    Mw0 = O.mobility_wave_dense(pos, L, xi, kmax).reshape(22, 22)
+    assert np.abs(Mw0 - Mw).max() > 1e-3 * np.abs(Mw).max()
