@@ -154,3 +154,31 @@ def test_brownian_slip_with_tilt(pkg, sysLE, prec, tol):
     # the tilt matters for the sample
     uw0 = BO.brownian_wave_slip(unw, L, xi, n, field)
     assert rel(uw0, uw) > 1e-3
+
+
+def test_batch_lees_edwards_steps_match_single(pkg, sysLE):
+    pos, body, L = sysLE
+    rng = np.random.default_rng(8)
+    shapes = [synth.random_attachment_aggregate(k, rng) for k in (2, 3, 2)]
+    L2 = 15.0
+    pos2, body2 = synth.pack_suspension(shapes, L2, rng, h_gen=0.05)
+    prm = dict(flags=pkg.FSD_FLAG_LEES_EDWARDS, lub_cutoff=3.0, tilt=0.1 * L, **HI)
+    prm2 = dict(prm, tilt=-0.2 * L2)
+    B = pkg.Batch([(pos, body, L), (pos2, body2, L2)], params=[prm, prm2])
+    rates = np.array([0.6, -0.9])
+    for _ in range(3):
+        B.step(None, rates, 0.02)
+    pb, qb = B.beads()
+    tilts = [B.system(k).params["tilt"] for k in range(2)]
+    B.close()
+    ref_p, ref_t = [], []
+    for (p, b, Lk), kw, g in (((pos, body, L), prm, 0.6), ((pos2, body2, L2), prm2, -0.9)):
+        s = pkg.Suspension(p, b, Lk, **kw)
+        for _ in range(3):
+            s.step(None, g, 0.02)
+        ref_p.append(s.beads()[0])
+        ref_t.append(s.params["tilt"])
+        s.close()
+    assert np.allclose(tilts, ref_t, rtol=0, atol=1e-12)
+    assert abs(ref_t[0] - (0.1 * L + 3 * 0.6 * L * 0.02)) < 1e-12
+    assert np.allclose(pb, np.concatenate(ref_p), rtol=0, atol=1e-9)
