@@ -227,6 +227,57 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ multi-rank helpers
+# One process per GPU; ranks step independent work (replicas of the
+# suspension, or shards of the batched form) with no data-path collective:
+# only the timing is reduced.
+def reduce_max(x):
+    """Max of x over the ranks of the default process group (x alone when
+    there is none)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x):
+    """Sum of x over the ranks of the default process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def weak_value(units_local, seconds_local):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return reduce_sum(units_local) / reduce_max(seconds_local)
+
+
+def shard_by_cost(costs, world):
+    """Independent systems assigned to ranks, most expensive first, each to
+    the least loaded rank (longest processing time first); returns the
+    sorted system indices of every rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 # ------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -257,11 +308,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x)
 
     def timed_steps(s, K, ft=None, vel=None):
         """K steps timed with CUDA events on the library stream."""
@@ -566,12 +613,20 @@ def run_batch(args, rank, world, local_rank):
     import torch
 
     torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
     import paper_2607_25161_gb300 as pkg
     from __graft_entry__ import build
 
     t_gen = time.perf_counter()
-    systems = batch_systems()
+    systems_all = batch_systems()
     t_gen = time.perf_counter() - t_gen
+    # N > 1: each rank advances its share of the independent systems
+    mine = shard_by_cost([len(p) for p, _, _ in systems_all], world)[rank]
+    systems = [systems_all[i] for i in mine]
     build()
     b = BATCH
     nb = sum(len(p) for p, _, _ in systems)
@@ -585,6 +640,8 @@ def run_batch(args, rank, world, local_rank):
         B.step(None, rates, b["dt"])
     clk = ClockSampler(local_rank)
     clk.start()
+    if dist is not None:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     iters = launches = 0
@@ -595,7 +652,9 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     dt_b = time.perf_counter() - t0
     clocks = clk.stop()
-    value = nb * args.steps / dt_b
+    value = weak_value(nb * args.steps, dt_b)
+    dt_b = reduce_max(dt_b)
+    launches = int(reduce_sum(launches))
     # end to end: pinned host forces in and velocities out every step
     ft_h = torch.zeros((B.n_agg, 6), dtype=torch.float64).pin_memory()
     vel_h = torch.zeros((B.n_agg, 6), dtype=torch.float64).pin_memory()
@@ -606,6 +665,7 @@ def run_batch(args, rank, world, local_rank):
         B.step(ft_h, rates, b["dt"], vel=vel_h)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    e2e_value = weak_value(nb * K2, e2e_s)
     # the same systems (same contexts and parameters), one at a time
     views = [B.system(s) for s in range(B.n_sys)]
     K1 = max(2, min(args.steps, 3))
@@ -616,7 +676,7 @@ def run_batch(args, rank, world, local_rank):
             v.step(None, b["shear"], b["dt"])
     torch.cuda.synchronize()
     dt_1 = time.perf_counter() - t0
-    one = nb * K1 / dt_1
+    one = weak_value(nb * K1, dt_1)
     # dominant kernel group of the largest system, profiled alone
     big = int(np.argmax([len(p) for p, _, _ in systems]))
     sv = views[big]
@@ -646,15 +706,20 @@ def run_batch(args, rank, world, local_rank):
     roof["traffic"] = None
     xis = sorted(set(round(p["xi"], 3) for p in B.params))
     B.close()
+    if rank != 0:
+        return
     line = {
         "metric": "bead-steps/sec of 64 independent suspensions advanced together (GMRES 1e-6, mixed)",
-        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt_b / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "batched form: %d suspensions, %d beads (%d..%d per system, log-uniform), "
                                "aggregate sizes 2..64, phi 0.05..0.3, shear 1, lubrication 3a, GMRES 1e-6"
-                               % (B.n_sys, nb, min(len(p) for p, _, _ in systems),
-                                  max(len(p) for p, _, _ in systems)),
+                               % (len(systems_all), sum(len(p) for p, _, _ in systems_all),
+                                  min(len(p) for p, _, _ in systems_all),
+                                  max(len(p) for p, _, _ in systems_all)),
+                   "parallelism": ("systems sharded over %d ranks by bead count (no collective; "
+                                   "rank 0's roofline and statistics)" % world) if world > 1 else "single GPU",
                    "autotune": "xi per system by timing (chosen: %s), real-space tile per system" % xis,
                    "execution": "fsd_step_batch: one CUDA graph per system and step on its own stream, "
                                 "all systems in flight; launch phase on 8 host threads",
@@ -666,7 +731,7 @@ def run_batch(args, rank, world, local_rank):
         "iters_per_system_step": iters / (args.steps * len(systems)),
         "roofline": roof,
         "cpu_baseline": cpu_baseline(3),
-        "e2e": {"value": nb * K2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(ft_h.numel() * 8),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ft_h.numel() * 8),
                 "d2h_bytes_per_step": int(vel_h.numel() * 8), "steps": K2,
                 "api": "fsd_step_batch with pinned host forces in and velocities out"},
         "gpu_launches": launches,
@@ -806,8 +871,7 @@ def main():
         run_profile(args, local_rank)
         return
     if args.workload == "batch":
-        if rank == 0:
-            run_batch(args, rank, world, local_rank)
+        run_batch(args, rank, world, local_rank)
         return
     if args.workload == "rods":
         if rank == 0:
