@@ -105,3 +105,28 @@ def test_fullsize_fp64_and_mixed_solves_agree(big):
         out[prec] = (vel, S)
     assert rel(out[MIXED][0], out[FP64][0]) < 1e-5
     assert rel(out[MIXED][1], out[FP64][1]) < 1e-5
+
+
+def test_fullsize_brownian_wave_sample_linear_and_scaled(big):
+    # properties of u^B = sqrt(2 kT/dt) M_w^(1/2) psi_w at any size: linear in
+    # the random field, scaled by sqrt(kT/dt), zero for a zero field
+    from oracle import brownian_oracle as BO
+
+    pkg, pos, body, L = big["pkg"], big["pos"], big["body"], big["L"]
+    s = pkg.Suspension(pos, body, L, precision=MIXED, **PARAMS)
+    n = s.params["grid"]
+    rng = np.random.default_rng(43)
+    f1 = BO.hermitian_field(n, rng)
+    f2 = BO.hermitian_field(n, rng)
+    z11 = np.zeros((len(pos), 11))
+    z6 = np.zeros((len(pos), 6))
+    u1, _, _ = s.brownian(1.0, 1.0, wave_field=f1, psi_real=z11, psi_nf=z6)
+    u2, _, _ = s.brownian(1.0, 1.0, wave_field=f2, psi_real=z11, psi_nf=z6)
+    u12, _, _ = s.brownian(1.0, 1.0, wave_field=f1 + 0.5 * f2, psi_real=z11, psi_nf=z6)
+    u1s, _, _ = s.brownian(4.0, 0.25, wave_field=f1, psi_real=z11, psi_nf=z6)
+    u0, _, _ = s.brownian(1.0, 1.0, wave_field=0.0 * f1, psi_real=z11, psi_nf=z6)
+    s.close()
+    assert np.abs(u1).max() > 0
+    assert rel(u12, u1 + 0.5 * u2) < 1e-5
+    assert rel(u1s, 4.0 * u1) < 1e-12
+    assert np.all(u0 == 0.0)
