@@ -158,8 +158,34 @@ static const double *dev_in(Ctx &c, const double *p, size_t count, DBuf<double> 
 // ------------------------------------------------------------------ solver
 template <typename T>
 void apply_saddle(Ctx &c, const double *x, double *y) {
-  launch_realspace<T>(c, x, y, true, false);
-  launch_wavespace<T>(c, x, y);
+  if (!c.overlap || c.prof) {
+    launch_realspace<T>(c, x, y, true, false);
+    launch_wavespace<T>(c, x, y);
+  } else {
+    // the real-space sum on the second stream, the wave-space chain into yw
+    // on this one; joined before the sum and the aggregate rows (in a
+    // captured graph these are two parallel branches)
+    const int64_t nb = (int64_t)LDB * c.Nt;
+    FSD_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+    FSD_CUDA(cudaStreamWaitEvent(c.stream2, c.ev_fork, 0));
+    cudaStream_t main = c.stream;
+    c.stream = c.stream2;
+    c.rs_overlapped = true;
+    try {
+      launch_realspace<T>(c, x, y, true, false);
+    } catch (...) {
+      c.stream = main;
+      c.rs_overlapped = false;
+      throw;
+    }
+    c.rs_overlapped = false;
+    FSD_CUDA(cudaEventRecord(c.ev_join, c.stream2));
+    c.stream = main;
+    FSD_CUDA(cudaMemsetAsync(c.yw.p, 0, nb * sizeof(double), c.stream));
+    launch_wavespace<T>(c, x, c.yw.p);
+    FSD_CUDA(cudaStreamWaitEvent(c.stream, c.ev_join, 0));
+    launch_axpy(c, c.yw.p, y, nb);
+  }
   launch_body_rows<T>(c, x, y, true);
 }
 template void apply_saddle<float>(Ctx &, const double *, double *);
@@ -355,6 +381,16 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
     FSD_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
     c.own_stream = true;
   }
+  {
+    const char *e = std::getenv("FSD_OPERATOR_STREAMS");
+    c.overlap = !(e && std::atoi(e) == 1);
+    if (const char *b = std::getenv("FSD_RS_BLOCKS_PER_SM")) c.rs_blocks_per_sm = std::max(0, std::atoi(b));
+    if (c.overlap) {
+      FSD_CUDA(cudaStreamCreateWithFlags(&c.stream2, cudaStreamNonBlocking));
+      FSD_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+      FSD_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+    }
+  }
   // ---- inputs to host
   std::vector<double> pos(3 * (size_t)c.Nt);
   std::vector<int32_t> ids(c.Nt);
@@ -522,6 +558,7 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.op32.lever.alloc(4 * (size_t)Nt);
   c.wpos64.alloc(4 * (size_t)Nt);
   c.wpos32.alloc(4 * (size_t)Nt);
+  if (c.overlap) c.yw.alloc((size_t)LDB * Nt);
   FSD_CUDA(cudaMemcpy(c.body_start.p, c.h_body_start.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice));
   FSD_CUDA(cudaMemcpy(c.bead_body.p, bead_body.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
   FSD_CUDA(cudaMemcpy(c.perm_bead.p, c.h_perm_bead.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
@@ -1493,6 +1530,12 @@ void fsd_destroy(fsd_ctx *ctx) {
   prof_collect(c);
   for (cudaEvent_t e : c.ev_pool) cudaEventDestroy(e);
   c.ev_pool.clear();
+  if (c.stream2) {
+    cudaStreamSynchronize(c.stream2);
+    cudaStreamDestroy(c.stream2);
+  }
+  if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+  if (c.ev_join) cudaEventDestroy(c.ev_join);
   cudaStream_t s = c.stream;
   bool own = c.own_stream;
   delete ctx;

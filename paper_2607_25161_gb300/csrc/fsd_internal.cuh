@@ -145,6 +145,17 @@ struct Ctx {
   // ---- stream
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // second stream: an operator application runs the real-space sum (ALU
+  // bound) on it beside the wave-space chain (L2 / shared-memory bound)
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool overlap = false;        // use it (off while profiling)
+  bool rs_overlapped = false;  // the real-space launch in progress is the overlapped one
+  int rs_blocks_per_sm = 2;    // persistent real-space blocks per SM when overlapped (0: all
+                               // that fit); 2 leaves room for the wave-space kernels beside
+                               // it: measured 84.8 ms per step against 86.2 (all) and 87.0
+                               // (one stream) on the 32768-bead step
+  DBuf<double> yw;             // wave-space part of an overlapped application
   // ---- geometry (internal order: beads grouped by aggregate, aggregates
   //      sorted spatially)
   std::vector<int> h_perm_bead;  // internal bead -> user bead

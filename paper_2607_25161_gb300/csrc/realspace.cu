@@ -816,7 +816,8 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, b
   const T c8 = (T)(1.0 / (8.0 * kPi * c.eta));
 #define FSD_RS_LAUNCH(GG)                                                                    \
   {                                                                                          \
-    const int per_sm = realspace_occupancy<T, GG>(smem, threads);                            \
+    int per_sm = realspace_occupancy<T, GG>(smem, threads);                                  \
+    if (c.rs_overlapped && c.rs_blocks_per_sm > 0) per_sm = std::min(per_sm, c.rs_blocks_per_sm); \
     k_realspace<T, GG><<<std::min<int64_t>(ceil_div((int64_t)c.Nt * GG, threads),             \
                                            (int64_t)std::max(1, per_sm) * c.num_sms),       \
                          threads, smem, c.stream>>>(                                         \
