@@ -10,7 +10,7 @@ FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path is
 reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload step|batch|rods]
+                  [--workload step|batch|rods|seeds]
 
 With N > 1 (torchrun) every rank steps its own replica of the suspension (the
 single-suspension solve does not shard); value = beads x steps x ranks / the
@@ -31,7 +31,11 @@ autotuned splitting.
 --workload rods runs the rod scaling study of Sec. 3.3: Brownian rigid rods
 (8 and 27 beads) with Hertz contact at phi 0.01, 0.05, 0.10 and 8192 / 32768
 beads, xi = 0.5 and xi = 25/L; it reports t_s (wall time per step per bead)
-for every point."""
+for every point.
+
+--workload seeds times the step benchmark's mixed path on five independently
+generated suspensions of the same workload (median and interquartile
+range)."""
 
 import argparse
 import hashlib
@@ -740,6 +744,64 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ seed spread
+SEEDS = (1, 2, 3, 4, 5)
+
+
+def _seed_system(seed):
+    import synth
+
+    w = WORKLOAD
+    return synth.suspension(w["n_agg"], w["n_b"], w["phi"], seed)
+
+
+def run_seeds(args, local_rank):
+    """The step benchmark (mixed, one graph per step) on independently
+    generated suspensions of the same workload: median and interquartile
+    range of bead-steps/s over the seeds."""
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(min(len(SEEDS), os.cpu_count() or 1)) as pool:
+        systems = pool.map(_seed_system, SEEDS)
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import paper_2607_25161_gb300 as pkg
+    from __graft_entry__ import build
+
+    build()
+    w = WORKLOAD
+    stream = torch.cuda.Stream()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    vals, its = [], []
+    for seed, (pos, body, L) in zip(SEEDS, systems):
+        s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED,
+                           xi=w["xi"], lub_cutoff=w["lub"], tol=w["tol"], precond_cutoff=w["rp"],
+                           flags=pkg.FSD_FLAG_COMOVING | pkg.FSD_FLAG_GRAPH)
+        for _ in range(args.warmup):
+            s.step(None, w["shear"], w["dt"])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it = 0
+        for _ in range(args.steps):
+            st, _ = s.step(None, w["shear"], w["dt"])
+            it += st["iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        vals.append(len(pos) * args.steps / (e0.elapsed_time(e1) / 1e3))
+        its.append(it / args.steps)
+    clocks = clk.stop()
+    q1, med, q3 = (float(np.percentile(vals, q)) for q in (25, 50, 75))
+    print(json.dumps({"metric": METRIC, "workload": workload_name(w), "seeds": list(SEEDS),
+                      "values": vals, "iters_per_step": its, "median": med, "iqr": [q1, q3],
+                      "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "clocks": clocks}),
+          flush=True)
+
+
 # ------------------------------------------------------ rod scaling study
 # Sec. 3.3: N Brownian rigid rods of n_b beads in a periodic cube with normal
 # contact between rods; t_s = wall time per step per bead at phi in {0.01,
@@ -856,7 +918,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="step", choices=("step", "batch", "rods"))
+    ap.add_argument("--workload", default="step", choices=("step", "batch", "rods", "seeds"))
     ap.add_argument("--profile-run", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -876,6 +938,10 @@ def main():
     if args.workload == "rods":
         if rank == 0:
             run_rods(args, local_rank)
+        return
+    if args.workload == "seeds":
+        if rank == 0:
+            run_seeds(args, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 
