@@ -385,6 +385,7 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
     const char *e = std::getenv("FSD_OPERATOR_STREAMS");
     c.overlap = !(e && std::atoi(e) == 1);
     if (const char *b = std::getenv("FSD_RS_BLOCKS_PER_SM")) c.rs_blocks_per_sm = std::max(0, std::atoi(b));
+    if (const char *g = std::getenv("FSD_SPREAD_ATOMIC")) c.spread_gather = std::atoi(g) != 1;
     if (c.overlap) {
       FSD_CUDA(cudaStreamCreateWithFlags(&c.stream2, cudaStreamNonBlocking));
       FSD_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
@@ -622,6 +623,7 @@ static void prepare(Ctx &c) {
     c.n_pairs = s;
   }
   build_lubrication(c);
+  if (c.spread_gather && !c.tiles_valid) build_spread_tiles(c);
 }
 
 static void fill_stats(Ctx &c, fsd_stats *st, const KStats &k, double rel, double ms) {

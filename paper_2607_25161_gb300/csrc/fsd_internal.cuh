@@ -156,6 +156,12 @@ struct Ctx {
                                // it: measured 84.8 ms per step against 86.2 (all) and 87.0
                                // (one stream) on the 32768-bead step
   DBuf<double> yw;             // wave-space part of an overlapped application
+  // grid-centric FP32 spreading: the grid in 8^3 tiles, per tile the beads
+  // whose window reaches it (rebuilt when the positions change)
+  bool spread_gather = true;
+  bool tiles_valid = false;
+  int tile_n = 0;                    // tiles per side
+  DBuf<int> tile_count, tile_start, tile_cursor, tile_beads;
   // ---- geometry (internal order: beads grouped by aggregate, aggregates
   //      sorted spatially)
   std::vector<int> h_perm_bead;  // internal bead -> user bead
@@ -276,6 +282,10 @@ template <typename T>
 void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint,
                       bool self_only_real);
 void launch_wrap_positions(Ctx &c);  // pos64 / op*.pos / levers from X, q, rbody
+__global__ void k_exclusive_scan(int n, const int *__restrict__ in, int *out, int *cursor);
+__global__ void k_sort_cells(int ncells, const int *__restrict__ cell_start, int *cell_beads);
+// wavespace.cu: per-tile bead lists of the grid-centric spreading
+void build_spread_tiles(Ctx &c);
 int realspace_group(const Ctx &c);   // lanes per bead of the pair sum
 
 // wavespace.cu

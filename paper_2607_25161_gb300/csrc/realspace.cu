@@ -227,6 +227,7 @@ __global__ void k_wrap_positions(int Nt, double L, double tilt, const int *__res
 }
 
 void launch_wrap_positions(Ctx &c) {
+  c.tiles_valid = false;  // the spreading tiles follow the positions
   k_wrap_positions<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(
       c.Nt, c.L, c.tilt, c.bead_body.p, c.X.p, c.q.p, c.rbody.p, (double4 *)c.pos64.p,
       (double4 *)c.lever64.p, (float4 *)c.op32.pos.p, (float4 *)c.op32.lever.p,

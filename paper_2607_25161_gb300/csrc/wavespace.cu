@@ -1289,6 +1289,161 @@ __global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restr
   yr[10] += s2 * 0.5 * (G12 + G21);
 }
 
+// ------------------------------------------- grid-centric FP32 spreading
+// The same sums as k_spread_v4, organised by grid point instead of by bead:
+// the grid is cut into 8^3 tiles and each tile keeps the list of beads whose
+// P^3 window reaches it (built once per geometry).  One block of 64 threads
+// per tile, one thread per (y, z) row of the tile summing, in registers, the
+// contributions of the tile's beads to its 8 points: no atomics, and every
+// grid point is written exactly once (no zeroing pass).
+constexpr int kTS = 8;      // tile side
+constexpr int kTCH = 32;    // beads per shared-memory chunk
+
+// distinct tiles (per axis) covered by the window of a bead at coordinate p
+__device__ __forceinline__ int window_tiles(float p, float h, int P, int n, int t[5]) {
+  const int g0 = (int)floorf(p / h) - P / 2 + 1;
+  int cnt = 0;
+  for (int k = 0; k < P; ++k) {
+    const int g = ((g0 + k) % n + n) % n;
+    const int tt = g / kTS;
+    bool seen = false;
+    for (int q = 0; q < cnt; ++q) seen |= t[q] == tt;
+    if (!seen && cnt < 5) t[cnt++] = tt;
+  }
+  return cnt;
+}
+
+template <bool FILL>
+__global__ void k_tile_bin(int Nt, const float4 *__restrict__ pos, float h, int P, int n, int nt,
+                           int *count_or_cursor, int *tile_beads, int64_t cap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const float4 p = pos[i];
+  int tx[5], ty[5], tz[5];
+  const int cx = window_tiles(p.x, h, P, n, tx), cy = window_tiles(p.y, h, P, n, ty),
+            cz = window_tiles(p.z, h, P, n, tz);
+  for (int a = 0; a < cz; ++a)
+    for (int b = 0; b < cy; ++b)
+      for (int d = 0; d < cx; ++d) {
+        const int id = (tz[a] * nt + ty[b]) * nt + tx[d];
+        const int slot = atomicAdd(&count_or_cursor[id], 1);
+        if (FILL && slot < cap) tile_beads[slot] = i;
+      }
+}
+
+__global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, float h, float alpha,
+                                                      float cnorm, float tau,
+                                                      const float4 *__restrict__ pos,
+                                                      const double *__restrict__ x,
+                                                      const int *__restrict__ tile_start,
+                                                      const int *__restrict__ tile_beads,
+                                                      float *grid) {
+  __shared__ float sw[kTCH][3][kTS], sy[kTCH][3][kTS];
+  __shared__ float sm[kTCH][12];
+  const int tile = blockIdx.x;
+  const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
+  const int x0 = tx * kTS, y0 = ty * kTS, z0 = tz * kTS;
+  const int iy = threadIdx.x & 7, iz = threadIdx.x >> 3;
+  float acc[6][kTS];
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int k = 0; k < kTS; ++k) acc[c][k] = 0.f;
+  const int b0 = tile_start[tile], b1 = tile_start[tile + 1];
+  const float ta = 2.f * alpha;
+  for (int cb = b0; cb < b1; cb += kTCH) {
+    const int nc = min(kTCH, b1 - cb);
+    __syncthreads();
+    // 1D window factors and offsets of each bead at this tile's coordinates
+    for (int e = threadIdx.x; e < nc * 3 * kTS; e += blockDim.x) {
+      const int bi = e / (3 * kTS), r = e - bi * 3 * kTS, d = r / kTS, k = r - d * kTS;
+      const float4 p = pos[tile_beads[cb + bi]];
+      const float pc = d == 0 ? p.x : (d == 1 ? p.y : p.z);
+      const int g0 = (int)floorf(pc / h) - P / 2 + 1;
+      const int gt = (d == 0 ? x0 : (d == 1 ? y0 : z0)) + k;
+      float w = 0.f, yv = 0.f;
+      if (gt < n) {
+        const int off = ((gt - g0) % n + n) % n;  // slot of this grid index in the window
+        if (off < P) {
+          yv = float(g0 + off) * h - pc;
+          w = expf(-alpha * yv * yv);
+        }
+      }
+      sw[bi][d][k] = w;
+      sy[bi][d][k] = yv;
+    }
+    // moments: F and the dipole D (= S + antisym(L); column 0 takes -tau
+    // column 1 in a Lees-Edwards box), with the window norm and 2 alpha
+    for (int bi = threadIdx.x; bi < nc; bi += blockDim.x) {
+      const double *xr = x + (size_t)tile_beads[cb + bi] * LDB;
+      const float F0 = (float)xr[0], F1 = (float)xr[1], F2 = (float)xr[2];
+      const float L0 = (float)xr[3], L1 = (float)xr[4], L2 = (float)xr[5];
+      const float r2i = 0.70710678118654752440f, r6i = 0.40824829046386301637f;
+      const float s0 = (float)xr[6], s1 = (float)xr[7], s2 = (float)xr[8], s3 = (float)xr[9],
+                  s4 = (float)xr[10];
+      const float Sxx = r2i * s0 - r6i * s1, Syy = -r2i * s0 - r6i * s1, Szz = 2.f * r6i * s1;
+      const float Sxy = r2i * s2, Sxz = r2i * s3, Syz = r2i * s4;
+      const float D01 = Sxy - 0.5f * L2, D11 = Syy, D21 = Syz + 0.5f * L0;
+      const float D00 = Sxx - tau * D01, D02 = Sxz + 0.5f * L1;
+      const float D10 = Sxy + 0.5f * L2 - tau * D11, D12 = Syz - 0.5f * L0;
+      const float D20 = Sxz - 0.5f * L1 - tau * D21, D22 = Szz;
+      const float cd = ta * cnorm;
+      float *m = sm[bi];
+      m[0] = cnorm * F0;
+      m[1] = cnorm * F1;
+      m[2] = cnorm * F2;
+      m[3] = cd * D00;
+      m[4] = cd * D01;
+      m[5] = cd * D02;
+      m[6] = cd * D10;
+      m[7] = cd * D11;
+      m[8] = cd * D12;
+      m[9] = cd * D20;
+      m[10] = cd * D21;
+      m[11] = cd * D22;
+    }
+    __syncthreads();
+    for (int bi = 0; bi < nc; ++bi) {
+      const float wyz = sw[bi][1][iy] * sw[bi][2][iz];
+      if (wyz == 0.f) continue;
+      const float yy = sy[bi][1][iy], yz = sy[bi][2][iz];
+      const float *m = sm[bi];
+      const float f0 = m[0] * wyz, f1 = m[1] * wyz, f2 = m[2] * wyz;
+      const float a0 = m[3] * wyz, a1 = m[6] * wyz, a2 = m[9] * wyz;
+      const float c0 = (m[4] * yy + m[5] * yz) * wyz, c1 = (m[7] * yy + m[8] * yz) * wyz,
+                  c2 = (m[10] * yy + m[11] * yz) * wyz;
+#pragma unroll
+      for (int k = 0; k < kTS; ++k) {
+        const float wx = sw[bi][0][k], yx = sy[bi][0][k];
+        acc[0][k] += f0 * wx;
+        acc[1][k] += f1 * wx;
+        acc[2][k] += f2 * wx;
+        acc[3][k] += wx * (a0 * yx + c0);
+        acc[4][k] += wx * (a1 * yx + c1);
+        acc[5][k] += wx * (a2 * yx + c2);
+      }
+    }
+  }
+  const int yg = y0 + iy, zg = z0 + iz;
+  if (yg >= n || zg >= n) return;
+  const int64_t n3 = (int64_t)n * n * n;
+  float *row = grid + ((int64_t)zg * n + yg) * n + x0;
+  if (x0 + kTS <= n && (n & 3) == 0) {  // 16-byte aligned rows
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float4 *r4 = (float4 *)(row + c * n3);
+      r4[0] = make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+      r4[1] = make_float4(acc[c][4], acc[c][5], acc[c][6], acc[c][7]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int k = 0; k < kTS; ++k)
+        if (x0 + k < n) row[c * n3 + k] = acc[c][k];
+  }
+}
+
 // ------------------------------------------------------------ host side
 
 static double j0h(double z) {
@@ -1468,6 +1623,40 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
 }
 
 
+// Per-tile bead lists of the grid-centric spreading, from the FP32
+// wave-space positions: count, scan, fill, then each list sorted (a fixed
+// summation order).  Device-only (no host round trip).
+void build_spread_tiles(Ctx &c) {
+  const int n = c.n, nt = ceil_div(n, kTS);
+  const int ntiles = nt * nt * nt;
+  // a window of P consecutive grid indices meets at most ceil(P/8) + 1
+  // aligned tiles, one more when it wraps past a partial last tile
+  const int per_axis = ceil_div(c.P, kTS) + 2;
+  const size_t cap = (size_t)c.Nt * per_axis * per_axis * per_axis;
+  if (c.tile_n != nt || !c.tile_count.p) {
+    c.tile_n = nt;
+    c.tile_count.alloc(ntiles);
+    c.tile_start.alloc(ntiles + 1);
+    c.tile_cursor.alloc(ntiles);
+  }
+  if (c.tile_beads.n < cap) c.tile_beads.alloc(cap);
+  const float h = (float)c.h;
+  FSD_CUDA(cudaMemsetAsync(c.tile_count.p, 0, ntiles * sizeof(int), c.stream));
+  k_tile_bin<false><<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p, h, c.P, n,
+                                                              nt, c.tile_count.p, nullptr, 0);
+  FSD_LAUNCHED(c);
+  k_exclusive_scan<<<1, 1024, 0, c.stream>>>(ntiles, c.tile_count.p, c.tile_start.p, c.tile_cursor.p);
+  FSD_LAUNCHED(c);
+  k_tile_bin<true><<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p, h, c.P, n,
+                                                             nt, c.tile_cursor.p, c.tile_beads.p,
+                                                             (int64_t)c.tile_beads.n);
+  FSD_LAUNCHED(c);
+  k_sort_cells<<<ceil_div(ntiles, 128), 128, 0, c.stream>>>(ntiles, c.tile_start.p, c.tile_beads.p);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+  c.tiles_valid = true;
+}
+
 template <typename T>
 void launch_wavespace(Ctx &c, const double *x, double *y) {
   OpData<T> &op = opd<T>(c);
@@ -1477,6 +1666,14 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const size_t gbytes = (size_t)6 * n * n * n * sizeof(T);
   {
   ProfScope ps(c, PG_SPREAD);
+  if (sizeof(T) == 4 && c.spread_gather) {
+    if (!c.tiles_valid) build_spread_tiles(c);
+    const int nt = c.tile_n;
+    k_spread_gather<<<nt * nt * nt, 64, 0, c.stream>>>(n, nt, P, (float)h, (float)alpha, (float)cn,
+                                                       (float)(c.tilt / c.L), (const float4 *)c.wpos32.p,
+                                                       x, c.tile_start.p, c.tile_beads.p,
+                                                       (float *)op.grid.p);
+  } else {
   FSD_CUDA(cudaMemsetAsync(op.grid.p, 0, gbytes, c.stream));
   if (sizeof(T) == 4 && n % 4 == 0)
     k_spread_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p, x,
@@ -1486,6 +1683,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   else
     k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
                                                         alpha, (T)cn, (T)(c.tilt / c.L));
+  }
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   }
