@@ -1363,7 +1363,10 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
       const int gt = (d == 0 ? x0 : (d == 1 ? y0 : z0)) + k;
       float w = 0.f, yv = 0.f;
       if (gt < n) {
-        const int off = ((gt - g0) % n + n) % n;  // slot of this grid index in the window
+        // slot of this grid index in the window (g0 is within one box of gt)
+        int off = gt - g0;
+        if (off < 0) off += n;
+        if (off >= n) off -= n;
         if (off < P) {
           yv = float(g0 + off) * h - pc;
           w = expf(-alpha * yv * yv);
