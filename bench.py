@@ -142,8 +142,9 @@ def group_work(group, s, prm, st, prec_bytes=4):
     if group == "realspace":
         return "alu", st["n_pairs"] * FLOP_PER_PAIR, "TFLOP/s"
     if group == "spread":
-        # zero + write the six density grids, read bead moments and positions
-        return "hbm", 2 * 6 * G * w + Nt * (12 * 8 + 4 * w), "GB/s"
+        # write the six density grids once (the grid-centric kernel needs no
+        # zeroing pass), read bead moments and positions
+        return "hbm", 6 * n ** 3 * w + Nt * (12 * 8 + 4 * w), "GB/s"
     if group == "fft_green":
         # one forward and one inverse 3D transform of six real grids, each
         # reading and writing every grid value once
