@@ -689,6 +689,8 @@ def run_batch(args, rank, world, local_rank):
     e2e_value = weak_value(nb * K2, e2e_s)
     # the same systems (same contexts and parameters), one at a time
     views = [B.system(s) for s in range(B.n_sys)]
+    for v in views:  # untimed: each view captures its own step graph first
+        v.step(None, b["shear"], b["dt"])
     K1 = max(2, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
