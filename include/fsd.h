@@ -101,6 +101,18 @@ enum {
                               offset changes every step) */
 };
 
+/* Environment (read when a context is set up; defaults in brackets):
+ *   FSD_OPERATOR_STREAMS=1   run an operator application on one stream
+ *                            [2: the real-space sum beside the wave-space
+ *                            chain on a second stream]
+ *   FSD_RS_BLOCKS_PER_SM=k   persistent real-space blocks per SM while
+ *                            overlapped [2; 0: as many as fit]
+ *   FSD_SPREAD_ATOMIC=1      FP32 spreading by vector atomic adds per bead
+ *                            [grid-centric gather by 8^3 tiles]
+ *   FSD_BATCH_THREADS=k      host threads of the batched launch phase [8]
+ * Each choice changes speed only, not the arithmetic's result beyond the
+ * order of FP32 sums. */
+
 typedef struct {
   double a;              /* bead radius (1)                                        */
   double eta;            /* viscosity (1)                                          */
