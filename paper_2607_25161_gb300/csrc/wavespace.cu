@@ -1193,7 +1193,7 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
 // sums of k_interp, with each lane reading an aligned quad of four x points
 // of one grid row per field (six 16-byte loads); slots outside the bead's x
 // window carry weight 0 (the quads of k_spread_v4).
-__global__ void __launch_bounds__(256) k_interp_v4(int Nt, const float4 *__restrict__ pos,
+__global__ void __launch_bounds__(256, 4) k_interp_v4(int Nt, const float4 *__restrict__ pos,
                                                    const float *__restrict__ field, double *y, int n,
                                                    int P, float h, float alpha, float cnorm_h3,
                                                    double tau) {
