@@ -37,10 +37,13 @@ Readings (paper silent or garbled):
 Pins (tests/test_oracle_drift.py): the displacement is a rigid motion whose
 first-order part is h (v_t + v_w x r); the RFD summed over the basis vectors
 of dq equals the divergence of the body mobility from central differences
-with exact (Rodrigues) rotations; the Fixman drift summed over the basis
-vectors of the Brownian noise equals that same divergence (which holds only
-if the Brownian velocity has covariance 2 kT/dt times the body mobility, so
-it also pins the Brownian sampling); translation invariance of a lone body.
+with exact (Rodrigues) rotations, velocity and stresslet; a lone body has no
+translational drift; the Fixman drift at large m is (dt/2) times the
+derivative of the Brownian solve along U0 (exact-rotation central
+differences), velocity and stresslet.  The Fixman drift summed over the
+Brownian noise's basis vectors does not reproduce the divergence for this
+formulation (the slip, not the aggregate force, is held fixed at x'); that
+is a property of the scheme as printed, measured, not pinned.
 """
 
 import numpy as np
@@ -49,11 +52,12 @@ from . import brownian_oracle as B
 from . import fsd_oracle as F
 
 
-def displaced(pos, body, L, v, h):
+def displaced(pos, body, L, v, h, tilt=0.0):
     """Bead positions of the rigid configuration moved by h v (see the
-    reading in the module docstring); positions are returned unwrapped."""
+    reading in the module docstring); positions are returned unwrapped.
+    tilt: the Lees-Edwards offset of the box (0: cubic)."""
     body = np.asarray(body)
-    unw, X, r = F.body_geometry(pos, body, L)
+    unw, X, r = F.body_geometry(pos, body, L, tilt)
     v = np.asarray(v, dtype=np.float64).reshape(-1, 6)
     q = np.concatenate([np.ones((len(v), 1)), 0.5 * h * v[:, 3:6]], axis=1)
     q /= np.linalg.norm(q, axis=1, keepdims=True)
@@ -62,14 +66,15 @@ def displaced(pos, body, L, v, h):
     return Xn[body] + np.einsum("bij,bj->bi", R[body], r)
 
 
-def rfd(pos, body, L, dq, eps, kT=1.0, rlub=3.0, a=1.0, eta=1.0, hmin=1e-3):
+def rfd(pos, body, L, dq, eps, kT=1.0, rlub=3.0, a=1.0, eta=1.0, hmin=1e-3, tilt=0.0):
     """(U_drift [N][6], S^B [N][3][3], (out+, out-)) by random finite
     differences with the given dq."""
     dq = np.asarray(dq, dtype=np.float64).reshape(-1, 6)
     outs = []
     for s in (1.0, -1.0):
-        p = displaced(pos, body, L, dq, 0.5 * s * eps)
-        outs.append(F.solve(p, body, L, gamma=0.0, FT=dq, a=a, eta=eta, rlub=rlub, hmin=hmin))
+        p = displaced(pos, body, L, dq, 0.5 * s * eps, tilt)
+        outs.append(F.solve(p, body, L, gamma=0.0, FT=dq, a=a, eta=eta, rlub=rlub, hmin=hmin,
+                            tilt=tilt))
     up, um = outs
     return kT * (up["U"] - um["U"]) / eps, kT * (up["SH"] - um["SH"]) / eps, outs
 

@@ -69,3 +69,20 @@ def test_contact_across_the_boundary_and_invalid(pkg):
     with pytest.raises(pkg.FsdError):
         s.contact(-1.0)
     s.close()
+
+
+def test_contact_full_size_rods_balance(pkg):
+    # the 8-bead rod workload at phi 0.1 squeezed by 2 %: many contacts;
+    # central pair forces sum to zero, and the torques about the origin of
+    # the unwrapped bodies with them
+    import oracle as O
+
+    pos, body, L = synth.rod_suspension(4096, 8, 0.10, seed=7)
+    c = O.body_geometry(pos, body, L)[1]
+    pos = pos + (0.98 - 1.0) * c[body]  # move the centroids inward, rigidly
+    s = pkg.Suspension(pos, body, L * 0.98, xi=0.5)
+    ft = s.contact(1e4)
+    s.close()
+    assert np.count_nonzero(np.abs(ft).sum(axis=1)) > 10
+    scale = np.abs(ft[:, :3]).max()
+    assert np.abs(ft[:, :3].sum(axis=0)).max() < 1e-9 * scale * len(ft)

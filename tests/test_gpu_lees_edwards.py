@@ -182,3 +182,20 @@ def test_batch_lees_edwards_steps_match_single(pkg, sysLE):
     assert np.allclose(tilts, ref_t, rtol=0, atol=1e-12)
     assert abs(ref_t[0] - (0.1 * L + 3 * 0.6 * L * 0.02)) < 1e-12
     assert np.allclose(pb, np.concatenate(ref_p), rtol=0, atol=1e-9)
+
+
+def test_rfd_drift_with_tilt(pkg, sysLE):
+    # random finite differences in the sheared box: the displaced
+    # configurations are wrapped with the sheared images on both sides
+    from oracle import drift_oracle as DO
+
+    pos, body, L = sysLE
+    tilt = 0.33 * L
+    dq = np.random.default_rng(21).normal(size=(body.max() + 1, 6))
+    ref, refS, _ = DO.rfd(pos, body, L, dq, 0.05, kT=0.7, rlub=3.0, tilt=tilt)
+    s = pkg.Suspension(pos, body, L, tilt=tilt, lub_cutoff=3.0, **HI)
+    drift, _, SB, _, status = s.drift(pkg.FSD_DRIFT_RFD, 0.7, param=0.05, dq=dq)
+    s.close()
+    assert status == pkg.FSD_OK
+    assert rel(drift, ref) < 1e-5
+    assert rel(SB, refS) < 1e-5
