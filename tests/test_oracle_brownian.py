@@ -162,3 +162,32 @@ def test_wave_sample_covariance_with_tilt():
     assert np.abs(cov - Mw).max() < 1e-10 * np.abs(Mw).max()
     Mw0 = O.mobility_wave_dense(pos, L, xi, kmax).reshape(22, 22)
     assert np.abs(Mw0 - Mw).max() > 1e-3 * np.abs(Mw).max()
+
+
+def test_pairwise_near_field_sampler_has_covariance_R():
+    # the map from the pair noises to the force is linear: summing the outer
+    # products of its columns gives the covariance, which must be R_FU^nf
+    import synth
+
+    rng = np.random.default_rng(8)
+    shapes = [synth.random_attachment_aggregate(k, rng) for k in (2, 3, 2, 3)]
+    L = synth.box_for_phi(10, 0.15)
+    pos, body = synth.pack_suspension(shapes, L, rng, h_gen=0.05)
+    R = O.split_grand(O.lubrication_dense(pos, body, L, rcut=3.0), len(pos))[0]
+    assert np.abs(R).max() > 0
+    pairs = [(i, j) for i in range(len(pos)) for j in range(i + 1, len(pos))
+             if body[i] != body[j]
+             and np.linalg.norm(O.min_image(pos[j] - pos[i], L)) < 3.0]
+    cov = np.zeros_like(R)
+    for p in pairs:
+        for k in range(12):
+            col = B.pairwise_nf_apply(pos, body, L, lambda i, j: np.eye(12)[k] if (i, j) == p else np.zeros(12))
+            cov += np.outer(col.reshape(-1), col.reshape(-1))
+    assert np.abs(cov - R).max() < 1e-10 * np.abs(R).max()
+
+
+def test_pair_normals_layout():
+    z = B.pair_normals(11, 3, 2, 9)
+    assert z.shape == (12,)
+    assert np.allclose(z[:4], B.box_muller4(B.philox4x32_10((2, 5 << 8, 9, 3), (11, 0))))
+    assert not np.allclose(B.pair_normals(11, 3, 2, 9), B.pair_normals(11, 3, 9, 2))
