@@ -466,6 +466,29 @@ def run_ours(args, rank, world, local_rank):
             "iters_first_last": [its_le[0], its_le[-1]], "tilt_end": tilt_end,
             "note": "Lees-Edwards box (sheared images), full velocity, host-driven steps"}
 
+    # ---- the same Brownian step with the pairwise near-field sampler
+    s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED,
+                       **dict(common, nf_sampler=pkg.FSD_NF_PAIRWISE))
+    for k in range(min(args.warmup, 3)):
+        s.brownian(1.0, w["dt"], seed=11, step=k, outputs=False)
+        s.step(None, w["shear"], w["dt"])
+    barrier()
+    torch.cuda.synchronize()
+    ep0 = torch.cuda.Event(enable_timing=True)
+    ep1 = torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    for k in range(args.steps):
+        s.brownian(1.0, w["dt"], seed=11, step=1000 + k, outputs=False)
+        s.step(None, w["shear"], w["dt"])
+    ep1.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    msp = max_over_ranks(ep0.elapsed_time(ep1))
+    brown["pairwise_near_field"] = {
+        "value": Nt * args.steps * world / (msp / 1e3), "ms_per_step": msp / args.steps,
+        "note": "near-field force by the pairwise decomposition sum_p R_p^(1/2) psi_p "
+                "(exact covariance, no Lanczos)"}
+
     # ---- Brownian step with the drift (Sec. 2.4; appendix on the drift):
     #      fsd_brownian, fsd_drift (two solves at displaced configurations),
     #      then the step's solve: three solves per step either way

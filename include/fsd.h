@@ -60,6 +60,9 @@ typedef enum {
   FSD_ETIMEOUT = 7  /* a bounded device wait gave up                    */
 } fsd_status;
 
+/* Near-field Brownian samplers (fsd_params.nf_sampler). */
+enum { FSD_NF_LANCZOS = 0, FSD_NF_PAIRWISE = 1 };
+
 /* Precision of the operator applications inside the solve. */
 enum { FSD_FP64 = 0, FSD_MIXED = 1 };
 
@@ -157,6 +160,11 @@ typedef struct {
                             modulo L into [-L/2, L/2) (0: the cube).  With a
                             non-zero tilt (or FSD_FLAG_LEES_EDWARDS) R_c and
                             the lubrication cut-off must stay below 0.447 L    */
+  int nf_sampler;        /* fsd_brownian's near-field force: FSD_NF_LANCZOS (0,
+                            the paper's preconditioned Lanczos) or
+                            FSD_NF_PAIRWISE (sum over lubrication pairs of
+                            R_p^(1/2) psi_p: exact covariance R_FU^nf, no
+                            iteration; pair noise from Philox stream 5)        */
 } fsd_params;
 
 typedef struct {
@@ -353,6 +361,11 @@ void fsd_destroy_batch(fsd_batch *b);
  *     Gaussians, Hermitian in the kx = 0 plane; Nyquist points and k = 0 are
  *     ignored;
  *   psi_real [n_beads][11], psi_nf [n_beads][6]: standard normals.
+ * With nf_sampler = FSD_NF_PAIRWISE the near-field force is
+ * sum_p R_p^(1/2) psi_p over the lubrication pairs p = (i < j, input order),
+ * R_p the pair's 12x12 block of R_FU^nf, psi_p 12 normals from Philox with
+ * counter (i, 5 * 256 + call, j, step mod 2^32), calls 0..2; psi_nf must then
+ * be NULL.
  * Outputs (NULL to skip): slip [n_beads][11] = u^B, force_nf [n_beads][6] =
  * F^B.  stats: iters = real-space Lanczos steps, outer_iters = near-field
  * Lanczos steps (each stops when its coefficients change by less than

@@ -21,6 +21,7 @@ FSD_FLAG_GRAPH = 4
 FSD_FLAG_AUTOTUNE = 8
 FSD_FLAG_LEES_EDWARDS = 16
 FSD_DRIFT_RFD, FSD_DRIFT_FIXMAN = 0, 1
+FSD_NF_LANCZOS, FSD_NF_PAIRWISE = 0, 1
 STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",
                 5: "FSD_ENUMERIC", 6: "FSD_EOVERLAP", 7: "FSD_ETIMEOUT"}
 
@@ -47,7 +48,7 @@ class FsdParams(ctypes.Structure):
         ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_restart", ctypes.c_int),
         ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int), ("tile", ctypes.c_int),
         ("lanczos_tol", ctypes.c_double), ("lanczos_max_iter", ctypes.c_int),
-        ("tilt", ctypes.c_double),
+        ("tilt", ctypes.c_double), ("nf_sampler", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -531,6 +531,8 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-7;
   c.prm.lanczos_tol = p.lanczos_tol > 0 ? p.lanczos_tol : 1e-7;
   c.prm.lanczos_max_iter = p.lanczos_max_iter > 0 ? std::max(p.lanczos_max_iter, 2) : 60;
+  if (p.nf_sampler != FSD_NF_LANCZOS && p.nf_sampler != FSD_NF_PAIRWISE)
+    throw Invalid{"nf_sampler must be FSD_NF_LANCZOS or FSD_NF_PAIRWISE"};
   if (p.tile != 0 && p.tile != 4 && p.tile != 8 && p.tile != 16 && p.tile != 32)
     throw Invalid{"tile must be 0, 4, 8, 16 or 32"};
   c.prm.xi = c.xi;

@@ -345,7 +345,12 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
   vec_axpby(c, c.bslip.p, 1.0, c.t2.p, 1.0, n);
   // near-field part: F^B = R_FU^(1/2) psi_nf (Lanczos on the bead-level blocks)
   int inf = 0;
-  if (c.n_lub > 0) {
+  if (c.n_lub > 0 && c.prm.nf_sampler == FSD_NF_PAIRWISE) {
+    // exact in distribution, no Krylov iteration: sum over pairs of
+    // R_p^(1/2) psi_p (the pair noise drawn here, Philox stream 5)
+    if (psi_nf_dev) throw Invalid{"the pairwise near-field sampler draws its own pair noise: psi_nf must be NULL"};
+    launch_nf_pairwise(c, seed, step, c.bfnf.p);
+  } else if (c.n_lub > 0) {
     FSD_CUDA(cudaMemsetAsync(c.bwork.p, 0, n * sizeof(double), c.stream));
     if (psi_nf_dev)
       k_psi_in<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(c.Nt, c.perm_bead.p, psi_nf_dev, 6, c.bwork.p);

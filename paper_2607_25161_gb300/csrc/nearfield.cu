@@ -607,6 +607,122 @@ __global__ void k_contact_body(int N, const int *__restrict__ body_start,
   for (int k = 0; k < 6; ++k) ft[6 * (size_t)J + k] = o[k];
 }
 
+// --------------------------------------- pairwise near-field Brownian force
+// The near-field resistance is a sum of pair blocks, R_FU^nf = sum_p R_p
+// (R_p: 12x12 on the velocities of the pair's two beads), so
+// F = sum_p R_p^(1/2) psi_p with independent 12-vectors psi_p has covariance
+// exactly R_FU^nf.  Thread per bead; each pair is taken once, by its bead of
+// smaller input index; R_p^(1/2) from a cyclic Jacobi eigendecomposition in
+// FP64 whose rotation updates both mirrored entries from the same values
+// (the matrix stays exactly symmetric); the pair noise from Philox with
+// counter (i, 5 * 256 + call, j, step mod 2^32) in input order.
+__device__ void sym_sqrt_apply12(double *A, const double *x, double *y) {
+  constexpr int m = 12;
+  double V[m * m];
+  for (int e = 0; e < m * m; ++e) V[e] = (e / m == e % m) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) (i == j ? dg : off) += A[i * m + j] * A[i * m + j];
+    if (off <= 1e-30 * dg || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p * m + q];
+        if (apq == 0.0) continue;
+        const double th = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        const double app = A[p * m + p] - t * apq, aqq = A[q * m + q] + t * apq;
+        for (int r = 0; r < m; ++r) {
+          if (r == p || r == q) continue;
+          const double arp = A[r * m + p], arq = A[r * m + q];
+          const double np_ = cs * arp - sn * arq, nq = sn * arp + cs * arq;
+          A[r * m + p] = np_;
+          A[p * m + r] = np_;
+          A[r * m + q] = nq;
+          A[q * m + r] = nq;
+        }
+        A[p * m + p] = app;
+        A[q * m + q] = aqq;
+        A[p * m + q] = 0.0;
+        A[q * m + p] = 0.0;
+        for (int k = 0; k < m; ++k) {
+          const double vp = V[k * m + p], vq = V[k * m + q];
+          V[k * m + p] = cs * vp - sn * vq;
+          V[k * m + q] = sn * vp + cs * vq;
+        }
+      }
+  }
+  // y = V diag(sqrt(max(lambda, 0))) V^T x
+  double c[m];
+  for (int k = 0; k < m; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += V[i * m + k] * x[i];
+    c[k] = s * sqrt(fmax(A[k * m + k], 0.0));
+  }
+  for (int i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += V[i * m + k] * c[k];
+    y[i] = s;
+  }
+}
+
+__global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int *__restrict__ lnbr,
+                              const int *__restrict__ lcnt, int lcap, const int *__restrict__ perm,
+                              double L, double tilt, double a, double eta, double rcut, double hmin,
+                              uint64_t seed, uint64_t step, double *f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt) return;
+  const int iu = perm[i];
+  const double4 pi = pos[i];
+  const int cnt = lcnt[i];
+  for (int k = 0; k < cnt; ++k) {
+    const int j = lnbr[(size_t)i * lcap + k];
+    const int ju = perm[j];
+    if (ju < iu) continue;  // the pair belongs to its bead of smaller input index
+    const double4 pj = pos[j];
+    double d0 = pj.x - pi.x, d1 = pj.y - pi.y, d2 = pj.z - pi.z;
+    min_image(d0, d1, d2, L, tilt);
+    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    const double n[3] = {d0 / r, d1 / r, d2 / r}, nm[3] = {-n[0], -n[1], -n[2]};
+    const PairCoef pc = lub_coef(r, a, eta, rcut, hmin);
+    double Rii[36], Rij[36], Rjj[36], Rji[36];
+    pair_blocks(n, r, pc, Rii, Rij);
+    pair_blocks(nm, r, pc, Rjj, Rji);
+    double M[144];
+    for (int a_ = 0; a_ < 6; ++a_)
+      for (int b = 0; b < 6; ++b) {
+        M[a_ * 12 + b] = Rii[6 * a_ + b];
+        M[a_ * 12 + 6 + b] = Rij[6 * a_ + b];
+        M[(6 + a_) * 12 + b] = Rji[6 * a_ + b];
+        M[(6 + a_) * 12 + 6 + b] = Rjj[6 * a_ + b];
+      }
+    double psi[12];
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int call = 0; call < 3; ++call) {
+      uint32_t cw[4] = {(uint32_t)iu, (5u << 8) | (uint32_t)call, (uint32_t)ju, (uint32_t)step};
+      philox4x32_10(cw, k0, k1);
+      const double sc = 2.3283064365386963e-10;  // 2^-32
+      const double u0 = ((double)cw[0] + 1.0) * sc, u1 = ((double)cw[1] + 1.0) * sc;
+      const double u2 = ((double)cw[2] + 1.0) * sc, u3 = ((double)cw[3] + 1.0) * sc;
+      const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+      double s0, c0, s1, c1;
+      sincospi(2.0 * u1, &s0, &c0);
+      sincospi(2.0 * u3, &s1, &c1);
+      psi[4 * call] = r0 * c0;
+      psi[4 * call + 1] = r0 * s0;
+      psi[4 * call + 2] = r1 * c1;
+      psi[4 * call + 3] = r1 * s1;
+    }
+    double v[12];
+    sym_sqrt_apply12(M, psi, v);
+    for (int e = 0; e < 6; ++e) {
+      atomicAdd(&f[(size_t)i * LDB + e], v[e]);
+      atomicAdd(&f[(size_t)j * LDB + e], v[6 + e]);
+    }
+  }
+}
+
 // ============================================================ host side
 
 static void strain6(double shear, double *e) {
@@ -771,6 +887,15 @@ void launch_contact(Ctx &c, double kn, double *fb_scratch, double *ft_int) {
   FSD_LAUNCHED(c);
   k_contact_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
                                                           (const double4 *)c.lever64.p, fb_scratch, ft_int);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void launch_nf_pairwise(Ctx &c, uint64_t seed, uint64_t step, double *f) {
+  FSD_CUDA(cudaMemsetAsync(f, 0, (size_t)c.nunk * sizeof(double), c.stream));
+  k_nf_pairwise<<<ceil_div(c.Nt, 64), 64, 0, c.stream>>>(
+      c.Nt, (const double4 *)c.pos64.p, c.lnbr.p, c.lcnt.p, c.lcap, c.perm_bead.p, c.L, c.tilt, c.a,
+      c.eta, c.prm.lub_cutoff, c.prm.lub_hmin, seed, step, f);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }

@@ -177,3 +177,20 @@ def test_wave_sample_on_a_grid_too_large_for_the_fused_fft(pkg):
         out.append(slip)
     assert np.abs(out[0]).max() > 0
     assert rel(out[1], out[0]) < 1e-5
+
+
+def test_pairwise_near_field_sampler_matches_oracle(pkg, sysB):
+    # nf_sampler = FSD_NF_PAIRWISE: sum over lubrication pairs of
+    # R_p^(1/2) psi_p with Philox pair noise, against the oracle's sampler
+    d = sysB
+    seed, step = 77, 5
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], nf_sampler=pkg.FSD_NF_PAIRWISE, **HI)
+    slip, fnf, st = s.brownian(1.0, 1.0, seed=seed, step=step, psi_real=np.zeros_like(d["psi_r"]))
+    with pytest.raises(pkg.FsdError):
+        s.brownian(1.0, 1.0, psi_nf=d["psi_nf"])  # the pair noise is drawn, not given
+    s.close()
+    unw, X, r = O.body_geometry(d["pos"], d["body"], d["L"])
+    ref = BO.pairwise_nf_force(unw, d["body"], d["L"], seed, step, rlub=3.0)
+    assert np.abs(ref).max() > 0
+    assert st["outer_iters"] == 0  # no near-field Lanczos steps
+    assert rel(fnf / np.sqrt(2.0), ref) < 1e-8
