@@ -163,8 +163,9 @@ typedef struct {
   int nf_sampler;        /* fsd_brownian's near-field force: FSD_NF_LANCZOS (0,
                             the paper's preconditioned Lanczos) or
                             FSD_NF_PAIRWISE (sum over lubrication pairs of
-                            R_p^(1/2) psi_p: exact covariance R_FU^nf, no
-                            iteration; pair noise from Philox stream 5)        */
+                            K_p^T psi_p, K_p the pair's dissipation-form
+                            factor: exact covariance R_FU^nf, no iteration;
+                            pair noise from Philox stream 5)                  */
 } fsd_params;
 
 typedef struct {
@@ -362,10 +363,11 @@ void fsd_destroy_batch(fsd_batch *b);
  *     ignored;
  *   psi_real [n_beads][11], psi_nf [n_beads][6]: standard normals.
  * With nf_sampler = FSD_NF_PAIRWISE the near-field force is
- * sum_p R_p^(1/2) psi_p over the lubrication pairs p = (i < j, input order),
- * R_p the pair's 12x12 block of R_FU^nf, psi_p 12 normals from Philox with
- * counter (i, 5 * 256 + call, j, step mod 2^32), calls 0..2; psi_nf must then
- * be NULL.
+ * sum_p K_p^T psi_p over the lubrication pairs p = (i < j, input order),
+ * K_p (6 x 12) the pair's dissipation-form factor (K_p^T K_p = the pair's
+ * 12x12 block of R_FU^nf), psi_p 6 normals from Philox with counter
+ * (i, 5 * 256 + call, j, step mod 2^32), calls 0 and 1; psi_nf must then be
+ * NULL.
  * Outputs (NULL to skip): slip [n_beads][11] = u^B, force_nf [n_beads][6] =
  * F^B.  stats: iters = real-space Lanczos steps, outer_iters = near-field
  * Lanczos steps (each stops when its coefficients change by less than

@@ -27,8 +27,9 @@ Algorithm 1 step 3):
   for any invertible G (pinned); R_FU^nf is the bead-level near-field
   resistance;
 * alternatively (a sampler this build adds beside the paper's Lanczos one),
-  the near-field force by the pairwise decomposition R_FU^nf = sum_p R_p of
-  the pair model: F^B_nf = sqrt(2 kT/dt) sum_p R_p^(1/2) psi_p, psi_p 12
+  the near-field force by the pairwise decomposition of the pair model's
+  dissipation form, R_FU^nf = sum_p K_p^T K_p with K_p = [G^(1/2) Ls;
+  Gt^(1/2) Lt] (6 x 12): F^B_nf = sqrt(2 kT/dt) sum_p K_p^T psi_p, psi_p 6
   independent normals per pair; its covariance is exactly R_FU^nf (pinned);
 * the saddle-point right-hand side with them (Eq. spm_agg): bead rows + u^B,
   body rows - Sigma F^B_nf.
@@ -55,7 +56,8 @@ Box-Muller transform, with this counter layout:
     stream 3: psi_nf, index = bead (input order), calls 0..1 give 8 normals,
               the first 6 used;
     stream 5 (pairwise near-field sampler): counter (i, 5 * 256 + call, j,
-              step mod 2^32) for the pair i < j, calls 0..2, 12 normals.
+              step mod 2^32) for the pair i < j, calls 0 and 1, the first 6
+              of 8 normals.
     Box-Muller on one output (x0, x1, x2, x3): u_j = (x_j + 1) 2^-32,
     (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), (z2, z3) likewise
     from (u2, u3).
@@ -217,25 +219,26 @@ def block_precond_sqrt_apply(R, v, bs=6):
 
 
 def pair_normals(seed, step, i, j):
-    """12 standard normals of the bead pair (i < j, input order) for the
+    """6 standard normals of the bead pair (i < j, input order) for the
     pairwise near-field sampler: Philox4x32-10 with key = seed and counter
-    (i, 5 * 256 + call, j, step mod 2^32), calls 0..2, Box-Muller."""
+    (i, 5 * 256 + call, j, step mod 2^32), calls 0 and 1 (the first 6 of 8),
+    Box-Muller."""
     key = (seed & M32, (seed >> 32) & M32)
     out = []
-    for call in range(3):
+    for call in range(2):
         out += box_muller4(philox4x32_10((i & M32, (5 << 8) | call, j & M32, step & M32), key))
-    return np.array(out)
+    return np.array(out[:6])
 
 
 def pairwise_nf_apply(pos, body, L, psi_of_pair, rlub=3.0, a=1.0, eta=1.0, hmin=1e-3, tilt=0.0):
-    """sum over inter-body pairs p = (i < j), r < rlub, of R_p^(1/2) psi_p,
-    R_p the pair's 12 x 12 block of R_FU^nf on the velocities of i and j and
-    psi_p = psi_of_pair(i, j) (12 values); (N_tot, 6)."""
+    """sum over inter-body pairs p = (i < j), r < rlub, of K_p^T psi_p, K_p
+    (6 x 12) the pair's dissipation-form factor (K_p^T K_p = the pair's
+    12 x 12 block of R_FU^nf on the velocities of i and j) and
+    psi_p = psi_of_pair(i, j) (6 values); (N_tot, 6)."""
     pos = np.asarray(pos, dtype=np.float64)
     body = np.asarray(body)
     Nt = len(pos)
     out = np.zeros((Nt, 6))
-    idx = np.r_[0:6, 11:17]
     for i in range(Nt):
         for j in range(i + 1, Nt):
             if body[i] == body[j]:
@@ -243,8 +246,8 @@ def pairwise_nf_apply(pos, body, L, psi_of_pair, rlub=3.0, a=1.0, eta=1.0, hmin=
             d = F.min_image(pos[j] - pos[i], L, tilt)
             if np.linalg.norm(d) >= rlub:
                 continue
-            Rp = F.lub_pair_matrix(np.zeros(3), d, a, eta, rlub, hmin)[np.ix_(idx, idx)]
-            v = sqrtm_apply(Rp, np.asarray(psi_of_pair(i, j), dtype=np.float64))
+            K = F.lub_pair_factor(np.zeros(3), d, a, eta, rlub, hmin)
+            v = K.T @ np.asarray(psi_of_pair(i, j), dtype=np.float64)
             out[i] += v[:6]
             out[j] += v[6:]
     return out
@@ -252,7 +255,7 @@ def pairwise_nf_apply(pos, body, L, psi_of_pair, rlub=3.0, a=1.0, eta=1.0, hmin=
 
 def pairwise_nf_force(pos, body, L, seed, step, rlub=3.0, a=1.0, eta=1.0, hmin=1e-3, tilt=0.0):
     """Near-field Brownian force (unscaled) by the pairwise decomposition
-    R_FU^nf = sum_p R_p: F = sum_p R_p^(1/2) psi_p with independent
+    R_FU^nf = sum_p K_p^T K_p: F = sum_p K_p^T psi_p with independent
     psi_p (pair_normals), whose covariance is exactly R_FU^nf."""
     return pairwise_nf_apply(pos, body, L, lambda i, j: pair_normals(seed, step, i, j), rlub, a, eta,
                              hmin, tilt)

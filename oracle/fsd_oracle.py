@@ -541,6 +541,30 @@ def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     return Ls.T @ G @ Ls + Lt.T @ Gt @ Lt
 
 
+def lub_pair_factor(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
+    """K (6 x 12) with K^T K = the FU block of lub_pair_matrix (velocities
+    and rotations of i, then of j): the dissipation form's own factor,
+    K = [G^(1/2) Ls; Gt^(1/2) Lt] restricted to the velocity columns, with
+    G^(1/2) = sqrt(A) nn + sqrt(B) (I - nn), Gt^(1/2) = sqrt(D) (I - nn)."""
+    x = xj - xi
+    r = np.linalg.norm(x)
+    n = x / r
+    A, B, D = lub_coefficients(r - 2 * a, a, eta, rcut, hmin)
+    nn = np.outer(n, n)
+    Gh = np.sqrt(A) * nn + np.sqrt(B) * (I3 - nn)
+    Gth = np.sqrt(D) * (I3 - nn)
+    nx = np.einsum("abc,b->ac", EPS, n)
+    Ls = np.zeros((3, 12))
+    Ls[:, 0:3] = I3
+    Ls[:, 3:6] = -0.5 * r * nx
+    Ls[:, 6:9] = -I3
+    Ls[:, 9:12] = -0.5 * r * nx
+    Lt = np.zeros((3, 12))
+    Lt[:, 3:6] = -I3
+    Lt[:, 9:12] = I3
+    return np.vstack([Gh @ Ls, Gth @ Lt])
+
+
 def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, tilt=0.0):
     """Bead-level grand near-field resistance (11 Nt x 11 Nt), per bead
     ordering (6 velocity, 5 strain), summed over inter-body pairs with

@@ -608,65 +608,17 @@ __global__ void k_contact_body(int N, const int *__restrict__ body_start,
 }
 
 // --------------------------------------- pairwise near-field Brownian force
-// The near-field resistance is a sum of pair blocks, R_FU^nf = sum_p R_p
-// (R_p: 12x12 on the velocities of the pair's two beads), so
-// F = sum_p R_p^(1/2) psi_p with independent 12-vectors psi_p has covariance
-// exactly R_FU^nf.  Thread per bead; each pair is taken once, by its bead of
-// smaller input index; R_p^(1/2) from a cyclic Jacobi eigendecomposition in
-// FP64 whose rotation updates both mirrored entries from the same values
-// (the matrix stays exactly symmetric); the pair noise from Philox with
+// The near-field resistance is a sum over pairs of the pair model's
+// dissipation form, R_FU^nf = sum_p K_p^T K_p with
+// K_p = [G^(1/2) Ls; Gt^(1/2) Lt] (6 x 12): s = (du_j - du_i) +
+// (r/2) n x (dw_i + dw_j) and t = dw_i - dw_j are the pair's relative surface
+// velocity and rotation, G = A nn + B (I - nn), Gt = D (I - nn).  So
+// F = sum_p K_p^T eta_p with 6 independent normals per pair has covariance
+// exactly R_FU^nf: with g_s = G^(1/2) eta_s and g_t = Gt^(1/2) eta_t,
+// force_i = g_s, torque_i = (r/2) n x g_s - g_t, force_j = -g_s,
+// torque_j = (r/2) n x g_s + g_t.  Thread per bead; each pair is taken once,
+// by its bead of smaller input index; the pair noise from Philox with
 // counter (i, 5 * 256 + call, j, step mod 2^32) in input order.
-__device__ void sym_sqrt_apply12(double *A, const double *x, double *y) {
-  constexpr int m = 12;
-  double V[m * m];
-  for (int e = 0; e < m * m; ++e) V[e] = (e / m == e % m) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, dg = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) (i == j ? dg : off) += A[i * m + j] * A[i * m + j];
-    if (off <= 1e-30 * dg || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = A[p * m + q];
-        if (apq == 0.0) continue;
-        const double th = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
-        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
-        const double app = A[p * m + p] - t * apq, aqq = A[q * m + q] + t * apq;
-        for (int r = 0; r < m; ++r) {
-          if (r == p || r == q) continue;
-          const double arp = A[r * m + p], arq = A[r * m + q];
-          const double np_ = cs * arp - sn * arq, nq = sn * arp + cs * arq;
-          A[r * m + p] = np_;
-          A[p * m + r] = np_;
-          A[r * m + q] = nq;
-          A[q * m + r] = nq;
-        }
-        A[p * m + p] = app;
-        A[q * m + q] = aqq;
-        A[p * m + q] = 0.0;
-        A[q * m + p] = 0.0;
-        for (int k = 0; k < m; ++k) {
-          const double vp = V[k * m + p], vq = V[k * m + q];
-          V[k * m + p] = cs * vp - sn * vq;
-          V[k * m + q] = sn * vp + cs * vq;
-        }
-      }
-  }
-  // y = V diag(sqrt(max(lambda, 0))) V^T x
-  double c[m];
-  for (int k = 0; k < m; ++k) {
-    double s = 0.0;
-    for (int i = 0; i < m; ++i) s += V[i * m + k] * x[i];
-    c[k] = s * sqrt(fmax(A[k * m + k], 0.0));
-  }
-  for (int i = 0; i < m; ++i) {
-    double s = 0.0;
-    for (int k = 0; k < m; ++k) s += V[i * m + k] * c[k];
-    y[i] = s;
-  }
-}
-
 __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int *__restrict__ lnbr,
                               const int *__restrict__ lcnt, int lcap, const int *__restrict__ perm,
                               double L, double tilt, double a, double eta, double rcut, double hmin,
@@ -676,6 +628,7 @@ __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int
   const int iu = perm[i];
   const double4 pi = pos[i];
   const int cnt = lcnt[i];
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int k = 0; k < cnt; ++k) {
     const int j = lnbr[(size_t)i * lcap + k];
     const int ju = perm[j];
@@ -684,22 +637,10 @@ __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int
     double d0 = pj.x - pi.x, d1 = pj.y - pi.y, d2 = pj.z - pi.z;
     min_image(d0, d1, d2, L, tilt);
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    const double n[3] = {d0 / r, d1 / r, d2 / r}, nm[3] = {-n[0], -n[1], -n[2]};
+    const double n[3] = {d0 / r, d1 / r, d2 / r};
     const PairCoef pc = lub_coef(r, a, eta, rcut, hmin);
-    double Rii[36], Rij[36], Rjj[36], Rji[36];
-    pair_blocks(n, r, pc, Rii, Rij);
-    pair_blocks(nm, r, pc, Rjj, Rji);
-    double M[144];
-    for (int a_ = 0; a_ < 6; ++a_)
-      for (int b = 0; b < 6; ++b) {
-        M[a_ * 12 + b] = Rii[6 * a_ + b];
-        M[a_ * 12 + 6 + b] = Rij[6 * a_ + b];
-        M[(6 + a_) * 12 + b] = Rji[6 * a_ + b];
-        M[(6 + a_) * 12 + 6 + b] = Rjj[6 * a_ + b];
-      }
-    double psi[12];
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int call = 0; call < 3; ++call) {
+    double z[8];
+    for (int call = 0; call < 2; ++call) {
       uint32_t cw[4] = {(uint32_t)iu, (5u << 8) | (uint32_t)call, (uint32_t)ju, (uint32_t)step};
       philox4x32_10(cw, k0, k1);
       const double sc = 2.3283064365386963e-10;  // 2^-32
@@ -709,16 +650,27 @@ __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int
       double s0, c0, s1, c1;
       sincospi(2.0 * u1, &s0, &c0);
       sincospi(2.0 * u3, &s1, &c1);
-      psi[4 * call] = r0 * c0;
-      psi[4 * call + 1] = r0 * s0;
-      psi[4 * call + 2] = r1 * c1;
-      psi[4 * call + 3] = r1 * s1;
+      z[4 * call] = r0 * c0;
+      z[4 * call + 1] = r0 * s0;
+      z[4 * call + 2] = r1 * c1;
+      z[4 * call + 3] = r1 * s1;
     }
-    double v[12];
-    sym_sqrt_apply12(M, psi, v);
-    for (int e = 0; e < 6; ++e) {
-      atomicAdd(&f[(size_t)i * LDB + e], v[e]);
-      atomicAdd(&f[(size_t)j * LDB + e], v[6 + e]);
+    const double sA = sqrt(pc.A), sB = sqrt(pc.B), sD = sqrt(pc.D);
+    const double ns = n[0] * z[0] + n[1] * z[1] + n[2] * z[2];
+    const double nt = n[0] * z[3] + n[1] * z[4] + n[2] * z[5];
+    double gs[3], gt[3];
+    for (int e = 0; e < 3; ++e) {
+      gs[e] = sA * ns * n[e] + sB * (z[e] - ns * n[e]);
+      gt[e] = sD * (z[3 + e] - nt * n[e]);
+    }
+    const double h = 0.5 * r;
+    const double cx[3] = {h * (n[1] * gs[2] - n[2] * gs[1]), h * (n[2] * gs[0] - n[0] * gs[2]),
+                          h * (n[0] * gs[1] - n[1] * gs[0])};
+    for (int e = 0; e < 3; ++e) {
+      atomicAdd(&f[(size_t)i * LDB + e], gs[e]);
+      atomicAdd(&f[(size_t)i * LDB + 3 + e], cx[e] - gt[e]);
+      atomicAdd(&f[(size_t)j * LDB + e], -gs[e]);
+      atomicAdd(&f[(size_t)j * LDB + 3 + e], cx[e] + gt[e]);
     }
   }
 }

@@ -180,8 +180,9 @@ def test_wave_sample_on_a_grid_too_large_for_the_fused_fft(pkg):
 
 
 def test_pairwise_near_field_sampler_matches_oracle(pkg, sysB):
-    # nf_sampler = FSD_NF_PAIRWISE: sum over lubrication pairs of
-    # R_p^(1/2) psi_p with Philox pair noise, against the oracle's sampler
+    # nf_sampler = FSD_NF_PAIRWISE: sum over lubrication pairs of K_p^T psi_p
+    # (the pair's dissipation-form factor) with Philox pair noise, against
+    # the oracle's sampler
     d = sysB
     seed, step = 77, 5
     s = pkg.Suspension(d["pos"], d["body"], d["L"], nf_sampler=pkg.FSD_NF_PAIRWISE, **HI)
@@ -193,4 +194,4 @@ def test_pairwise_near_field_sampler_matches_oracle(pkg, sysB):
     ref = BO.pairwise_nf_force(unw, d["body"], d["L"], seed, step, rlub=3.0)
     assert np.abs(ref).max() > 0
     assert st["outer_iters"] == 0  # no near-field Lanczos steps
-    assert rel(fnf / np.sqrt(2.0), ref) < 1e-8
+    assert rel(fnf / np.sqrt(2.0), ref) < 1e-12

@@ -180,14 +180,20 @@ def test_pairwise_near_field_sampler_has_covariance_R():
              and np.linalg.norm(O.min_image(pos[j] - pos[i], L)) < 3.0]
     cov = np.zeros_like(R)
     for p in pairs:
-        for k in range(12):
-            col = B.pairwise_nf_apply(pos, body, L, lambda i, j: np.eye(12)[k] if (i, j) == p else np.zeros(12))
+        for k in range(6):
+            col = B.pairwise_nf_apply(pos, body, L, lambda i, j: np.eye(6)[k] if (i, j) == p else np.zeros(6))
             cov += np.outer(col.reshape(-1), col.reshape(-1))
     assert np.abs(cov - R).max() < 1e-10 * np.abs(R).max()
+    # and the factor of each pair reproduces that pair's block
+    d = O.min_image(pos[pairs[0][1]] - pos[pairs[0][0]], L)
+    K = O.lub_pair_factor(np.zeros(3), d)
+    idx = np.r_[0:6, 11:17]
+    Rp = O.lub_pair_matrix(np.zeros(3), d)[np.ix_(idx, idx)]
+    assert np.abs(K.T @ K - Rp).max() < 1e-12 * np.abs(Rp).max()
 
 
 def test_pair_normals_layout():
     z = B.pair_normals(11, 3, 2, 9)
-    assert z.shape == (12,)
+    assert z.shape == (6,)
     assert np.allclose(z[:4], B.box_muller4(B.philox4x32_10((2, 5 << 8, 9, 3), (11, 0))))
     assert not np.allclose(B.pair_normals(11, 3, 2, 9), B.pair_normals(11, 3, 9, 2))
