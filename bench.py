@@ -486,8 +486,8 @@ def run_ours(args, rank, world, local_rank):
     msp = max_over_ranks(ep0.elapsed_time(ep1))
     brown["pairwise_near_field"] = {
         "value": Nt * args.steps * world / (msp / 1e3), "ms_per_step": msp / args.steps,
-        "note": "near-field force by the pairwise decomposition sum_p R_p^(1/2) psi_p "
-                "(exact covariance, no Lanczos)"}
+        "note": "near-field force by the pairwise decomposition sum_p K_p^T psi_p, K_p the pair "
+                "model's dissipation-form factor (exact covariance, no Lanczos)"}
 
     # ---- Brownian step with the drift (Sec. 2.4; appendix on the drift):
     #      fsd_brownian, fsd_drift (two solves at displaced configurations),
