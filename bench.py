@@ -10,7 +10,7 @@ FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path is
 reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload step|batch|rods|seeds]
+                  [--workload step|batch|rods|seeds|oracle-ladder]
 
 With N > 1 (torchrun) every rank steps its own replica of the suspension (the
 single-suspension solve does not shard); value = beads x steps x ranks / the
@@ -35,7 +35,8 @@ for every point.
 
 --workload seeds times the step benchmark's mixed path on five independently
 generated suspensions of the same workload (median and interquartile
-range)."""
+range); --workload oracle-ladder times the CPU oracle on 32, 128 and 512
+beads (no GPU)."""
 
 import argparse
 import hashlib
@@ -786,6 +787,29 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- oracle ladder
+def run_oracle_ladder(args):
+    """The CPU oracle (dense FP64 Ewald mobility + LAPACK) on 8-bead
+    aggregate suspensions of 32, 128 and 512 beads at phi 0.1 (the
+    512-aggregate workload's generator): seconds per solve, bead-steps/s,
+    and the power law t ~ N^p fitted through the ladder.  CPU only."""
+    import oracle as O
+    import synth
+
+    pts = []
+    for n_agg in (4, 16, 64):
+        pos, body, L = synth.suspension(n_agg, 8, 0.1, 1)
+        t = time.perf_counter()
+        O.solve(pos, body, L, gamma=1.0, rlub=3.0)
+        dt = time.perf_counter() - t
+        pts.append({"beads": len(pos), "seconds": round(dt, 3), "bead_steps_per_s": len(pos) / dt})
+    x = np.log([q["beads"] for q in pts])
+    y = np.log([q["seconds"] for q in pts])
+    p = float(np.polyfit(x, y, 1)[0])
+    print(json.dumps({"impl": "reference", "workload": "oracle ladder, 8-bead aggregates, phi 0.1",
+                      "points": pts, "cost_exponent": p, "cores": os.cpu_count()}), flush=True)
+
+
 # ------------------------------------------------------------ seed spread
 SEEDS = (1, 2, 3, 4, 5)
 
@@ -960,7 +984,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="step", choices=("step", "batch", "rods", "seeds"))
+    ap.add_argument("--workload", default="step",
+                    choices=("step", "batch", "rods", "seeds", "oracle-ladder"))
     ap.add_argument("--profile-run", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -970,6 +995,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "oracle-ladder":
+        if rank == 0:
+            run_oracle_ladder(args)
         return
     if args.profile_run:
         run_profile(args, local_rank)
