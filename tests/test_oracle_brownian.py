@@ -15,7 +15,11 @@ Eq. UBff):
 * a near-field Brownian force enters the body rows exactly like an applied
   aggregate force and torque (the same Sigma projection, the same sign);
 * Box-Muller normals from Philox have zero mean, unit variance, no
-  correlation between components.
+  correlation between components;
+* fluctuation-dissipation: over an orthonormal basis of all the noise the
+  Brownian body velocities have covariance (2 kT/dt) N, N the body
+  mobility (only with the strain rows of u^B);
+* the pairwise near-field sampler has covariance R_FU^nf.
 """
 
 import numpy as np
@@ -197,3 +201,53 @@ def test_pair_normals_layout():
     assert z.shape == (6,)
     assert np.allclose(z[:4], B.box_muller4(B.philox4x32_10((2, 5 << 8, 9, 3), (11, 0))))
     assert not np.allclose(B.pair_normals(11, 3, 2, 9), B.pair_normals(11, 3, 9, 2))
+
+
+def test_brownian_velocity_covariance_is_the_body_mobility():
+    # fluctuation-dissipation: with u^B = s M^(1/2) psi (all 11 components,
+    # reading r24) and F^B = s R^(1/2) psi_nf, s^2 = 2 kT/dt, the body
+    # velocities of the Brownian solve have covariance s^2 N, N the body
+    # mobility (the solve's response to unit aggregate forces and torques).
+    # Summed over an orthonormal basis of the noise the identity is exact.
+    import synth
+
+    rng = np.random.default_rng(3)
+    shapes = [synth.random_attachment_aggregate(k, rng) for k in (2, 3, 4, 2, 3)]
+    L = synth.box_for_phi(14, 0.15)
+    pos, body = synth.pack_suspension(shapes, L, rng, h_gen=0.05)
+    unw, X, r = O.body_geometry(pos, body, L)
+    Nt, nb = len(pos), 5
+    M = O.mobility_dense(unw, L)
+    R = O.split_grand(O.lubrication_dense(unw, body, L, rcut=3.0), Nt)[0]
+    assert np.abs(R).max() > 0  # near pairs: the near-field noise matters
+    kT, dt = 0.8, 0.05
+    s = np.sqrt(2.0 * kT / dt)
+    Mh = np.linalg.cholesky(M)  # any square root gives the same covariance
+    w, V = np.linalg.eigh(R)
+    Rh = V @ np.diag(np.sqrt(np.clip(w, 0, None)))
+    cov = np.zeros((6 * nb, 6 * nb))
+    for k in range(11 * Nt + 6 * Nt):
+        if k < 11 * Nt:
+            uB, fB = s * Mh[:, k].reshape(Nt, 11), np.zeros((Nt, 6))
+        else:
+            uB, fB = np.zeros((Nt, 11)), s * Rh[:, k - 11 * Nt].reshape(Nt, 6)
+        u = B.solve_brownian(pos, body, L, uB, fB, gamma=0.0, rlub=3.0, M=M)["U"].reshape(-1)
+        cov += np.outer(u, u)
+    Nm = np.column_stack([O.solve(pos, body, L, gamma=0.0, FT=np.eye(6 * nb)[j].reshape(nb, 6),
+                                  rlub=3.0, M=M)["U"].reshape(-1) for j in range(6 * nb)])
+    assert np.abs(Nm - Nm.T).max() < 1e-10 * np.abs(Nm).max()
+    assert np.abs(cov - s * s * Nm).max() < 1e-9 * np.abs(s * s * Nm).max()
+    # without the strain rows of u^B the far-field part of the identity
+    # fails (reading r24)
+    covf = np.zeros_like(cov)
+    covf6 = np.zeros_like(cov)
+    for k in range(11 * Nt):
+        uB = s * Mh[:, k].reshape(Nt, 11)
+        uB6 = uB.copy()
+        uB6[:, 6:] = 0.0
+        z6 = np.zeros((Nt, 6))
+        u = B.solve_brownian(pos, body, L, uB, z6, gamma=0.0, rlub=3.0, M=M)["U"].reshape(-1)
+        u6 = B.solve_brownian(pos, body, L, uB6, z6, gamma=0.0, rlub=3.0, M=M)["U"].reshape(-1)
+        covf += np.outer(u, u)
+        covf6 += np.outer(u6, u6)
+    assert np.abs(covf6 - covf).max() > 1e-3 * np.abs(covf).max()
