@@ -12,7 +12,9 @@ Eq. rfd and the modified Fixman scheme):
   box, so the translational RFD vanishes;
 * Fixman: for large m, (m/2)(U' - U0) is (dt/2) times the derivative of the
   Brownian solve along U0, again from central differences with exact
-  rotations; the stresslet likewise with the sign the paper prints.
+  rotations; the stresslet likewise with the sign the paper prints;
+* the RFD identity holds in a Lees-Edwards box too, where the drift differs
+  from the cubic box's.
 """
 
 import numpy as np
@@ -33,10 +35,10 @@ def rodrigues(w):
     return np.eye(3) + np.sin(th) * K + (1.0 - np.cos(th)) * K @ K
 
 
-def moved_exact(pos, body, L, v, h):
+def moved_exact(pos, body, L, v, h, tilt=0.0):
     """Rigid motion by translation h v_t and the exact rotation by the angle
     h |v_w| about v_w, per body."""
-    unw, X, r = O.body_geometry(pos, body, L)
+    unw, X, r = O.body_geometry(pos, body, L, tilt)
     v = np.asarray(v).reshape(-1, 6)
     new = unw.copy()
     for J in range(len(v)):
@@ -121,3 +123,25 @@ def test_fixman_large_m_is_the_directional_derivative(doublets):
     # O(dt |U0| / m) from the finite step, O(h^2) from the differences
     assert np.linalg.norm(drift - dU) < 1e-4 * np.linalg.norm(dU)
     assert np.linalg.norm(SB - dS) < 1e-4 * np.linalg.norm(dS)
+
+
+def test_rfd_in_the_sheared_box():
+    # the same identity in a Lees-Edwards box: the displaced configurations
+    # and the solves take the sheared images
+    pos, body, L = synth.config_doublets(2, 9.0, seed=6)
+    tilt = 0.3 * L
+    n6, h, eps, kT = 12, 1e-4, 1e-4, 1.0
+    div = np.zeros(n6)
+    rs = np.zeros(n6)
+    for i in range(n6):
+        e = np.eye(n6)[i].reshape(-1, 6)
+        op = O.solve(moved_exact(pos, body, L, e, h, tilt), body, L, gamma=0.0, FT=e, rlub=3.0, tilt=tilt)
+        om = O.solve(moved_exact(pos, body, L, e, -h, tilt), body, L, gamma=0.0, FT=e, rlub=3.0, tilt=tilt)
+        div += (op["U"] - om["U"]).reshape(-1) / (2 * h)
+        rs += D.rfd(pos, body, L, e, eps, kT=kT, rlub=3.0, tilt=tilt)[0].reshape(-1)
+    assert np.linalg.norm(rs - div) < 1e-6 * np.linalg.norm(div)
+    div0 = np.zeros(n6)
+    for i in range(n6):
+        e = np.eye(n6)[i].reshape(-1, 6)
+        div0 += D.rfd(pos, body, L, e, eps, kT=kT, rlub=3.0)[0].reshape(-1)
+    assert np.linalg.norm(div0 - div) > 1e-3 * np.linalg.norm(div)
