@@ -347,7 +347,8 @@ void brownian_sample(Ctx &c, double kT, double dt, uint64_t seed, uint64_t step,
   int inf = 0;
   if (c.n_lub > 0 && c.prm.nf_sampler == FSD_NF_PAIRWISE) {
     // exact in distribution, no Krylov iteration: sum over pairs of
-    // R_p^(1/2) psi_p (the pair noise drawn here, Philox stream 5)
+    // K_p^T psi_p, K_p the pair's dissipation-form factor (the pair noise
+    // drawn here, Philox stream 5)
     if (psi_nf_dev) throw Invalid{"the pairwise near-field sampler draws its own pair noise: psi_nf must be NULL"};
     launch_nf_pairwise(c, seed, step, c.bfnf.p);
   } else if (c.n_lub > 0) {
