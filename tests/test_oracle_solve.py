@@ -260,3 +260,65 @@ def test_sampled_lubrication_rows_equal_dense():
     bodies = [0, 3, 11]
     got = O.lubrication_rows(pos, body, L, bodies, dU)
     assert np.allclose(got, dense[bodies], rtol=0, atol=1e-12 * np.abs(dense).max())
+
+
+# ------------------------------------------------ reciprocity and the strain columns
+
+
+def test_aggregate_reciprocity_of_velocity_and_stresslet():
+    """Lorentz reciprocity of the aggregate grand mobility (Sec. 2.1 grand
+    resistance convention, Eq. FH_agg, Eq. stress_comp a and d).  Eliminating
+    F from (F; S) = R (U_inf - U; E) gives U - U_inf = R_FU^-1 (F^P + R_FE E)
+    and S = -R_SU R_FU^-1 F^P + ..., with R_SU = R_FE^T, so the disturbance
+    velocity per unit shear rate of body J equals minus the derivative of the
+    suspension's total S_xy (hydrodynamic plus constraint parts) with respect
+    to the applied force and torque on J.  Lubricated multi-bead bodies make
+    both the lever-arm (constraint) stresslet and the near-field strain terms
+    enter."""
+    pos, body, L = synth.suspension(6, 3, 0.2, 11)
+    body = np.asarray(body)
+    nb = int(body.max()) + 1
+    unw = O.body_geometry(pos, body, L)[0]
+    assert np.abs(O.lubrication_dense(unw, body, L, rcut=3.0)).max() > 0.0  # near pairs present
+    M = O.mobility_dense(unw, L)
+    out = O.solve(pos, body, L, gamma=1.0, FT=np.zeros((nb, 6)), rlub=3.0, M=M)
+    A = out["dU"]
+    Bm = np.zeros((nb, 6))
+    for J in range(nb):
+        for k in range(6):
+            FT = np.zeros((nb, 6))
+            FT[J, k] = 1.0
+            o = O.solve(pos, body, L, gamma=0.0, FT=FT, rlub=3.0, M=M)
+            Bm[J, k] = o["S"][:, 0, 1].sum()
+    # the constraint part is not negligible in this check
+    assert np.abs(out["SC"]).max() > 0.05 * np.abs(out["S"]).max()
+    assert np.linalg.norm(A + Bm) < 1e-10 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("gap", [1e-3, 0.07, 0.6])
+def test_lubrication_strain_columns_equal_affine_bead_motion(gap):
+    """The pair model (a dissipation form of the pair's relative surface
+    velocity and relative rotation) sees an imposed strain E only through
+    s = r E.n, which is exactly what the beads would see moving with
+    nu = -E.x_b in still fluid (s = nu_i - nu_j): R (0, E) = R (-E x, 0) on
+    every force and stresslet row."""
+    rng = np.random.default_rng(int(gap * 1e4) + 5)
+    xi, xj = _two_body_pair(gap, 7)
+    xi = xi + rng.normal(size=3)
+    xj = xj + (xi - np.zeros(3))
+    R = O.lub_pair_matrix(xi, xj)
+    for _ in range(3):
+        E = rng.normal(size=(3, 3))
+        E = 0.5 * (E + E.T)
+        E -= np.trace(E) / 3.0 * np.eye(3)
+        e5 = O.sym_to_vec5(E)
+        nu_strain = np.zeros(22)
+        nu_strain[6:11] = e5
+        nu_strain[17:22] = e5
+        nu_move = np.zeros(22)
+        nu_move[0:3] = -E @ xi
+        nu_move[11:14] = -E @ xj
+        f1 = R @ nu_strain
+        f2 = R @ nu_move
+        assert np.abs(f1).max() > 1e-3 * np.abs(R).max() * np.abs(E).max()
+        assert np.abs(f1 - f2).max() < 1e-12 * np.abs(R).max() * np.abs(E).max() * 4.0
