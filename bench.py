@@ -182,6 +182,118 @@ def traffic_for(group):
     return e["bytes_per_launch"]
 
 
+def group_roofline(group, ms_per_launch, s, prm, st, pk, pk_kind, alu32):
+    """Achieved rate and fraction of the binding peak for one kernel group:
+    HBM groups against the measured copy bandwidth, the real-space pair sum
+    against the FP32 FMA rate measured in this run (fsd_fma_throughput)."""
+    bound, work, unit = group_work(group, s, prm, st)
+    r = {"bound": bound, "launch_ms": round(ms_per_launch, 5)}
+    if work is None:
+        return r
+    if bound == "alu":
+        achieved = work / (ms_per_launch / 1e3) / 1e12
+        peak = alu32 / 1e12
+        r.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                  "peak_source": "FP32 FMA rate measured in this run (fsd_fma_throughput)",
+                  "flops_per_launch": work})
+    else:
+        achieved = work / (ms_per_launch / 1e3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        r.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                  "peak_source": "hbm_gbs (%s)" % pk_kind, "bytes_per_launch": work})
+    return r
+
+
+def subbox_reference():
+    """The stored oracle solution of the 384-bead accuracy sub-box (written
+    by tests/golden/make_subbox_reference.py from the oracle alone)."""
+    import importlib.util
+
+    path = os.path.join(ROOT, "tests", "golden", "make_subbox_reference.py")
+    spec = importlib.util.spec_from_file_location("make_subbox_reference", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.load()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def accuracy_subbox(pkg, stream):
+    """Relative L2 error of U, Omega and S against the dense oracle on a
+    384-bead sub-box of the benchmark's suspension (same generator, phi 0.2,
+    8-bead aggregates), solved at the benchmark's settings: xi 0.5, default
+    P and grid (x_err 1e-6), GMRES 1e-6, r_p 2a, lubrication 3a, graph loop."""
+    w = WORKLOAD
+    g = subbox_reference()
+    out = {"workload": "384 beads: 48 x 8-bead aggregates, phi 0.2, L %.2f, shear 1 (and shear plus "
+                       "random aggregate forces / torques)" % g["L"]}
+    for name, prec in (("mixed", pkg.FSD_MIXED), ("fp64", pkg.FSD_FP64)):
+        s = pkg.Suspension(g["pos"], g["body"], g["L"], stream=stream, precision=prec, xi=w["xi"],
+                           tol=w["tol"], lub_cutoff=w["lub"], precond_cutoff=w["rp"],
+                           flags=pkg.FSD_FLAG_GRAPH)
+        prm = s.params
+        errs = {}
+        for case, ft in (("shear", None), ("shear+forces", np.ascontiguousarray(g["ft"]))):
+            Uref, Sref = g["cases"][case]
+            vel, S, st, _ = s.solve(ft, w["shear"])
+            errs[case] = {"U": _rel(vel[:, :3], Uref[:, :3]), "Omega": _rel(vel[:, 3:], Uref[:, 3:]),
+                          "S": _rel(S, Sref), "iters": st["iters"], "rel_residual": st["rel_residual"]}
+        s.close()
+        out[name] = errs
+        out["grid_P"] = [prm["grid"], prm["P"]]
+    out["gate"] = "1e-5 on each of U, Omega, S (tests/test_gpu_benchmark_settings.py)"
+    return out
+
+
+def fft_vs_library(n, xi, L, hand_ms):
+    """cuFFT (through torch.fft) on the same six n^3 FP32 grids: forward R2C
+    and inverse C2R alone, and with a Green's-function scaling pass between
+    them, next to the library's hand-written fused chain (x + y, z with the
+    Green's function, y + x; `hand_ms` from the library profiler).  A
+    comparison only: the library does not call cuFFT."""
+    import torch
+
+    g = torch.randn(6, n, n, n, device="cuda", dtype=torch.float32)
+    kk = 2.0 * np.pi / L * torch.fft.fftfreq(n, 1.0 / n, device="cuda", dtype=torch.float32)
+    kr = 2.0 * np.pi / L * torch.fft.rfftfreq(n, 1.0 / n, device="cuda", dtype=torch.float32)
+    k2 = kk[:, None, None] ** 2 + kk[None, :, None] ** 2 + kr[None, None, :] ** 2
+    k2[0, 0, 0] = 1.0
+    A = (1.0 + k2 / (4 * xi * xi)) * torch.exp(-k2 / (4 * xi * xi)) / k2
+    A[0, 0, 0] = 0.0
+
+    def transforms():
+        return torch.fft.irfftn(torch.fft.rfftn(g, dim=(1, 2, 3)), s=(n, n, n), dim=(1, 2, 3))
+
+    def with_green():
+        sp = torch.fft.rfftn(g, dim=(1, 2, 3))
+        sp.mul_(A)
+        return torch.fft.irfftn(sp, s=(n, n, n), dim=(1, 2, 3))
+
+    res = {}
+    for name, fn in (("cufft_r2c_c2r_ms", transforms), ("cufft_with_green_scaling_ms", with_green)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / 10
+    del g, A, k2
+    torch.cuda.empty_cache()
+    res.update({"hand_written_fused_ms": hand_ms, "grid": n, "fields": 6,
+                "note": "same six FP32 real grids, forward and inverse 3D transforms; the hand-written "
+                        "chain also applies the full Green's function (projection, Faxen factors, six "
+                        "read-out fields), the cuFFT leg a scalar scaling only"})
+    res["speedup_hand_written_vs_cufft_transforms"] = res["cufft_r2c_c2r_ms"] / hand_ms
+    return res
+
+
 # ------------------------------------------------------------ oracle arm
 def oracle_sample_step(seed):
     import oracle as O
@@ -286,6 +398,14 @@ def shard_by_cost(costs, world):
 
 # ------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
+    import multiprocessing as mp
+
+    # the batched form's 64 suspensions are generated on host cores while
+    # the GPU measurements run (spawned workers, started before CUDA is used)
+    jobs = batch_jobs()
+    mine = shard_by_cost([int(j[2]) for j in jobs], world)[rank]
+    pool = mp.get_context("spawn").Pool(max(1, min(8, (os.cpu_count() or 2) // (2 * world))))
+    batch_async = pool.map_async(_batch_system, [jobs[i] for i in mine])
     import torch
 
     torch.cuda.set_device(local_rank)
@@ -354,6 +474,9 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end: pinned host input and output every step (fresh context)
     s = make(pkg.FSD_MIXED)
+    # its first solve, on the initial configuration, is compared with the
+    # FP64 path's below (the 32768-bead system is too large for the oracle)
+    v_mixed, S_mixed, _, _ = s.solve(None, w["shear"])
     for _ in range(args.warmup):
         s.step(None, w["shear"], w["dt"])
     ft_h = torch.zeros((w["n_agg"], 6), dtype=torch.float64).pin_memory()
@@ -522,6 +645,11 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- plain FP64 path on the same initial configuration
     s64 = make(pkg.FSD_FP64)
+    v_64, S_64, _, _ = s64.solve(None, w["shear"])
+    agree = {"U": _rel(v_mixed[:, :3], v_64[:, :3]), "Omega": _rel(v_mixed[:, 3:], v_64[:, 3:]),
+             "S": _rel(S_mixed, S_64),
+             "note": "mixed vs plain FP64 GPU solve of the 32768-bead initial configuration, both at "
+                     "GMRES 1e-6 (relative L2)"}
     for _ in range(max(1, min(args.warmup, 2))):
         s64.step(None, w["shear"], w["dt"])
     K64 = max(2, min(args.steps, 5))
@@ -535,35 +663,47 @@ def run_ours(args, rank, world, local_rank):
             "iters_per_step": iters64 / K64,
             "kernel_ms_per_step": {g: round(v[0], 4) for g, v in prof64.items()}}
 
+    # ---- batched form: 64 independent suspensions advanced together, and
+    #      the same contexts one at a time (no autotuning on either side)
+    systems_mine = batch_async.get()
+    pool.close()
+    pool.join()
+    Bt, _, batch = batch_measure(pkg, systems_mine, max(3, min(args.steps, 5)), 3, tuned=False,
+                                 world=world)
+    Bt.close()
+    nj = [int(j[2]) for j in jobs]
+    batch["workload"] = ("%d suspensions, %d beads (%d..%d per system, log-uniform), aggregate sizes "
+                         "2..64, phi 0.05..0.3, shear 1, lubrication 3a, GMRES 1e-6, mixed, default xi"
+                         % (len(jobs), sum(nj), min(nj), max(nj)))
+    batch["execution"] = ("fsd_step_batch: one CUDA graph per system and step on its own stream, all "
+                          "systems in flight" + ("; systems sharded over ranks" if world > 1 else ""))
+
+    # ---- measured arithmetic peaks, accuracy against the oracle, cuFFT
+    alu32 = pkg.fma_throughput(32, stream.cuda_stream)
+    alu64 = pkg.fma_throughput(64, stream.cuda_stream)
+    accuracy = accuracy_subbox(pkg, stream.cuda_stream)
+    accuracy["agreement_32768_beads"] = agree
+    fftcmp = fft_vs_library(prm["grid"], w["xi"], L, prof_op["fft_green"][0] / KA)
+
     if rank != 0:
         return
 
-    # ---- roofline of the dominant kernel group of an FP32 operator
-    #      application (the work the Krylov iterations repeat)
+    # ---- roofline of every kernel group of an FP32 operator application
+    #      (the work the Krylov iterations repeat); the dominant one leads
     pk, pk_kind = peaks()
     op_groups = ("realspace", "spread", "fft_green", "interp")
     dom = max(op_groups, key=lambda g: prof_op[g][0])
-    per_launch_ms = prof_op[dom][0] / KA
-    bound, work, unit = group_work(dom, s, prm, stp)
-    roof = {"kernel_group": dom, "bound": bound, "launch_ms": per_launch_ms,
-            "launch": "one FP32 operator application (the group's kernels), mean of %d" % KA,
-            "operator_ms_by_group": {g: round(prof_op[g][0] / KA, 4) for g in op_groups}}
-    if work is not None:
-        if bound == "alu":
-            mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
-            achieved = work / (per_launch_ms / 1e3) / 1e12
-            roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "peak_source": "FP32 ALU: 152 SM x 128 lanes x "
-                         "2 flop x %.0f MHz (%s clock)" % (mhz, pk_kind),
-                         "flops_per_launch": work})
-        else:
-            achieved = work / (per_launch_ms / 1e3) / 1e9
-            peak = pk.get("hbm_gbs", 6800.0)
-            roof.update({"achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": "hbm_gbs (%s)" % pk_kind,
-                         "bytes_per_launch": work})
-    roof["traffic"] = traffic_for(dom)
+    groups = {g: group_roofline(g, prof_op[g][0] / KA, s, prm, stp, pk, pk_kind, alu32)
+              for g in op_groups}
+    for g in op_groups:
+        groups[g]["traffic"] = traffic_for(g)
+    roof = {"kernel_group": dom}
+    roof.update(groups[dom])
+    roof.update({"launch": "one FP32 operator application (the group's kernels), mean of %d" % KA,
+                 "groups": groups,
+                 "measured_fma": {"fp32_tflops": alu32 / 1e12, "fp64_tflops": alu64 / 1e12,
+                                  "how": "fsd_fma_throughput: independent FMA chains on every SM, "
+                                         "best of 3 launches, CUDA events"}})
 
     base = cpu_baseline(3) if world == 1 or rank == 0 else None
     line = {
@@ -592,6 +732,9 @@ def run_ours(args, rank, world, local_rank):
         "brownian": brown,
         "brownian_drift": drift_lines,
         "lees_edwards": lees,
+        "accuracy": accuracy,
+        "fft_vs_library": fftcmp,
+        "batch": batch,
         "roofline": roof,
         "cpu_baseline": base,
         "e2e": e2e,
@@ -645,13 +788,80 @@ def batch_systems():
     process is forked after CUDA is initialised)."""
     import multiprocessing as mp
 
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        return pool.map(_batch_system, batch_jobs())
+
+
+def batch_jobs():
     b = BATCH
     rng = np.random.default_rng(b["seed"])
     n = np.rint(np.exp(rng.uniform(np.log(b["n_lo"]), np.log(b["n_hi"]), size=b["n_sys"]))).astype(int)
     phi = rng.uniform(b["phi_lo"], b["phi_hi"], size=b["n_sys"])
-    jobs = [(s, b["seed"], n[s], phi[s]) for s in range(b["n_sys"])]
-    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
-        return pool.map(_batch_system, jobs)
+    return [(s, b["seed"], n[s], phi[s]) for s in range(b["n_sys"])]
+
+
+def batch_measure(pkg, systems, steps, warmup, tuned, world=1):
+    """The batched form on `systems`: fsd_step_batch timed over `steps`
+    steps (wall clock, device synchronised on both sides), end to end with
+    pinned host forces in and velocities out, and the same contexts stepped
+    one at a time.  tuned: FSD_FLAG_AUTOTUNE per system (both sides use the
+    same contexts either way)."""
+    import torch
+
+    b = BATCH
+    nb = sum(len(p) for p, _, _ in systems)
+    flags = pkg.FSD_FLAG_COMOVING | (pkg.FSD_FLAG_AUTOTUNE if tuned else 0)
+    prm = dict(precision=pkg.FSD_MIXED, tol=b["tol"], lub_cutoff=b["lub"], precond_cutoff=b["rp"],
+               flags=flags)
+    t_set = time.perf_counter()
+    B = pkg.Batch(systems, prm)
+    t_set = time.perf_counter() - t_set
+    rates = np.full(B.n_sys, b["shear"])
+    for _ in range(warmup):
+        B.step(None, rates, b["dt"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = launches = 0
+    for _ in range(steps):
+        st, _ = B.step(None, rates, b["dt"])
+        iters += sum(x["iters"] for x in st)
+        launches += sum(x["kernel_launches"] for x in st)
+    torch.cuda.synchronize()
+    dt_b = time.perf_counter() - t0
+    value = weak_value(nb * steps, dt_b)
+    dt_b = reduce_max(dt_b)
+    ft_h = torch.zeros((B.n_agg, 6), dtype=torch.float64).pin_memory()
+    vel_h = torch.zeros((B.n_agg, 6), dtype=torch.float64).pin_memory()
+    K2 = max(2, steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        B.step(ft_h, rates, b["dt"], vel=vel_h)
+    torch.cuda.synchronize()
+    e2e_value = weak_value(nb * K2, time.perf_counter() - t0)
+    views = [B.system(k) for k in range(B.n_sys)]
+    for v in views:  # untimed: each view captures its own step graph first
+        v.step(None, b["shear"], b["dt"])
+    K1 = max(2, min(steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K1):
+        for v in views:
+            v.step(None, b["shear"], b["dt"])
+    torch.cuda.synchronize()
+    dt_1 = time.perf_counter() - t0
+    one = weak_value(nb * K1, dt_1)
+    out = {"value": value, "unit": UNIT, "ms_per_step": dt_b / steps * 1e3, "steps": steps,
+           "beads": nb, "systems": len(systems), "iters_per_system_step": iters / (steps * len(systems)),
+           "setup_s": round(t_set, 1), "autotuned": bool(tuned),
+           "one_at_a_time": {"value": one, "ms_per_step": dt_1 / K1 * 1e3, "steps": K1,
+                             "note": "the same contexts (same parameters) stepped sequentially with fsd_step"},
+           "speedup_batched": value / one,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ft_h.numel() * 8),
+                   "d2h_bytes_per_step": int(vel_h.numel() * 8), "steps": K2,
+                   "api": "fsd_step_batch with pinned host forces in and velocities out"},
+           "gpu_launches": int(reduce_sum(launches))}
+    return B, views, out
 
 
 def run_batch(args, rank, world, local_rank):
@@ -674,56 +884,13 @@ def run_batch(args, rank, world, local_rank):
     systems = [systems_all[i] for i in mine]
     build()
     b = BATCH
-    nb = sum(len(p) for p, _, _ in systems)
-    prm = dict(precision=pkg.FSD_MIXED, tol=b["tol"], lub_cutoff=b["lub"], precond_cutoff=b["rp"],
-               flags=pkg.FSD_FLAG_COMOVING | pkg.FSD_FLAG_AUTOTUNE)
-    t_set = time.perf_counter()
-    B = pkg.Batch(systems, prm)
-    t_set = time.perf_counter() - t_set
-    rates = np.full(B.n_sys, b["shear"])
-    for _ in range(args.warmup):
-        B.step(None, rates, b["dt"])
     clk = ClockSampler(local_rank)
     clk.start()
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    iters = launches = 0
-    for _ in range(args.steps):
-        st, _ = B.step(None, rates, b["dt"])
-        iters += sum(x["iters"] for x in st)
-        launches += sum(x["kernel_launches"] for x in st)
-    torch.cuda.synchronize()
-    dt_b = time.perf_counter() - t0
+    B, views, meas = batch_measure(pkg, systems, args.steps, args.warmup, tuned=True, world=world)
     clocks = clk.stop()
-    value = weak_value(nb * args.steps, dt_b)
-    dt_b = reduce_max(dt_b)
-    launches = int(reduce_sum(launches))
-    # end to end: pinned host forces in and velocities out every step
-    ft_h = torch.zeros((B.n_agg, 6), dtype=torch.float64).pin_memory()
-    vel_h = torch.zeros((B.n_agg, 6), dtype=torch.float64).pin_memory()
-    K2 = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(K2):
-        B.step(ft_h, rates, b["dt"], vel=vel_h)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = weak_value(nb * K2, e2e_s)
-    # the same systems (same contexts and parameters), one at a time
-    views = [B.system(s) for s in range(B.n_sys)]
-    for v in views:  # untimed: each view captures its own step graph first
-        v.step(None, b["shear"], b["dt"])
-    K1 = max(2, min(args.steps, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(K1):
-        for v in views:
-            v.step(None, b["shear"], b["dt"])
-    torch.cuda.synchronize()
-    dt_1 = time.perf_counter() - t0
-    one = weak_value(nb * K1, dt_1)
+    value = meas["value"]
     # dominant kernel group of the largest system, profiled alone
     big = int(np.argmax([len(p) for p, _, _ in systems]))
     sv = views[big]
@@ -745,11 +912,11 @@ def run_batch(args, rank, world, local_rank):
         roof.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": "hbm_gbs (%s)" % pk_kind, "bytes_per_launch": work})
     elif work is not None:
-        mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        peak = pkg.fma_throughput(32) / 1e12
         achieved = work / (per_launch_ms / 1e3) / 1e12
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": "FP32 ALU (%s clock)" % pk_kind, "flops_per_launch": work})
+                     "peak_source": "FP32 FMA rate measured in this run (fsd_fma_throughput)",
+                     "flops_per_launch": work})
     roof["traffic"] = None
     xis = sorted(set(round(p["xi"], 3) for p in B.params))
     B.close()
@@ -758,7 +925,7 @@ def run_batch(args, rank, world, local_rank):
     line = {
         "metric": "bead-steps/sec of 64 independent suspensions advanced together (GMRES 1e-6, mixed)",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": dt_b / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": meas["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "batched form: %d suspensions, %d beads (%d..%d per system, log-uniform), "
                                "aggregate sizes 2..64, phi 0.05..0.3, shear 1, lubrication 3a, GMRES 1e-6"
@@ -771,17 +938,13 @@ def run_batch(args, rank, world, local_rank):
                    "execution": "fsd_step_batch: one CUDA graph per system and step on its own stream, "
                                 "all systems in flight; launch phase on 8 host threads",
                    "l2": "working set > L2 (64 grids and Krylov bases)",
-                   "generation_s": round(t_gen, 1), "setup_s": round(t_set, 1)},
-        "one_at_a_time": {"value": one, "ms_per_step": dt_1 / K1 * 1e3, "steps": K1,
-                          "speedup_batched": value / one,
-                          "note": "the same contexts stepped sequentially with fsd_step"},
-        "iters_per_system_step": iters / (args.steps * len(systems)),
+                   "generation_s": round(t_gen, 1), "setup_s": meas["setup_s"]},
+        "one_at_a_time": dict(meas["one_at_a_time"], speedup_batched=meas["speedup_batched"]),
+        "iters_per_system_step": meas["iters_per_system_step"],
         "roofline": roof,
         "cpu_baseline": cpu_baseline(3),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ft_h.numel() * 8),
-                "d2h_bytes_per_step": int(vel_h.numel() * 8), "steps": K2,
-                "api": "fsd_step_batch with pinned host forces in and velocities out"},
-        "gpu_launches": launches,
+        "e2e": meas["e2e"],
+        "gpu_launches": meas["gpu_launches"],
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

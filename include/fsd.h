@@ -263,9 +263,10 @@ const char *fsd_profile_group_name(int g);
 
 /* Wave-space mobility without any allocation (the paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory,
- * e.g. code inside a captured CUDA graph, under a memory pool it does not
- * own, or in a loop where an allocation and its implicit synchronisation are
- * not allowed).  Computes out = M_wave . in with the FP32 wave-space operator
+ * e.g. code whose device memory belongs to an allocator or pool it does not
+ * own, a plug-in that must not grow the process's device footprint after
+ * start-up, or a loop where an allocation and its implicit synchronisation
+ * are not allowed).  Computes out = M_wave . in with the FP32 wave-space operator
  * of fsd_apply_mobility (part 2, precision FSD_MIXED): Gaussian spreading,
  * FFT with the Green's function, interpolation.  No context: the parameters
  * are given directly (m_shape <= 0 selects 0.976 sqrt(pi P)).
@@ -274,13 +275,15 @@ const char *fsd_profile_group_name(int g);
  *   Limits: n_beads <= 4096, grid <= 48 (even, 2,3,5-smooth), P even in
  *   4..24 and <= grid; larger requests return FSD_EINVAL before any GPU work.
  * Every intermediate lives in one 10 MiB file-scope device array that each
- * device loading the library holds until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress):
- * make that first call before any stream capture.  All calls share the
+ * device loading the library holds until the process exits.  Each call looks
+ * up that array's device address in the current device context
+ * (cudaGetSymbolAddress; FSD_ECUDA if that fails).  All calls share the
  * array: calls whose GPU work overlaps race on it, so order them on one
  * stream (or with events).  Each call rewrites or zeroes everything it
  * reads.  Work is enqueued on cuda_stream (NULL: the default stream); out is
- * ready when that stream is. */
+ * ready when that stream is.  An error already pending in the CUDA runtime
+ * when the call starts is left in place and the call returns FSD_ECUDA
+ * without doing anything. */
 fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead_pos,
                                   const double *in, double *out, double box,
                                   double xi, int grid, int P, double m_shape,
@@ -425,6 +428,16 @@ fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque)
 /* Sets the Lees-Edwards offset of the box (see fsd_params.tilt; taken
  * modulo L).  fsd_get_params reports the current offset. */
 fsd_status fsd_set_tilt(fsd_ctx *ctx, double tilt);
+
+/* Measured fused multiply-add throughput of the current device (no
+ * counterpart in the paper: the real-space pair sum and the FP64 operator
+ * are bound by the FMA rate, so their rooflines need the rate of the GPU at
+ * hand).  fp_bits 32 or 64; *flop_per_s = 2 x FMAs per second of a kernel of
+ * independent FMA chains filling every SM (best of three ~2-5 ms launches,
+ * CUDA events on cuda_stream; NULL: the default stream).  Synchronises
+ * cuda_stream; allocates and frees a few bytes.  FSD_EINVAL for another
+ * fp_bits or a NULL output, FSD_ECUDA on a CUDA error. */
+fsd_status fsd_fma_throughput(int fp_bits, double *flop_per_s, void *cuda_stream);
 
 /* Parameters actually used (after the defaulting rules). */
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p);

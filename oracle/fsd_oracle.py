@@ -415,6 +415,33 @@ def mobility_wave_dense(pos, L, xi, kmax, a=1.0, eta=1.0, tilt=0.0):
     return M
 
 
+def mobility_wave_apply(pos, F, L, xi, kmax, a=1.0, eta=1.0, tilt=0.0, chunk=100000):
+    """The wave-space Ewald sum of `mobility_wave_dense` applied to moments
+    F (N, 11) without forming the matrix:
+        u_i = (1/V) sum_{k != 0} H(k,xi)/(eta k^2) e^{ik.x_i} Q(k)^H (I - kk)
+              sum_j Q(k) e^{-ik.x_j} F_j
+    over the half lattice (x2 and the real part for -k), in chunks of k.
+    Returns (N, 11).  For boxes whose wave-vector count makes the dense
+    matrix impractical (a 144^3-point grid's range of k)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    F = np.asarray(F, dtype=np.float64).reshape(len(pos), 11)
+    k_all = wave_vectors(L, kmax, tilt)
+    u = np.zeros((len(pos), 11))
+    for c0 in range(0, k_all.shape[0], chunk):
+        k = k_all[c0:c0 + chunk]
+        kn = np.linalg.norm(k, axis=1)
+        kh = k / kn[:, None]
+        Q = source_operator(k, a)
+        ph = k @ pos.T  # (K, N)
+        rho = np.exp(-1j * ph) @ F  # sum_j e^{-ik.x_j} F_j: (K, 11)
+        g = np.einsum("pat,pt->pa", Q, rho)
+        g = g - kh * np.einsum("pa,pa->p", kh, g)[:, None]  # (I - kk) g
+        v = np.einsum("pas,pa->ps", Q.conj(), g)
+        w = 2.0 * hasimoto(kn, xi) / (eta * kn * kn) / L ** 3
+        u += (np.exp(1j * ph).T @ (v * w[:, None])).real
+    return u
+
+
 def mobility_dense(pos, L, a=1.0, eta=1.0, xi=None, tilt=0.0):
     """Periodic FTS mobility M_inf, dense (11N x 11N), bead-major (a
     Lees-Edwards box when tilt != 0)."""

@@ -33,7 +33,7 @@ EXPORTS = (
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
     "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
     "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian", "fsd_drift",
-    "fsd_contact_forces", "fsd_set_tilt",
+    "fsd_contact_forces", "fsd_set_tilt", "fsd_fma_throughput",
 )
 PROF_GROUPS = 10
 
@@ -118,6 +118,7 @@ def load(path=LIB_PATH):
                               ctypes.POINTER(FsdStats)]
     lib.fsd_contact_forces.argtypes = [P, D, P]
     lib.fsd_set_tilt.argtypes = [P, D]
+    lib.fsd_fma_throughput.argtypes = [I, ctypes.POINTER(D), P]
     lib.fsd_destroy_batch.argtypes = [P]
     lib.fsd_destroy_batch.restype = None
     for name in EXPORTS:
@@ -157,6 +158,17 @@ def default_params(**kw):
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def fma_throughput(fp_bits, stream=None):
+    """fsd_fma_throughput: measured FP32 (32) or FP64 (64) FMA rate of the
+    current device in flop/s (2 per FMA)."""
+    lib = load()
+    out = ctypes.c_double()
+    st = lib.fsd_fma_throughput(int(fp_bits), ctypes.byref(out), stream)
+    if st != FSD_OK:
+        raise FsdError(st, "fsd_fma_throughput failed")
+    return out.value
 
 
 class Suspension:

@@ -600,7 +600,7 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.rhs.alloc(c.nunk);
   c.res.alloc(c.nunk);
   c.xprev.alloc(c.nunk);
-  c.partial.alloc(std::max<int64_t>((int64_t)64 * 4 * 152, cgs_partial_size(c.nunk, mm + 1)));
+  c.partial.alloc(std::max<int64_t>((int64_t)64 * kDotPartials, cgs_partial_size(c.nunk, mm + 1)));
   c.hcol.alloc(512);
   FSD_CUDA(cudaMallocHost(&c.h_pinned, 512 * sizeof(double)));
   build_real_table(c);
@@ -683,7 +683,7 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
   if (c.vextra_pending) launch_add_velocity(c, vel_int);
   c.vextra_pending = false;  // consumed by this solve
   FSD_CUDA(cudaMemsetAsync(c.flags.p + 6, 0, sizeof(int), c.stream));
-  k_nan_check<<<152, 256, 0, c.stream>>>(vel_int, 6 * (int64_t)c.N, c.flags.p + 6);
+  k_nan_check<<<c.num_sms, 256, 0, c.stream>>>(vel_int, 6 * (int64_t)c.N, c.flags.p + 6);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaMemcpyAsync(c.h_flags, c.flags.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   FSD_CUDA(cudaStreamSynchronize(c.stream));

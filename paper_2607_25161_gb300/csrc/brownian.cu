@@ -449,7 +449,9 @@ __global__ void k_axpy1(int64_t n, const double *__restrict__ x, double *y) {
     y[i] += x[i];
 }
 
-static int small_grid(int64_t n) { return (int)std::min<int64_t>(ceil_div(n, 256), 4 * 152); }
+static int small_grid(const Ctx &c, int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * (int64_t)c.num_sms));
+}
 
 void launch_dq_philox(Ctx &c, uint64_t seed, uint64_t step, double *user) {
   k_dq_philox<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, seed, step, user);
@@ -458,13 +460,13 @@ void launch_dq_philox(Ctx &c, uint64_t seed, uint64_t step, double *user) {
 }
 
 void launch_scaled_diff(Ctx &c, const double *a, const double *b, double s, double *out, int64_t n) {
-  k_scaled_diff<<<small_grid(n), 256, 0, c.stream>>>(n, a, b, s, out);
+  k_scaled_diff<<<small_grid(c, n), 256, 0, c.stream>>>(n, a, b, s, out);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 void launch_axpy(Ctx &c, const double *x, double *y, int64_t n) {
-  k_axpy1<<<small_grid(n), 256, 0, c.stream>>>(n, x, y);
+  k_axpy1<<<small_grid(c, n), 256, 0, c.stream>>>(n, x, y);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }

@@ -328,6 +328,10 @@ void cgs_pass_dev(Ctx &c, int mode, const double *V, int64_t ld, const int *k_de
                   double *out_dev);  // the same with k = *k_dev + k_add read on the device
 void axpy_multi_dev(Ctx &c, double *w, const double *V, int64_t ld, const int *k_dev,
                     const double *coef_dev, double sign);
+// Partial sums per dot product: a fixed count (not the SM count), so that the
+// reduction order and hence every result is the same on any GPU; 608 is 4 per
+// SM on a 152-SM part.
+constexpr int kDotPartials = 608;
 int64_t cgs_partial_size(int64_t nunk, int kmax);
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b,
                int64_t n);                          // y = a x + b y

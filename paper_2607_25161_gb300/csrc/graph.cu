@@ -341,7 +341,9 @@ static cudaGraphConditionalHandle new_handle(cudaGraph_t g) {
   return h;
 }
 
-static int vec_blocks(int64_t n) { return std::max(1, std::min<int>(ceil_div(n, 256), 8 * 152)); }
+static int vec_blocks(const Ctx &c, int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms));
+}
 
 // One Arnoldi step of the flexible GMRES on the operator of precision T:
 // z_j = P^-1 v_j, w = A z_j, CGS2 against V_0..V_j, Givens update, v_{j+1}.
@@ -349,7 +351,7 @@ template <typename T>
 static void arnoldi_step(Ctx &c, GState *s, cudaGraphConditionalHandle h_arn) {
   GraphCache &gc = *c.gcache;
   const int64_t ld = c.nunk, n = c.nunk;
-  const int nb = vec_blocks(n);
+  const int nb = vec_blocks(c, n);
   const int mm = std::max(c.m, c.m_in);
   k_g_get_col<<<nb, 256, 0, c.stream>>>(gc.vin.p, c.V.p, ld, s, n);
   FSD_LAUNCHED(c);
@@ -380,7 +382,7 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
   GraphCache &gc = *c.gcache;
   GState *s = gc.state.p;
   const int64_t n = c.nunk;
-  const int nb = vec_blocks(n);
+  const int nb = vec_blocks(c, n);
   double *x = c.xsol.p, *b = c.rhs.p, *w = c.w.p;
   const bool mixed = c.prm.precision == FSD_MIXED;
   int64_t l0;
@@ -594,7 +596,7 @@ static GraphEntry &build_entry(Ctx &c, const GraphRun &o, const GraphKey &k) {
     launch_outputs(c, c.xsol.p, o.shear, c.t1.p, o.with_str ? c.res.p : nullptr);
     if (o.add_vel) launch_add_velocity(c, c.t1.p);
     FSD_CUDA(cudaMemsetAsync(c.flags.p + 6, 0, sizeof(int), c.stream));
-    k_g_nan_check<<<152, 256, 0, c.stream>>>(c.t1.p, 6 * (int64_t)c.N, c.flags.p + 6);
+    k_g_nan_check<<<c.num_sms, 256, 0, c.stream>>>(c.t1.p, 6 * (int64_t)c.N, c.flags.p + 6);
     FSD_LAUNCHED(c);
     if (o.integrate) {
       launch_integrate(c, c.t1.p, o.dt, o.shear);

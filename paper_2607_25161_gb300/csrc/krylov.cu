@@ -9,7 +9,7 @@
 
 namespace fsd {
 
-constexpr int kDotBlocks = 4 * 152;  // partial sums per dot (multiple of the SM count)
+constexpr int kDotBlocks = kDotPartials;
 constexpr int kDotChunk = 16;        // basis vectors per pass
 
 // partial[j * nb + blk] = sum over this block's grid-stride slice of V_j . w
@@ -252,7 +252,7 @@ void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k, const dou
   if (k <= 0) return;
   ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
-  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
+  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms);
   k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, k, nullptr, coef_dev, sign, n);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
@@ -263,7 +263,7 @@ void axpy_multi_dev(Ctx &c, double *w, const double *V, int64_t ld, const int *k
                     const double *coef_dev, double sign) {
   ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
-  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
+  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms);
   k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, 0, k_dev, coef_dev, sign, n);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
@@ -283,7 +283,7 @@ __global__ void k_axpby(double *y, double a, const double *__restrict__ x, doubl
 
 void vec_scale_host(Ctx &c, double *y, const double *x, double s) {
   ProfScope ps(c, PG_KRYLOV);
-  int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * 152);
+  int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * (int64_t)c.num_sms);
   k_scale<<<blocks, 256, 0, c.stream>>>(y, x, s, c.nunk);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
@@ -291,7 +291,7 @@ void vec_scale_host(Ctx &c, double *y, const double *x, double s) {
 
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b, int64_t n) {
   ProfScope ps(c, PG_KRYLOV);
-  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * 152);
+  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms);
   k_axpby<<<blocks, 256, 0, c.stream>>>(y, a, x, b, n);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());

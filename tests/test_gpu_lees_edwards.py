@@ -199,3 +199,28 @@ def test_rfd_drift_with_tilt(pkg, sysLE):
     assert status == pkg.FSD_OK
     assert rel(drift, ref) < 1e-5
     assert rel(SB, refS) < 1e-5
+
+
+def test_pairwise_near_field_sampler_with_tilt(pkg):
+    # three lubrication pairs exist only through the sheared image across y
+    # (bead B sits at A + d + (tilt, L, 0)); the pairwise sampler's forces
+    # and torques must follow the sheared nearest image, as in the oracle
+    L, tilt = 14.0, 0.3 * 14.0
+    A = np.array([5.0, 0.3, 7.0])
+    d = np.array([0.5, -2.2, 0.3])
+    B = A + d + np.array([tilt, L, 0.0])
+    B[0] = np.mod(B[0], L)
+    pos = np.array([A, A + [0.0, 0.0, 2.0], B, B + [0.0, 0.0, 2.0], [10.0, 7.0, 3.0],
+                    [2.0, 7.0, 12.0]])
+    body = np.array([0, 0, 1, 1, 2, 3], dtype=np.int32)
+    seed, step = 91, 3
+    s = pkg.Suspension(pos, body, L, tilt=tilt, lub_cutoff=3.0, nf_sampler=pkg.FSD_NF_PAIRWISE,
+                       **HI)
+    _, fnf, st = s.brownian(1.0, 1.0, seed=seed, step=step, psi_real=np.zeros((len(pos), 11)))
+    s.close()
+    unw, X, r = O.body_geometry(pos, body, L, tilt)
+    ref = BO.pairwise_nf_force(unw, body, L, seed, step, rlub=3.0, tilt=tilt)
+    assert np.abs(ref[:4]).max() > 0 and np.abs(ref[4:]).max() == 0.0
+    # in the cube the same beads have no near pairs at all
+    assert np.abs(BO.pairwise_nf_force(unw, body, L, seed, step, rlub=3.0)).max() == 0.0
+    assert rel(fnf / np.sqrt(2.0), ref) < 1e-12

@@ -1,10 +1,13 @@
-"""GPU check of the two FP32 spreading kernels.
+"""GPU checks of the FP32 wave-space kernels on grids of different shapes.
 
-Grids whose side is a multiple of 4 spread with 16-byte vector reductions
-(aligned quads of x points); other grids use one scalar atomic per point.
-Both must give the FP32 wave-space operator within 1e-5 (relative L2) of
-the FP64 operator at the same grid, and the two grids must agree with the
-oracle's wave-space sum to the accuracy of the grid rule."""
+FP32 spreading is grid-centric: the grid is cut into 8^3 tiles, and each
+tile gathers the window contributions of the beads listed for it (a grid
+side of 50 leaves partial tiles at the upper faces, 48 does not).  The FP32
+wave-space operator must agree with the FP64 operator at the same grid
+within 1e-5 (relative L2), and with the oracle's wave-space sum to the
+accuracy of the grid rule, on grids with and without partial tiles; the
+fused (planar) and separate (interleaved) FFT passes are checked the same
+way."""
 
 import numpy as np
 import pytest
@@ -31,13 +34,13 @@ def pkg():
     return p
 
 
-def test_vector_and_scalar_spreading_agree(pkg):
+def test_spreading_with_full_and_partial_tiles_agrees(pkg):
     pos, body, L = synth.mixed_suspension(40, 0.1, 31, size_hi=8)
     rng = np.random.default_rng(7)
     F = rng.normal(size=(len(pos), 11))
     xi = 1.2  # the xerr = 1e-8 rule asks for 43 points per side here
     ref = O.mobility_wave_dense(pos, L, xi, 2.0 * xi * np.sqrt(46.0)).reshape(11 * len(pos), -1) @ F.reshape(-1)
-    for grid in (48, 50):  # 48: vector quads; 50: scalar atomics
+    for grid in (48, 50):  # 48: full 8^3 tiles; 50: partial tiles at the upper faces
         s = pkg.Suspension(pos, body, L, xi=xi, grid=grid, P=12)
         w64 = s.apply_mobility(F, part=2, precision=FP64).reshape(-1)
         w32 = s.apply_mobility(F, part=2, precision=MIXED).reshape(-1)

@@ -204,8 +204,10 @@ def test_pair_normals_layout():
 
 
 def test_brownian_velocity_covariance_is_the_body_mobility():
-    # fluctuation-dissipation: with u^B = s M^(1/2) psi (all 11 components,
-    # reading r24) and F^B = s R^(1/2) psi_nf, s^2 = 2 kT/dt, the body
+    # fluctuation-dissipation: with u^B = s M^(1/2) psi (all 11 components:
+    # velocity, rotation and strain rows all carry noise, since eliminating
+    # F from the saddle system mixes the strain rows into the body
+    # velocities) and F^B = s R^(1/2) psi_nf, s^2 = 2 kT/dt, the body
     # velocities of the Brownian solve have covariance s^2 N, N the body
     # mobility (the solve's response to unit aggregate forces and torques).
     # Summed over an orthonormal basis of the noise the identity is exact.
@@ -238,7 +240,7 @@ def test_brownian_velocity_covariance_is_the_body_mobility():
     assert np.abs(Nm - Nm.T).max() < 1e-10 * np.abs(Nm).max()
     assert np.abs(cov - s * s * Nm).max() < 1e-9 * np.abs(s * s * Nm).max()
     # without the strain rows of u^B the far-field part of the identity
-    # fails (reading r24)
+    # fails: the stresslet constraint couples them into the body velocities
     covf = np.zeros_like(cov)
     covf6 = np.zeros_like(cov)
     for k in range(11 * Nt):

@@ -51,3 +51,34 @@ def test_two_beads_far_box_reduce_to_free_pair():
     diff = M[1, :3, 0, :3] - M[0, :3, 0, :3]
     ref = O.free_blocks(x[None])[0][:3, :3] - O.self_block()[:3, :3]
     assert np.abs(diff - ref).max() < 2e-4 * np.abs(ref).max()
+
+
+def test_applied_wave_sum_equals_dense_wave_matrix():
+    # the matrix-free form of the wave-space sum (used where the dense matrix
+    # of a fine grid's wave-vector range is too large) against the dense one,
+    # in the cube and in a Lees-Edwards box, with several k chunks
+    rng = np.random.default_rng(21)
+    L = 11.0
+    pos = rng.uniform(0, L, size=(5, 3))
+    F = rng.normal(size=(5, 11))
+    for tilt in (0.0, 2.3):
+        Md = O.mobility_wave_dense(pos, L, 0.9, 6.0, tilt=tilt).reshape(55, 55)
+        u = O.mobility_wave_apply(pos, F, L, 0.9, 6.0, tilt=tilt, chunk=700)
+        ref = (Md @ F.reshape(-1)).reshape(5, 11)
+        assert np.abs(u - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_applied_wave_sum_completes_the_split_independently_of_xi():
+    # real-space part (dense) + applied wave-space part = the same periodic
+    # mobility for two splitting parameters (the Ewald sum does not depend on xi)
+    rng = np.random.default_rng(22)
+    L = 13.0
+    pos = rng.uniform(0, L, size=(4, 3))
+    F = rng.normal(size=(4, 11))
+    res = []
+    for xi in (0.7, 1.1):
+        rc = 2.0 + np.sqrt(46.0) / xi
+        Mr = O.mobility_real_dense(pos, L, xi, rc).reshape(44, 44)
+        uw = O.mobility_wave_apply(pos, F, L, xi, 2.0 * xi * np.sqrt(46.0))
+        res.append(Mr @ F.reshape(-1) + uw.reshape(-1))
+    assert np.abs(res[0] - res[1]).max() < 1e-11 * np.abs(res[0]).max()
