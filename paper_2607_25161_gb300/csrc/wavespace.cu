@@ -293,11 +293,16 @@ __device__ __forceinline__ void stockham_stage(const Cx<T> *in, Cx<T> *out, int 
     const Cx<T> *src = in + line * ls;
     Cx<T> v[R];
     v[0] = src[fpad(j)];
+    if (Ns == 1) {  // first stage: every twiddle is 1
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      Cx<T> w = tw[(r - 1) * Ns + k];
-      w.y *= -sg;  // tables hold the forward twiddles
-      v[r] = cmul(src[fpad(j + r * nb)], w);
+      for (int r = 1; r < R; ++r) v[r] = src[fpad(j + r * nb)];
+    } else {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        Cx<T> w = tw[(r - 1) * Ns + k];
+        w.y *= -sg;  // tables hold the forward twiddles
+        v[r] = cmul(src[fpad(j + r * nb)], w);
+      }
     }
     dft_small<T, R>(v, sg);
     Cx<T> *dst = out + line * ls;
