@@ -533,8 +533,9 @@ def run_ours(args, rank, world, local_rank):
             "iters_per_step": itw / args.steps,
             "note": "same workload and tolerance; GMRES starts from the previous step's solution"}
 
-    # ---- Brownian step: fsd_brownian (PSE far-field slip, near-field force,
-    #      Lanczos square roots) before each step, kT = 1 (same workload)
+    # ---- Brownian step: fsd_brownian (PSE far-field slip: analytic wave
+    #      part + Lanczos real-space square root; near-field force by the
+    #      default pairwise sampler) before each step, kT = 1 (same workload)
     s = make(pkg.FSD_MIXED)
     for k in range(args.warmup):
         s.brownian(1.0, w["dt"], seed=11, step=k, outputs=False)
@@ -559,11 +560,12 @@ def run_ours(args, rank, world, local_rank):
     msb = max_over_ranks(eb0.elapsed_time(eb1))
     brown = {"value": Nt * args.steps * world / (msb / 1e3), "ms_per_step": msb / args.steps,
              "kT": 1.0, "dt": w["dt"], "iters_per_step": itb / args.steps,
-             "lanczos_real_per_step": lz_r / args.steps, "lanczos_near_per_step": lz_n / args.steps,
-             "lanczos_last_change_max": lz_ch,
+             "lanczos_real_per_step": lz_r / args.steps, "lanczos_real_last_change_max": lz_ch,
+             "near_field_sampler": "pairwise (library default): sum_p K_p^T psi_p, K_p the pair model's "
+                                   "dissipation-form factor; covariance exactly R_FU^nf, no iteration",
              "note": "each step: PSE far-field slip (analytic wave part + Lanczos real-space square root, "
-                     "FP32 operator) and near-field Brownian force (Lanczos, FP64), then the mixed solve "
-                     "with them; drift not included (see brownian_drift)"}
+                     "FP32 operator) and the near-field Brownian force, then the mixed solve with them; "
+                     "drift not included (see brownian_drift)"}
 
     # ---- sheared periodic box: the same workload stepped with
     #      FSD_FLAG_LEES_EDWARDS (bodies move by their full velocity, the box
@@ -590,9 +592,10 @@ def run_ours(args, rank, world, local_rank):
             "iters_first_last": [its_le[0], its_le[-1]], "tilt_end": tilt_end,
             "note": "Lees-Edwards box (sheared images), full velocity, host-driven steps"}
 
-    # ---- the same Brownian step with the pairwise near-field sampler
+    # ---- the same Brownian step with the paper's near-field sampler
+    #      (preconditioned Lanczos, Sec. 2.2)
     s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED,
-                       **dict(common, nf_sampler=pkg.FSD_NF_PAIRWISE))
+                       **dict(common, nf_sampler=pkg.FSD_NF_LANCZOS))
     for k in range(min(args.warmup, 3)):
         s.brownian(1.0, w["dt"], seed=11, step=k, outputs=False)
         s.step(None, w["shear"], w["dt"])
@@ -601,17 +604,23 @@ def run_ours(args, rank, world, local_rank):
     ep0 = torch.cuda.Event(enable_timing=True)
     ep1 = torch.cuda.Event(enable_timing=True)
     ep0.record(stream)
+    lz_n = 0
+    lz_ch = 0.0
     for k in range(args.steps):
-        s.brownian(1.0, w["dt"], seed=11, step=1000 + k, outputs=False)
+        _, _, stl = s.brownian(1.0, w["dt"], seed=11, step=1000 + k, outputs=False)
+        lz_n += stl["outer_iters"]
+        lz_ch = max(lz_ch, stl["rel_residual"])
         s.step(None, w["shear"], w["dt"])
     ep1.record(stream)
     torch.cuda.synchronize()
     s.close()
     msp = max_over_ranks(ep0.elapsed_time(ep1))
-    brown["pairwise_near_field"] = {
+    brown["lanczos_near_field"] = {
         "value": Nt * args.steps * world / (msp / 1e3), "ms_per_step": msp / args.steps,
-        "note": "near-field force by the pairwise decomposition sum_p K_p^T psi_p, K_p the pair "
-                "model's dissipation-form factor (exact covariance, no Lanczos)"}
+        "lanczos_near_per_step": lz_n / args.steps, "lanczos_last_change_max": lz_ch,
+        "note": "near-field force by the paper's preconditioned Lanczos (block-Cholesky "
+                "preconditioner, stopping at lanczos_tol 1e-7 or 60 steps; the last relative change "
+                "is reported)"}
 
     # ---- Brownian step with the drift (Sec. 2.4; appendix on the drift):
     #      fsd_brownian, fsd_drift (two solves at displaced configurations),
@@ -1141,6 +1150,130 @@ def run_rods(args, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------- configurations 2 and 5
+# Config 2: 512 x 8-bead aggregates (4096 beads) at phi 0.1, shear 1,
+# lubrication 3a, the plain FP64 method with xi = 25/L (the size rule) and
+# xi = 0.5, 100 steps.  Config 5: 16-bead aggregates, lubrication 3a, shear
+# 0.1, Brownian (kT 1, PSE), mixed, xi = 0.5 and 25/L, scaling in N at
+# 32768, 65536, 131072 and 262144 beads.
+CFG2 = dict(n_agg=512, n_b=8, phi=0.1, seed=2, shear=1.0, lub=3.0, tol=1e-6, dt=1e-3, rp=2.0)
+CFG5 = dict(n_b=16, phi=0.24, seed=5, shear=0.1, lub=3.0, tol=1e-6, dt=1e-3, rp=2.0, kT=1.0,
+            base_aggs=(256, 512, 1024, 2048))
+
+
+def _cfg5_base(n_agg):
+    import synth
+
+    c = CFG5
+    return synth.dense_suspension(n_agg, c["n_b"], c["phi"], c["seed"])
+
+
+def _time_steps(pkg, s, stream, K, warm, shear, dt, brownian_kT=0.0):
+    import torch
+
+    def one(k):
+        if brownian_kT > 0:
+            s.brownian(brownian_kT, dt, seed=17, step=k, outputs=False)
+        st, _ = s.step(None, shear, dt)
+        return st
+    for k in range(warm):
+        one(k)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = launches = 0
+    for k in range(K):
+        st = one(100 + k)
+        its += st["iters"]
+        launches += st["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K, its / K, launches
+
+
+def run_configs(args, local_rank):
+    """Configurations 2 and 5: one JSON line with every point."""
+    import multiprocessing as mp
+
+    c5 = CFG5
+    pool = mp.get_context("spawn").Pool(len(c5["base_aggs"]))
+    bases = pool.imap(_cfg5_base, c5["base_aggs"])  # smallest first
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import synth
+    import paper_2607_25161_gb300 as pkg
+    from __graft_entry__ import build
+
+    build()
+    stream = torch.cuda.Stream()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    launches = 0
+    # ---- config 2
+    c2 = CFG2
+    pos, body, L = synth.suspension(c2["n_agg"], c2["n_b"], c2["phi"], c2["seed"])
+    L2 = L
+    K2 = args.steps
+    cfg2 = []
+    for prec, pname in ((pkg.FSD_FP64, "fp64"), (pkg.FSD_MIXED, "mixed")):
+        for xi_mode in ("25/L", "0.5"):
+            xi = 25.0 / L if xi_mode == "25/L" else 0.5
+            s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=prec, xi=xi,
+                               lub_cutoff=c2["lub"], tol=c2["tol"], precond_cutoff=c2["rp"],
+                               flags=pkg.FSD_FLAG_COMOVING | pkg.FSD_FLAG_GRAPH)
+            prm = s.params
+            ms, its, nl = _time_steps(pkg, s, stream, K2, 3, c2["shear"], c2["dt"])
+            launches += nl
+            s.close()
+            cfg2.append({"precision": pname, "xi": xi_mode, "xi_value": round(xi, 4),
+                         "rc": round(prm["rc"], 3), "grid": prm["grid"], "ms_per_step": round(ms, 4),
+                         "bead_steps_per_s": len(pos) * 1e3 / ms, "iters_per_step": its})
+            print(json.dumps(dict(cfg2[-1], config=2)), file=sys.stderr, flush=True)
+    # ---- config 5: each size is the 2 x 2 x 2 periodic replica of a base box
+    cfg5 = []
+    K5 = max(3, min(args.steps, 10))
+    for n_agg, (bp, bb, bL) in zip(c5["base_aggs"], bases):
+        pos, body, Ls = synth.replicate_box(bp, bb, bL, (2, 2, 2))
+        L = Ls[0]
+        phi = len(pos) * 4.0 / 3.0 * np.pi / L ** 3
+        for xi_mode in ("0.5", "25/L"):
+            xi = 25.0 / L if xi_mode == "25/L" else 0.5
+            s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED, xi=xi,
+                               lub_cutoff=c5["lub"], tol=c5["tol"], precond_cutoff=c5["rp"],
+                               flags=pkg.FSD_FLAG_COMOVING | pkg.FSD_FLAG_GRAPH)
+            prm = s.params
+            ms, its, nl = _time_steps(pkg, s, stream, K5, 3, c5["shear"], c5["dt"], c5["kT"])
+            launches += nl
+            s.close()
+            cfg5.append({"beads": len(pos), "aggregates": int(body.max()) + 1, "L": round(L, 3),
+                         "phi": round(phi, 4), "xi": xi_mode, "xi_value": round(xi, 4),
+                         "rc": round(prm["rc"], 3), "grid": prm["grid"], "ms_per_step": round(ms, 3),
+                         "bead_steps_per_s": len(pos) * 1e3 / ms, "t_s_us": 1e3 * ms / len(pos),
+                         "iters_per_step": its})
+            print(json.dumps(dict(cfg5[-1], config=5)), file=sys.stderr, flush=True)
+    pool.close()
+    pool.join()
+    clocks = clk.stop()
+    head = next(p for p in cfg5 if p["beads"] == 262144 and p["xi"] == "0.5")
+    line = {
+        "metric": "bead-steps/sec of configurations 2 (FP64, 4096 beads) and 5 (Brownian, 32k-262k beads)",
+        "value": head["bead_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": K5, "warmup": 3,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "value = config 5 at 262144 beads, xi 0.5",
+                   "config2": "512 x 8-bead aggregates, phi 0.1, L %.2f, shear 1, lubrication 3a, GMRES 1e-6, "
+                              "%d timed steps after 3; FP64 (the config) and mixed" % (L2, K2),
+                   "config5": "16-bead aggregates at phi %.2f (the densest reachable: see DESIGN), each size the "
+                              "2x2x2 periodic replica of a generated box of 1/8 the beads; shear 0.1, lubrication "
+                              "3a, Brownian kT 1 (PSE far field, pairwise near field), mixed, GMRES 1e-6, %d timed "
+                              "steps after 3" % (c5["phi"], K5)},
+        "config2": cfg2, "config5": cfg5, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1148,7 +1281,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="step",
-                    choices=("step", "batch", "rods", "seeds", "oracle-ladder"))
+                    choices=("step", "batch", "rods", "seeds", "oracle-ladder", "configs"))
     ap.add_argument("--profile-run", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1176,6 +1309,10 @@ def main():
     if args.workload == "seeds":
         if rank == 0:
             run_seeds(args, local_rank)
+        return
+    if args.workload == "configs":
+        if rank == 0:
+            run_configs(args, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

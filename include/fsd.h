@@ -160,12 +160,15 @@ typedef struct {
                             modulo L into [-L/2, L/2) (0: the cube).  With a
                             non-zero tilt (or FSD_FLAG_LEES_EDWARDS) R_c and
                             the lubrication cut-off must stay below 0.447 L    */
-  int nf_sampler;        /* fsd_brownian's near-field force: FSD_NF_LANCZOS (0,
-                            the paper's preconditioned Lanczos) or
-                            FSD_NF_PAIRWISE (sum over lubrication pairs of
+  int nf_sampler;        /* fsd_brownian's near-field force: FSD_NF_PAIRWISE
+                            (fsd_default_params: sum over lubrication pairs of
                             K_p^T psi_p, K_p the pair's dissipation-form
                             factor: exact covariance R_FU^nf, no iteration;
-                            pair noise from Philox stream 5)                  */
+                            pair noise from Philox stream 5) or
+                            FSD_NF_LANCZOS (0: the paper's preconditioned
+                            Lanczos, Sec. 2.2; stops after lanczos_max_iter
+                            steps, short of lanczos_tol on dense lubricated
+                            suspensions)                                       */
 } fsd_params;
 
 typedef struct {

@@ -605,6 +605,8 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   FSD_CUDA(cudaMallocHost(&c.h_pinned, 512 * sizeof(double)));
   build_real_table(c);
   build_wave(c);
+  c.tilt_dev.alloc(1);
+  sync_tilt(c);
   launch_wrap_positions(c);
   FSD_CUDA(cudaStreamSynchronize(c.stream));
 }
@@ -710,9 +712,18 @@ static fsd_status solve_internal(Ctx &c, const double *ft_user, double shear, do
 //      then the whole solve (+ update) as one graph launch; the end half
 //      waits and turns the device state into a status.
 static bool use_graph(const Ctx &c) {
-  // a Lees-Edwards step changes the box offset, which the kernels take as an
-  // argument: those steps run host-driven
-  return (c.prm.flags & FSD_FLAG_GRAPH) && !c.prof && !(c.prm.flags & FSD_FLAG_LEES_EDWARDS);
+  // Lees-Edwards steps too: their operator kernels read the box offset from
+  // device memory, which the host updates between graph launches
+  return (c.prm.flags & FSD_FLAG_GRAPH) && !c.prof;
+}
+
+// After a Lees-Edwards step the images across y have moved with the imposed
+// flow: offset += shear L dt (host value and device copy).
+static void advance_tilt(Ctx &c, double shear_rate, double dt) {
+  if (!(c.prm.flags & FSD_FLAG_LEES_EDWARDS)) return;
+  c.tilt = wrap_tilt(c.tilt + shear_rate * c.L * dt, c.L);
+  c.prm.tilt = c.tilt;
+  sync_tilt(c);
 }
 
 struct StepMark {
@@ -727,6 +738,7 @@ static StepMark graph_step_begin(Ctx &c, const double *ft_user, double shear, bo
   mk.l0 = c.launches;
   if (!c.geom_fresh) prepare(c);
   c.geom_fresh = false;
+  refresh_le_tables(c);  // Lees-Edwards: the sheared Green's factors of this offset
   GraphRun o;
   o.warm = (c.prm.flags & FSD_FLAG_WARM_START) && c.have_prev;
   o.has_ft = ft_user != nullptr;
@@ -1082,6 +1094,10 @@ void fsd_default_params(fsd_params *p) {
   p->tile = 0;
   p->lanczos_tol = 1e-7;
   p->lanczos_max_iter = 60;
+  // the pairwise near-field sampler is exact and needs no iteration; the
+  // paper's preconditioned Lanczos stops at its step limit on dense
+  // lubricated suspensions (FSD_NF_LANCZOS selects it)
+  p->nf_sampler = FSD_NF_PAIRWISE;
 }
 
 fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
@@ -1172,6 +1188,7 @@ fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque, double shear_r
     const StepMark mk = graph_step_begin(c, agg_force_torque, shear_rate, false, true, dt);
     fsd_status st = graph_step_end(c, mk, stats);
     if (st != FSD_OK && st != FSD_ENOCONV && st != FSD_EOVERLAP) return st;
+    advance_tilt(c, shear_rate, dt);
     const int64_t l1 = c.launches;
     if (agg_velocity) bodies_out(c, vel_int, agg_velocity, 6);
     if (stats) stats->kernel_launches += c.launches - l1;
@@ -1184,11 +1201,7 @@ fsd_status fsd_step(fsd_ctx *ctx, const double *agg_force_torque, double shear_r
   const int64_t l1 = c.launches;
   if (agg_velocity) bodies_out(c, vel_int, agg_velocity, 6);
   launch_integrate(c, vel_int, dt, shear_rate);
-  if (c.prm.flags & FSD_FLAG_LEES_EDWARDS) {
-    // the images across y move with the imposed flow: offset += shear L dt
-    c.tilt = wrap_tilt(c.tilt + shear_rate * c.L * dt, c.L);
-    c.prm.tilt = c.tilt;
-  }
+  advance_tilt(c, shear_rate, dt);
   launch_wrap_positions(c);
   FSD_CUDA(cudaStreamSynchronize(c.stream));
   if (stats) stats->kernel_launches += c.launches - l1;
@@ -1452,6 +1465,7 @@ fsd_status fsd_set_tilt(fsd_ctx *ctx, double tilt) {
     throw Invalid{"in a Lees-Edwards box R_c and the lubrication cut-off must be below 0.447 L"};
   c.tilt = t;
   c.prm.tilt = t;
+  sync_tilt(c);
   launch_wrap_positions(c);
   FSD_CUDA(cudaStreamSynchronize(c.stream));
   c.geom_fresh = false;
@@ -1682,10 +1696,7 @@ static fsd_status batch_run(fsd_batch *b, const double *ft, const double *shear_
           st[s] = solve_internal(c, fts, shear_rates[s], c.t1.p, str_int, stats ? stats + s : nullptr, 0.0);
           if (integrate && status_rank(st[s]) < 3) {
             launch_integrate(c, c.t1.p, dt, shear_rates[s]);
-            if (c.prm.flags & FSD_FLAG_LEES_EDWARDS) {
-              c.tilt = wrap_tilt(c.tilt + shear_rates[s] * c.L * dt, c.L);
-              c.prm.tilt = c.tilt;
-            }
+            advance_tilt(c, shear_rates[s], dt);
             launch_wrap_positions(c);
           }
         }
@@ -1706,7 +1717,10 @@ static fsd_status batch_run(fsd_batch *b, const double *ft, const double *shear_
   for (int s : b->order) {
     Ctx &c = b->sys[s]->c;
     try {
-      if (launched[s]) st[s] = graph_step_end(c, mk[s], stats ? stats + s : nullptr);
+      if (launched[s]) {
+        st[s] = graph_step_end(c, mk[s], stats ? stats + s : nullptr);
+        if (integrate && status_rank(st[s]) < 3) advance_tilt(c, shear_rates[s], dt);
+      }
       if (status_rank(st[s]) < 3) {
         if (vel) bodies_out(c, c.t1.p, vel + 6 * b->agg_off[s], 6);
         if (str) bodies_out(c, c.res.p, str + 9 * b->agg_off[s], 9);

@@ -172,6 +172,10 @@ struct Ctx {
   // Lees-Edwards box: offset of the image across y (0: cube); wave-space
   // positions in sheared coordinates s = (x - (tilt/L) y, y, z), wrapped
   double tilt = 0.0;
+  // device copy of tilt: with FSD_FLAG_LEES_EDWARDS the operator kernels read
+  // the offset from it, so that a captured step graph follows the offset
+  // (written on the stream whenever tilt changes)
+  DBuf<double> tilt_dev;
   DBuf<double> wpos64;
   DBuf<float> wpos32;
   // ---- neighbour lists
@@ -286,6 +290,18 @@ __global__ void k_exclusive_scan(int n, const int *__restrict__ in, int *out, in
 __global__ void k_sort_cells(int ncells, const int *__restrict__ cell_start, int *cell_beads);
 // wavespace.cu: per-tile bead lists of the grid-centric spreading
 void build_spread_tiles(Ctx &c);
+// Lees-Edwards offset as the kernels take it: the host value and, with
+// FSD_FLAG_LEES_EDWARDS, the device copy they read instead.
+struct TauArg {
+  double tau = 0.0;             // tilt / L (host value)
+  const double *dev = nullptr;  // device tilt (overrides tau when set)
+  double invL = 0.0;
+};
+__device__ __forceinline__ double tau_of(const TauArg &t) { return t.dev ? *t.dev * t.invL : t.tau; }
+const double *tilt_dev_ptr(const Ctx &c);
+TauArg tau_arg(const Ctx &c);
+void sync_tilt(Ctx &c);
+void refresh_le_tables(Ctx &c);
 int realspace_group(const Ctx &c);   // lanes per bead of the pair sum
 
 // wavespace.cu

@@ -43,7 +43,7 @@ struct GState {
 };
 
 struct GraphKey {
-  int mixed, warm, has_ft, integrate, with_str, group, lub, brown, add_vel, str_hydro;
+  int mixed, warm, has_ft, integrate, with_str, group, lub, brown, add_vel, str_hydro, le;
   double shear, dt, brown_scale, tilt;
   const void *nbr, *lnbr, *bcol, *bval64, *bval32, *packed64, *packed32;
   int cap, lcap;
@@ -529,7 +529,10 @@ static GraphKey make_key(Ctx &c, const GraphRun &o) {
   k.brown = o.brown;
   k.brown_scale = o.brown ? o.brown_scale : 0.0;
   k.add_vel = o.add_vel;
-  k.tilt = c.tilt;
+  // a Lees-Edwards context's kernels read the offset from device memory: one
+  // graph serves every offset
+  k.le = tilt_dev_ptr(c) != nullptr;
+  k.tilt = k.le ? 0.0 : c.tilt;
   k.str_hydro = o.str_hydro;
   k.nbr = c.nbr.p;
   k.lnbr = c.lnbr.p;

@@ -226,6 +226,17 @@ __global__ void k_wrap_positions(int Nt, double L, double tilt, const int *__res
   wpos32[i] = make_float4((float)sx, (float)y, (float)z, 0.f);
 }
 
+__global__ void k_set_scalar(double *p, double v) { *p = v; }
+
+// Device copy of the box offset (read by the operator kernels of a
+// Lees-Edwards context); never called inside a stream capture.
+void sync_tilt(Ctx &c) {
+  if (!c.tilt_dev.p) return;
+  k_set_scalar<<<1, 1, 0, c.stream>>>(c.tilt_dev.p, c.tilt);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
 void launch_wrap_positions(Ctx &c) {
   c.tiles_valid = false;  // the spreading tiles follow the positions
   k_wrap_positions<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(
@@ -642,7 +653,8 @@ __global__ void __launch_bounds__(256, 4) k_realspace(
     const int *__restrict__ ncnt, int cap, const double *__restrict__ x, double *__restrict__ y,
     const T *__restrict__ tab_g, int nint, T inv_h, T L, T tilt, T a, T c8, T self_t, T self_r,
     T self_s, int add_constraint, const int *__restrict__ bead_body,
-    const double4 *__restrict__ lever, int Nt_off) {
+    const double4 *__restrict__ lever, int Nt_off, const double *__restrict__ tilt_dev) {
+  if (tilt_dev) tilt = (T)*tilt_dev;  // Lees-Edwards steps: the offset in device memory
   // the radial table is staged once per (persistent) CTA in shared memory
   extern __shared__ __align__(16) unsigned char tab_raw[];
   T *tab = (T *)tab_raw;
@@ -825,7 +837,7 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, b
         c.Nt, op.packed.p, c.nbr.p, c.ncnt.p, c.cap, x, y, op.table.p, c.tab_nint, inv_h,    \
         (T)c.L, (T)c.tilt, (T)c.a, c8, op.self_real[0], op.self_real[1], op.self_real[2],  \
         add_constraint ? 1 : 0, c.bead_body.p, (const double4 *)c.lever64.p,                 \
-        (int)(LDB * (int64_t)c.Nt));                                                         \
+        (int)(LDB * (int64_t)c.Nt), tilt_dev_ptr(c));                                        \
   }
   switch (G) {
     case 32: FSD_RS_LAUNCH(32); FSD_LAUNCHED(c); break;

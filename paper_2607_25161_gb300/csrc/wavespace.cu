@@ -670,6 +670,9 @@ __global__ void __launch_bounds__(1024) k_fft_xy_inv(T *field, const Cx<T> *__re
 // (the same expression the cubic table holds, with k_s = k there).
 struct GreenLE {
   double tau = 0.0, ks2 = 0.0, xi = 0.0, alpha = 0.0, a = 0.0, eta = 0.0, inv_n3 = 0.0;
+  int on = 0;                   // sheared box: the tabulated factors and the physical k
+  const double *dev = nullptr;  // device tilt (overrides tau when set)
+  double invL = 0.0;
   double isv = 0.0;  // 1 / sqrt(V): the Brownian wave-field scale
 };
 
@@ -758,6 +761,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
   Cx<T> *Z = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(-1));
   // Green's function, one (kx, ky, kz) per thread iteration
   const int ky = yy <= n / 2 ? yy : yy - n;
+  const double le_tau = le.dev ? *le.dev * le.invL : le.tau;
   for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
     const int t = e & (TX - 1), zz = e >> LTX;
     const int kx = kx0 + t;
@@ -773,7 +777,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     Cx<T> oD[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     if (m > 0 && kx < nh) {
       T t1, t2, t3, kk[3], im;
-      if (le.tau == 0.0) {
+      if (!le.on) {
         t1 = green[3 * m];
         t2 = green[3 * m + 1];
         t3 = green[3 * m + 2];
@@ -787,7 +791,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
         // (kx, ky - tau kx, kz) (in 2 pi / L).  The window factor stays on
         // |k_s|^2; H(k), 1/k^2, the form factors and the projection take
         // the physical k (evaluated here in FP64)
-        const double kyp = (double)ky - le.tau * (double)kx;
+        const double kyp = (double)ky - le_tau * (double)kx;
         const double mp = (double)kx * kx + kyp * kyp + (double)kz * kz;
         // factors of this box offset, tabulated once per offset
         const T *gq = gle + 3 * (((size_t)yy * nh + kx) * n + zz);
@@ -983,7 +987,8 @@ constexpr int kMaxP = 24;
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread(int Nt, const typename V4Of<T>::type *__restrict__ pos,
                                                 const double *__restrict__ x, T *grid, int n, int P,
-                                                T h, T alpha, T cnorm, T tau) {
+                                                T h, T alpha, T cnorm, TauArg ta_) {
+  const T tau = (T)tau_of(ta_);
   __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP];
   __shared__ int si[8][3][kMaxP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1049,7 +1054,8 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
 
 __global__ void __launch_bounds__(256) k_spread_v4(int Nt, const float4 *__restrict__ pos,
                                                    const double *__restrict__ x, float *grid, int n,
-                                                   int P, float h, float alpha, float cnorm, float tau) {
+                                                   int P, float h, float alpha, float cnorm, TauArg ta_) {
+  const float tau = (float)tau_of(ta_);
   __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
   __shared__ int si[8][2][kMaxP];
   __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
@@ -1127,7 +1133,8 @@ __global__ void __launch_bounds__(256) k_spread_v4(int Nt, const float4 *__restr
 template <typename T, bool PL>
 __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::type *__restrict__ pos,
                                                 const T *__restrict__ grid, double *y, int n, int P,
-                                                T h, T alpha, T cnorm_h3, double tau) {
+                                                T h, T alpha, T cnorm_h3, TauArg ta_) {
+  const double tau = tau_of(ta_);
   __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP];
   __shared__ int si[8][3][kMaxP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1214,7 +1221,8 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
 __global__ void __launch_bounds__(256, 4) k_interp_v4(int Nt, const float4 *__restrict__ pos,
                                                    const float *__restrict__ field, double *y, int n,
                                                    int P, float h, float alpha, float cnorm_h3,
-                                                   double tau) {
+                                                   TauArg ta_) {
+  const double tau = tau_of(ta_);
   __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
   __shared__ int si[8][2][kMaxP];
   __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
@@ -1358,12 +1366,13 @@ __global__ void k_tile_bin(int Nt, const float4 *__restrict__ pos, float h, int 
 // a warp runs the largest count among its rows instead of every bead listed
 // for the tile.
 __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, float h, float alpha,
-                                                      float cnorm, float tau,
+                                                      float cnorm, TauArg ta_,
                                                       const float4 *__restrict__ pos,
                                                       const double *__restrict__ x,
                                                       const int *__restrict__ tile_start,
                                                       const int *__restrict__ tile_beads,
                                                       float *grid) {
+  const float tau = (float)tau_of(ta_);
   // records padded to an odd number of 16-byte units (bank spread when the
   // lanes of a warp read different beads)
   __shared__ __align__(16) float swx[kTCH][20];      // w[8], w * offset[8], pad
@@ -1668,14 +1677,14 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
     k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p,
                                                          (const float *)op.gout.p, y, n, P,
                                                          (float)h, (float)alpha, (float)(cn * h3),
-                                                         c.tilt / c.L);
+                                                         tau_arg(c));
   else if (planar)
     k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
-                                                              h, alpha, (T)(cn * h3), c.tilt / c.L);
+                                                              h, alpha, (T)(cn * h3), tau_arg(c));
   else
     k_interp<T, false><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
                                                                P, h, alpha, (T)(cn * h3),
-                                                               c.tilt / c.L);
+                                                               tau_arg(c));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -1715,6 +1724,47 @@ void build_spread_tiles(Ctx &c) {
   c.tiles_valid = true;
 }
 
+const double *tilt_dev_ptr(const Ctx &c) {
+  return (c.prm.flags & FSD_FLAG_LEES_EDWARDS) && c.tilt_dev.p ? c.tilt_dev.p : nullptr;
+}
+
+TauArg tau_arg(const Ctx &c) {
+  TauArg t;
+  t.tau = c.tilt / c.L;
+  t.dev = tilt_dev_ptr(c);
+  t.invL = 1.0 / c.L;
+  return t;
+}
+
+// Sheared-lattice Green's function factors of the current offset (built on
+// the stream; a captured step graph reads them through the same pointer).
+template <typename T>
+static void refresh_le_table(Ctx &c, OpData<T> &op) {
+  if (op.green_le_tilt == c.tilt && op.green_le.p) return;
+  const int n = c.n, nh = n / 2 + 1;
+  GreenLE le;
+  le.on = 1;
+  le.tau = c.tilt / c.L;
+  le.ks2 = (2.0 * kPi / c.L) * (2.0 * kPi / c.L);
+  le.xi = c.xi;
+  le.alpha = c.alpha;
+  le.a = c.a;
+  le.eta = c.eta;
+  le.inv_n3 = 1.0 / ((double)n * n * n);
+  const size_t cnt = (size_t)3 * n * nh * n;
+  if (op.green_le.n < cnt) op.green_le.alloc(cnt);
+  k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(n, le, op.green_le.p);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+  op.green_le_tilt = c.tilt;
+}
+
+void refresh_le_tables(Ctx &c) {
+  if (!tilt_dev_ptr(c)) return;
+  refresh_le_table<double>(c, opd<double>(c));
+  if (c.prm.precision == FSD_MIXED) refresh_le_table<float>(c, opd<float>(c));
+}
+
 template <typename T>
 void launch_wavespace(Ctx &c, const double *x, double *y) {
   OpData<T> &op = opd<T>(c);
@@ -1728,7 +1778,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     if (!c.tiles_valid) build_spread_tiles(c);
     const int nt = c.tile_n;
     k_spread_gather<<<nt * nt * nt, 64, 0, c.stream>>>(n, nt, P, (float)h, (float)alpha, (float)cn,
-                                                       (float)(c.tilt / c.L), (const float4 *)c.wpos32.p,
+                                                       tau_arg(c), (const float4 *)c.wpos32.p,
                                                        x, c.tile_start.p, c.tile_beads.p,
                                                        (float *)op.grid.p);
   } else {
@@ -1737,10 +1787,10 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     k_spread_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p, x,
                                                          (float *)op.grid.p, n, P, (float)h,
                                                          (float)alpha, (float)cn,
-                                                         (float)(c.tilt / c.L));
+                                                         tau_arg(c));
   else
     k_spread<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), x, op.grid.p, n, P, h,
-                                                        alpha, (T)cn, (T)(c.tilt / c.L));
+                                                        alpha, (T)cn, tau_arg(c));
   }
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
@@ -1787,8 +1837,11 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     set_smem<T>((const void *)k_fft_z_green<T>, sm);
     int blocks = n * ceil_div(nh, TX);
     GreenLE le;
-    if (c.tilt != 0.0) {
+    if (c.tilt != 0.0 || tilt_dev_ptr(c)) {
+      le.on = 1;
       le.tau = c.tilt / c.L;
+      le.dev = tilt_dev_ptr(c);
+      le.invL = 1.0 / c.L;
       le.ks2 = (2.0 * kPi / c.L) * (2.0 * kPi / c.L);
       le.xi = c.xi;
       le.alpha = c.alpha;
@@ -2062,7 +2115,7 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
     return FSD_ECUDA;
   const double cn = std::pow(alpha / kPi, 1.5);
   k_spread<float><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, x, gridp, n, P, (float)h, (float)alpha,
-                                               (float)cn, 0.f);
+                                               (float)cn, TauArg());
   const int ntw = plan.ntw;
   k_fft_x_fwd<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gridp, spec, plan, tw, 4);
@@ -2077,7 +2130,7 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   k_fft_x_inv<float><<<(n * n + 3) / 4, threads, (ntw + 2 * 3 * 4 * fft_ls(n)) * sizeof(Cx<float>),
                        st>>>(gout, spec, plan, tw, 4);
   k_interp<float, false><<<(nb + 7) / 8, 256, 0, st>>>(nb, pos4, gout, y, n, P, (float)h, (float)alpha,
-                                               (float)(cn * h * h * h), 0.0);
+                                               (float)(cn * h * h * h), TauArg());
   k_na_stage_out<<<(nb + 127) / 128, 128, 0, st>>>(nb, y, out);
   if (cudaGetLastError() != cudaSuccess) return FSD_ECUDA;
   return FSD_OK;

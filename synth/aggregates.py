@@ -30,6 +30,8 @@ __all__ = [
     "compress_suspension",
     "compress_mixed",
     "mixed_suspension",
+    "dense_suspension",
+    "replicate_box",
     "batch_workload",
     "rod",
     "rod_suspension",
@@ -456,6 +458,43 @@ def mixed_suspension(n_beads, phi, seed, size_lo=2, size_hi=64, a=1.0, h_gen=0.1
         return compress_mixed(shapes, phi, seed + 1, a, h_gen)
     pos, body = pack_suspension(shapes, L, rng, a, h_gen)
     return pos, body, L
+
+
+def dense_suspension(n_agg, n_b, phi, seed, a=1.0, h_gen=0.1):
+    """n_agg random-attachment aggregates of n_b beads at bead volume
+    fraction phi, compressed like the batched form's systems: where the
+    branched aggregates jam before phi (16-bead aggregates near phi = 0.3),
+    the densest packing reached is kept and its box L gives the actual
+    phi.  Returns (bead_pos, agg_id, L)."""
+    rng = np.random.default_rng(seed)
+    shapes = [random_attachment_aggregate(n_b, rng, a) for _ in range(n_agg)]
+    if phi <= 0.12:
+        L = box_for_phi(n_agg * n_b, phi, a)
+        pos, body = pack_suspension(shapes, L, rng, a, h_gen)
+        return pos, body, L
+    return compress_mixed(shapes, phi, seed + 1, a, h_gen)
+
+
+def replicate_box(pos, body, L, reps):
+    """Periodic replica of a cubic suspension: the box of side L tiled
+    reps = (rx, ry, rz) times (the larger box is a non-cubic periodic cell
+    when the reps differ).  Returns (bead_pos, agg_id, box sides); the copy
+    (i, j, k) is shifted by (i, j, k) L and its aggregate ids offset by the
+    number of aggregates before it.  A periodic suspension and its tiling are
+    the same infinite suspension, at the same volume fraction."""
+    pos = np.asarray(pos, dtype=np.float64)
+    body = np.asarray(body)
+    nb = int(body.max()) + 1
+    out_p, out_b = [], []
+    c = 0
+    for i in range(reps[0]):
+        for j in range(reps[1]):
+            for k in range(reps[2]):
+                out_p.append(pos + L * np.array([i, j, k], dtype=np.float64))
+                out_b.append(body + c * nb)
+                c += 1
+    return (np.concatenate(out_p), np.concatenate(out_b).astype(np.int32),
+            (L * reps[0], L * reps[1], L * reps[2]))
 
 
 def batch_workload(n_sys, seed, n_lo=256, n_hi=8192, phi_lo=0.05, phi_hi=0.3, size_lo=2,

@@ -23,7 +23,8 @@ from oracle import brownian_oracle as BO
 pytestmark = pytest.mark.gpu
 
 FP64, MIXED = 0, 1
-HI = dict(xi=1.2, P=16, xerr=1e-8, tol=1e-10, lub_cutoff=3.0)
+# the near-field noise these tests give is that of the Lanczos sampler
+HI = dict(xi=1.2, P=16, xerr=1e-8, tol=1e-10, lub_cutoff=3.0, nf_sampler=0)
 
 
 def rel(a, b):
@@ -185,7 +186,7 @@ def test_pairwise_near_field_sampler_matches_oracle(pkg, sysB):
     # the oracle's sampler
     d = sysB
     seed, step = 77, 5
-    s = pkg.Suspension(d["pos"], d["body"], d["L"], nf_sampler=pkg.FSD_NF_PAIRWISE, **HI)
+    s = pkg.Suspension(d["pos"], d["body"], d["L"], **dict(HI, nf_sampler=pkg.FSD_NF_PAIRWISE))
     slip, fnf, st = s.brownian(1.0, 1.0, seed=seed, step=step, psi_real=np.zeros_like(d["psi_r"]))
     with pytest.raises(pkg.FsdError):
         s.brownian(1.0, 1.0, psi_nf=d["psi_nf"])  # the pair noise is drawn, not given

@@ -21,7 +21,8 @@ from oracle import drift_oracle as DO
 pytestmark = pytest.mark.gpu
 
 FP64, MIXED = 0, 1
-HI = dict(xi=1.2, P=16, xerr=1e-8, tol=1e-10, lub_cutoff=3.0)
+# the near-field noise these tests give is that of the Lanczos sampler
+HI = dict(xi=1.2, P=16, xerr=1e-8, tol=1e-10, lub_cutoff=3.0, nf_sampler=0)
 
 
 def rel(a, b):

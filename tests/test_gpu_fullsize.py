@@ -113,7 +113,7 @@ def test_fullsize_brownian_wave_sample_linear_and_scaled(big):
     from oracle import brownian_oracle as BO
 
     pkg, pos, body, L = big["pkg"], big["pos"], big["body"], big["L"]
-    s = pkg.Suspension(pos, body, L, precision=MIXED, **PARAMS)
+    s = pkg.Suspension(pos, body, L, precision=MIXED, nf_sampler=pkg.FSD_NF_LANCZOS, **PARAMS)
     n = s.params["grid"]
     rng = np.random.default_rng(43)
     f1 = BO.hermitian_field(n, rng)

@@ -136,7 +136,7 @@ def test_brownian_slip_with_tilt(pkg, sysLE, prec, tol):
     # root of the sheared real-space part, against the dense oracle
     pos, body, L = sysLE
     tilt = 0.27 * L
-    s = pkg.Suspension(pos, body, L, tilt=tilt, precision=prec, **HI)
+    s = pkg.Suspension(pos, body, L, tilt=tilt, precision=prec, nf_sampler=pkg.FSD_NF_LANCZOS, **HI)
     prm = s.params
     n, xi = prm["grid"], prm["xi"]
     rng = np.random.default_rng(17)
@@ -224,3 +224,32 @@ def test_pairwise_near_field_sampler_with_tilt(pkg):
     # in the cube the same beads have no near pairs at all
     assert np.abs(BO.pairwise_nf_force(unw, body, L, seed, step, rlub=3.0)).max() == 0.0
     assert rel(fnf / np.sqrt(2.0), ref) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_graph_lees_edwards_steps_match_host_driven(pkg, sysLE, prec):
+    # with FSD_FLAG_GRAPH a Lees-Edwards step is one captured graph whose
+    # kernels read the box offset from device memory (one graph for every
+    # offset); five steps must reproduce the host-driven loop's velocities,
+    # beads, orientations and offsets
+    pos, body, L = sysLE
+    gamma, dt = 0.7, 0.04
+    out = []
+    for flags in (pkg.FSD_FLAG_LEES_EDWARDS, pkg.FSD_FLAG_LEES_EDWARDS | pkg.FSD_FLAG_GRAPH):
+        s = pkg.Suspension(pos, body, L, flags=flags, lub_cutoff=3.0, tilt=0.2 * L, precision=prec,
+                           **HI)
+        vels, tilts = [], []
+        for _ in range(5):
+            vel = np.zeros((body.max() + 1, 6))
+            s.step(None, gamma, dt, vel=vel)
+            vels.append(vel)
+            tilts.append(s.params["tilt"])
+        p, q = s.beads()
+        s.close()
+        out.append((np.array(vels), np.array(tilts), p, q))
+    (v0, t0, p0, q0), (v1, t1, p1, q1) = out
+    assert np.allclose(t1, t0, rtol=0, atol=1e-12)
+    assert abs(t0[0] - (0.2 * L + gamma * L * dt)) < 1e-12
+    assert rel(v1, v0) < 1e-9
+    assert np.allclose(p1, p0, rtol=0, atol=1e-9)
+    assert np.allclose(q1, q0, rtol=0, atol=1e-12)
