@@ -169,6 +169,14 @@ typedef struct {
                             Lanczos, Sec. 2.2; stops after lanczos_max_iter
                             steps, short of lanczos_tol on dense lubricated
                             suspensions)                                       */
+  double rough_alpha;    /* surface roughness of the lubrication pairs (Sec. 4,
+                            Eq. tan_fric): below the asperity height rough_h0
+                            the sliding and rolling coefficients of the pair
+                            model gain 6 pi eta a f(h) and 8 pi eta a^3 f(h),
+                            f = rough_alpha (a/h0) (h0/h - 3 h/h0 + 2 h^2/h0^2)
+                            (h the gap, clamped at lub_hmin): O(1/h) instead of
+                            O(ln 1/h).  0: smooth spheres (default)            */
+  double rough_h0;       /* asperity height h0 (> 0 when rough_alpha > 0)       */
 } fsd_params;
 
 typedef struct {
@@ -427,6 +435,32 @@ fsd_status fsd_drift(fsd_ctx *ctx, int method, double kT, double dt, double para
  * the applied force).  kn in units of force / length^1.5.  The neighbour
  * lists built here are reused by the next solve. */
 fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque);
+
+/* Interparticle forces of Sec. 4 between beads of different aggregates. */
+typedef struct {
+  double kn;       /* Hertz normal contact k_n delta^1.5 (0: none)                 */
+  double hamaker;  /* Hamaker constant A_H of the van der Waals attraction (0: none) */
+  double zeta;     /* double-layer strength Z, energy per length: the repulsion is
+                      (a^2/r) Z exp(-kappa (r - 2a)) (0: none)                      */
+  double kappa;    /* inverse Debye length (> 0 when zeta != 0)                    */
+  double h_c;      /* van der Waals regularisation: evaluated at gap h + h_c; under
+                      overlap the attraction keeps its value at contact          */
+  double r_cut;    /* DLVO cut-off on the centre distance; at most the real-space
+                      cut-off R_c of the context (its neighbour list is used)     */
+} fsd_pair_forces;
+
+/* Hertz contact plus DLVO forces (Sec. 4, Eq. dlvo_potential, F = -grad V)
+ * between beads of different aggregates at the current configuration: per
+ * pair the central force f(r) n, f = k_n (2a - r)^1.5 [r < 2a] - dV/dr
+ * [r < r_cut], with V = -(A_H/6) [2a^2/(r'^2 - 4a^2) + 2a^2/r'^2 +
+ * ln(1 - 4a^2/r'^2)] (r' = max(r, 2a) + h_c in the attraction's derivative;
+ * the sphere-sphere Hamaker form) + (a^2/r) Z exp(-kappa (r - 2a)).  The bead
+ * forces are summed per aggregate into a force and a torque about the
+ * centroid, written to agg_force_torque [N][6] (host or device), to be passed
+ * to fsd_step / fsd_solve as the applied force.  FSD_EINVAL for r_cut above
+ * R_c, a negative stiffness, or zeta != 0 with kappa <= 0. */
+fsd_status fsd_interparticle_forces(fsd_ctx *ctx, const fsd_pair_forces *p,
+                                    double *agg_force_torque);
 
 /* Sets the Lees-Edwards offset of the box (see fsd_params.tilt; taken
  * modulo L).  fsd_get_params reports the current offset. */

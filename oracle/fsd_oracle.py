@@ -515,7 +515,7 @@ def B_op(Nt):
 # ---------------------------------------------------------------------------
 
 
-def lub_coefficients(h, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
+def lub_coefficients(h, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, rough=(0.0, 0.0)):
     """Pair resistance coefficients as functions of the surface gap h
     (eps = h/a, clamped below at hmin/a), each shifted to vanish at the
     cut-off gap eps_c = rcut/a - 2:
@@ -523,7 +523,13 @@ def lub_coefficients(h, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
       B (sliding)        6 pi eta a (1/6) ln(1/eps)
       D (relative roll)  8 pi eta a^3 (1/10) ln(1/eps)
     (leading two-sphere lubrication terms for equal spheres).  All >= 0 for
-    eps <= eps_c, so the pair form is positive semi-definite."""
+    eps <= eps_c, so the pair form is positive semi-definite.
+
+    rough = (alpha, h0), alpha > 0: surface roughness (Sec. 4, Eq. tan_fric):
+    below the asperity height h0 the tangential coefficients gain
+    f(h) = alpha (a/h0) (h0/h - 3 h/h0 + 2 h^2/h0^2) (h the clamped gap),
+    B += 6 pi eta a f and D += 8 pi eta a^3 f: sliding and rolling resist
+    O(1/h) instead of O(ln 1/h); the squeeze term is unchanged."""
     ec = rcut / a - 2.0
     e = max(h / a, hmin / a)
 
@@ -533,10 +539,16 @@ def lub_coefficients(h, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     A = 6 * PI * eta * a * (sq(e) - sq(ec))
     B = 6 * PI * eta * a * (1.0 / 6.0) * np.log(ec / e)
     D = 8 * PI * eta * a ** 3 * 0.1 * np.log(ec / e)
+    alpha, h0 = rough
+    hc = e * a
+    if alpha > 0.0 and h0 > 0.0 and hc < h0:
+        f = alpha * (a / h0) * (h0 / hc - 3.0 * hc / h0 + 2.0 * hc * hc / (h0 * h0))
+        B += 6 * PI * eta * a * f
+        D += 8 * PI * eta * a ** 3 * f
     return A, B, D
 
 
-def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
+def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, rough=(0.0, 0.0)):
     """22x22 grand resistance of one inter-body pair acting on
     nu = (U_inf - U, E_inf) per bead (11 each: 6 velocity, 5 strain),
     returning (F, S) per bead (the grand-resistance convention of Sec. 2.1).
@@ -549,7 +561,7 @@ def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     x = xj - xi
     r = np.linalg.norm(x)
     n = x / r
-    A, B, D = lub_coefficients(r - 2 * a, a, eta, rcut, hmin)
+    A, B, D = lub_coefficients(r - 2 * a, a, eta, rcut, hmin, rough)
     nn = np.outer(n, n)
     G = A * nn + B * (I3 - nn)
     Gt = D * (I3 - nn)
@@ -568,7 +580,7 @@ def lub_pair_matrix(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     return Ls.T @ G @ Ls + Lt.T @ Gt @ Lt
 
 
-def lub_pair_factor(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
+def lub_pair_factor(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, rough=(0.0, 0.0)):
     """K (6 x 12) with K^T K = the FU block of lub_pair_matrix (velocities
     and rotations of i, then of j): the dissipation form's own factor,
     K = [G^(1/2) Ls; Gt^(1/2) Lt] restricted to the velocity columns, with
@@ -576,7 +588,7 @@ def lub_pair_factor(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     x = xj - xi
     r = np.linalg.norm(x)
     n = x / r
-    A, B, D = lub_coefficients(r - 2 * a, a, eta, rcut, hmin)
+    A, B, D = lub_coefficients(r - 2 * a, a, eta, rcut, hmin, rough)
     nn = np.outer(n, n)
     Gh = np.sqrt(A) * nn + np.sqrt(B) * (I3 - nn)
     Gth = np.sqrt(D) * (I3 - nn)
@@ -592,7 +604,7 @@ def lub_pair_factor(xi, xj, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3):
     return np.vstack([Gh @ Ls, Gth @ Lt])
 
 
-def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, tilt=0.0):
+def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, tilt=0.0, rough=(0.0, 0.0)):
     """Bead-level grand near-field resistance (11 Nt x 11 Nt), per bead
     ordering (6 velocity, 5 strain), summed over inter-body pairs with
     r < rcut (minimum image).  Intra-body pairs are excluded (Alg. 1 step 1)."""
@@ -609,7 +621,7 @@ def lubrication_dense(pos, body, L, a=1.0, eta=1.0, rcut=3.0, hmin=1e-3, tilt=0.
             d = min_image(d, L, tilt)
             if np.linalg.norm(d) >= rcut:
                 continue
-            Rp = lub_pair_matrix(np.zeros(3), d, a, eta, rcut, hmin)
+            Rp = lub_pair_matrix(np.zeros(3), d, a, eta, rcut, hmin, rough)
             ii = np.r_[11 * i:11 * i + 11]
             jj = np.r_[11 * j:11 * j + 11]
             idx = np.r_[ii, jj]
@@ -631,7 +643,7 @@ def split_grand(R, Nt):
 
 
 def assemble(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None,
-             hmin=1e-3, tilt=0.0):
+             hmin=1e-3, tilt=0.0, rough=(0.0, 0.0)):
     """Dense saddle-point matrix and right-hand side of Eq. spm_agg.
 
     Unknowns: (F (11 per bead), U - U_inf (6 per body)).  Returns a dict with
@@ -648,7 +660,7 @@ def assemble(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None,
     Bm = B_op(Nt)
     BST = Bm @ ST
     if rlub > 2.0 * a:
-        Rg = lubrication_dense(unw, body, L, a, eta, rlub, hmin, tilt)
+        Rg = lubrication_dense(unw, body, L, a, eta, rlub, hmin, tilt, rough)
     else:
         Rg = np.zeros((11 * Nt, 11 * Nt))
     RFU, RFE, RSU, RSE = split_grand(Rg, Nt)
@@ -713,11 +725,12 @@ def outputs(sys_, sol):
     return dict(U=U, dU=dU, S=S, SH=SH, SC=SC, F=Fm, Fnf=Fnf, Snf=Snf)
 
 
-def solve(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None, hmin=1e-3, tilt=0.0):
+def solve(pos, body, L, gamma=1.0, FT=None, a=1.0, eta=1.0, rlub=0.0, M=None, hmin=1e-3, tilt=0.0,
+          rough=(0.0, 0.0)):
     """Dense direct solve of Eq. spm_agg (LAPACK gesv).  Returns outputs plus
     the relative residual ||A x - b|| / ||b||.  tilt != 0: the Lees-Edwards
     box (images across y offset by tilt along x)."""
-    sys_ = assemble(pos, body, L, gamma, FT, a, eta, rlub, M, hmin, tilt)
+    sys_ = assemble(pos, body, L, gamma, FT, a, eta, rlub, M, hmin, tilt, rough)
     sys_["body"] = np.asarray(body)
     x = np.linalg.solve(sys_["A"], sys_["b"])
     res = np.linalg.norm(sys_["A"] @ x - sys_["b"]) / max(np.linalg.norm(sys_["b"]), 1e-300)

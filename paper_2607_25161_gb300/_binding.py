@@ -33,7 +33,7 @@ EXPORTS = (
     "fsd_profile_group_name", "fsd_apply_wave_noalloc", "fsd_last_error", "fsd_destroy",
     "fsd_setup_batch", "fsd_batch_info", "fsd_solve_batch", "fsd_step_batch", "fsd_batch_get_beads",
     "fsd_batch_system", "fsd_batch_last_error", "fsd_destroy_batch", "fsd_brownian", "fsd_drift",
-    "fsd_contact_forces", "fsd_set_tilt", "fsd_fma_throughput",
+    "fsd_contact_forces", "fsd_set_tilt", "fsd_fma_throughput", "fsd_interparticle_forces",
 )
 PROF_GROUPS = 10
 
@@ -49,10 +49,18 @@ class FsdParams(ctypes.Structure):
         ("inner_tol", ctypes.c_double), ("flags", ctypes.c_int), ("tile", ctypes.c_int),
         ("lanczos_tol", ctypes.c_double), ("lanczos_max_iter", ctypes.c_int),
         ("tilt", ctypes.c_double), ("nf_sampler", ctypes.c_int),
+        ("rough_alpha", ctypes.c_double), ("rough_h0", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FsdPairForces(ctypes.Structure):
+    _fields_ = [
+        ("kn", ctypes.c_double), ("hamaker", ctypes.c_double), ("zeta", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("h_c", ctypes.c_double), ("r_cut", ctypes.c_double),
+    ]
 
 
 class FsdStats(ctypes.Structure):
@@ -117,6 +125,7 @@ def load(path=LIB_PATH):
     lib.fsd_drift.argtypes = [P, I, D, D, D, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P,
                               ctypes.POINTER(FsdStats)]
     lib.fsd_contact_forces.argtypes = [P, D, P]
+    lib.fsd_interparticle_forces.argtypes = [P, ctypes.POINTER(FsdPairForces), P]
     lib.fsd_set_tilt.argtypes = [P, D]
     lib.fsd_fma_throughput.argtypes = [I, ctypes.POINTER(D), P]
     lib.fsd_destroy_batch.argtypes = [P]
@@ -305,6 +314,14 @@ class Suspension:
         if out is None:
             out = np.zeros((self.n_agg, 6))
         self._check(self.lib.fsd_contact_forces(self.ctx, float(kn), _ptr(out)))
+        return out
+
+    def interparticle(self, kn=0.0, hamaker=0.0, zeta=0.0, kappa=1.0, h_c=0.0, r_cut=0.0, out=None):
+        """fsd_interparticle_forces: Hertz + DLVO force / torque per aggregate [N, 6]."""
+        if out is None:
+            out = np.zeros((self.n_agg, 6))
+        pf = FsdPairForces(float(kn), float(hamaker), float(zeta), float(kappa), float(h_c), float(r_cut))
+        self._check(self.lib.fsd_interparticle_forces(self.ctx, ctypes.byref(pf), _ptr(out)))
         return out
 
     def profile(self, on=True):

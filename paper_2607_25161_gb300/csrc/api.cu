@@ -531,6 +531,9 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.prm.inner_tol = p.inner_tol > 0 ? p.inner_tol : 1e-7;
   c.prm.lanczos_tol = p.lanczos_tol > 0 ? p.lanczos_tol : 1e-7;
   c.prm.lanczos_max_iter = p.lanczos_max_iter > 0 ? std::max(p.lanczos_max_iter, 2) : 60;
+  if (!(p.rough_alpha >= 0.0) || !std::isfinite(p.rough_alpha) ||
+      (p.rough_alpha > 0.0 && !(p.rough_h0 > 0.0 && std::isfinite(p.rough_h0))))
+    throw Invalid{"rough_alpha must be >= 0, with rough_h0 > 0 when it is positive"};
   if (p.nf_sampler != FSD_NF_LANCZOS && p.nf_sampler != FSD_NF_PAIRWISE)
     throw Invalid{"nf_sampler must be FSD_NF_LANCZOS or FSD_NF_PAIRWISE"};
   if (p.tile != 0 && p.tile != 4 && p.tile != 8 && p.tile != 16 && p.tile != 32)
@@ -1098,6 +1101,8 @@ void fsd_default_params(fsd_params *p) {
   // paper's preconditioned Lanczos stops at its step limit on dense
   // lubricated suspensions (FSD_NF_LANCZOS selects it)
   p->nf_sampler = FSD_NF_PAIRWISE;
+  p->rough_alpha = 0.0;
+  p->rough_h0 = 0.0;
 }
 
 fsd_status fsd_setup(fsd_ctx **ctx, int64_t n_beads, const double *bead_pos, const int32_t *agg_id,
@@ -1473,23 +1478,43 @@ fsd_status fsd_set_tilt(fsd_ctx *ctx, double tilt) {
   FSD_API_CATCH(ctx)
 }
 
+static fsd_status pair_forces_impl(fsd_ctx *ctx, const fsd_pair_forces &pf, double *agg_force_torque) {
+  FSD_API_TRY
+  Ctx &c = ctx->c;
+  if (pf.r_cut > c.rc) throw Invalid{"r_cut must not exceed the real-space cut-off R_c"};
+  if (!c.geom_fresh) prepare(c);
+  c.geom_fresh = true;  // the next solve reuses this preparation
+  const size_t need = 3 * (size_t)c.Nt + 6 * (size_t)c.N;
+  if (c.cwork.n < need) c.cwork.alloc(need);
+  double *ft_int = c.cwork.p + 3 * (size_t)c.Nt;
+  launch_contact(c, pf, c.cwork.p, ft_int);
+  bodies_out(c, ft_int, agg_force_torque, 6);
+  return FSD_OK;
+  FSD_API_CATCH(ctx)
+}
+
 fsd_status fsd_contact_forces(fsd_ctx *ctx, double kn, double *agg_force_torque) {
   if (!ctx) return FSD_EINVAL;
   if (!(kn >= 0.0) || !std::isfinite(kn) || !agg_force_torque) {
     ctx->c.last_error = "kn must be finite and >= 0, agg_force_torque is required";
     return FSD_EINVAL;
   }
-  FSD_API_TRY
-  Ctx &c = ctx->c;
-  if (!c.geom_fresh) prepare(c);
-  c.geom_fresh = true;  // the next solve reuses this preparation
-  const size_t need = 3 * (size_t)c.Nt + 6 * (size_t)c.N;
-  if (c.cwork.n < need) c.cwork.alloc(need);
-  double *ft_int = c.cwork.p + 3 * (size_t)c.Nt;
-  launch_contact(c, kn, c.cwork.p, ft_int);
-  bodies_out(c, ft_int, agg_force_torque, 6);
-  return FSD_OK;
-  FSD_API_CATCH(ctx)
+  fsd_pair_forces pf{};
+  pf.kn = kn;
+  return pair_forces_impl(ctx, pf, agg_force_torque);
+}
+
+fsd_status fsd_interparticle_forces(fsd_ctx *ctx, const fsd_pair_forces *p, double *agg_force_torque) {
+  if (!ctx) return FSD_EINVAL;
+  const bool ok = p && agg_force_torque && std::isfinite(p->kn) && p->kn >= 0.0 &&
+                  std::isfinite(p->hamaker) && std::isfinite(p->zeta) && std::isfinite(p->kappa) &&
+                  std::isfinite(p->h_c) && p->h_c >= 0.0 && std::isfinite(p->r_cut) && p->r_cut >= 0.0 &&
+                  (p->zeta == 0.0 || p->kappa > 0.0);
+  if (!ok) {
+    ctx->c.last_error = "fsd_pair_forces: kn >= 0, h_c >= 0, r_cut >= 0 finite, kappa > 0 with zeta";
+    return FSD_EINVAL;
+  }
+  return pair_forces_impl(ctx, *p, agg_force_torque);
 }
 
 fsd_status fsd_get_params(const fsd_ctx *ctx, fsd_params *p) {

@@ -322,7 +322,7 @@ void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int,
 void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear);
 // Hertz contact: per-bead forces into fb_scratch [Nt][3], aggregate force and
 // torque into ft_int [N][6] (internal order); needs the neighbour lists
-void launch_contact(Ctx &c, double kn, double *fb_scratch, double *ft_int);
+void launch_contact(Ctx &c, const fsd_pair_forces &pf, double *fb_scratch, double *ft_int);
 // pairwise near-field Brownian force (unscaled, solution layout) into f
 void launch_nf_pairwise(Ctx &c, uint64_t seed, uint64_t step, double *f);
 // brownian.cu: drift helpers

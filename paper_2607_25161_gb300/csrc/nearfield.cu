@@ -23,11 +23,25 @@ struct PairCoef {
   double A, B, D;
 };
 
+// Gap clamp and surface roughness of the pair model.
+struct LubModel {
+  double hmin = 1e-3;          // the gap is clamped below at hmin
+  double alpha = 0.0, h0 = 0.0;  // roughness (Sec. 4, Eq. tan_fric); alpha 0: smooth
+};
+
+static LubModel lub_model(const Ctx &c) {
+  LubModel m;
+  m.hmin = c.prm.lub_hmin;
+  m.alpha = c.prm.rough_alpha;
+  m.h0 = c.prm.rough_h0;
+  return m;
+}
+
 __device__ __forceinline__ PairCoef lub_coef(double r, double a, double eta, double rcut,
-                                            double hmin) {
+                                            LubModel m) {
   const double ec = rcut / a - 2.0;
   double e = (r - 2.0 * a) / a;
-  const double emin = hmin / a;
+  const double emin = m.hmin / a;
   if (e < emin) e = emin;
   const double qe = 0.25 / e + 0.225 * log(1.0 / e);
   const double qc = 0.25 / ec + 0.225 * log(1.0 / ec);
@@ -38,6 +52,16 @@ __device__ __forceinline__ PairCoef lub_coef(double r, double a, double eta, dou
   if (p.A < 0) p.A = 0;
   if (p.B < 0) p.B = 0;
   if (p.D < 0) p.D = 0;
+  // rough surfaces: below the asperity height the sliding and rolling
+  // resistances grow as 1/h (f vanishes at h0 and is added to the
+  // normalised tangential coefficients)
+  const double h = e * a;
+  if (m.alpha > 0.0 && m.h0 > 0.0 && h < m.h0) {
+    const double t = h / m.h0;
+    const double f = m.alpha * (a / m.h0) * (1.0 / t - 3.0 * t + 2.0 * t * t);
+    p.B += 6.0 * kPi * eta * a * f;
+    p.D += 8.0 * kPi * eta * a * a * a * f;
+  }
   return p;
 }
 
@@ -91,7 +115,7 @@ __global__ void k_lub_assemble(int Nt, const double4 *__restrict__ pos,
                                int lcap, const int *__restrict__ brow, int *bcol, double *bval64,
                                float *bval32, double *bdiag64, float *bdiag32, double *pdiag,
                                double L, double tilt, double a, double eta, double rcut,
-                               double rp, double hmin) {
+                               double rp, LubModel lm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   double Dg[36], Pg[36];
@@ -105,7 +129,7 @@ __global__ void k_lub_assemble(int Nt, const double4 *__restrict__ pos,
     min_image(d0, d1, d2, L, tilt);
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     const double n[3] = {d0 / r, d1 / r, d2 / r};
-    PairCoef p = lub_coef(r, a, eta, rcut, hmin);
+    PairCoef p = lub_coef(r, a, eta, rcut, lm);
     double Rii[36], Rij[36];
     pair_blocks(n, r, p, Rii, Rij);
     const int slot = brow[i] + k;
@@ -370,9 +394,11 @@ __global__ void k_nf_bead(int Nt, const double4 *__restrict__ pos,
                           const int *__restrict__ lnbr, const int *__restrict__ lcnt, int lcap,
                           const double *__restrict__ dU, double e00, double e11, double e22,
                           double e01, double e02, double e12, double *fnf, double *snf, double L,
-                          double tilt, double a, double eta, double rcut, double hmin) {
+                          double tilt, double a, double eta, double rcut, LubModel lm,
+                          const double *__restrict__ tilt_dev) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
+  if (tilt_dev) tilt = *tilt_dev;  // Lees-Edwards steps: the offset in device memory
   const double E[9] = {e00, e01, e02, e01, e11, e12, e02, e12, e22};
   auto bead_vel = [&](int b, double *du, double *dw) {
     const double4 rv = lever[b];
@@ -400,7 +426,7 @@ __global__ void k_nf_bead(int Nt, const double4 *__restrict__ pos,
     min_image(d0, d1, d2, L, tilt);
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     const double n[3] = {d0 / r, d1 / r, d2 / r};
-    PairCoef p = lub_coef(r, a, eta, rcut, hmin);
+    PairCoef p = lub_coef(r, a, eta, rcut, lm);
     double duj[3], dwj[3];
     bead_vel(j, duj, dwj);
     double sw[3] = {dwi[0] + dwj[0], dwi[1] + dwj[1], dwi[2] + dwj[2]};
@@ -557,14 +583,44 @@ __global__ void k_integrate(int N, const double *__restrict__ vel, double dt, do
 // benchmark of Sec. 3.3): bead i receives kn delta^1.5 (x_i - x_j)/r from
 // each such neighbour j.  The mobility neighbour list (r < R_c, R_c > 2a)
 // holds every pair that can touch.
+// Central force between two beads of different aggregates at distance r
+// (positive: repulsive): Hertz k_n delta^1.5 under overlap, and the DLVO
+// force -dV/dr (Sec. 4) within r_cut.  The van der Waals part is the
+// derivative of the sphere-sphere Hamaker energy
+//   -(A_H/6) [2a^2/(r^2 - 4a^2) + 2a^2/r^2 + ln((r^2 - 4a^2)/r^2)]
+// taken at r' = max(r, 2a) + h_c (gap shifted by h_c, held at its contact
+// value under overlap); the double layer (a^2/r) Z exp(-kappa (r - 2a)).
+__device__ __forceinline__ double pair_force_scalar(double r, double a, const fsd_pair_forces &pf) {
+  double f = 0.0;
+  const double two_a = 2.0 * a;
+  if (pf.kn > 0.0 && r < two_a) {
+    const double delta = two_a - r;
+    f += pf.kn * delta * sqrt(delta);
+  }
+  if (r < pf.r_cut) {
+    if (pf.hamaker != 0.0) {
+      const double rv = fmax(r, two_a) + pf.h_c;
+      const double s2 = two_a * two_a, q = rv * rv - s2, a2 = a * a;
+      const double dv = -4.0 * a2 * rv / (q * q) - 4.0 * a2 / (rv * rv * rv) + 2.0 * rv / q - 2.0 / rv;
+      f += pf.hamaker / 6.0 * dv;  // -(dV/dr) with V = -(A_H/6)(...)
+    }
+    if (pf.zeta != 0.0) {
+      const double e = exp(-pf.kappa * (r - two_a));
+      f += a * a * pf.zeta * e * (1.0 / (r * r) + pf.kappa / r);
+    }
+  }
+  return f;
+}
+
 __global__ void k_contact_bead(int Nt, const double4 *__restrict__ pos, const int *__restrict__ nbr,
                                const int *__restrict__ ncnt, int cap,
                                const int *__restrict__ bead_body, double L, double tilt,
-                               double two_a, double kn, double *fb) {
+                               double a, fsd_pair_forces pf, double *fb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
   const double4 p = pos[i];
   const int bi = bead_body[i];
+  const double reach = fmax(2.0 * a, pf.r_cut);
   double f0 = 0.0, f1 = 0.0, f2 = 0.0;
   const int n = ncnt[i];
   for (int k = 0; k < n; ++k) {
@@ -574,9 +630,9 @@ __global__ void k_contact_bead(int Nt, const double4 *__restrict__ pos, const in
     double d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z;
     le_image(d0, d1, d2, L, tilt);
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    if (r2 >= two_a * two_a || r2 == 0.0) continue;
-    const double r = sqrt(r2), delta = two_a - r;
-    const double s = kn * delta * sqrt(delta) / r;
+    if (r2 >= reach * reach || r2 == 0.0) continue;
+    const double r = sqrt(r2);
+    const double s = pair_force_scalar(r, a, pf) / r;
     f0 += s * d0;
     f1 += s * d1;
     f2 += s * d2;
@@ -622,7 +678,7 @@ __global__ void k_contact_body(int N, const int *__restrict__ body_start,
 // counter (i, 5 * 256 + call, j, step mod 2^32) in input order.
 __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int *__restrict__ lnbr,
                               const int *__restrict__ lcnt, int lcap, const int *__restrict__ perm,
-                              double L, double tilt, double a, double eta, double rcut, double hmin,
+                              double L, double tilt, double a, double eta, double rcut, LubModel lm,
                               uint64_t seed, uint64_t step, double *f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
@@ -639,7 +695,7 @@ __global__ void k_nf_pairwise(int Nt, const double4 *__restrict__ pos, const int
     min_image(d0, d1, d2, L, tilt);
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     const double n[3] = {d0 / r, d1 / r, d2 / r};
-    const PairCoef pc = lub_coef(r, a, eta, rcut, hmin);
+    const PairCoef pc = lub_coef(r, a, eta, rcut, lm);
     double z[8];
     for (int call = 0; call < 2; ++call) {
       uint32_t cw[4] = {(uint32_t)iu, (5u << 8) | (uint32_t)call, (uint32_t)ju, (uint32_t)step};
@@ -708,7 +764,7 @@ void build_lubrication(Ctx &c) {
   k_lub_assemble<<<ceil_div(Nt, 128), 128, 0, c.stream>>>(
       Nt, (const double4 *)c.pos64.p, c.lnbr.p, c.lcnt.p, c.lcap, c.brow.p, c.bcol.p,
       c.op64.bval.p, c.op32.bval.p, c.op64.bdiag.p, c.op32.bdiag.p, c.pdiag.p, c.L, c.tilt, c.a, c.eta, rl,
-      c.prm.precond_cutoff, c.prm.lub_hmin);
+      c.prm.precond_cutoff, lub_model(c));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   const double zeta0 = 6.0 * kPi * c.eta * c.a;
@@ -793,7 +849,7 @@ void launch_rhs(Ctx &c, const double *ft_int, double shear, double *b) {
     k_nf_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
         c.Nt, (const double4 *)c.pos64.p, (const double4 *)c.lever64.p, c.bead_body.p, c.lnbr.p,
         c.lcnt.p, c.lcap, nullptr, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.tilt, c.a,
-        c.eta, rl, c.prm.lub_hmin);
+        c.eta, rl, lub_model(c), tilt_dev_ptr(c));
     FSD_LAUNCHED(c);
   }
   k_rhs_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
@@ -813,7 +869,7 @@ void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int, doub
     k_nf_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
         c.Nt, (const double4 *)c.pos64.p, (const double4 *)c.lever64.p, c.bead_body.p, c.lnbr.p,
         c.lcnt.p, c.lcap, x + off, e[0], e[1], e[2], e[3], e[4], e[5], c.fnf.p, c.snf.p, c.L, c.tilt, c.a,
-        c.eta, c.prm.lub_cutoff, c.prm.lub_hmin);
+        c.eta, c.prm.lub_cutoff, lub_model(c), tilt_dev_ptr(c));
     FSD_LAUNCHED(c);
   }
   k_outputs<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
@@ -832,10 +888,10 @@ void launch_integrate(Ctx &c, const double *vel_int, double dt, double shear) {
   FSD_CUDA(cudaGetLastError());
 }
 
-void launch_contact(Ctx &c, double kn, double *fb_scratch, double *ft_int) {
+void launch_contact(Ctx &c, const fsd_pair_forces &pf, double *fb_scratch, double *ft_int) {
   ProfScope ps(c, PG_MISC);
   k_contact_bead<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
-      c.Nt, (const double4 *)c.pos64.p, c.nbr.p, c.ncnt.p, c.cap, c.bead_body.p, c.L, c.tilt, 2.0 * c.a, kn,
+      c.Nt, (const double4 *)c.pos64.p, c.nbr.p, c.ncnt.p, c.cap, c.bead_body.p, c.L, c.tilt, c.a, pf,
       fb_scratch);
   FSD_LAUNCHED(c);
   k_contact_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(c.N, c.body_start.p,
@@ -848,7 +904,7 @@ void launch_nf_pairwise(Ctx &c, uint64_t seed, uint64_t step, double *f) {
   FSD_CUDA(cudaMemsetAsync(f, 0, (size_t)c.nunk * sizeof(double), c.stream));
   k_nf_pairwise<<<ceil_div(c.Nt, 64), 64, 0, c.stream>>>(
       c.Nt, (const double4 *)c.pos64.p, c.lnbr.p, c.lcnt.p, c.lcap, c.perm_bead.p, c.L, c.tilt, c.a,
-      c.eta, c.prm.lub_cutoff, c.prm.lub_hmin, seed, step, f);
+      c.eta, c.prm.lub_cutoff, lub_model(c), seed, step, f);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }

@@ -226,13 +226,32 @@ def test_pairwise_near_field_sampler_with_tilt(pkg):
     assert rel(fnf / np.sqrt(2.0), ref) < 1e-12
 
 
+def straddling_system():
+    """Aggregates whose lubrication pairs exist only through the sheared image
+    across y (at tilt 0.2 L), plus two free aggregates."""
+    L, tilt = 14.0, 0.2 * 14.0
+    A = np.array([5.0, 0.4, 7.0])
+    B = A + np.array([0.5, -2.25, 0.3]) + np.array([tilt, L, 0.0])
+    B[0] = np.mod(B[0], L)
+    C = np.array([9.0, 13.5, 2.0])
+    D = C + np.array([-0.4, 2.3, 0.2]) - np.array([tilt, L, 0.0])
+    D[0] = np.mod(D[0], L)
+    pos = np.array([A, A + [0.0, 0.0, 2.0], B, B + [2.0, 0.0, 0.0], C, C + [0.0, 0.0, 2.0], D,
+                    [2.0, 7.0, 3.0], [4.0, 7.0, 3.0], [11.0, 6.0, 11.0]])
+    body = np.array([0, 0, 1, 1, 2, 2, 3, 4, 4, 5], dtype=np.int32)
+    return pos, body, L
+
+
+@pytest.mark.parametrize("system", ["packed", "straddling"])
 @pytest.mark.parametrize("prec", [FP64, MIXED])
-def test_graph_lees_edwards_steps_match_host_driven(pkg, sysLE, prec):
+def test_graph_lees_edwards_steps_match_host_driven(pkg, sysLE, prec, system):
     # with FSD_FLAG_GRAPH a Lees-Edwards step is one captured graph whose
     # kernels read the box offset from device memory (one graph for every
     # offset); five steps must reproduce the host-driven loop's velocities,
-    # beads, orientations and offsets
-    pos, body, L = sysLE
+    # beads, orientations and offsets, also with lubrication pairs that
+    # exist only across the sheared boundary (every kernel of the graph must
+    # take the current offset, not the one at capture)
+    pos, body, L = sysLE if system == "packed" else straddling_system()
     gamma, dt = 0.7, 0.04
     out = []
     for flags in (pkg.FSD_FLAG_LEES_EDWARDS, pkg.FSD_FLAG_LEES_EDWARDS | pkg.FSD_FLAG_GRAPH):

@@ -8,6 +8,7 @@ import numpy as np
 import synth
 from oracle import contact_oracle as C
 from oracle import fsd_oracle as F
+from oracle import fsd_oracle as O
 
 
 def test_single_pair_closed_form():
@@ -66,3 +67,73 @@ def test_rod_generator():
         assert np.allclose(np.cross(P - P[0], u), 0.0, atol=1e-10)  # straight
     out, _ = C.hertz_contact(pos, body, L, 1e4)
     assert np.all(out == 0.0)  # inserted with gaps >= 0.1a
+
+
+# ------------------------------------------------------------------ DLVO
+
+
+def test_dlvo_force_is_minus_the_potential_derivative():
+    # both parts, with the van der Waals regularisation, away from contact
+    a, AH, Z, kappa, hc = 1.0, 15.0, 4.0, 1.0, 0.03
+    for r in (2.01, 2.1, 2.5, 3.3, 5.0):
+        e = 1e-6 * r
+        fd = -(C.dlvo_potential(r + e, a, AH, Z, kappa, hc)
+               - C.dlvo_potential(r - e, a, AH, Z, kappa, hc)) / (2 * e)
+        f = C.dlvo_force_scalar(r, a, AH, Z, kappa, hc)
+        assert abs(f - fd) < 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_van_der_waals_far_field_is_the_textbook_sphere_limit():
+    # two equal spheres far apart: V -> -(16/9) A_H a^6 / r^6 (the leading
+    # term of the Hamaker sphere-sphere energy); corrections O((2a/r)^2)
+    # (a radius other than 1 separates 2 a1 a2 from the printed 2 a1 a2^2)
+    AH = 15.0
+    for a in (1.0, 1.7):
+        for r in (40.0 * a, 80.0 * a):
+            v = C.dlvo_potential(r, a, AH, 0.0, 1.0, 0.0)
+            ref = -16.0 / 9.0 * AH * a ** 6 / r ** 6
+            assert abs(v / ref - 1.0) < 40.0 * (2 * a / r) ** 2
+
+
+def test_double_layer_screening_and_contact_value():
+    a, Z, kappa = 1.0, 4.0, 2.0
+    v0 = C.dlvo_potential(2.0 * a, a, 0.0, Z, kappa, 0.0)
+    assert abs(v0 - a * a / (2 * a) * Z) < 1e-14
+    v1 = C.dlvo_potential(2.0 * a + 1.0 / kappa, a, 0.0, Z, kappa, 0.0)
+    assert abs(v1 / v0 - (2 * a / (2 * a + 1.0 / kappa)) * np.exp(-1.0)) < 1e-14
+
+
+def test_van_der_waals_attraction_capped_under_overlap_and_finite_at_contact():
+    a, AH, hc = 1.0, 15.0, 0.03
+    f_contact = C.dlvo_force_scalar(2.0 * a, a, AH, 0.0, 1.0, hc)
+    assert np.isfinite(f_contact) and f_contact < 0.0  # attractive
+    for r in (1.99, 1.95, 1.9):
+        assert C.dlvo_force_scalar(r, a, AH, 0.0, 1.0, hc) == f_contact
+    # the attraction grows towards contact
+    assert abs(C.dlvo_force_scalar(2.2, a, AH, 0.0, 1.0, hc)) < abs(f_contact)
+
+
+def test_dlvo_and_hertz_newton_third_law_cutoff_and_intrabody():
+    pos, body, L = synth.suspension(6, 4, 0.15, 3)
+    pos, body, L = C.F.body_geometry(pos, body, L)[0] + L, np.asarray(body), 3.0 * L
+    # (unwrapped aggregates in the middle of a box three times larger: no
+    # pair acts across the periodic boundary, so torques about one origin
+    # must cancel)
+    kw = dict(kn=1e3, A_H=15.0, Z=4.0, kappa=1.0, h_c=0.03, r_cut=4.0)
+    ft, fb = C.pair_forces(pos, body, L, **kw)
+    assert np.abs(fb).max() > 0
+    unw, X, r = O.body_geometry(pos, body, L)
+    assert np.abs(ft[:, :3].sum(axis=0)).max() < 1e-10 * np.abs(ft).max()
+    tot = ft[:, 3:].sum(axis=0) + np.cross(X, ft[:, :3]).sum(axis=0)
+    assert np.abs(tot).max() < 1e-9 * np.abs(ft).max() * L
+    # nothing beyond the cut-off (r_cut below every inter-body distance)
+    d = O.min_image(unw[:, None] - unw[None], L)
+    dist = np.linalg.norm(d, axis=-1)
+    inter = np.asarray(body)[:, None] != np.asarray(body)[None]
+    rmin = dist[inter].min()
+    ft0, fb0 = C.pair_forces(pos, body, L, A_H=15.0, Z=4.0, kappa=1.0, r_cut=0.99 * rmin)
+    assert np.abs(fb0).max() == 0.0
+    # a single aggregate feels nothing from itself
+    one = np.zeros(len(pos), dtype=int)
+    _, fb1 = C.pair_forces(pos, one, L, **kw)
+    assert np.abs(fb1).max() == 0.0

@@ -322,3 +322,50 @@ def test_lubrication_strain_columns_equal_affine_bead_motion(gap):
         f2 = R @ nu_move
         assert np.abs(f1).max() > 1e-3 * np.abs(R).max() * np.abs(E).max()
         assert np.abs(f1 - f2).max() < 1e-12 * np.abs(R).max() * np.abs(E).max() * 4.0
+
+
+# ------------------------------------------------- surface roughness (Sec. 4)
+
+
+def test_roughness_enhances_only_the_tangential_modes_below_h0():
+    rough = (0.01, 0.01)
+    for h in (1e-3, 3e-3, 6e-3, 0.0099):
+        A0, B0, D0 = O.lub_coefficients(h)
+        A1, B1, D1 = O.lub_coefficients(h, rough=rough)
+        assert A1 == A0  # squeeze untouched
+        assert B1 > B0 and D1 > D0
+        # the sliding and rolling increments are in the ratio of the two
+        # normalisations, 6 pi eta a and 8 pi eta a^3
+        assert abs((D1 - D0) / (B1 - B0) - 8.0 / 6.0) < 1e-12
+    for h in (0.01, 0.02, 0.5):
+        assert O.lub_coefficients(h, rough=rough) == O.lub_coefficients(h)
+    # continuous at the asperity height
+    below = O.lub_coefficients(0.01 * (1 - 1e-9), rough=rough)[1]
+    assert abs(below - O.lub_coefficients(0.01)[1]) < 1e-6
+
+
+def test_roughness_diverges_as_one_over_the_gap():
+    # f(h) ~ alpha a / h as h -> 0: h (B_rough - B_smooth) -> 6 pi eta a alpha a
+    alpha, h0 = 0.01, 0.01
+    vals = []
+    for h in (4e-3, 2e-3, 1e-3):
+        dB = O.lub_coefficients(h, rough=(alpha, h0))[1] - O.lub_coefficients(h)[1]
+        vals.append(h * dB / (6 * PI * alpha))
+    # approaches 1 (in units of a) with corrections O(h / h0)
+    assert vals[0] < vals[1] < vals[2] < 1.0 + 1e-12 and vals[2] > 0.69
+
+
+@pytest.mark.parametrize("gap", [1e-3, 0.004, 0.02])
+def test_rough_pair_symmetric_psd_and_rigid_invariant(gap):
+    xi, xj = _two_body_pair(gap, 4)
+    R = O.lub_pair_matrix(xi, xj, rough=(0.01, 0.01))
+    assert np.abs(R - R.T).max() < 1e-12 * np.abs(R).max()
+    assert np.linalg.eigvalsh(R).min() > -1e-10 * np.abs(R).max()
+    rng = np.random.default_rng(5)
+    V, W = rng.normal(size=3), rng.normal(size=3)
+    c = 0.5 * (xi + xj)
+    nu = np.zeros(22)
+    for k, x in ((0, xi), (11, xj)):
+        nu[k:k + 3] = -(V + np.cross(W, x - c))
+        nu[k + 3:k + 6] = -W
+    assert np.abs(R @ nu).max() < 1e-9 * np.abs(R).max()
