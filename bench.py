@@ -148,8 +148,11 @@ def group_work(group, s, prm, st, prec_bytes=4):
         return "hbm", 6 * n ** 3 * w + Nt * (12 * 8 + 4 * w), "GB/s"
     if group == "fft_green":
         # one forward and one inverse 3D transform of six real grids, each
-        # reading and writing every grid value once
-        return "hbm", 4 * 6 * G * w, "GB/s"
+        # reading and writing every grid value once; in a Lees-Edwards box the
+        # z pass also reads the three Green's factors of every half-spectrum
+        # point (they depend on the wave vector, not only on |k|)
+        le = 3 * n * (n // 2 + 1) * n * w if prm.get("flags", 0) & 16 else 0
+        return "hbm", 4 * 6 * G * w + le, "GB/s"
     if group == "interp":
         return "hbm", 6 * G * w + Nt * (12 * 8 + 4 * w), "GB/s"
     return "hbm", None, "GB/s"
