@@ -5,9 +5,9 @@ Metric: bead-steps/sec (beads x timed steps / seconds) of the full step
 saddle-point solve to a relative residual of 1e-6, outputs, rigid-body
 update) on 32768 beads = 4096 rigid 8-bead random-attachment aggregates at
 bead volume fraction 0.2 in simple shear (rate 1), lubrication cut-off 3a,
-constant xi = 0.5.  `value` is the mixed-precision path (FP32 operator inside
-FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path is
-reported beside it.
+constant xi = 0.5.  `value` is the mixed-precision path (FP32 operator and
+FP32 Krylov basis inside FP64 iterative refinement; FP64 residual, Hessenberg
+and LU); the plain FP64 path is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload step|batch|rods|seeds|oracle-ladder]
@@ -723,7 +723,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_name(w), "beads": Nt, "aggregates": w["n_agg"],
                    "method": "grid %d^3, P %d (wave-space operator error ~7e-7), rc %.2f"
                              % (prm["grid"], prm["P"], prm["rc"]),
-                   "precision": "mixed: FP32 operator in FP64 iterative refinement; FP64 Arnoldi, LU, residual",
+                   "precision": "mixed: FP32 operator and FP32 inner Krylov basis in FP64 iterative refinement; FP64 residual, Hessenberg, LU",
                    "l2": "working set per step > L2 (grids, Krylov basis, neighbour lists ~0.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "initial_guess": "zero each step",

@@ -199,43 +199,64 @@ static double host_norm(Ctx &c, const double *x) {
   return std::sqrt(std::max(0.0, c.h_pinned[0]));
 }
 
+// Krylov bases per operator precision: FP64 for the FP64 solve, FP32 for the
+// inner GMRES of the mixed solve.
+template <typename T> static T *krylov_v(Ctx &c);
+template <> double *krylov_v<double>(Ctx &c) { return c.V.p; }
+template <> float *krylov_v<float>(Ctx &c) { return c.V32.p; }
+template <typename T> static T *krylov_z(Ctx &c);
+template <> double *krylov_z<double>(Ctx &c) { return c.Z.p; }
+template <> float *krylov_z<float>(Ctx &c) { return c.Z32.p; }
+
 // Right-preconditioned restarted flexible GMRES (Z stores P^-1 v_j), CGS2
-// Arnoldi in FP64, Givens rotations on the host.  The operator precision is
-// T.  Solves A x = b from x (x_zero: x = 0).  Stops when the residual is
-// below tol * bnorm (the true residual when true_check), or after max_iter
+// Arnoldi, Givens rotations on the host.  The operator precision is T, and
+// so is the basis: FP64, or FP32 for the inner solve of the mixed path (its
+// basis vectors are widened to FP64 for the preconditioner, and the operator
+// is applied to the FP32 value of z_j that the update x += Z y uses).
+// Solves A x = b from x (x_zero: x = 0).  Stops when the residual is below
+// tol * bnorm (the true residual when true_check), or after max_iter
 // iterations.  Returns the last residual / bnorm.
 template <typename T>
 static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol, int max_iter,
                     int m, bool x_zero, bool true_check, KStats &st) {
+  constexpr bool f64 = sizeof(T) == 8;
   const int64_t ld = c.nunk;
-  double *V = c.V.p, *Z = c.Z.p, *w = c.w.p;
+  T *V = krylov_v<T>(c), *Z = krylov_z<T>(c);
+  double *w = c.w.p;
   int total = 0;
   double rel = 1.0;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1);
   while (true) {
-    if (x_zero) {
-      FSD_CUDA(cudaMemcpyAsync(V, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-    } else {
+    const double *r = b;
+    if (!x_zero) {
+      // w = b - A x
       apply_saddle<T>(c, x, w);
-      (sizeof(T) == 8 ? st.m64 : st.m32)++;
-      FSD_CUDA(cudaMemcpyAsync(V, b, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-      vec_axpby(c, V, -1.0, w, 1.0, ld);
+      (f64 ? st.m64 : st.m32)++;
+      vec_axpby(c, w, 1.0, b, -1.0, ld);
+      r = w;
     }
-    const double beta = host_norm(c, V);
+    const double beta = host_norm(c, r);
     rel = beta / bnorm;
     if (!(beta == beta)) throw Invalid{"NaN in the Krylov residual"};
     if (beta <= tol * bnorm || total >= max_iter) return rel;
-    vec_scale_host(c, V, V, 1.0 / beta);
+    vec_scale_host(c, V, r, 1.0 / beta);
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j = 0;
     double resid = beta;
     for (; j < m && total < max_iter;) {
-      double *vj = V + (int64_t)j * ld, *zj = Z + (int64_t)j * ld;
-      launch_precond(c, vj, zj);
-      apply_saddle<T>(c, zj, w);
-      (sizeof(T) == 8 ? st.m64 : st.m32)++;
+      if constexpr (f64) {
+        double *vj = V + (int64_t)j * ld, *zj = Z + (int64_t)j * ld;
+        launch_precond(c, vj, zj);
+        apply_saddle<T>(c, zj, w);
+      } else {
+        vec_widen(c, c.kv.p, V + (int64_t)j * ld);
+        launch_precond(c, c.kv.p, c.kz.p);
+        vec_round_f32(c, Z + (int64_t)j * ld, c.kz.p);
+        apply_saddle<T>(c, c.kz.p, w);
+      }
+      (f64 ? st.m64 : st.m32)++;
       double *h1 = c.hcol.p, *h2 = c.hcol.p + 64, *hn = c.hcol.p + 128;
       // classical Gram-Schmidt applied twice, three fused passes over V
       cgs_pass(c, 0, V, ld, j + 1, w, nullptr, h1);
@@ -294,7 +315,8 @@ static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol
 
 // Solve A x = b.  FP64: restarted GMRES on the FP64 operator.  Mixed: FP64
 // iterative refinement; each correction from GMRES on the FP32 operator
-// (FP64 vectors, Arnoldi and LU), each residual from the FP64 operator.
+// (FP32 Krylov bases, FP64 Hessenberg, Givens rotations and LU), each
+// residual from the FP64 operator.
 static double solve_system(Ctx &c, const double *b, double *x, KStats &st, bool warm) {
   const int64_t ld = c.nunk;
   const double bnorm = host_norm(c, b);
@@ -594,8 +616,17 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   FSD_CUDA(cudaMemset(c.fnf.p, 0, (size_t)Nt * 6 * sizeof(double)));
   FSD_CUDA(cudaMemset(c.snf.p, 0, (size_t)Nt * 5 * sizeof(double)));
   const int mm = std::max(c.m, c.m_in);
+  // V: FP64 GMRES and the Lanczos square roots (at most mm + 1 vectors);
+  // the mixed solve's inner GMRES keeps its bases in FP32
   c.V.alloc((size_t)(mm + 1) * c.nunk);
-  c.Z.alloc((size_t)mm * c.nunk);
+  if (c.prm.precision == FSD_MIXED) {
+    c.V32.alloc((size_t)(c.m_in + 1) * c.nunk);
+    c.Z32.alloc((size_t)c.m_in * c.nunk);
+    c.kv.alloc(c.nunk);
+    c.kz.alloc(c.nunk);
+  } else {
+    c.Z.alloc((size_t)c.m * c.nunk);
+  }
   c.w.alloc(c.nunk);
   c.t1.alloc(c.nunk);
   c.t2.alloc(c.nunk);

@@ -196,6 +196,11 @@ struct Ctx {
   // ---- Krylov workspace
   int m = 30, m_in = 30;
   DBuf<double> V, Z, w, t1, t2, xsol, rhs, res, xprev, partial, hcol;
+  // FP32 Krylov basis and preconditioned basis of the mixed solve's inner
+  // GMRES ((m_in + 1) and m_in vectors); V (FP64) serves the FP64 solve and
+  // the Lanczos square roots, Z (FP64) the FP64 solve
+  DBuf<float> V32, Z32;
+  DBuf<double> kv, kz;  // FP64 copies of v_j and z_j for the FP32 basis
   double *h_pinned = nullptr;  // host pinned scratch (dots)
   bool have_prev = false;
   // ---- outputs / near field scratch
@@ -344,6 +349,19 @@ void cgs_pass_dev(Ctx &c, int mode, const double *V, int64_t ld, const int *k_de
                   double *out_dev);  // the same with k = *k_dev + k_add read on the device
 void axpy_multi_dev(Ctx &c, double *w, const double *V, int64_t ld, const int *k_dev,
                     const double *coef_dev, double sign);
+// the same over an FP32 basis (inner GMRES of the mixed solve): FP32 products
+// and in-warp sums, FP64 w and cross-warp sums
+void axpy_multi(Ctx &c, double *w, const float *V, int64_t ld, int k, const double *coef_dev,
+                double sign);
+void cgs_pass(Ctx &c, int mode, const float *V, int64_t ld, int k, double *w,
+              const double *coef_dev, double *out_dev);
+void cgs_pass_dev(Ctx &c, int mode, const float *V, int64_t ld, const int *k_dev, int k_add,
+                  int kmax, double *w, const double *coef_dev, double *out_dev);
+void axpy_multi_dev(Ctx &c, double *w, const float *V, int64_t ld, const int *k_dev,
+                    const double *coef_dev, double sign);
+void vec_scale_host(Ctx &c, float *y, const double *x, double s);  // y = (float)(s x)
+void vec_widen(Ctx &c, double *y, const float *x);                 // y = (double) x
+void vec_round_f32(Ctx &c, float *z32, double *z);  // z32 = (float) z, z = (double) z32
 // Partial sums per dot product: a fixed count (not the SM count), so that the
 // reduction order and hence every result is the same on any GPU; 608 is 4 per
 // SM on a 152-SM part.

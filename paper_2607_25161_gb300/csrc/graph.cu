@@ -198,30 +198,39 @@ __global__ void k_g_inner_begin(GState *s, cudaGraphConditionalHandle h_arn) {
   set_cond(h_arn, true);
 }
 
-// y = scale * x (scale from the state); the first thread arms a handle.
-__global__ void k_g_scale(double *y, const double *x, const GState *s, int64_t n,
+// y = scale * x (scale from the state; y in the basis precision B); the
+// first thread arms a handle.
+template <typename B>
+__global__ void k_g_scale(B *y, const double *x, const GState *s, int64_t n,
                           cudaGraphConditionalHandle h, int arm) {
   if (arm && (threadIdx.x | blockIdx.x) == 0) set_cond(h, true);
   const double sc = s->scale;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    y[i] = x[i] * sc;
+    y[i] = (B)(x[i] * sc);
 }
 
-// out = V_j, with j read from the state
-__global__ void k_g_get_col(double *out, const double *__restrict__ V, int64_t ld, const GState *s,
+// out = V_j (widened to FP64), with j read from the state
+template <typename B>
+__global__ void k_g_get_col(double *out, const B *__restrict__ V, int64_t ld, const GState *s,
                             int64_t n) {
-  const double *v = V + (int64_t)s->j * ld;
+  const B *v = V + (int64_t)s->j * ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = v[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (double)v[i];
 }
 
-// Z_j = in
-__global__ void k_g_put_col(double *Z, int64_t ld, const double *__restrict__ in, const GState *s,
-                            int64_t n) {
-  double *z = Z + (int64_t)s->j * ld;
+// Z_j = in; with an FP32 basis in is rounded to the stored value, so that the
+// operator is applied to the vector that the update x += Z y uses
+template <typename B>
+__global__ void k_g_put_col(B *Z, int64_t ld, double *in, const GState *s, int64_t n) {
+  B *z = Z + (int64_t)s->j * ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) z[i] = in[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const B v = (B)in[i];
+    z[i] = v;
+    if constexpr (sizeof(B) == 4) in[i] = (double)v;
+  }
 }
 
 // Hessenberg column j from the two Gram-Schmidt passes, the earlier Givens
@@ -268,13 +277,15 @@ __global__ void k_g_givens(GState *s, cudaGraphConditionalHandle h_arn, int is64
 }
 
 // V_j = w / h_{j,j-1} when the loop goes on
-__global__ void k_g_next_col(double *V, int64_t ld, const double *__restrict__ w, const GState *s,
+template <typename B>
+__global__ void k_g_next_col(B *V, int64_t ld, const double *__restrict__ w, const GState *s,
                              int64_t n) {
   if (!s->cont) return;
-  double *v = V + (int64_t)s->j * ld;
+  B *v = V + (int64_t)s->j * ld;
   const double sc = s->scale;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] = w[i] * sc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    v[i] = (B)(w[i] * sc);
 }
 
 // y = R^-1 g, R the rotated j x j upper triangle
@@ -345,35 +356,45 @@ static int vec_blocks(const Ctx &c, int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms));
 }
 
-// One Arnoldi step of the flexible GMRES on the operator of precision T:
-// z_j = P^-1 v_j, w = A z_j, CGS2 against V_0..V_j, Givens update, v_{j+1}.
+// Krylov bases per operator precision: FP64 for the FP64 solve, FP32 for the
+// inner GMRES of the mixed solve.
+static double *basis_v(Ctx &c, double) { return c.V.p; }
+static float *basis_v(Ctx &c, float) { return c.V32.p; }
+static double *basis_z(Ctx &c, double) { return c.Z.p; }
+static float *basis_z(Ctx &c, float) { return c.Z32.p; }
+
+// One Arnoldi step of the flexible GMRES on the operator of precision T
+// (basis in the same precision): z_j = P^-1 v_j, w = A z_j, CGS2 against
+// V_0..V_j, Givens update, v_{j+1}.
 template <typename T>
 static void arnoldi_step(Ctx &c, GState *s, cudaGraphConditionalHandle h_arn) {
   GraphCache &gc = *c.gcache;
   const int64_t ld = c.nunk, n = c.nunk;
   const int nb = vec_blocks(c, n);
-  const int mm = std::max(c.m, c.m_in);
-  k_g_get_col<<<nb, 256, 0, c.stream>>>(gc.vin.p, c.V.p, ld, s, n);
+  const int mm = sizeof(T) == 8 ? c.m : c.m_in;
+  T *V = basis_v(c, T()), *Z = basis_z(c, T());
+  k_g_get_col<T><<<nb, 256, 0, c.stream>>>(gc.vin.p, V, ld, s, n);
   FSD_LAUNCHED(c);
   launch_precond(c, gc.vin.p, gc.zf.p);
-  k_g_put_col<<<nb, 256, 0, c.stream>>>(c.Z.p, ld, gc.zf.p, s, n);
+  k_g_put_col<T><<<nb, 256, 0, c.stream>>>(Z, ld, gc.zf.p, s, n);
   FSD_LAUNCHED(c);
   apply_saddle<T>(c, gc.zf.p, c.w.p);
-  cgs_pass_dev(c, 0, c.V.p, ld, &s->j, 1, mm, c.w.p, nullptr, s->h);
-  cgs_pass_dev(c, 1, c.V.p, ld, &s->j, 1, mm, c.w.p, s->h, s->h + 64);
-  cgs_pass_dev(c, 2, c.V.p, ld, &s->j, 1, mm, c.w.p, s->h + 64, s->h + 128);
+  cgs_pass_dev(c, 0, V, ld, &s->j, 1, mm, c.w.p, nullptr, s->h);
+  cgs_pass_dev(c, 1, V, ld, &s->j, 1, mm, c.w.p, s->h, s->h + 64);
+  cgs_pass_dev(c, 2, V, ld, &s->j, 1, mm, c.w.p, s->h + 64, s->h + 128);
   k_g_givens<<<1, 32, 0, c.stream>>>(s, h_arn, sizeof(T) == 8 ? 1 : 0);
   FSD_LAUNCHED(c);
-  k_g_next_col<<<nb, 256, 0, c.stream>>>(c.V.p, ld, c.w.p, s, n);
+  k_g_next_col<T><<<nb, 256, 0, c.stream>>>(V, ld, c.w.p, s, n);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
 // x += Z y after a cycle
+template <typename T>
 static void cycle_update(Ctx &c, GState *s, double *x) {
   k_g_trisolve<<<1, 32, 0, c.stream>>>(s);
   FSD_LAUNCHED(c);
-  axpy_multi_dev(c, x, c.Z.p, c.nunk, &s->ky, s->y, 1.0);
+  axpy_multi_dev(c, x, basis_z(c, T()), c.nunk, &s->ky, s->y, 1.0);
 }
 
 // The captured solve of A x = b into c.xsol (b = c.rhs).  Appends to graph g
@@ -439,7 +460,7 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
         cudaGraphConditionalHandle h_arn = new_handle(run);
         cap_begin(c, run, r);
         l0 = c.launches;
-        k_g_scale<<<nb, 256, 0, c.stream>>>(c.V.p, c.V.p, s, n, h_arn, 1);
+        k_g_scale<double><<<nb, 256, 0, c.stream>>>(c.V.p, c.V.p, s, n, h_arn, 1);
         FSD_LAUNCHED(c);
         e.l_run += c.launches - l0;
         r = cap_end(c);
@@ -453,7 +474,7 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
         }
         cap_begin(c, run, r);
         l0 = c.launches;
-        cycle_update(c, s, x);
+        cycle_update<double>(c, s, x);
         e.l_run += c.launches - l0;
         cap_end(c);
       }
@@ -480,7 +501,7 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
       l0 = c.launches;
       k_g_inner_begin<<<1, 32, 0, c.stream>>>(s, h_arn);
       FSD_LAUNCHED(c);
-      k_g_scale<<<nb, 256, 0, c.stream>>>(c.V.p, c.res.p, s, n, 0, 0);
+      k_g_scale<float><<<nb, 256, 0, c.stream>>>(c.V32.p, c.res.p, s, n, 0, 0);
       FSD_LAUNCHED(c);
       e.l_run += c.launches - l0;
       d = cap_end(c);
@@ -494,7 +515,7 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
       }
       cap_begin(c, outer, d);
       l0 = c.launches;
-      cycle_update(c, s, x);
+      cycle_update<float>(c, s, x);
       apply_saddle<double>(c, x, w);
       k_g_residual<<<nb, 256, 0, c.stream>>>(c.res.p, b, w, s, n);
       FSD_LAUNCHED(c);

@@ -1,8 +1,9 @@
-// FP64 Krylov primitives for the GMRES of Algorithm 1 step 4: fused
-// multi-vector dot products (classical Gram-Schmidt, applied twice), fused
-// multi-vector updates, scaling.  The basis is stored as k vectors of
-// length n with leading dimension ld.  Reductions are two-stage and
-// deterministic (fixed block partials, fixed reduction order).
+// Krylov primitives for the GMRES of Algorithm 1 step 4: fused multi-vector
+// dot products (classical Gram-Schmidt, applied twice), fused multi-vector
+// updates, scaling.  The basis is stored as k vectors of length n with
+// leading dimension ld, in FP64 or (inner solve of the mixed path) FP32.
+// Reductions are two-stage and deterministic (fixed block partials, fixed
+// reduction order).
 #include "fsd_internal.cuh"
 
 #include <algorithm>
@@ -82,33 +83,43 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, doub
 // basis vectors are taken four at a time so that 4 kE loads are in flight
 // per thread; warp partials go to partial[j * nwarps + warp] (fixed
 // reduction order).
+//
+// The basis element type B is double (the FP64 solve and the Lanczos square
+// roots: every product and sum in FP64) or float (the inner GMRES of the
+// mixed solve, whose operator is FP32 anyway).  With a float basis the
+// products and the sums within a warp are FP32 (exact products of two FP32
+// numbers would need FP64, whose rate is 1/74 of FP32 on this part), the
+// update sum_j coef_j V_j is formed in FP32 and subtracted from the FP64 w,
+// and the cross-warp sums stay FP64.
 constexpr int kE = 4;
 
 // Warp sums of four values with six shuffles: after the exchange across
 // lane bit 4 each lane keeps two of the four partial sums, after bit 3 one;
 // bits 2..0 finish it.  Lane 8 q holds the full sum of value q.
-__device__ __forceinline__ double warp_sum4(const double a[4], int lane) {
+template <typename R>
+__device__ __forceinline__ R warp_sum4(const R a[4], int lane) {
   const bool h4 = lane & 16;
-  const double s0 = h4 ? a[0] : a[2], s1 = h4 ? a[1] : a[3];
-  double b0 = (h4 ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
-  double b1 = (h4 ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
+  const R s0 = h4 ? a[0] : a[2], s1 = h4 ? a[1] : a[3];
+  R b0 = (h4 ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
+  R b1 = (h4 ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
   const bool h3 = lane & 8;
-  double c = (h3 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h3 ? b0 : b1, 8);
+  R c = (h3 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h3 ? b0 : b1, 8);
   c += __shfl_xor_sync(0xffffffffu, c, 4);
   c += __shfl_xor_sync(0xffffffffu, c, 2);
   c += __shfl_xor_sync(0xffffffffu, c, 1);
   return c;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64_t ld, int k,
+template <int MODE, typename B>
+__global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld, int k,
                                              const int *k_dev, int k_add, double *w,
                                              const double *__restrict__ coef, int64_t n,
                                              double *partial) {
+  constexpr bool f64 = sizeof(B) == 8;
   if (k_dev) k = *k_dev + k_add;
-  __shared__ double cs[64];
+  __shared__ B cs[64];
   if (MODE > 0)
-    for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = coef[j];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = (B)coef[j];
   __syncthreads();
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,36 +131,51 @@ __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64
     const int64_t i = t0 + e * T;
     wv[e] = i < n ? w[i] : 0.0;
   }
-  auto ld_col = [&](const double *vj, double *out) {
+  auto ld_col = [&](const B *vj, B *out) {
     if (full) {
 #pragma unroll
       for (int e = 0; e < kE; ++e) out[e] = vj[e * T];
     } else {
 #pragma unroll
-      for (int e = 0; e < kE; ++e) out[e] = t0 + e * T < n ? vj[e * T] : 0.0;
+      for (int e = 0; e < kE; ++e) out[e] = t0 + e * T < n ? vj[e * T] : (B)0;
     }
   };
   if (MODE > 0) {
-    const double *vj = V + t0;
+    const B *vj = V + t0;
+    B us[kE];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) us[e] = (B)0;
     int j = 0;
     for (; j + 4 <= k; j += 4) {
-      double v[4][kE];
+      B v[4][kE];
 #pragma unroll
       for (int q = 0; q < 4; ++q) ld_col(vj + q * ld, v[q]);
       vj += 4 * ld;
 #pragma unroll
-      for (int e = 0; e < kE; ++e)
-        wv[e] -= cs[j] * v[0][e] + cs[j + 1] * v[1][e] + cs[j + 2] * v[2][e] + cs[j + 3] * v[3][e];
+      for (int e = 0; e < kE; ++e) {
+        const B g = cs[j] * v[0][e] + cs[j + 1] * v[1][e] + cs[j + 2] * v[2][e] + cs[j + 3] * v[3][e];
+        if constexpr (f64)
+          wv[e] -= g;
+        else
+          us[e] += g;
+      }
     }
     for (; j < k; ++j, vj += ld) {
-      double v[kE];
+      B v[kE];
       ld_col(vj, v);
 #pragma unroll
-      for (int e = 0; e < kE; ++e) wv[e] -= cs[j] * v[e];
+      for (int e = 0; e < kE; ++e) {
+        if constexpr (f64)
+          wv[e] -= cs[j] * v[e];
+        else
+          us[e] += cs[j] * v[e];
+      }
     }
 #pragma unroll
-    for (int e = 0; e < kE; ++e)
+    for (int e = 0; e < kE; ++e) {
+      if constexpr (!f64) wv[e] -= (double)us[e];
       if (t0 + e * T < n) w[t0 + e * T] = wv[e];
+    }
   }
   const int lane = threadIdx.x & 31;
   const int64_t gw = t0 >> 5;
@@ -163,31 +189,34 @@ __global__ void __launch_bounds__(256) k_cgs(const double *__restrict__ V, int64
     if (lane == 0) partial[gw] = acc;
     return;
   }
-  const double *vj = V + t0;
+  B wb[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) wb[e] = (B)wv[e];
+  const B *vj = V + t0;
   int j = 0;
   for (; j + 4 <= k; j += 4) {
-    double v[4][kE], acc[4];
+    B v[4][kE], acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) ld_col(vj + q * ld, v[q]);
     vj += 4 * ld;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      acc[q] = 0.0;
+      acc[q] = (B)0;
 #pragma unroll
-      for (int e = 0; e < kE; ++e) acc[q] += v[q][e] * wv[e];
+      for (int e = 0; e < kE; ++e) acc[q] += v[q][e] * wb[e];
     }
-    const double r = warp_sum4(acc, lane);
-    if ((lane & 7) == 0) partial[(int64_t)(j + (lane >> 3)) * nwarps + gw] = r;
+    const B r = warp_sum4<B>(acc, lane);
+    if ((lane & 7) == 0) partial[(int64_t)(j + (lane >> 3)) * nwarps + gw] = (double)r;
   }
   for (; j < k; ++j, vj += ld) {
-    double v[kE];
+    B v[kE];
     ld_col(vj, v);
-    double acc = 0.0;
+    B acc = (B)0;
 #pragma unroll
-    for (int e = 0; e < kE; ++e) acc += v[e] * wv[e];
+    for (int e = 0; e < kE; ++e) acc += v[e] * wb[e];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) partial[(int64_t)j * nwarps + gw] = acc;
+    if (lane == 0) partial[(int64_t)j * nwarps + gw] = (double)acc;
   }
 }
 
@@ -196,18 +225,19 @@ static int cgs_blocks(int64_t n) { return std::max(1, ceil_div(n, 256LL * kE)); 
 // out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef.  With k_dev
 // non-null the basis size is read on the device (k = *k_dev + k_add <= kmax),
 // so the pass can sit in a captured loop whose trip count the host never sees.
-static void cgs_launch(Ctx &c, int mode, const double *V, int64_t ld, int k, const int *k_dev,
+template <typename B>
+static void cgs_launch(Ctx &c, int mode, const B *V, int64_t ld, int k, const int *k_dev,
                        int k_add, int kmax, double *w, const double *coef_dev, double *out_dev) {
   ProfScope ps(c, PG_KRYLOV);
   const int64_t n = c.nunk;
   const int blocks = cgs_blocks(n);
   const int nwarps = blocks * 8;
   if (mode == 0)
-    k_cgs<0><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
+    k_cgs<0, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
   else if (mode == 1)
-    k_cgs<1><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
+    k_cgs<1, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
   else
-    k_cgs<2><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
+    k_cgs<2, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
   FSD_LAUNCHED(c);
   if (mode == 2)
     k_dot_final<<<1, 256, 0, c.stream>>>(c.partial.p, nwarps, 1, nullptr, 0, out_dev);
@@ -222,7 +252,17 @@ void cgs_pass(Ctx &c, int mode, const double *V, int64_t ld, int k, double *w,
   cgs_launch(c, mode, V, ld, k, nullptr, 0, k, w, coef_dev, out_dev);
 }
 
+void cgs_pass(Ctx &c, int mode, const float *V, int64_t ld, int k, double *w,
+              const double *coef_dev, double *out_dev) {
+  cgs_launch(c, mode, V, ld, k, nullptr, 0, k, w, coef_dev, out_dev);
+}
+
 void cgs_pass_dev(Ctx &c, int mode, const double *V, int64_t ld, const int *k_dev, int k_add,
+                  int kmax, double *w, const double *coef_dev, double *out_dev) {
+  cgs_launch(c, mode, V, ld, 0, k_dev, k_add, kmax, w, coef_dev, out_dev);
+}
+
+void cgs_pass_dev(Ctx &c, int mode, const float *V, int64_t ld, const int *k_dev, int k_add,
                   int kmax, double *w, const double *coef_dev, double *out_dev) {
   cgs_launch(c, mode, V, ld, 0, k_dev, k_add, kmax, w, coef_dev, out_dev);
 }
@@ -231,42 +271,60 @@ int64_t cgs_partial_size(int64_t nunk, int kmax) {
   return (int64_t)cgs_blocks(nunk) * 8 * (kmax + 1);
 }
 
-// w[i] += sign * sum_j coef[j] V_j[i]
-__global__ void k_axpy_multi(double *w, const double *__restrict__ V, int64_t ld, int k,
+// w[i] += sign * sum_j coef[j] V_j[i]; with a float basis the sum over j is
+// FP32 and is added to the FP64 w.
+template <typename B>
+__global__ void k_axpy_multi(double *w, const B *__restrict__ V, int64_t ld, int k,
                              const int *k_dev, const double *__restrict__ coef, double sign,
                              int64_t n) {
   if (k_dev) k = *k_dev;
-  __shared__ double cs[128];
-  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = sign * coef[j];
+  __shared__ B cs[128];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = (B)(sign * coef[j]);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double s = w[i];
-    for (int j = 0; j < k; ++j) s += cs[j] * V[(int64_t)j * ld + i];
-    w[i] = s;
+    if constexpr (sizeof(B) == 8) {
+      double s = w[i];
+      for (int j = 0; j < k; ++j) s += cs[j] * V[(int64_t)j * ld + i];
+      w[i] = s;
+    } else {
+      B s = (B)0;
+      for (int j = 0; j < k; ++j) s += cs[j] * V[(int64_t)j * ld + i];
+      w[i] += (double)s;
+    }
   }
+}
+
+template <typename B>
+static void axpy_multi_launch(Ctx &c, double *w, const B *V, int64_t ld, int k, const int *k_dev,
+                              const double *coef_dev, double sign) {
+  ProfScope ps(c, PG_KRYLOV);
+  const int64_t n = c.nunk;
+  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms);
+  k_axpy_multi<B><<<blocks, 256, 0, c.stream>>>(w, V, ld, k, k_dev, coef_dev, sign, n);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
 }
 
 void axpy_multi(Ctx &c, double *w, const double *V, int64_t ld, int k, const double *coef_dev,
                 double sign) {
-  if (k <= 0) return;
-  ProfScope ps(c, PG_KRYLOV);
-  const int64_t n = c.nunk;
-  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms);
-  k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, k, nullptr, coef_dev, sign, n);
-  FSD_LAUNCHED(c);
-  FSD_CUDA(cudaGetLastError());
+  if (k > 0) axpy_multi_launch(c, w, V, ld, k, nullptr, coef_dev, sign);
+}
+
+void axpy_multi(Ctx &c, double *w, const float *V, int64_t ld, int k, const double *coef_dev,
+                double sign) {
+  if (k > 0) axpy_multi_launch(c, w, V, ld, k, nullptr, coef_dev, sign);
 }
 
 // w += sign * sum_{j < *k_dev} coef[j] V_j (count read on the device)
 void axpy_multi_dev(Ctx &c, double *w, const double *V, int64_t ld, const int *k_dev,
                     const double *coef_dev, double sign) {
-  ProfScope ps(c, PG_KRYLOV);
-  const int64_t n = c.nunk;
-  int blocks = std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms);
-  k_axpy_multi<<<blocks, 256, 0, c.stream>>>(w, V, ld, 0, k_dev, coef_dev, sign, n);
-  FSD_LAUNCHED(c);
-  FSD_CUDA(cudaGetLastError());
+  axpy_multi_launch(c, w, V, ld, 0, k_dev, coef_dev, sign);
+}
+
+void axpy_multi_dev(Ctx &c, double *w, const float *V, int64_t ld, const int *k_dev,
+                    const double *coef_dev, double sign) {
+  axpy_multi_launch(c, w, V, ld, 0, k_dev, coef_dev, sign);
 }
 
 __global__ void k_scale(double *y, const double *__restrict__ x, double s, int64_t n) {
@@ -285,6 +343,55 @@ void vec_scale_host(Ctx &c, double *y, const double *x, double s) {
   ProfScope ps(c, PG_KRYLOV);
   int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * (int64_t)c.num_sms);
   k_scale<<<blocks, 256, 0, c.stream>>>(y, x, s, c.nunk);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+// y = (float)(s x)
+__global__ void k_scale_f32(float *y, const double *__restrict__ x, double s, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = (float)(x[i] * s);
+}
+
+void vec_scale_host(Ctx &c, float *y, const double *x, double s) {
+  ProfScope ps(c, PG_KRYLOV);
+  int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * (int64_t)c.num_sms);
+  k_scale_f32<<<blocks, 256, 0, c.stream>>>(y, x, s, c.nunk);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+// y = (double) x
+__global__ void k_widen(double *y, const float *__restrict__ x, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = (double)x[i];
+}
+
+// z32 = (float) z and z = (double) z32: the FP32 copy and the operator input
+// hold the same values
+__global__ void k_round_f32(float *z32, double *z, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float v = (float)z[i];
+    z32[i] = v;
+    z[i] = (double)v;
+  }
+}
+
+void vec_widen(Ctx &c, double *y, const float *x) {
+  ProfScope ps(c, PG_KRYLOV);
+  int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * (int64_t)c.num_sms);
+  k_widen<<<blocks, 256, 0, c.stream>>>(y, x, c.nunk);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
+}
+
+void vec_round_f32(Ctx &c, float *z32, double *z) {
+  ProfScope ps(c, PG_KRYLOV);
+  int blocks = std::min<int64_t>(ceil_div(c.nunk, 256), 8 * (int64_t)c.num_sms);
+  k_round_f32<<<blocks, 256, 0, c.stream>>>(z32, z, c.nunk);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
