@@ -201,6 +201,7 @@ struct Ctx {
   // the Lanczos square roots, Z (FP64) the FP64 solve
   DBuf<float> V32, Z32;
   DBuf<double> kv, kz;  // FP64 copies of v_j and z_j for the FP32 basis
+  DBuf<unsigned> cgs_ticket;  // blocks finished in the running Gram-Schmidt pass (0 between passes)
   double *h_pinned = nullptr;  // host pinned scratch (dots)
   bool have_prev = false;
   // ---- outputs / near field scratch
@@ -366,6 +367,7 @@ void vec_round_f32(Ctx &c, float *z32, double *z);  // z32 = (float) z, z = (dou
 // reduction order and hence every result is the same on any GPU; 608 is 4 per
 // SM on a 152-SM part.
 constexpr int kDotPartials = 608;
+constexpr int kMaxBasis = 64;  // longest basis a Gram-Schmidt pass takes
 int64_t cgs_partial_size(int64_t nunk, int kmax);
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b,
                int64_t n);                          // y = a x + b y

@@ -81,8 +81,8 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, doub
 //   MODE 2:  w -= sum_j coef_j V_j, then partial ||w||^2
 // Each thread owns kE elements spaced by the grid's thread count (coalesced);
 // basis vectors are taken four at a time so that 4 kE loads are in flight
-// per thread; warp partials go to partial[j * nwarps + warp] (fixed
-// reduction order).
+// per thread; block partials go to partial[j * blocks + block] and the last
+// block to finish reduces them into out (fixed reduction order throughout).
 //
 // The basis element type B is double (the FP64 solve and the Lanczos square
 // roots: every product and sum in FP64) or float (the inner GMRES of the
@@ -114,10 +114,12 @@ template <int MODE, typename B>
 __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld, int k,
                                              const int *k_dev, int k_add, double *w,
                                              const double *__restrict__ coef, int64_t n,
-                                             double *partial) {
+                                             double *partial, double *out, unsigned *ticket) {
   constexpr bool f64 = sizeof(B) == 8;
   if (k_dev) k = *k_dev + k_add;
-  __shared__ B cs[64];
+  __shared__ B cs[kMaxBasis];
+  __shared__ double wred[kMaxBasis][8];  // per basis vector, per warp
+  __shared__ int last;
   if (MODE > 0)
     for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = (B)coef[j];
   __syncthreads();
@@ -131,13 +133,13 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
     const int64_t i = t0 + e * T;
     wv[e] = i < n ? w[i] : 0.0;
   }
-  auto ld_col = [&](const B *vj, B *out) {
+  auto ld_col = [&](const B *vj, B *out_) {
     if (full) {
 #pragma unroll
-      for (int e = 0; e < kE; ++e) out[e] = vj[e * T];
+      for (int e = 0; e < kE; ++e) out_[e] = vj[e * T];
     } else {
 #pragma unroll
-      for (int e = 0; e < kE; ++e) out[e] = t0 + e * T < n ? vj[e * T] : (B)0;
+      for (int e = 0; e < kE; ++e) out_[e] = t0 + e * T < n ? vj[e * T] : (B)0;
     }
   };
   if (MODE > 0) {
@@ -177,72 +179,92 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
       if (t0 + e * T < n) w[t0 + e * T] = wv[e];
     }
   }
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = t0 >> 5;
-  const int64_t nwarps = T >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (MODE == 2) {
     double acc = 0.0;
 #pragma unroll
     for (int e = 0; e < kE; ++e) acc += wv[e] * wv[e];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) partial[gw] = acc;
-    return;
-  }
-  B wb[kE];
+    if (lane == 0) wred[0][warp] = acc;
+  } else {
+    B wb[kE];
 #pragma unroll
-  for (int e = 0; e < kE; ++e) wb[e] = (B)wv[e];
-  const B *vj = V + t0;
-  int j = 0;
-  for (; j + 4 <= k; j += 4) {
-    B v[4][kE], acc[4];
+    for (int e = 0; e < kE; ++e) wb[e] = (B)wv[e];
+    const B *vj = V + t0;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      B v[4][kE], acc[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ld_col(vj + q * ld, v[q]);
-    vj += 4 * ld;
+      for (int q = 0; q < 4; ++q) ld_col(vj + q * ld, v[q]);
+      vj += 4 * ld;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      acc[q] = (B)0;
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = (B)0;
 #pragma unroll
-      for (int e = 0; e < kE; ++e) acc[q] += v[q][e] * wb[e];
+        for (int e = 0; e < kE; ++e) acc[q] += v[q][e] * wb[e];
+      }
+      const B r = warp_sum4<B>(acc, lane);
+      if ((lane & 7) == 0) wred[j + (lane >> 3)][warp] = (double)r;
     }
-    const B r = warp_sum4<B>(acc, lane);
-    if ((lane & 7) == 0) partial[(int64_t)(j + (lane >> 3)) * nwarps + gw] = (double)r;
-  }
-  for (; j < k; ++j, vj += ld) {
-    B v[kE];
-    ld_col(vj, v);
-    B acc = (B)0;
+    for (; j < k; ++j, vj += ld) {
+      B v[kE];
+      ld_col(vj, v);
+      B acc = (B)0;
 #pragma unroll
-    for (int e = 0; e < kE; ++e) acc += v[e] * wb[e];
+      for (int e = 0; e < kE; ++e) acc += v[e] * wb[e];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) partial[(int64_t)j * nwarps + gw] = (double)acc;
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) wred[j][warp] = (double)acc;
+    }
   }
+  // block partials (warps summed in a fixed order), then the last block to
+  // finish sums the block partials in a fixed order: no second launch, and
+  // the result does not depend on which block finishes last
+  const int kr = MODE == 2 ? 1 : k;
+  __syncthreads();
+  if (threadIdx.x < kr) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += wred[threadIdx.x][q];
+    partial[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  for (int jj = warp; jj < kr; jj += 8) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (int64_t)jj * gridDim.x + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[jj] = s;
+  }
+  if (threadIdx.x == 0) atomicExch(ticket, 0u);
 }
 
 static int cgs_blocks(int64_t n) { return std::max(1, ceil_div(n, 256LL * kE)); }
 
-// out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef.  With k_dev
-// non-null the basis size is read on the device (k = *k_dev + k_add <= kmax),
-// so the pass can sit in a captured loop whose trip count the host never sees.
+// out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef (mode 2:
+// out[0] = ||w||^2).  With k_dev non-null the basis size is read on the
+// device (k = *k_dev + k_add <= kmax), so the pass can sit in a captured loop
+// whose trip count the host never sees.  One launch per pass.
 template <typename B>
 static void cgs_launch(Ctx &c, int mode, const B *V, int64_t ld, int k, const int *k_dev,
                        int k_add, int kmax, double *w, const double *coef_dev, double *out_dev) {
   ProfScope ps(c, PG_KRYLOV);
+  if (std::max(k, kmax) > kMaxBasis) throw Invalid{"Krylov basis longer than 64 vectors"};
   const int64_t n = c.nunk;
   const int blocks = cgs_blocks(n);
-  const int nwarps = blocks * 8;
+  unsigned *tk = c.cgs_ticket.p;
+  double *pp = c.partial.p;
   if (mode == 0)
-    k_cgs<0, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
+    k_cgs<0, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, pp, out_dev, tk);
   else if (mode == 1)
-    k_cgs<1, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
+    k_cgs<1, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, pp, out_dev, tk);
   else
-    k_cgs<2, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, c.partial.p);
-  FSD_LAUNCHED(c);
-  if (mode == 2)
-    k_dot_final<<<1, 256, 0, c.stream>>>(c.partial.p, nwarps, 1, nullptr, 0, out_dev);
-  else
-    k_dot_final<<<kmax, 256, 0, c.stream>>>(c.partial.p, nwarps, k, k_dev, k_add, out_dev);
+    k_cgs<2, B><<<blocks, 256, 0, c.stream>>>(V, ld, k, k_dev, k_add, w, coef_dev, n, pp, out_dev, tk);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -268,7 +290,7 @@ void cgs_pass_dev(Ctx &c, int mode, const float *V, int64_t ld, const int *k_dev
 }
 
 int64_t cgs_partial_size(int64_t nunk, int kmax) {
-  return (int64_t)cgs_blocks(nunk) * 8 * (kmax + 1);
+  return (int64_t)cgs_blocks(nunk) * (kmax + 1);
 }
 
 // w[i] += sign * sum_j coef[j] V_j[i]; with a float basis the sum over j is
