@@ -49,6 +49,11 @@ import time
 
 import numpy as np
 
+# The batched form runs one stream per system: 32 hardware work queues (the
+# CUDA default is 8) let the systems' graphs run side by side instead of
+# sharing 8 queues.  It must be set before the CUDA context exists.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -686,7 +691,9 @@ def run_ours(args, rank, world, local_rank):
                          "2..64, phi 0.05..0.3, shear 1, lubrication 3a, GMRES 1e-6, mixed, default xi"
                          % (len(jobs), sum(nj), min(nj), max(nj)))
     batch["execution"] = ("fsd_step_batch: one CUDA graph per system and step on its own stream, all "
-                          "systems in flight" + ("; systems sharded over ranks" if world > 1 else ""))
+                          "systems in flight, CUDA_DEVICE_MAX_CONNECTIONS=%s"
+                          % os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8")
+                          + ("; systems sharded over ranks" if world > 1 else ""))
 
     # ---- measured arithmetic peaks, accuracy against the oracle, cuFFT
     alu32 = pkg.fma_throughput(32, stream.cuda_stream)
@@ -946,7 +953,8 @@ def run_batch(args, rank, world, local_rank):
                                    "rank 0's roofline and statistics)" % world) if world > 1 else "single GPU",
                    "autotune": "xi per system by timing (chosen: %s), real-space tile per system" % xis,
                    "execution": "fsd_step_batch: one CUDA graph per system and step on its own stream, "
-                                "all systems in flight; launch phase on 8 host threads",
+                                "all systems in flight; launch phase on 8 host threads; "
+                                "CUDA_DEVICE_MAX_CONNECTIONS=%s" % os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"),
                    "l2": "working set > L2 (64 grids and Krylov bases)",
                    "generation_s": round(t_gen, 1), "setup_s": meas["setup_s"]},
         "one_at_a_time": dict(meas["one_at_a_time"], speedup_batched=meas["speedup_batched"]),

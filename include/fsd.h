@@ -308,7 +308,11 @@ fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead_pos,
  * stream; each system's solve (or step) is one captured CUDA graph
  * (FSD_FLAG_GRAPH is forced on), and all systems' graphs are launched before
  * any is waited for, most expensive first, so they run concurrently.  Results
- * are those of fsd_solve / fsd_step on each system alone.
+ * are those of fsd_solve / fsd_step on each system alone.  The streams share
+ * the device's hardware work queues: the environment variable
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 (set before the process creates its CUDA
+ * context; the default is 8) lets up to 32 systems' kernels run side by side
+ * (measured on 64 systems: 438 -> 390 ms per step).
  * ------------------------------------------------------------------------- */
 typedef struct fsd_batch fsd_batch;
 
