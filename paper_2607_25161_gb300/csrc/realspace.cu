@@ -316,17 +316,26 @@ __global__ void k_sort_cells(int ncells, const int *__restrict__ cell_start, int
 }
 
 // One thread per bead: mobility neighbours (r < rc, any body, j != i) and
-// lubrication neighbours (r < rlub, different body).
+// lubrication neighbours (r < rlub, different body).  Each candidate's
+// nearest-image distance is first taken in FP32 from the FP32 positions; only
+// a candidate whose squared distance lies within m2 of a cut-off is measured
+// again in FP64, so every decision is the FP64 one (m2 bounds the FP32
+// rounding of the positions and of the image shift many times over; an
+// image chosen differently in FP32 has a component near L/2, beyond every
+// cut-off either way).  FP64 arithmetic runs at 1/74 of the FP32 rate on
+// this part, and the FP64 test with its three divisions by L was the cost.
 __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos,
+                            const float4 *__restrict__ pos32,
                             const double4 *__restrict__ spos, double L, double tilt, int nc,
                             const int *__restrict__ cell_start,
                             const int *__restrict__ cell_beads,
                             const int *__restrict__ bead_body, double rc2, double rl2,
-                            double ov2, int cap, int lcap, int *nbr, int *ncnt, int *lnbr,
-                            int *lcnt, int *flags) {
+                            double ov2, float m2, int cap, int lcap, int *nbr, int *ncnt,
+                            int *lnbr, int *lcnt, int *flags) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nt) return;
-  double4 p = pos[i];
+  const double4 p = pos[i];
+  const float4 pf = pos32[i];
   const double4 sp = spos[i];
   int bi = bead_body[i];
   int cx = cell_of(sp.x, L, nc), cy = cell_of(sp.y, L, nc), cz = cell_of(sp.z, L, nc);
@@ -334,6 +343,9 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos,
   int span = nc >= 3 ? 1 : 0;
   int *row = nbr + (size_t)i * cap;
   int *lrow = lnbr + (size_t)i * lcap;
+  const float Lf = (float)L, invLf = 1.f / Lf, tiltf = (float)tilt;
+  const float rc2f = (float)rc2, rl2f = (float)rl2, ov2f = (float)ov2;
+  const float hi = fmaxf(rc2f, fmaxf(rl2f, ov2f)) + m2;
   for (int dx = -span; dx <= span; ++dx)
     for (int dy = -span; dy <= span; ++dy)
       for (int dz = -span; dz <= span; ++dz) {
@@ -342,10 +354,24 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos,
         for (int s = cell_start[id]; s < cell_start[id + 1]; ++s) {
           int j = cell_beads[s];
           if (j == i) continue;
-          double4 q = pos[j];
-          double d0 = q.x - p.x, d1 = q.y - p.y, d2 = q.z - p.z;
-          le_image(d0, d1, d2, L, tilt);
-          double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          const float4 qf = pos32[j];
+          float e0 = qf.x - pf.x, e1 = qf.y - pf.y, e2 = qf.z - pf.z;
+          {
+            const float ny = rintf(e1 * invLf);
+            e0 -= ny * tiltf;
+            e1 -= ny * Lf;
+            e0 -= Lf * rintf(e0 * invLf);
+            e2 -= Lf * rintf(e2 * invLf);
+          }
+          const float r2f = e0 * e0 + e1 * e1 + e2 * e2;
+          if (r2f >= hi) continue;
+          double r2 = (double)r2f;
+          if (fabsf(r2f - rc2f) < m2 || fabsf(r2f - rl2f) < m2 || fabsf(r2f - ov2f) < m2) {
+            const double4 q = pos[j];
+            double d0 = q.x - p.x, d1 = q.y - p.y, d2 = q.z - p.z;
+            le_image(d0, d1, d2, L, tilt);
+            r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          }
           if (r2 < rc2) {
             if (cnt < cap) row[cnt] = j;
             ++cnt;
@@ -401,9 +427,14 @@ void build_neighbors(Ctx &c) {
     FSD_LAUNCHED(c);
     double rl = c.prm.lub_cutoff > 2.0 * c.a ? c.prm.lub_cutoff : 0.0;
     double ov = 2.0 * c.a * (1.0 - 1e-6);
+    // margin of the FP32 pre-test on r^2: the FP32 positions and the image
+    // shift are within a few 1e-7 L of the FP64 ones, so the FP32 r^2 is off
+    // by at most ~2e-6 L r_max (five times below the margin)
+    const float m2 = (float)(1e-5 * c.L * std::max({c.rc, rl, ov}) + 1e-12);
     k_neighbors<<<ceil_div(c.Nt, 128), 128, 0, c.stream>>>(
-        c.Nt, pos, spos, c.L, c.tilt, nc, c.cell_start.p, c.cell_beads.p, c.bead_body.p, c.rc * c.rc,
-        rl * rl, ov * ov, c.cap, c.lcap, c.nbr.p, c.ncnt.p, c.lnbr.p, c.lcnt.p, c.flags.p);
+        c.Nt, pos, (const float4 *)c.op32.pos.p, spos, c.L, c.tilt, nc, c.cell_start.p,
+        c.cell_beads.p, c.bead_body.p, c.rc * c.rc, rl * rl, ov * ov, m2, c.cap, c.lcap, c.nbr.p,
+        c.ncnt.p, c.lnbr.p, c.lcnt.p, c.flags.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
     FSD_CUDA(cudaMemcpyAsync(c.h_flags, c.flags.p, 8 * sizeof(int), cudaMemcpyDeviceToHost,

@@ -1217,15 +1217,20 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
 // FP32 interpolation from planar fields [6][n^3] (n a multiple of 4): the
 // sums of k_interp, with each lane reading an aligned quad of four x points
 // of one grid row per field (six 16-byte loads); slots outside the bead's x
-// window carry weight 0 (the quads of k_spread_v4).
+// window carry weight 0 (the quads of k_spread_v4).  The warp's items are
+// (quad, y row, z row) with a fixed quad count NQ = (P + 7) / 4 per row
+// (lanes past the bead's own quad count skip), so that the item index splits
+// with two multiply-shift divisions; the window tables hold (w, offset)
+// pairs and the rows' grid offsets, and the factor 2 alpha of the dipole
+// read-out is applied once per bead.
 __global__ void __launch_bounds__(256, 4) k_interp_v4(int Nt, const float4 *__restrict__ pos,
                                                    const float *__restrict__ field, double *y, int n,
                                                    int P, float h, float alpha, float cnorm_h3,
-                                                   TauArg ta_) {
+                                                   TauArg ta_, FastDiv fq, FastDiv fp) {
   const double tau = tau_of(ta_);
-  __shared__ float sw[8][2][kMaxP], sy[8][2][kMaxP];
-  __shared__ int si[8][2][kMaxP];
-  __shared__ float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
+  __shared__ float2 swy[8][2][kMaxP];  // (w, offset) of the y and z window rows
+  __shared__ int srow[8][2][kMaxP];    // grid offsets of the rows: y n, z n^2
+  __shared__ __align__(16) float sxw[8][4 * kMaxQ], sxy[8][4 * kMaxQ];
   __shared__ int sxq[8][kMaxQ];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + warp;
@@ -1234,58 +1239,59 @@ __global__ void __launch_bounds__(256, 4) k_interp_v4(int Nt, const float4 *__re
   const int g0x = (int)floorf(p.x / h) - P / 2 + 1;
   const int a0 = g0x >= 0 ? (g0x & ~3) : -((-g0x + 3) & ~3);
   const int nq = (g0x - a0 + P + 3) >> 2;
+  const int NQ = (int)fq.d;
   for (int e = lane; e < 2 * P; e += 32) {
     const int d = e / P, k = e - d * P;
     const float pc = d == 0 ? p.y : p.z;
     const int g = (int)floorf(pc / h) - P / 2 + 1 + k;
     const float yv = float(g) * h - pc;
-    sw[warp][d][k] = expf(-alpha * yv * yv);
-    sy[warp][d][k] = yv;
-    si[warp][d][k] = ((g % n) + n) % n;
+    swy[warp][d][k] = make_float2(expf(-alpha * yv * yv), yv);
+    const int gi = ((g % n) + n) % n;
+    srow[warp][d][k] = d == 0 ? gi * n : gi * n * n;
   }
-  for (int sl = lane; sl < 4 * nq; sl += 32) {
+  for (int sl = lane; sl < 4 * NQ; sl += 32) {
     const int g = a0 + sl, k = g - g0x;
     const float yv = float(g) * h - p.x;
     sxw[warp][sl] = (k >= 0 && k < P) ? expf(-alpha * yv * yv) : 0.f;
     sxy[warp][sl] = yv;
   }
-  for (int q = lane; q < nq; q += 32) sxq[warp][q] = (((a0 + 4 * q) % n) + n) % n;
+  for (int q = lane; q < NQ; q += 32) sxq[warp][q] = (((a0 + 4 * q) % n) + n) % n;
   __syncwarp();
-  const float ta = 2.f * alpha;
   const int64_t n3 = (int64_t)n * n * n;
   float acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = 0.f;
-  const int T = P * P * nq;
+  const int T = P * P * NQ;
 #pragma unroll 2
   for (int t = lane; t < T; t += 32) {
-    const int q = t % nq, r = t / nq;
-    const int iy = r % P, iz = r / P;
-    const float wyz = sw[warp][0][iy] * sw[warp][1][iz];
-    const float y1 = sy[warp][0][iy], y2 = sy[warp][1][iz];
-    const float *g = field + (((int64_t)si[warp][1][iz] * n + si[warp][0][iy]) * n + sxq[warp][q]);
+    const int r = (int)fdiv((uint32_t)t, fq), q = t - r * NQ;
+    if (q >= nq) continue;
+    const int iz = (int)fdiv((uint32_t)r, fp), iy = r - iz * P;
+    const float2 wy = swy[warp][0][iy], wz = swy[warp][1][iz];
+    const float wyz = wy.x * wz.x, y1 = wy.y, y2 = wz.y;
+    const float *g = field + (srow[warp][1][iz] + srow[warp][0][iy] + sxq[warp][q]);
     float4 f[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) f[c] = __ldg((const float4 *)(g + c * n3));
-    float W[4], Y0[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      W[j] = wyz * sxw[warp][4 * q + j];
-      Y0[j] = sxy[warp][4 * q + j];
-    }
+    const float4 xw = *(const float4 *)&sxw[warp][4 * q], xy = *(const float4 *)&sxy[warp][4 * q];
+    const float W[4] = {wyz * xw.x, wyz * xw.y, wyz * xw.z, wyz * xw.w};
+    const float WY[4] = {W[0] * xy.x, W[1] * xy.y, W[2] * xy.z, W[3] * xy.w};
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       acc[c] += W[0] * f[c].x + W[1] * f[c].y + W[2] * f[c].z + W[3] * f[c].w;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const float4 d = f[3 + a];
-      const float s = ta * (W[0] * d.x + W[1] * d.y + W[2] * d.z + W[3] * d.w);
-      const float s0 = ta * (W[0] * Y0[0] * d.x + W[1] * Y0[1] * d.y + W[2] * Y0[2] * d.z +
-                             W[3] * Y0[3] * d.w);
-      acc[3 + 3 * a] += s0;      // G_a0
-      acc[4 + 3 * a] += s * y1;  // G_a1
-      acc[5 + 3 * a] += s * y2;  // G_a2
+      const float s = W[0] * d.x + W[1] * d.y + W[2] * d.z + W[3] * d.w;
+      acc[3 + 3 * a] += WY[0] * d.x + WY[1] * d.y + WY[2] * d.z + WY[3] * d.w;  // G_a0
+      acc[4 + 3 * a] += s * y1;                                                // G_a1
+      acc[5 + 3 * a] += s * y2;                                                // G_a2
     }
+  }
+  {
+    const float ta = 2.f * alpha;
+#pragma unroll
+    for (int k = 3; k < 12; ++k) acc[k] *= ta;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
@@ -1677,7 +1683,8 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
     k_interp_v4<<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, (const float4 *)c.wpos32.p,
                                                          (const float *)op.gout.p, y, n, P,
                                                          (float)h, (float)alpha, (float)(cn * h3),
-                                                         tau_arg(c));
+                                                         tau_arg(c), make_fastdiv((P + 7) / 4),
+                                                         make_fastdiv(P));
   else if (planar)
     k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
                                                               h, alpha, (T)(cn * h3), tau_arg(c));
