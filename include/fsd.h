@@ -109,7 +109,7 @@ enum {
  *                            [2: the real-space sum beside the wave-space
  *                            chain on a second stream]
  *   FSD_RS_BLOCKS_PER_SM=k   persistent real-space blocks per SM while
- *                            overlapped [2; 0: as many as fit]
+ *                            overlapped [0: as many as fit]
  *   FSD_SPREAD_ATOMIC=1      FP32 spreading by vector atomic adds per bead
  *                            [grid-centric gather by 8^3 tiles]
  *   FSD_BATCH_THREADS=k      host threads of the batched launch phase [8]

@@ -151,10 +151,9 @@ struct Ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool overlap = false;        // use it (off while profiling)
   bool rs_overlapped = false;  // the real-space launch in progress is the overlapped one
-  int rs_blocks_per_sm = 2;    // persistent real-space blocks per SM when overlapped (0: all
-                               // that fit); 2 leaves room for the wave-space kernels beside
-                               // it: measured 84.8 ms per step against 86.2 (all) and 87.0
-                               // (one stream) on the 32768-bead step
+  int rs_blocks_per_sm = 0;    // persistent real-space blocks per SM when overlapped (0: all
+                               // that fit): on the 32768-bead step 63.6 ms (all) against
+                               // 65.8 (two) and 65.4 (one stream)
   DBuf<double> yw;             // wave-space part of an overlapped application
   // grid-centric FP32 spreading: the grid in 8^3 tiles, per tile the beads
   // whose window reaches it (rebuilt when the positions change)

@@ -100,10 +100,10 @@ struct FftPlan {
   FftStage st[kMaxStages];
 };
 
-// Stages 16^a 9^b 8^c 4^d 2^e 3^f 5^g with big_radix (FP32: the largest
-// register DFTs first, fewer passes through shared memory), else
-// 4^d 2^e 3^f 5^g (FP64: the register cost of a 16-point DFT in doubles
-// costs more occupancy than the saved passes gain); per stage the twiddles
+// Stages 16^a 9^b 8^c 4^d 2^e 3^f 5^g with big_radix (the largest register
+// DFTs first: fewer passes through shared memory, and fewer twiddle products,
+// which is what an FP64 transform spends its time on where FP64 runs at 1/74
+// of the FP32 rate), else 4^d 2^e 3^f 5^g; per stage the twiddles
 // exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns, stored contiguously
 // (complex) from toff.
 static FftPlan make_plan(int n, std::vector<double> *tw, bool big_radix) {
@@ -320,20 +320,12 @@ __device__ Cx<T> *fft_lines(Cx<T> *A, Cx<T> *B, int nl, int n, int ls, const Fft
   Cx<T> *in = A, *out = B;
   for (int s = 0; s < plan.nst; ++s) {
     const FftStage &st = plan.st[s];
-    bool done = false;
-    if constexpr (sizeof(T) == 4) {  // FP32 plans use the register DFTs
-      done = true;
-      if (st.R == 16)
-        stockham_stage<T, 16>(in, out, nl, n, ls, st, tws, sg);
-      else if (st.R == 9)
-        stockham_stage<T, 9>(in, out, nl, n, ls, st, tws, sg);
-      else if (st.R == 8)
-        stockham_stage<T, 8>(in, out, nl, n, ls, st, tws, sg);
-      else
-        done = false;
-    }
-    if (done)
-      ;
+    if (st.R == 16)
+      stockham_stage<T, 16>(in, out, nl, n, ls, st, tws, sg);
+    else if (st.R == 9)
+      stockham_stage<T, 9>(in, out, nl, n, ls, st, tws, sg);
+    else if (st.R == 8)
+      stockham_stage<T, 8>(in, out, nl, n, ls, st, tws, sg);
     else if (st.R == 4)
       stockham_stage<T, 4>(in, out, nl, n, ls, st, tws, sg);
     else if (st.R == 2)
@@ -1214,6 +1206,99 @@ __global__ void __launch_bounds__(256) k_interp(int Nt, const typename V4Of<T>::
   yr[10] += s2 * 0.5 * (G12 + G21);
 }
 
+// The sums of k_interp from interleaved fields [n^3][8], factored by grid
+// row: each lane takes whole (y, z) rows of the window and first sums the
+// row along x (the six fields weighted by w_x, the three dipole fields also
+// by w_x (x - p_x)), then adds the row's sums with its y and z factors.
+// Ten products per window point instead of eighteen: the FP64 operator,
+// whose arithmetic runs at 1/74 of the FP32 rate, spends its interpolation
+// there.
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp_rows(int Nt, const typename V4Of<T>::type *__restrict__ pos,
+                                                     const T *__restrict__ grid, double *y, int n,
+                                                     int P, T h, T alpha, T cnorm_h3, TauArg ta_,
+                                                     FastDiv fp) {
+  const double tau = tau_of(ta_);
+  __shared__ T sw[8][3][kMaxP], sy[8][3][kMaxP], swx[8][kMaxP];
+  __shared__ int si[8][3][kMaxP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= Nt) return;
+  const auto p = pos[i];
+  const T pc[3] = {p.x, p.y, p.z};
+  for (int e = lane; e < 3 * P; e += 32) {
+    int d = e / P, k = e - d * P;
+    int g0 = (int)floor_t<T>(pc[d] / h) - P / 2 + 1;
+    int g = g0 + k;
+    T yv = T(g) * h - pc[d];
+    const T w = exp_t<T>(-alpha * yv * yv);
+    sw[warp][d][k] = w;
+    sy[warp][d][k] = yv;
+    si[warp][d][k] = ((g % n) + n) % n;
+    if (d == 0) swx[warp][k] = w * yv;
+  }
+  __syncwarp();
+  const T ta = T(2) * alpha;
+  T acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = T(0);
+  for (int r = lane; r < P * P; r += 32) {
+    const int iz = (int)fdiv((uint32_t)r, fp), iy = r - iz * P;
+    const T* row = grid + (((int64_t)si[warp][2][iz] * n + si[warp][1][iy]) * n << 3);
+    T S[6], Tx[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) S[c] = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Tx[a] = T(0);
+    for (int ix = 0; ix < P; ++ix) {
+      T g6[6];
+      load6<T>(row + ((int64_t)si[warp][0][ix] << 3), g6);
+      const T w = sw[warp][0][ix], wy = swx[warp][ix];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) S[c] += w * g6[c];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Tx[a] += wy * g6[3 + a];
+    }
+    const T wyz = sw[warp][1][iy] * sw[warp][2][iz];
+    const T tw = ta * wyz, t1 = tw * sy[warp][1][iy], t2 = tw * sy[warp][2][iz];
+    acc[0] += wyz * S[0];
+    acc[1] += wyz * S[1];
+    acc[2] += wyz * S[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[3 + 3 * a] += tw * Tx[a];     // G_a0
+      acc[4 + 3 * a] += t1 * S[3 + a];  // G_a1
+      acc[5 + 3 * a] += t2 * S[3 + a];  // G_a2
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  if (lane != 0) return;
+  double a_[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a_[k] = (double)acc[k] * (double)cnorm_h3;
+  // Lees-Edwards box: d/dy = d/ds_y - tau d/ds_x on the sheared window
+  const double G00 = a_[3], G01 = a_[4] - tau * a_[3], G02 = a_[5], G10 = a_[6],
+               G11 = a_[7] - tau * a_[6], G12 = a_[8], G20 = a_[9], G21 = a_[10] - tau * a_[9],
+               G22 = a_[11];
+  const double r2i = 0.70710678118654752440, r6i = 0.40824829046386301637,
+               s2 = 1.41421356237309504880;
+  double *yr = y + (size_t)i * LDB;
+  yr[0] += a_[0];
+  yr[1] += a_[1];
+  yr[2] += a_[2];
+  yr[3] += 0.5 * (G21 - G12);
+  yr[4] += 0.5 * (G02 - G20);
+  yr[5] += 0.5 * (G10 - G01);
+  yr[6] += r2i * (G00 - G11);
+  yr[7] += r6i * (2.0 * G22 - G00 - G11);
+  yr[8] += s2 * 0.5 * (G01 + G10);
+  yr[9] += s2 * 0.5 * (G02 + G20);
+  yr[10] += s2 * 0.5 * (G12 + G21);
+}
+
 // FP32 interpolation from planar fields [6][n^3] (n a multiple of 4): the
 // sums of k_interp, with each lane reading an aligned quad of four x points
 // of one grid row per field (six 16-byte loads); slots outside the bead's x
@@ -1548,9 +1633,8 @@ void build_wave(Ctx &c) {
   c.op32.spec.alloc(ssize);
   // per-stage twiddle tables of the plan
   std::vector<double> tw;
-  make_plan(n, &tw, false);
-  upload(c.op64.twiddle, tw);
   make_plan(n, &tw, true);
+  upload(c.op64.twiddle, tw);
   upload(c.op32.twiddle, tw);
   // Green table by m = kx^2 + ky^2 + kz^2
   const int hm = n / 2;
@@ -1689,9 +1773,9 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
     k_interp<T, true><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n, P,
                                                               h, alpha, (T)(cn * h3), tau_arg(c));
   else
-    k_interp<T, false><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
-                                                               P, h, alpha, (T)(cn * h3),
-                                                               tau_arg(c));
+    k_interp_rows<T><<<ceil_div(c.Nt, 8), 256, 0, c.stream>>>(c.Nt, posp<T>(c), op.gout.p, y, n,
+                                                              P, h, alpha, (T)(cn * h3),
+                                                              tau_arg(c), make_fastdiv(P));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -1802,7 +1886,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   }
-  const FftPlan plan = make_plan(n, nullptr, sizeof(T) == 4);
+  const FftPlan plan = make_plan(n, nullptr, true);
   Cx<T> *spec = (Cx<T> *)op.spec.p;
   {
   ProfScope ps(c, PG_FFT);
@@ -1881,7 +1965,7 @@ template <typename T>
 void launch_brownian_wave(Ctx &c, const double *field, uint64_t seed, uint64_t step, double *out) {
   OpData<T> &op = opd<T>(c);
   const int n = c.n, nh = n / 2 + 1;
-  const FftPlan plan = make_plan(n, nullptr, sizeof(T) == 4);
+  const FftPlan plan = make_plan(n, nullptr, true);
   Cx<T> *spec = (Cx<T> *)op.spec.p;
   {
     ProfScope ps(c, PG_FFT);
