@@ -136,7 +136,11 @@ class ClockSampler:
 
 # ----------------------------------------------------------- work model
 # Algorithmic work per launch of each kernel group.
-FLOP_PER_PAIR = 410  # FP32 flops of one directed FTS pair (operator form, FMA = 2)
+# FP32 flops of one directed FTS pair (operator form, FMA = 2): geometry 21,
+# moment expansion 10, radial table 75 (six coefficients: five Horner steps
+# of two flops for seven functions, the interval index), free-space scalars
+# 38, operator-form contraction 206
+FLOP_PER_PAIR = 350
 
 
 def group_work(group, s, prm, st, prec_bytes=4):

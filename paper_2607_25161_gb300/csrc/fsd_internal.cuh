@@ -17,8 +17,22 @@ namespace fsd {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int LDB = 12;     // doubles per bead in a solution vector (11 + zero pad)
 constexpr int NFUNC = 7;    // radial functions of the real-space table
-constexpr int TCOEF = 10;   // polynomial coefficients per function per interval
-constexpr int TSTRIDE = TCOEF * 8 + 4;  // table values per interval (padded: bank spread)
+// Polynomial coefficients per function per interval of the real-space radial
+// table, per precision.  The functions are band-limited by K = 2 xi sqrt(46)
+// and an interval is 1.6 / K long, so the Chebyshev fit's error relative to
+// each function's largest value does not depend on xi: 6e-11 with 6
+// coefficients (FP32 table), 1.5e-14 with 8 (FP64), 4e-9 with 5.
+template <typename T>
+constexpr int tab_coef() {
+  return sizeof(T) == 4 ? 6 : 8;
+}
+// table values per interval: 8 per power (seven functions and a pad), plus
+// 4 so that an FP32 interval spans an odd number of 16-byte units (bank
+// spread when the lanes of a warp read different intervals)
+template <typename T>
+constexpr int tab_stride() {
+  return tab_coef<T>() * 8 + 4;
+}
 constexpr int BLK = 36;     // 6x6 block
 
 // ------------------------------------------------------------------ errors
@@ -63,7 +77,7 @@ struct DBuf {
 // Everything the FP32 or the FP64 operator needs beyond the shared geometry.
 template <typename T>
 struct OpData {
-  DBuf<T> table;      // real-space radial table [nint][NFUNC][TCOEF]
+  DBuf<T> table;      // real-space radial table [nint][power][function padded to 8]
   T self_real[3];     // real-space self mobilities (translation, rotation, strain)
   DBuf<T> grid;       // spread densities, planar: [6][n^3]
   DBuf<T> spec;       // half spectra, planar: [6][n][n][n/2 + 1] complex

@@ -117,6 +117,40 @@ static double wave_phi(const WaveQuad &q, int f, double r) {
   return sign * acc / (2.0 * kPi * kPi * q.eta);
 }
 
+// Chebyshev fit of the seven wave-part functions on nint intervals of
+// length ht with NC coefficients each, stored as monomials in t in [-1, 1]:
+// layout [interval][power p][function, padded to 8], stride values per
+// interval.
+static std::vector<double> fit_table(const WaveQuad &q, int nint, double ht, int NC, int stride) {
+  std::vector<double> tab((size_t)nint * stride, 0.0);
+  std::vector<double> tk(NC), v(NC), cc(NC);
+  for (int k = 0; k < NC; ++k) tk[k] = std::cos(kPi * (k + 0.5) / NC);
+  // Chebyshev T_j(t) as monomials: cheb[j][p]
+  std::vector<std::vector<double>> cheb(NC, std::vector<double>(NC, 0.0));
+  cheb[0][0] = 1.0;
+  if (NC > 1) cheb[1][1] = 1.0;
+  for (int j = 2; j < NC; ++j)
+    for (int p = 0; p < NC; ++p)
+      cheb[j][p] = (p > 0 ? 2.0 * cheb[j - 1][p - 1] : 0.0) - cheb[j - 2][p];
+  for (int iv = 0; iv < nint; ++iv) {
+    double r0 = iv * ht;
+    for (int f = 0; f < NFUNC; ++f) {
+      for (int k = 0; k < NC; ++k) v[k] = wave_phi(q, f, r0 + 0.5 * (tk[k] + 1.0) * ht);
+      for (int j = 0; j < NC; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < NC; ++k) s += v[k] * std::cos(j * kPi * (k + 0.5) / NC);
+        cc[j] = (j == 0 ? 1.0 : 2.0) * s / NC;
+      }
+      for (int p = 0; p < NC; ++p) {
+        double s = 0.0;
+        for (int j = 0; j < NC; ++j) s += cc[j] * cheb[j][p];
+        tab[(size_t)iv * stride + (size_t)p * 8 + f] = s;
+      }
+    }
+  }
+  return tab;
+}
+
 void build_real_table(Ctx &c) {
   double K = 2.0 * c.xi * std::sqrt(46.0);
   double ht = std::min(1.6 / K, 0.25);
@@ -124,36 +158,8 @@ void build_real_table(Ctx &c) {
   c.tab_h = ht;
   c.tab_nint = nint;
   WaveQuad q = make_quad(c.xi, c.a, c.eta, 400);
-  std::vector<double> tab((size_t)nint * TSTRIDE, 0.0);
-  const int NC = TCOEF;
-  double tk[NC];
-  for (int k = 0; k < NC; ++k) tk[k] = std::cos(kPi * (k + 0.5) / NC);
-  // Chebyshev T_j(t) as monomials: cheb[j][p]
-  double cheb[NC][NC] = {};
-  cheb[0][0] = 1.0;
-  cheb[1][1] = 1.0;
-  for (int j = 2; j < NC; ++j)
-    for (int p = 0; p < NC; ++p)
-      cheb[j][p] = (p > 0 ? 2.0 * cheb[j - 1][p - 1] : 0.0) - cheb[j - 2][p];
-  for (int iv = 0; iv < nint; ++iv) {
-    double r0 = iv * ht;
-    for (int f = 0; f < NFUNC; ++f) {
-      double v[NC];
-      for (int k = 0; k < NC; ++k) v[k] = wave_phi(q, f, r0 + 0.5 * (tk[k] + 1.0) * ht);
-      double cc[NC];
-      for (int j = 0; j < NC; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < NC; ++k) s += v[k] * std::cos(j * kPi * (k + 0.5) / NC);
-        cc[j] = (j == 0 ? 1.0 : 2.0) * s / NC;
-      }
-      // layout [interval][power p][function, padded to 8]
-      for (int p = 0; p < NC; ++p) {
-        double s = 0.0;
-        for (int j = 0; j < NC; ++j) s += cc[j] * cheb[j][p];
-        tab[(size_t)iv * TSTRIDE + (size_t)p * 8 + f] = s;
-      }
-    }
-  }
+  const std::vector<double> tab = fit_table(q, nint, ht, tab_coef<double>(), tab_stride<double>());
+  const std::vector<double> tab32 = fit_table(q, nint, ht, tab_coef<float>(), tab_stride<float>());
   // real-space self terms: isolated-sphere self mobilities minus the wave
   // part at r = 0 (translation 2 Phi1_MM, rotation -5/2 Phi2_DD, strain -3 Phi2_DD)
   double mt = 1.0 / (6.0 * kPi * c.eta * c.a);
@@ -164,7 +170,7 @@ void build_real_table(Ctx &c) {
   c.op64.table.alloc(tab.size());
   FSD_CUDA(cudaMemcpy(c.op64.table.p, tab.data(), tab.size() * sizeof(double),
                       cudaMemcpyHostToDevice));
-  std::vector<float> tabf(tab.begin(), tab.end());
+  std::vector<float> tabf(tab32.begin(), tab32.end());
   c.op32.table.alloc(tabf.size());
   FSD_CUDA(cudaMemcpy(c.op32.table.p, tabf.data(), tabf.size() * sizeof(float),
                       cudaMemcpyHostToDevice));
@@ -558,11 +564,12 @@ __device__ __forceinline__ void wave_table<float>(const float *tab, int nint, fl
   int iv = (int)s;
   iv = iv < 0 ? 0 : (iv >= nint ? nint - 1 : iv);
   const float t = 2.f * (s - (float)iv) - 1.f;
-  const float4 *c = (const float4 *)(tab + (size_t)iv * TSTRIDE);
-  float4 lo = c[2 * (TCOEF - 1)], hi = c[2 * (TCOEF - 1) + 1];
+  constexpr int NC = tab_coef<float>();
+  const float4 *c = (const float4 *)(tab + (size_t)iv * tab_stride<float>());
+  float4 lo = c[2 * (NC - 1)], hi = c[2 * (NC - 1) + 1];
   float v0 = lo.x, v1 = lo.y, v2 = lo.z, v3 = lo.w, v4 = hi.x, v5 = hi.y, v6 = hi.z;
 #pragma unroll
-  for (int p = TCOEF - 2; p >= 0; --p) {
+  for (int p = NC - 2; p >= 0; --p) {
     lo = c[2 * p];
     hi = c[2 * p + 1];
     v0 = v0 * t + lo.x; v1 = v1 * t + lo.y; v2 = v2 * t + lo.z; v3 = v3 * t + lo.w;
@@ -577,16 +584,17 @@ __device__ __forceinline__ void wave_table<double>(const double *tab, int nint, 
   int iv = (int)s;
   iv = iv < 0 ? 0 : (iv >= nint ? nint - 1 : iv);
   const double t = 2.0 * (s - (double)iv) - 1.0;
-  const double2 *c = (const double2 *)(tab + (size_t)iv * TSTRIDE);
+  constexpr int NC = tab_coef<double>();
+  const double2 *c = (const double2 *)(tab + (size_t)iv * tab_stride<double>());
   double v[8];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const double2 a = c[4 * (TCOEF - 1) + q];
+    const double2 a = c[4 * (NC - 1) + q];
     v[2 * q] = a.x;
     v[2 * q + 1] = a.y;
   }
 #pragma unroll
-  for (int p = TCOEF - 2; p >= 0; --p)
+  for (int p = NC - 2; p >= 0; --p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const double2 a = c[4 * p + q];
@@ -690,7 +698,7 @@ __global__ void __launch_bounds__(256, 4) k_realspace(
   extern __shared__ __align__(16) unsigned char tab_raw[];
   T *tab = (T *)tab_raw;
   {
-    const int nv = nint * TSTRIDE * (int)sizeof(T) / 16;
+    const int nv = nint * tab_stride<T>() * (int)sizeof(T) / 16;
     const uint4 *src = (const uint4 *)tab_g;
     uint4 *dst = (uint4 *)tab_raw;
     for (int q = threadIdx.x; q < nv; q += blockDim.x) dst[q] = src[q];
@@ -854,7 +862,7 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint, b
                                                               op.packed.p);
   FSD_LAUNCHED(c);
   const int G = realspace_group(c);
-  const size_t smem = (size_t)c.tab_nint * TSTRIDE * sizeof(T);
+  const size_t smem = (size_t)c.tab_nint * tab_stride<T>() * sizeof(T);
   if (smem > 200 * 1024) throw Invalid{"real-space table too large (reduce rc or raise xi)"};
   const T inv_h = (T)(1.0 / c.tab_h);
   const T c8 = (T)(1.0 / (8.0 * kPi * c.eta));
