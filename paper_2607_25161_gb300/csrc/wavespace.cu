@@ -342,6 +342,56 @@ __device__ Cx<T> *fft_lines(Cx<T> *A, Cx<T> *B, int nl, int n, int ls, const Fft
   return in;
 }
 
+// The 144-point transform (radix 16 then 9) on lines of stride kLS144 = 153
+// (= 9 mod 16): the first stage reads the lines in natural order and writes
+// padded order (element i at i + i/16), the second reads padded order and
+// writes natural order back into A.  Every access is a fixed offset from the
+// butterfly's base address (no per-element index arithmetic), and neither
+// stage has shared-memory bank conflicts: in natural order the lanes of a
+// half-warp read 16 consecutive elements of one or two lines, 153 apart; the
+// padding spreads the first stage's stride-16 writes and the second stage's
+// stride-16 reads.  tw2: the second stage's twiddles exp(-2 pi i r j / 144),
+// [r - 1][j], r < 9, j < 16.
+constexpr int kLS144 = 153;
+
+template <typename T>
+__device__ __forceinline__ void fft144_lines(Cx<T> *A, Cx<T> *B, int nl, const Cx<T> *tw2, T sg) {
+  for (int b = threadIdx.x; b < nl * 9; b += blockDim.x) {
+    const int line = b / 9, j = b - line * 9;
+    const Cx<T> *src = A + line * kLS144 + j;
+    Cx<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = src[9 * r];
+    dft_small<T, 16>(v, sg);
+    Cx<T> *dst = B + line * kLS144 + 17 * j;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) dst[r] = v[r];
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nl * 16; b += blockDim.x) {
+    const int line = b >> 4, j = b & 15;
+    const Cx<T> *src = B + line * kLS144 + j;
+    Cx<T> v[9];
+    v[0] = src[0];
+#pragma unroll
+    for (int r = 1; r < 9; ++r) {
+      Cx<T> w = tw2[(r - 1) * 16 + j];
+      w.y *= -sg;  // tables hold the forward twiddles
+      v[r] = cmul(src[17 * r], w);
+    }
+    dft_small<T, 9>(v, sg);
+    Cx<T> *dst = A + line * kLS144 + j;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) dst[16 * r] = v[r];
+  }
+  __syncthreads();
+}
+
+// Plans served by fft144_lines: n = 144 as 16 x 9 with lines of stride 153.
+__host__ __device__ __forceinline__ bool is_fft144(const FftPlan &p) {
+  return p.n == 144 && p.nst == 2 && p.st[0].R == 16 && p.st[1].R == 9 && fft_ls(144) == kLS144;
+}
+
 template <typename T>
 __device__ __forceinline__ void load_twiddles(Cx<T> *tw_s, const T *__restrict__ tw, int ntw) {
   for (int t = threadIdx.x; t < ntw; t += blockDim.x) tw_s[t] = {tw[2 * t], tw[2 * t + 1]};
@@ -548,11 +598,13 @@ __global__ void k_fft_y(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw, int
 // A_k = (Z_k + conj Z_{n-k})/2 and B_k = (Z_k - conj Z_{n-k})/(2i), k <= n/2.
 // They are transposed into nh = n/2 + 1 lines along y, transformed, and
 // written as spec[comp][z][y][kx].
-template <typename T>
+template <typename T, bool S144>
 __global__ void __launch_bounds__(1024) k_fft_xy_fwd(const T *__restrict__ grid, Cx<T> *spec,
                                                     FftPlan plan, const T *__restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1, nr = n / 2;
+  // element i of a line: natural order for the 144-point path, padded else
+  auto P = [](int i) { return S144 ? i : fpad(i); };
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;  // nh lines of ls
   Cx<T> *B = A + nh * ls;
@@ -577,26 +629,39 @@ __global__ void __launch_bounds__(1024) k_fft_xy_fwd(const T *__restrict__ grid,
         const int e = e0 + u * blockDim.x;
         if (e >= total) continue;
         const int r = (int)fdiv((uint32_t)e, plan.fn), x = e - r * n;
-        A[r * ls + fpad(x)] = {va[u], vb[u]};
+        A[r * ls + P(x)] = {va[u], vb[u]};
       }
     }
   }
   __syncthreads();
-  Cx<T> *Z = fft_lines<T>(A, B, nr, n, ls, plan, tw_s, T(-1));
-  Cx<T> *Y = (Z == A) ? B : A;
+  Cx<T> *Z, *Y;
+  if constexpr (S144) {
+    fft144_lines<T>(A, B, nr, tw_s + plan.st[1].toff, T(-1));
+    Z = A;
+    Y = B;
+  } else {
+    Z = fft_lines<T>(A, B, nr, n, ls, plan, tw_s, T(-1));
+    Y = (Z == A) ? B : A;
+  }
   for (int e = threadIdx.x; e < nr * nh; e += blockDim.x) {
     const int r = (int)fdiv((uint32_t)e, plan.fnh), k = e - r * nh;
-    const Cx<T> zk = Z[r * ls + fpad(k)];
-    const Cx<T> zm = Z[r * ls + fpad(k == 0 ? 0 : n - k)];
-    Y[k * ls + fpad(2 * r)] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
-    Y[k * ls + fpad(2 * r + 1)] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
+    const Cx<T> zk = Z[r * ls + P(k)];
+    const Cx<T> zm = Z[r * ls + P(k == 0 ? 0 : n - k)];
+    Y[k * ls + P(2 * r)] = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+    Y[k * ls + P(2 * r + 1)] = {T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
   }
   __syncthreads();
-  Cx<T> *R = fft_lines<T>(Y, Z, nh, n, ls, plan, tw_s, T(-1));
+  Cx<T> *R;
+  if constexpr (S144) {
+    fft144_lines<T>(Y, Z, nh, tw_s + plan.st[1].toff, T(-1));
+    R = Y;
+  } else {
+    R = fft_lines<T>(Y, Z, nh, n, ls, plan, tw_s, T(-1));
+  }
   Cx<T> *out = spec + cz * n * nh;
   for (int e = threadIdx.x; e < n * nh; e += blockDim.x) {
     const int y = (int)fdiv((uint32_t)e, plan.fnh), k = e - y * nh;
-    out[e] = R[k * ls + fpad(y)];
+    out[e] = R[k * ls + P(y)];
   }
 }
 
@@ -604,11 +669,12 @@ __global__ void __launch_bounds__(1024) k_fft_xy_fwd(const T *__restrict__ grid,
 // 2r + 1 are packed as Z_k = A_k + i B_k (k <= n/2; conj(A_{n-k}) +
 // i conj(B_{n-k}) beyond), and the inverse x DFT gives the two real rows as
 // its real and imaginary parts, written to a planar field [comp][z][y][x].
-template <typename T>
+template <typename T, bool S144>
 __global__ void __launch_bounds__(1024) k_fft_xy_inv(T *field, const Cx<T> *__restrict__ spec,
                                                     FftPlan plan, const T *__restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1, nr = n / 2;
+  auto P = [](int i) { return S144 ? i : fpad(i); };
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + nh * ls;
@@ -630,25 +696,38 @@ __global__ void __launch_bounds__(1024) k_fft_xy_inv(T *field, const Cx<T> *__re
         const int e = e0 + u * blockDim.x;
         if (e >= total) continue;
         const int y = (int)fdiv((uint32_t)e, plan.fnh), k = e - y * nh;
-        A[k * ls + fpad(y)] = v[u];
+        A[k * ls + P(y)] = v[u];
       }
     }
   }
   __syncthreads();
-  Cx<T> *Y = fft_lines<T>(A, B, nh, n, ls, plan, tw_s, T(1));
-  Cx<T> *Z = (Y == A) ? B : A;
+  Cx<T> *Y, *Z;
+  if constexpr (S144) {
+    fft144_lines<T>(A, B, nh, tw_s + plan.st[1].toff, T(1));
+    Y = A;
+    Z = B;
+  } else {
+    Y = fft_lines<T>(A, B, nh, n, ls, plan, tw_s, T(1));
+    Z = (Y == A) ? B : A;
+  }
   for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
     const int r = (int)fdiv((uint32_t)e, plan.fn), k = e - r * n;
     const int kk = k <= n / 2 ? k : n - k;
-    const Cx<T> a = Y[kk * ls + fpad(2 * r)], b = Y[kk * ls + fpad(2 * r + 1)];
-    Z[r * ls + fpad(k)] = k <= n / 2 ? Cx<T>{a.x - b.y, a.y + b.x} : Cx<T>{a.x + b.y, -a.y + b.x};
+    const Cx<T> a = Y[kk * ls + P(2 * r)], b = Y[kk * ls + P(2 * r + 1)];
+    Z[r * ls + P(k)] = k <= n / 2 ? Cx<T>{a.x - b.y, a.y + b.x} : Cx<T>{a.x + b.y, -a.y + b.x};
   }
   __syncthreads();
-  Cx<T> *X = fft_lines<T>(Z, Y, nr, n, ls, plan, tw_s, T(1));
+  Cx<T> *X;
+  if constexpr (S144) {
+    fft144_lines<T>(Z, Y, nr, tw_s + plan.st[1].toff, T(1));
+    X = Z;
+  } else {
+    X = fft_lines<T>(Z, Y, nr, n, ls, plan, tw_s, T(1));
+  }
   T *o = field + cz * n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int y = (int)fdiv((uint32_t)e, plan.fn), x = e - y * n;
-    const Cx<T> v = X[(y >> 1) * ls + fpad(x)];
+    const Cx<T> v = X[(y >> 1) * ls + P(x)];
     o[e] = (y & 1) ? v.y : v.x;
   }
 }
@@ -707,7 +786,7 @@ __global__ void k_green_le_table(int n, GreenLE le, T *gle) {
   }
 }
 
-template <typename T>
+template <typename T, bool S144>
 __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ tw,
                               const T *__restrict__ green, int LTX, GreenLE le,
                               const T *__restrict__ gle) {
@@ -715,6 +794,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
   const int n = plan.n, ls = fft_ls(n), nh = n / 2 + 1;
   const int TX = 1 << LTX;
   const int NLn = 6 * TX;
+  auto P = [](int i) { return S144 ? i : fpad(i); };
   Cx<T> *tw_s = (Cx<T> *)smem_raw;
   Cx<T> *A = tw_s + plan.ntw;
   Cx<T> *B = A + NLn * ls;
@@ -745,12 +825,18 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
         if (e >= total) continue;
         const int t = e & (TX - 1), rest = e >> LTX;
         const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
-        A[(comp * TX + t) * ls + fpad(zz)] = v[u];
+        A[(comp * TX + t) * ls + P(zz)] = v[u];
       }
     }
   }
   __syncthreads();
-  Cx<T> *Z = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(-1));
+  Cx<T> *Z;
+  if constexpr (S144) {
+    fft144_lines<T>(A, B, NLn, tw_s + plan.st[1].toff, T(-1));
+    Z = A;
+  } else {
+    Z = fft_lines<T>(A, B, NLn, n, ls, plan, tw_s, T(-1));
+  }
   // Green's function, one (kx, ky, kz) per thread iteration
   const int ky = yy <= n / 2 ? yy : yy - n;
   const double le_tau = le.dev ? *le.dev * le.invL : le.tau;
@@ -762,8 +848,8 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     Cx<T> gF[3], gD[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      gF[d] = Z[(d * TX + t) * ls + fpad(zz)];
-      gD[d] = Z[((d + 3) * TX + t) * ls + fpad(zz)];
+      gF[d] = Z[(d * TX + t) * ls + P(zz)];
+      gD[d] = Z[((d + 3) * TX + t) * ls + P(zz)];
     }
     Cx<T> oM[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     Cx<T> oD[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
@@ -813,19 +899,25 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      Z[(d * TX + t) * ls + fpad(zz)] = oM[d];
-      Z[((d + 3) * TX + t) * ls + fpad(zz)] = oD[d];
+      Z[(d * TX + t) * ls + P(zz)] = oM[d];
+      Z[((d + 3) * TX + t) * ls + P(zz)] = oD[d];
     }
   }
   __syncthreads();
   Cx<T> *O = Z;
   Cx<T> *other = (Z == A) ? B : A;
-  Cx<T> *R = fft_lines<T>(O, other, NLn, n, ls, plan, tw_s, T(1));
+  Cx<T> *R;
+  if constexpr (S144) {
+    fft144_lines<T>(O, other, NLn, tw_s + plan.st[1].toff, T(1));
+    R = O;
+  } else {
+    R = fft_lines<T>(O, other, NLn, n, ls, plan, tw_s, T(1));
+  }
   for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
     const int t = e & (TX - 1), rest = e >> LTX;
     const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
     const int kx = kx0 + t;
-    if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + fpad(zz)];
+    if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + P(zz)];
   }
 }
 
@@ -1738,8 +1830,13 @@ static void wave_tail(Ctx &c, OpData<T> &op, const FftPlan &plan, Cx<T> *spec, d
   {
   ProfScope ps(c, PG_FFT);
   if (fused) {
-    set_smem<T>((const void *)k_fft_xy_inv<T>, sm_xy);
-    k_fft_xy_inv<T><<<6 * n, 1024, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
+    if (is_fft144(plan)) {
+      set_smem<T>((const void *)k_fft_xy_inv<T, true>, sm_xy);
+      k_fft_xy_inv<T, true><<<6 * n, 1024, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
+    } else {
+      set_smem<T>((const void *)k_fft_xy_inv<T, false>, sm_xy);
+      k_fft_xy_inv<T, false><<<6 * n, 1024, sm_xy, c.stream>>>(op.gout.p, spec, plan, op.twiddle.p);
+    }
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
@@ -1903,8 +2000,13 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
   const size_t smy = (size_t)(ntw + 2 * TXy * fft_ls(n)) * sizeof(Cx<T>);
   const int blocks_y = 6 * n * ceil_div(nh, TXy);
   if (fused) {
-    set_smem<T>((const void *)k_fft_xy_fwd<T>, sm_xy);
-    k_fft_xy_fwd<T><<<6 * n, 1024, sm_xy, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p);
+    if (is_fft144(plan)) {
+      set_smem<T>((const void *)k_fft_xy_fwd<T, true>, sm_xy);
+      k_fft_xy_fwd<T, true><<<6 * n, 1024, sm_xy, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p);
+    } else {
+      set_smem<T>((const void *)k_fft_xy_fwd<T, false>, sm_xy);
+      k_fft_xy_fwd<T, false><<<6 * n, 1024, sm_xy, c.stream>>>(op.grid.p, spec, plan, op.twiddle.p);
+    }
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   } else {
@@ -1925,7 +2027,9 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
     const int LTX = fit_log2_lines<T>(2, 6, n, ntw);
     const int TX = 1 << LTX;
     size_t sm = (size_t)(ntw + 2 * 6 * TX * fft_ls(n)) * sizeof(Cx<T>);
-    set_smem<T>((const void *)k_fft_z_green<T>, sm);
+    const bool s144 = is_fft144(plan);
+    set_smem<T>(s144 ? (const void *)k_fft_z_green<T, true> : (const void *)k_fft_z_green<T, false>,
+                sm);
     int blocks = n * ceil_div(nh, TX);
     GreenLE le;
     if (c.tilt != 0.0 || tilt_dev_ptr(c)) {
@@ -1949,8 +2053,12 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
         op.green_le_tilt = c.tilt;
       }
     }
-    k_fft_z_green<T><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p, op.green.p,
-                                                        LTX, le, op.green_le.p);
+    if (s144)
+      k_fft_z_green<T, true><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p,
+                                                                op.green.p, LTX, le, op.green_le.p);
+    else
+      k_fft_z_green<T, false><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p,
+                                                                 op.green.p, LTX, le, op.green_le.p);
     FSD_LAUNCHED(c);
     FSD_CUDA(cudaGetLastError());
   }
@@ -2213,7 +2321,7 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
   const int blocks_y = 6 * n * ((nh + 15) / 16);
   const size_t smy = (size_t)(ntw + 2 * 16 * fft_ls(n)) * sizeof(Cx<float>);
   k_fft_y<float><<<blocks_y, threads, smy, st>>>(spec, plan, tw, 4, -1.f);
-  k_fft_z_green<float><<<n * ((nh + 3) / 4), threads,
+  k_fft_z_green<float, false><<<n * ((nh + 3) / 4), threads,
                          (ntw + 2 * 6 * 4 * fft_ls(n)) * sizeof(Cx<float>), st>>>(spec, plan, tw,
                                                                                 green, 2, GreenLE(),
                                                                                 nullptr);
