@@ -588,6 +588,14 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.wpos32.alloc(4 * (size_t)Nt);
   if (c.overlap) c.yw.alloc((size_t)LDB * Nt);
   FSD_CUDA(cudaMemcpy(c.body_start.p, c.h_body_start.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  {
+    // lanes per aggregate of the aggregate-row kernels: the power of two
+    // (4..32) that covers the largest aggregate
+    int mb = 1;
+    for (int J = 0; J < N; ++J) mb = std::max(mb, c.h_body_start[J + 1] - c.h_body_start[J]);
+    c.body_lanes = 4;
+    while (c.body_lanes < 32 && c.body_lanes < mb) c.body_lanes *= 2;
+  }
   FSD_CUDA(cudaMemcpy(c.bead_body.p, bead_body.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
   FSD_CUDA(cudaMemcpy(c.perm_bead.p, c.h_perm_bead.data(), Nt * sizeof(int), cudaMemcpyHostToDevice));
   FSD_CUDA(cudaMemcpy(c.perm_body.p, c.h_perm_body.data(), N * sizeof(int), cudaMemcpyHostToDevice));

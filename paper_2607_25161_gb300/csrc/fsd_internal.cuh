@@ -180,6 +180,7 @@ struct Ctx {
   std::vector<int> h_perm_bead;  // internal bead -> user bead
   std::vector<int> h_perm_body;  // internal body -> user id
   std::vector<int> h_body_start;
+  int body_lanes = 32;  // lanes per aggregate in the aggregate-row kernels (4, 8, 16 or 32)
   DBuf<int> body_start, bead_body, perm_bead, perm_body;
   DBuf<double> X, q, rbody, pos64, lever64;
   // Lees-Edwards box: offset of the image across y (0: cube); wave-space

@@ -243,14 +243,23 @@ __device__ __forceinline__ void lu_solve6(const double *LU, const int *pv, doubl
 
 // Preconditioner (Table 1, aggregates; M_inf^-1 ~ zeta0 I):
 //   y2 = r2 - zeta0 Sigma B^T r1;  z2 = -B_J^-1 y2;  z1 = zeta0 (r1 - B Sigma^T z2)
-__global__ void k_precond_body(int N, const int *__restrict__ body_start,
-                               const double4 *__restrict__ lever, const double *__restrict__ r,
-                               double *z, const double *__restrict__ schur,
-                               const int *__restrict__ piv, double zeta0, int64_t off) {
-  int J = blockIdx.x * blockDim.x + threadIdx.x;
-  if (J >= N) return;
+// LPA lanes per aggregate (a power of two covering its beads): the lanes sum
+// Sigma B^T r1 over the aggregate's beads, reduce within their group, each
+// solve the 6x6 LU system (the same numbers in every lane of the group), and
+// then write the bead rows z1 of their beads from z2 held in registers.
+template <int LPA>
+__global__ void __launch_bounds__(256) k_precond(int N, const int *__restrict__ body_start,
+                                                 const double4 *__restrict__ lever,
+                                                 const double *__restrict__ r, double *z,
+                                                 const double *__restrict__ schur,
+                                                 const int *__restrict__ piv, double zeta0,
+                                                 int64_t off) {
+  const int J = (blockIdx.x * blockDim.x + threadIdx.x) / LPA;
+  const int sub = threadIdx.x & (LPA - 1);
+  const bool active = J < N;
+  const int b0 = active ? body_start[J] : 0, b1 = active ? body_start[J + 1] : 0;
   double g[6] = {0, 0, 0, 0, 0, 0};
-  for (int b = body_start[J]; b < body_start[J + 1]; ++b) {
+  for (int b = b0 + sub; b < b1; b += LPA) {
     const double *rb = r + (size_t)b * LDB;
     const double4 rv = lever[b];
     g[0] += rb[0];
@@ -260,30 +269,30 @@ __global__ void k_precond_body(int N, const int *__restrict__ body_start,
     g[4] += rb[4] + rv.z * rb[0] - rv.x * rb[2];
     g[5] += rb[5] + rv.x * rb[1] - rv.y * rb[0];
   }
+#pragma unroll
+  for (int o = LPA / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], o);
+  if (!active) return;
   double v[6];
   for (int k = 0; k < 6; ++k) v[k] = r[off + 6 * (size_t)J + k] - zeta0 * g[k];
   lu_solve6(schur + (size_t)J * 36, piv + 6 * J, v);
-  for (int k = 0; k < 6; ++k) z[off + 6 * (size_t)J + k] = -v[k];
-}
-
-__global__ void k_precond_bead(int Nt, const int *__restrict__ bead_body,
-                               const double4 *__restrict__ lever, const double *__restrict__ r,
-                               double *z, double zeta0, int64_t off) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Nt) return;
-  const int J = bead_body[i];
-  const double *u = z + off + 6 * (size_t)J;
-  const double4 rv = lever[i];
-  const double *ri = r + (size_t)i * LDB;
-  double *zi = z + (size_t)i * LDB;
-  zi[0] = zeta0 * (ri[0] - (u[0] + u[4] * rv.z - u[5] * rv.y));
-  zi[1] = zeta0 * (ri[1] - (u[1] + u[5] * rv.x - u[3] * rv.z));
-  zi[2] = zeta0 * (ri[2] - (u[2] + u[3] * rv.y - u[4] * rv.x));
-  zi[3] = zeta0 * (ri[3] - u[3]);
-  zi[4] = zeta0 * (ri[4] - u[4]);
-  zi[5] = zeta0 * (ri[5] - u[5]);
-  for (int k = 6; k < 11; ++k) zi[k] = zeta0 * ri[k];
-  zi[11] = 0.0;
+  // u = z2 = -v
+  if (sub == 0)
+    for (int k = 0; k < 6; ++k) z[off + 6 * (size_t)J + k] = -v[k];
+  for (int b = b0 + sub; b < b1; b += LPA) {
+    const double4 rv = lever[b];
+    const double *ri = r + (size_t)b * LDB;
+    double *zi = z + (size_t)b * LDB;
+    zi[0] = zeta0 * (ri[0] + (v[0] + v[4] * rv.z - v[5] * rv.y));
+    zi[1] = zeta0 * (ri[1] + (v[1] + v[5] * rv.x - v[3] * rv.z));
+    zi[2] = zeta0 * (ri[2] + (v[2] + v[3] * rv.y - v[4] * rv.x));
+    zi[3] = zeta0 * (ri[3] + v[3]);
+    zi[4] = zeta0 * (ri[4] + v[4]);
+    zi[5] = zeta0 * (ri[5] + v[5]);
+    for (int k = 6; k < 11; ++k) zi[k] = zeta0 * ri[k];
+    zi[11] = 0.0;
+  }
 }
 
 // -------------------------------------------------- aggregate rows (matvec)
@@ -298,21 +307,22 @@ struct LV<float> {
   using type = float4;
 };
 
-// Warp per aggregate: y2_J = Sigma B^T x1 - [Sigma R Sigma^T x2]_J, the BSR
-// row of every bead evaluated with its neighbours' rigid velocities formed
-// on the fly from x2 (constraint scatter fused into the SpMV).
-template <typename T>
+// LPA lanes per aggregate (a power of two covering its beads): y2_J =
+// Sigma B^T x1 - [Sigma R Sigma^T x2]_J, the BSR row of every bead evaluated
+// with its neighbours' rigid velocities formed on the fly from x2 (constraint
+// scatter fused into the SpMV).
+template <typename T, int LPA>
 __global__ void __launch_bounds__(256) k_body_rows(
     int N, const int *__restrict__ body_start, const int *__restrict__ bead_body,
     const typename LV<T>::type *__restrict__ lever, const double *__restrict__ x, double *y,
     const int *__restrict__ brow, const int *__restrict__ bcol, const T *__restrict__ bval,
     const T *__restrict__ bdiag, int with_lub, int64_t off, T sgn_bead, T sgn_lub) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= N) return;
-  const int J = warp;
+  const int J = (blockIdx.x * blockDim.x + threadIdx.x) / LPA;
+  const int sub = threadIdx.x & (LPA - 1);
+  const bool active = J < N;
+  const int b0 = active ? body_start[J] : 0, b1 = active ? body_start[J + 1] : 0;
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  for (int b = body_start[J] + lane; b < body_start[J + 1]; b += 32) {
+  for (int b = b0 + sub; b < b1; b += LPA) {
     const double *xb = x + (size_t)b * LDB;
     const auto rv = lever[b];
     const T F0 = (T)xb[0], F1 = (T)xb[1], F2 = (T)xb[2];
@@ -374,10 +384,10 @@ __global__ void __launch_bounds__(256) k_body_rows(
     acc[5] += f[5] + rv.x * f[1] - rv.y * f[0];
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int o = LPA / 2; o > 0; o >>= 1)
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-  if (lane == 0) {
+  if (active && sub == 0) {
     double *yr = y + off + 6 * (size_t)J;
     for (int k = 0; k < 6; ++k) yr[k] = (double)acc[k];
   }
@@ -797,14 +807,27 @@ OpData<float> &opx<float>(Ctx &c) {
 }
 
 template <typename T>
-void launch_body_rows(Ctx &c, const double *x, double *y, bool with_lub) {
-  ProfScope ps(c, PG_BODY);
+static void body_rows_launch(Ctx &c, const double *x, double *y, int lub, T sgn_bead, T sgn_lub) {
   OpData<T> &op = opx<T>(c);
   const int64_t off = (int64_t)LDB * c.Nt;
+#define FSD_BODY_ROWS(LPA)                                                                      \
+  k_body_rows<T, LPA><<<ceil_div((int64_t)c.N * LPA, 256), 256, 0, c.stream>>>(                \
+      c.N, c.body_start.p, c.bead_body.p, lever_ptr<T>(c), x, y, c.brow.p, c.bcol.p, op.bval.p, \
+      op.bdiag.p, lub, off, sgn_bead, sgn_lub)
+  switch (c.body_lanes) {
+    case 4: FSD_BODY_ROWS(4); break;
+    case 8: FSD_BODY_ROWS(8); break;
+    case 16: FSD_BODY_ROWS(16); break;
+    default: FSD_BODY_ROWS(32); break;
+  }
+#undef FSD_BODY_ROWS
+}
+
+template <typename T>
+void launch_body_rows(Ctx &c, const double *x, double *y, bool with_lub) {
+  ProfScope ps(c, PG_BODY);
   const bool lub = with_lub && c.n_lub > 0;
-  k_body_rows<T><<<ceil_div((int64_t)c.N * 32, 256), 256, 0, c.stream>>>(
-      c.N, c.body_start.p, c.bead_body.p, lever_ptr<T>(c), x, y, c.brow.p, c.bcol.p, op.bval.p,
-      op.bdiag.p, lub ? 1 : 0, off, T(1), T(-1));
+  body_rows_launch<T>(c, x, y, lub ? 1 : 0, T(1), T(-1));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -813,11 +836,7 @@ void launch_body_rows(Ctx &c, const double *x, double *y, bool with_lub) {
 template <typename T>
 void launch_lub_apply(Ctx &c, const double *x, double *y) {
   ProfScope ps(c, PG_BODY);
-  OpData<T> &op = opx<T>(c);
-  const int64_t off = (int64_t)LDB * c.Nt;
-  k_body_rows<T><<<ceil_div((int64_t)c.N * 32, 256), 256, 0, c.stream>>>(
-      c.N, c.body_start.p, c.bead_body.p, lever_ptr<T>(c), x, y, c.brow.p, c.bcol.p, op.bval.p,
-      op.bdiag.p, c.n_lub > 0 ? 1 : 0, off, T(0), T(1));
+  body_rows_launch<T>(c, x, y, c.n_lub > 0 ? 1 : 0, T(0), T(1));
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
@@ -826,11 +845,16 @@ void launch_precond(Ctx &c, const double *r, double *z) {
   ProfScope ps(c, PG_PRECOND);
   const int64_t off = (int64_t)LDB * c.Nt;
   const double zeta0 = 6.0 * kPi * c.eta * c.a;
-  k_precond_body<<<ceil_div(c.N, 128), 128, 0, c.stream>>>(
-      c.N, c.body_start.p, (const double4 *)c.lever64.p, r, z, c.schur.p, c.piv.p, zeta0, off);
-  FSD_LAUNCHED(c);
-  k_precond_bead<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(
-      c.Nt, c.bead_body.p, (const double4 *)c.lever64.p, r, z, zeta0, off);
+#define FSD_PRECOND(LPA)                                                                  \
+  k_precond<LPA><<<ceil_div((int64_t)c.N * LPA, 256), 256, 0, c.stream>>>(                \
+      c.N, c.body_start.p, (const double4 *)c.lever64.p, r, z, c.schur.p, c.piv.p, zeta0, off)
+  switch (c.body_lanes) {
+    case 4: FSD_PRECOND(4); break;
+    case 8: FSD_PRECOND(8); break;
+    case 16: FSD_PRECOND(16); break;
+    default: FSD_PRECOND(32); break;
+  }
+#undef FSD_PRECOND
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
