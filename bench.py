@@ -5,9 +5,9 @@ Metric: bead-steps/sec (beads x timed steps / seconds) of the full step
 saddle-point solve to a relative residual of 1e-6, outputs, rigid-body
 update) on 32768 beads = 4096 rigid 8-bead random-attachment aggregates at
 bead volume fraction 0.2 in simple shear (rate 1), lubrication cut-off 3a,
-constant xi = 0.5.  `value` is the mixed-precision path (FP32 operator and
-FP32 Krylov basis inside FP64 iterative refinement; FP64 residual, Hessenberg
-and LU); the plain FP64 path is reported beside it.
+constant xi = 0.5.  `value` is the mixed-precision path (FP32 operator inside
+FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path and the
+mixed path with an FP32 inner Krylov basis are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload step|batch|rods|seeds|oracle-ladder]
@@ -241,10 +241,11 @@ def accuracy_subbox(pkg, stream):
     g = subbox_reference()
     out = {"workload": "384 beads: 48 x 8-bead aggregates, phi 0.2, L %.2f, shear 1 (and shear plus "
                        "random aggregate forces / torques)" % g["L"]}
-    for name, prec in (("mixed", pkg.FSD_MIXED), ("fp64", pkg.FSD_FP64)):
+    for name, prec, extra in (("mixed", pkg.FSD_MIXED, 0), ("fp64", pkg.FSD_FP64, 0),
+                              ("mixed_fp32_krylov", pkg.FSD_MIXED, pkg.FSD_FLAG_FP32_KRYLOV)):
         s = pkg.Suspension(g["pos"], g["body"], g["L"], stream=stream, precision=prec, xi=w["xi"],
                            tol=w["tol"], lub_cutoff=w["lub"], precond_cutoff=w["rp"],
-                           flags=pkg.FSD_FLAG_GRAPH)
+                           flags=pkg.FSD_FLAG_GRAPH | extra)
         prm = s.params
         errs = {}
         for case, ft in (("shear", None), ("shear+forces", np.ascontiguousarray(g["ft"]))):
@@ -545,6 +546,22 @@ def run_ours(args, rank, world, local_rank):
             "iters_per_step": itw / args.steps,
             "note": "same workload and tolerance; GMRES starts from the previous step's solution"}
 
+    # ---- FP32 inner Krylov basis (FSD_FLAG_FP32_KRYLOV), reported beside
+    s = pkg.Suspension(pos, body, L, stream=stream.cuda_stream, precision=pkg.FSD_MIXED,
+                       **dict(common, flags=common["flags"] | pkg.FSD_FLAG_FP32_KRYLOV))
+    v_k32, S_k32, _, _ = s.solve(None, w["shear"])
+    for _ in range(args.warmup):
+        s.step(None, w["shear"], w["dt"])
+    msk, _, itk = timed_steps(s, args.steps)
+    s.close()
+    msk = max_over_ranks(msk)
+    fp32_krylov = {"value": Nt * args.steps * world / (msk / 1e3), "ms_per_step": msk / args.steps,
+                   "iters_per_step": itk / args.steps,
+                   "note": "same workload and tolerance with FSD_FLAG_FP32_KRYLOV: the inner GMRES "
+                           "keeps its Krylov bases in FP32 and orthogonalises with FP32 products "
+                           "(FP64 refinement residual, Hessenberg and LU); not the headline, whose "
+                           "Arnoldi orthogonalisation is FP64"}
+
     # ---- Brownian step: fsd_brownian (PSE far-field slip: analytic wave
     #      part + Lanczos real-space square root; near-field force by the
     #      default pairwise sampler) before each step, kT = 1 (same workload)
@@ -667,8 +684,10 @@ def run_ours(args, rank, world, local_rank):
     v_64, S_64, _, _ = s64.solve(None, w["shear"])
     agree = {"U": _rel(v_mixed[:, :3], v_64[:, :3]), "Omega": _rel(v_mixed[:, 3:], v_64[:, 3:]),
              "S": _rel(S_mixed, S_64),
-             "note": "mixed vs plain FP64 GPU solve of the 32768-bead initial configuration, both at "
-                     "GMRES 1e-6 (relative L2)"}
+             "fp32_krylov": {"U": _rel(v_k32[:, :3], v_64[:, :3]),
+                             "Omega": _rel(v_k32[:, 3:], v_64[:, 3:]), "S": _rel(S_k32, S_64)},
+             "note": "mixed (and mixed with the FP32 inner Krylov basis) vs plain FP64 GPU solve of "
+                     "the 32768-bead initial configuration, all at GMRES 1e-6 (relative L2)"}
     for _ in range(max(1, min(args.warmup, 2))):
         s64.step(None, w["shear"], w["dt"])
     K64 = max(2, min(args.steps, 5))
@@ -734,7 +753,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_name(w), "beads": Nt, "aggregates": w["n_agg"],
                    "method": "grid %d^3, P %d (wave-space operator error ~7e-7), rc %.2f"
                              % (prm["grid"], prm["P"], prm["rc"]),
-                   "precision": "mixed: FP32 operator and FP32 inner Krylov basis in FP64 iterative refinement; FP64 residual, Hessenberg, LU",
+                   "precision": "mixed: FP32 operator in FP64 iterative refinement; FP64 Arnoldi, residual, LU",
                    "l2": "working set per step > L2 (grids, Krylov basis, neighbour lists ~0.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "initial_guess": "zero each step",
@@ -750,6 +769,7 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms_per_step": {g: round(v[0] / PS, 4) for g, v in prof.items()},
         "profile_iters_per_step": prof_iters / PS,
         "warm_start": warm,
+        "fp32_krylov": fp32_krylov,
         "brownian": brown,
         "brownian_drift": drift_lines,
         "comoving_cube": lees,
@@ -783,11 +803,20 @@ def run_profile(args, local_rank):
     pos, body, L = synth.suspension(w["n_agg"], w["n_b"], w["phi"], w["seed"])
     s = pkg.Suspension(pos, body, L, precision=pkg.FSD_MIXED, xi=w["xi"], lub_cutoff=w["lub"],
                        tol=w["tol"], flags=pkg.FSD_FLAG_LEES_EDWARDS, precond_cutoff=w["rp"])
-    for _ in range(args.warmup + args.steps):
+    for _ in range(args.warmup):
         st, _ = s.step(None, w["shear"], w["dt"])
     torch.cuda.synchronize()
+    # the timed steps inside one NVTX range (ncu --nvtx --nvtx-include "timed_steps/")
+    torch.cuda.nvtx.range_push("timed_steps")
+    launches = []
+    for _ in range(args.steps):
+        st, _ = s.step(None, w["shear"], w["dt"])
+        launches.append(st["kernel_launches"])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     s.close()
-    print("profile run: %d steps, %d iterations in the last" % (args.warmup + args.steps, st["iters"]))
+    print("profile run: %d warm-up and %d timed steps, %d iterations and %s kernel launches in the "
+          "timed steps" % (args.warmup, args.steps, st["iters"], launches))
 
 
 # ---------------------------------------------------------- batched form

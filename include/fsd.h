@@ -95,13 +95,25 @@ enum {
                               each real-space tile on the device, with the
                               operator the Krylov iterations apply, and keep
                               the fastest.  Costs about eight set-ups */
-  FSD_FLAG_LEES_EDWARDS = 16 /* sheared periodic box for shear runs: fsd_step
+  FSD_FLAG_LEES_EDWARDS = 16, /* sheared periodic box for shear runs: fsd_step
                               moves the bodies by their full velocity and
                               advances the box offset `tilt` by shear_rate L dt
                               (wrapped to [-L/2, L/2)), so each body's images
                               across y move with the imposed flow.  Excludes
-                              FSD_FLAG_COMOVING; steps run host-driven (the
-                              offset changes every step) */
+                              FSD_FLAG_COMOVING.  The operator kernels read the
+                              offset from device memory, so one captured graph
+                              serves every step */
+  FSD_FLAG_FP32_KRYLOV = 32  /* mixed precision only: the inner GMRES keeps its
+                              Krylov bases V and Z in FP32 and orthogonalises
+                              with FP32 products and in-warp sums (FP64
+                              cross-warp sums, Hessenberg, Givens rotations,
+                              refinement residual and LU stay FP64).  Off by
+                              default: the Arnoldi orthogonalisation is FP64.
+                              On this part FP64 runs at 1/74 of the FP32 rate
+                              and the FP64 Gram-Schmidt passes are ALU-bound;
+                              the FP32 basis takes the 32768-bead step from
+                              ~66 to ~61 ms at the same iteration count and
+                              accuracy */
 };
 
 /* Environment (read when a context is set up; defaults in brackets):

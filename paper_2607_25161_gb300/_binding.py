@@ -20,6 +20,7 @@ FSD_FLAG_COMOVING = 2
 FSD_FLAG_GRAPH = 4
 FSD_FLAG_AUTOTUNE = 8
 FSD_FLAG_LEES_EDWARDS = 16
+FSD_FLAG_FP32_KRYLOV = 32
 FSD_DRIFT_RFD, FSD_DRIFT_FIXMAN = 0, 1
 FSD_NF_LANCZOS, FSD_NF_PAIRWISE = 0, 1
 STATUS_NAMES = {0: "FSD_OK", 1: "FSD_EINVAL", 2: "FSD_ENOMEM", 3: "FSD_ECUDA", 4: "FSD_ENOCONV",

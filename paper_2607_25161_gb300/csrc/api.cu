@@ -199,8 +199,8 @@ static double host_norm(Ctx &c, const double *x) {
   return std::sqrt(std::max(0.0, c.h_pinned[0]));
 }
 
-// Krylov bases per operator precision: FP64 for the FP64 solve, FP32 for the
-// inner GMRES of the mixed solve.
+// Krylov bases by element type: FP64, or FP32 for the inner GMRES of a mixed
+// solve with FSD_FLAG_FP32_KRYLOV.
 template <typename T> static T *krylov_v(Ctx &c);
 template <> double *krylov_v<double>(Ctx &c) { return c.V.p; }
 template <> float *krylov_v<float>(Ctx &c) { return c.V32.p; }
@@ -209,19 +209,20 @@ template <> double *krylov_z<double>(Ctx &c) { return c.Z.p; }
 template <> float *krylov_z<float>(Ctx &c) { return c.Z32.p; }
 
 // Right-preconditioned restarted flexible GMRES (Z stores P^-1 v_j), CGS2
-// Arnoldi, Givens rotations on the host.  The operator precision is T, and
-// so is the basis: FP64, or FP32 for the inner solve of the mixed path (its
-// basis vectors are widened to FP64 for the preconditioner, and the operator
-// is applied to the FP32 value of z_j that the update x += Z y uses).
-// Solves A x = b from x (x_zero: x = 0).  Stops when the residual is below
-// tol * bnorm (the true residual when true_check), or after max_iter
-// iterations.  Returns the last residual / bnorm.
-template <typename T>
+// Arnoldi, Givens rotations on the host.  The operator precision is T; the
+// basis element type B is FP64 (Arnoldi in FP64), or FP32 for the inner solve
+// of a mixed path with FSD_FLAG_FP32_KRYLOV (its basis vectors are widened to
+// FP64 for the preconditioner, and the operator is applied to the FP32 value
+// of z_j that the update x += Z y uses).  Solves A x = b from x (x_zero:
+// x = 0).  Stops when the residual is below tol * bnorm (the true residual
+// when true_check), or after max_iter iterations.  Returns the last residual
+// / bnorm.
+template <typename T, typename B>
 static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol, int max_iter,
                     int m, bool x_zero, bool true_check, KStats &st) {
   constexpr bool f64 = sizeof(T) == 8;
   const int64_t ld = c.nunk;
-  T *V = krylov_v<T>(c), *Z = krylov_z<T>(c);
+  B *V = krylov_v<B>(c), *Z = krylov_z<B>(c);
   double *w = c.w.p;
   int total = 0;
   double rel = 1.0;
@@ -246,7 +247,7 @@ static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol
     int j = 0;
     double resid = beta;
     for (; j < m && total < max_iter;) {
-      if constexpr (f64) {
+      if constexpr (sizeof(B) == 8) {
         double *vj = V + (int64_t)j * ld, *zj = Z + (int64_t)j * ld;
         launch_precond(c, vj, zj);
         apply_saddle<T>(c, zj, w);
@@ -315,8 +316,8 @@ static double gmres(Ctx &c, const double *b, double *x, double bnorm, double tol
 
 // Solve A x = b.  FP64: restarted GMRES on the FP64 operator.  Mixed: FP64
 // iterative refinement; each correction from GMRES on the FP32 operator
-// (FP32 Krylov bases, FP64 Hessenberg, Givens rotations and LU), each
-// residual from the FP64 operator.
+// (FP64 Arnoldi, Hessenberg, Givens rotations and LU; FP32 Krylov bases with
+// FSD_FLAG_FP32_KRYLOV), each residual from the FP64 operator.
 static double solve_system(Ctx &c, const double *b, double *x, KStats &st, bool warm) {
   const int64_t ld = c.nunk;
   const double bnorm = host_norm(c, b);
@@ -327,7 +328,7 @@ static double solve_system(Ctx &c, const double *b, double *x, KStats &st, bool 
   const double tol = c.prm.tol;
   if (c.prm.precision == FSD_FP64) {
     if (warm) FSD_CUDA(cudaMemcpyAsync(x, c.xprev.p, ld * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-    double rel = gmres<double>(c, b, x, bnorm, tol, c.prm.max_iter, c.m, !warm, true, st);
+    double rel = gmres<double, double>(c, b, x, bnorm, tol, c.prm.max_iter, c.m, !warm, true, st);
     st.outer = 1;
     return rel;
   }
@@ -348,7 +349,10 @@ static double solve_system(Ctx &c, const double *b, double *x, KStats &st, bool 
     const double rn = rel * bnorm;
     // the correction only has to close the remaining gap to tol
     const double itol = std::max(c.prm.inner_tol, 0.3 * tol / rel);
-    gmres<float>(c, r, d, rn, itol, c.m_in, c.m_in, true, false, st);
+    if (c.krylov32)
+      gmres<float, float>(c, r, d, rn, itol, c.m_in, c.m_in, true, false, st);
+    else
+      gmres<float, double>(c, r, d, rn, itol, c.m_in, c.m_in, true, false, st);
     vec_axpby(c, x, 1.0, d, 1.0, ld);
     apply_saddle<double>(c, x, c.w.p);
     st.m64++;
@@ -625,15 +629,17 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   FSD_CUDA(cudaMemset(c.snf.p, 0, (size_t)Nt * 5 * sizeof(double)));
   const int mm = std::max(c.m, c.m_in);
   // V: FP64 GMRES and the Lanczos square roots (at most mm + 1 vectors);
-  // the mixed solve's inner GMRES keeps its bases in FP32
+  // with FSD_FLAG_FP32_KRYLOV the mixed solve's inner GMRES keeps its bases
+  // in FP32
+  c.krylov32 = c.prm.precision == FSD_MIXED && (c.prm.flags & FSD_FLAG_FP32_KRYLOV);
   c.V.alloc((size_t)(mm + 1) * c.nunk);
-  if (c.prm.precision == FSD_MIXED) {
+  if (c.krylov32) {
     c.V32.alloc((size_t)(c.m_in + 1) * c.nunk);
     c.Z32.alloc((size_t)c.m_in * c.nunk);
     c.kv.alloc(c.nunk);
     c.kz.alloc(c.nunk);
   } else {
-    c.Z.alloc((size_t)c.m * c.nunk);
+    c.Z.alloc((size_t)mm * c.nunk);
   }
   c.w.alloc(c.nunk);
   c.t1.alloc(c.nunk);

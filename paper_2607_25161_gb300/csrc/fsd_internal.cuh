@@ -211,8 +211,9 @@ struct Ctx {
   int m = 30, m_in = 30;
   DBuf<double> V, Z, w, t1, t2, xsol, rhs, res, xprev, partial, hcol;
   // FP32 Krylov basis and preconditioned basis of the mixed solve's inner
-  // GMRES ((m_in + 1) and m_in vectors); V (FP64) serves the FP64 solve and
-  // the Lanczos square roots, Z (FP64) the FP64 solve
+  // GMRES with FSD_FLAG_FP32_KRYLOV ((m_in + 1) and m_in vectors); V (FP64)
+  // serves the FP64 bases and the Lanczos square roots
+  bool krylov32 = false;  // mixed with FSD_FLAG_FP32_KRYLOV: FP32 inner bases
   DBuf<float> V32, Z32;
   DBuf<double> kv, kz;  // FP64 copies of v_j and z_j for the FP32 basis
   DBuf<unsigned> cgs_ticket;  // blocks finished in the running Gram-Schmidt pass (0 between passes)
@@ -307,7 +308,8 @@ void launch_realspace(Ctx &c, const double *x, double *y, bool add_constraint,
                       bool self_only_real);
 void launch_wrap_positions(Ctx &c);  // pos64 / op*.pos / levers from X, q, rbody
 __global__ void k_exclusive_scan(int n, const int *__restrict__ in, int *out, int *cursor);
-__global__ void k_sort_cells(int ncells, const int *__restrict__ cell_start, int *cell_beads);
+__global__ void __launch_bounds__(128) k_sort_cells(int ncells, const int *__restrict__ cell_start,
+                                                    int *cell_beads);  // 128 threads: a warp per segment
 // wavespace.cu: per-tile bead lists of the grid-centric spreading
 void build_spread_tiles(Ctx &c);
 // Lees-Edwards offset as the kernels take it: the host value and, with

@@ -356,27 +356,27 @@ static int vec_blocks(const Ctx &c, int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)c.num_sms));
 }
 
-// Krylov bases per operator precision: FP64 for the FP64 solve, FP32 for the
-// inner GMRES of the mixed solve.
+// Krylov bases by element type: FP64, or FP32 for the inner GMRES of a mixed
+// solve with FSD_FLAG_FP32_KRYLOV.
 static double *basis_v(Ctx &c, double) { return c.V.p; }
 static float *basis_v(Ctx &c, float) { return c.V32.p; }
 static double *basis_z(Ctx &c, double) { return c.Z.p; }
 static float *basis_z(Ctx &c, float) { return c.Z32.p; }
 
-// One Arnoldi step of the flexible GMRES on the operator of precision T
-// (basis in the same precision): z_j = P^-1 v_j, w = A z_j, CGS2 against
-// V_0..V_j, Givens update, v_{j+1}.
-template <typename T>
+// One Arnoldi step of the flexible GMRES on the operator of precision T with
+// basis element type B: z_j = P^-1 v_j, w = A z_j, CGS2 against V_0..V_j,
+// Givens update, v_{j+1}.
+template <typename T, typename B>
 static void arnoldi_step(Ctx &c, GState *s, cudaGraphConditionalHandle h_arn) {
   GraphCache &gc = *c.gcache;
   const int64_t ld = c.nunk, n = c.nunk;
   const int nb = vec_blocks(c, n);
   const int mm = sizeof(T) == 8 ? c.m : c.m_in;
-  T *V = basis_v(c, T()), *Z = basis_z(c, T());
-  k_g_get_col<T><<<nb, 256, 0, c.stream>>>(gc.vin.p, V, ld, s, n);
+  B *V = basis_v(c, B()), *Z = basis_z(c, B());
+  k_g_get_col<B><<<nb, 256, 0, c.stream>>>(gc.vin.p, V, ld, s, n);
   FSD_LAUNCHED(c);
   launch_precond(c, gc.vin.p, gc.zf.p);
-  k_g_put_col<T><<<nb, 256, 0, c.stream>>>(Z, ld, gc.zf.p, s, n);
+  k_g_put_col<B><<<nb, 256, 0, c.stream>>>(Z, ld, gc.zf.p, s, n);
   FSD_LAUNCHED(c);
   apply_saddle<T>(c, gc.zf.p, c.w.p);
   cgs_pass_dev(c, 0, V, ld, &s->j, 1, mm, c.w.p, nullptr, s->h);
@@ -384,17 +384,17 @@ static void arnoldi_step(Ctx &c, GState *s, cudaGraphConditionalHandle h_arn) {
   cgs_pass_dev(c, 2, V, ld, &s->j, 1, mm, c.w.p, s->h + 64, s->h + 128);
   k_g_givens<<<1, 32, 0, c.stream>>>(s, h_arn, sizeof(T) == 8 ? 1 : 0);
   FSD_LAUNCHED(c);
-  k_g_next_col<T><<<nb, 256, 0, c.stream>>>(V, ld, c.w.p, s, n);
+  k_g_next_col<B><<<nb, 256, 0, c.stream>>>(V, ld, c.w.p, s, n);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
 }
 
-// x += Z y after a cycle
-template <typename T>
+// x += Z y after a cycle (Z of element type B)
+template <typename B>
 static void cycle_update(Ctx &c, GState *s, double *x) {
   k_g_trisolve<<<1, 32, 0, c.stream>>>(s);
   FSD_LAUNCHED(c);
-  axpy_multi_dev(c, x, basis_z(c, T()), c.nunk, &s->ky, s->y, 1.0);
+  axpy_multi_dev(c, x, basis_z(c, B()), c.nunk, &s->ky, s->y, 1.0);
 }
 
 // The captured solve of A x = b into c.xsol (b = c.rhs).  Appends to graph g
@@ -468,7 +468,7 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
         {
           cap_begin(c, arn, {});
           l0 = c.launches;
-          arnoldi_step<double>(c, s, h_arn);
+          arnoldi_step<double, double>(c, s, h_arn);
           e.l_arn += c.launches - l0;
           cap_end(c);
         }
@@ -501,7 +501,10 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
       l0 = c.launches;
       k_g_inner_begin<<<1, 32, 0, c.stream>>>(s, h_arn);
       FSD_LAUNCHED(c);
-      k_g_scale<float><<<nb, 256, 0, c.stream>>>(c.V32.p, c.res.p, s, n, 0, 0);
+      if (c.krylov32)
+        k_g_scale<float><<<nb, 256, 0, c.stream>>>(c.V32.p, c.res.p, s, n, 0, 0);
+      else
+        k_g_scale<double><<<nb, 256, 0, c.stream>>>(c.V.p, c.res.p, s, n, 0, 0);
       FSD_LAUNCHED(c);
       e.l_run += c.launches - l0;
       d = cap_end(c);
@@ -509,13 +512,19 @@ static Deps capture_solve(Ctx &c, GraphEntry &e, cudaGraph_t g, Deps deps, bool 
       {
         cap_begin(c, arn, {});
         l0 = c.launches;
-        arnoldi_step<float>(c, s, h_arn);
+        if (c.krylov32)
+          arnoldi_step<float, float>(c, s, h_arn);
+        else
+          arnoldi_step<float, double>(c, s, h_arn);
         e.l_arn += c.launches - l0;
         cap_end(c);
       }
       cap_begin(c, outer, d);
       l0 = c.launches;
-      cycle_update<float>(c, s, x);
+      if (c.krylov32)
+        cycle_update<float>(c, s, x);
+      else
+        cycle_update<double>(c, s, x);
       apply_saddle<double>(c, x, w);
       k_g_residual<<<nb, 256, 0, c.stream>>>(c.res.p, b, w, s, n);
       FSD_LAUNCHED(c);

@@ -120,8 +120,10 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
   __shared__ B cs[kMaxBasis];
   __shared__ double wred[kMaxBasis][8];  // per basis vector, per warp
   __shared__ int last;
+  // FP64: the update is a chain of fused multiply-adds with -coef (no
+  // separate products and sums on the FP64 pipe, which bounds these passes)
   if (MODE > 0)
-    for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = (B)coef[j];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = f64 ? (B)(-coef[j]) : (B)coef[j];
   __syncthreads();
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,11 +157,14 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
       vj += 4 * ld;
 #pragma unroll
       for (int e = 0; e < kE; ++e) {
-        const B g = cs[j] * v[0][e] + cs[j + 1] * v[1][e] + cs[j + 2] * v[2][e] + cs[j + 3] * v[3][e];
-        if constexpr (f64)
-          wv[e] -= g;
-        else
-          us[e] += g;
+        if constexpr (f64) {
+          wv[e] = fma(cs[j], v[0][e], wv[e]);
+          wv[e] = fma(cs[j + 1], v[1][e], wv[e]);
+          wv[e] = fma(cs[j + 2], v[2][e], wv[e]);
+          wv[e] = fma(cs[j + 3], v[3][e], wv[e]);
+        } else {
+          us[e] += cs[j] * v[0][e] + cs[j + 1] * v[1][e] + cs[j + 2] * v[2][e] + cs[j + 3] * v[3][e];
+        }
       }
     }
     for (; j < k; ++j, vj += ld) {
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
 #pragma unroll
       for (int e = 0; e < kE; ++e) {
         if constexpr (f64)
-          wv[e] -= cs[j] * v[e];
+          wv[e] = fma(cs[j], v[e], wv[e]);
         else
           us[e] += cs[j] * v[e];
       }
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
   if (MODE == 2) {
     double acc = 0.0;
 #pragma unroll
-    for (int e = 0; e < kE; ++e) acc += wv[e] * wv[e];
+    for (int e = 0; e < kE; ++e) acc = fma(wv[e], wv[e], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) wred[0][warp] = acc;
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
       for (int q = 0; q < 4; ++q) {
         acc[q] = (B)0;
 #pragma unroll
-        for (int e = 0; e < kE; ++e) acc[q] += v[q][e] * wb[e];
+        for (int e = 0; e < kE; ++e) acc[q] = fma(v[q][e], wb[e], acc[q]);
       }
       const B r = warp_sum4<B>(acc, lane);
       if ((lane & 7) == 0) wred[j + (lane >> 3)][warp] = (double)r;

@@ -9,6 +9,7 @@
 // biharmonic r/(8 pi eta)) minus the wave part (H-filtered, tabulated).
 #include "fsd_internal.cuh"
 
+#include <climits>
 #include <mutex>
 
 #include <algorithm>
@@ -307,18 +308,54 @@ __global__ void k_cell_fill(int Nt, const double4 *__restrict__ pos, double L, i
 // Sort each cell's bead indices (one thread per cell): with the cells
 // visited in a fixed order, every neighbour row, and so every pair sum, then
 // runs in an order that does not depend on the atomic fill.
-__global__ void k_sort_cells(int ncells, const int *__restrict__ cell_start, int *cell_beads) {
-  int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+// Sort each segment [start[c], start[c + 1]) of `items` ascending (the
+// atomically filled cell and tile lists, so that every later sum runs in a
+// fixed order).  One warp per segment: a bitonic sort in shared memory for
+// segments of up to kSortMax items (padded to a power of two with INT_MAX),
+// an insertion sort by one lane beyond that.
+constexpr int kSortMax = 512;
+
+__global__ void __launch_bounds__(128) k_sort_cells(int ncells, const int *__restrict__ cell_start,
+                                                    int *cell_beads) {
+  __shared__ int buf[4][kSortMax];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cidx = blockIdx.x * 4 + warp;
   if (cidx >= ncells) return;
-  int b = cell_start[cidx], e = cell_start[cidx + 1];
-  for (int s = b + 1; s < e; ++s) {
-    int v = cell_beads[s], k = s;
-    while (k > b && cell_beads[k - 1] > v) {
-      cell_beads[k] = cell_beads[k - 1];
-      --k;
-    }
-    cell_beads[k] = v;
+  const int b = cell_start[cidx], e = cell_start[cidx + 1], len = e - b;
+  if (len <= 1) return;
+  if (len > kSortMax) {
+    if (lane == 0)
+      for (int s = b + 1; s < e; ++s) {
+        int v = cell_beads[s], k = s;
+        while (k > b && cell_beads[k - 1] > v) {
+          cell_beads[k] = cell_beads[k - 1];
+          --k;
+        }
+        cell_beads[k] = v;
+      }
+    return;
   }
+  int p2 = 2;
+  while (p2 < len) p2 <<= 1;
+  int *a = buf[warp];
+  for (int i = lane; i < p2; i += 32) a[i] = i < len ? cell_beads[b + i] : INT_MAX;
+  __syncwarp();
+  for (int k = 2; k <= p2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < p2; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          if (up ? x > y : x < y) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  for (int i = lane; i < len; i += 32) cell_beads[b + i] = a[i];
 }
 
 // One thread per bead: mobility neighbours (r < rc, any body, j != i) and
@@ -428,7 +465,7 @@ void build_neighbors(Ctx &c) {
     k_cell_fill<<<ceil_div(c.Nt, 256), 256, 0, c.stream>>>(c.Nt, spos, c.L, nc, c.cell_cursor.p,
                                                            c.cell_beads.p);
     FSD_LAUNCHED(c);
-    k_sort_cells<<<ceil_div(ncells, 128), 128, 0, c.stream>>>(ncells, c.cell_start.p,
+    k_sort_cells<<<ceil_div(ncells, 4), 128, 0, c.stream>>>(ncells, c.cell_start.p,
                                                              c.cell_beads.p);
     FSD_LAUNCHED(c);
     double rl = c.prm.lub_cutoff > 2.0 * c.a ? c.prm.lub_cutoff : 0.0;

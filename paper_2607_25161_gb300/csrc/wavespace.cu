@@ -1906,7 +1906,7 @@ void build_spread_tiles(Ctx &c) {
                                                              nt, c.tile_cursor.p, c.tile_beads.p,
                                                              (int64_t)c.tile_beads.n);
   FSD_LAUNCHED(c);
-  k_sort_cells<<<ceil_div(ntiles, 128), 128, 0, c.stream>>>(ntiles, c.tile_start.p, c.tile_beads.p);
+  k_sort_cells<<<ceil_div(ntiles, 4), 128, 0, c.stream>>>(ntiles, c.tile_start.p, c.tile_beads.p);
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   c.tiles_valid = true;

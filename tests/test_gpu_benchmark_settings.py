@@ -129,12 +129,14 @@ def _subbox():
     return mod.load()
 
 
-@pytest.mark.parametrize("precision", [MIXED, FP64])
-def test_solve_at_benchmark_settings_matches_oracle_subbox(pkg, precision):
+@pytest.mark.parametrize("precision,fp32_krylov", [(MIXED, False), (MIXED, True), (FP64, False)])
+def test_solve_at_benchmark_settings_matches_oracle_subbox(pkg, precision, fp32_krylov):
+    # mixed: FP64 Arnoldi (the default) and the FP32 inner Krylov basis
     g = _subbox()
     pos, body, L = g["pos"], g["body"], g["L"]
+    flags = pkg.FSD_FLAG_GRAPH | (pkg.FSD_FLAG_FP32_KRYLOV if fp32_krylov else 0)
     s = pkg.Suspension(pos, body, L, xi=0.5, tol=1e-6, lub_cutoff=3.0, precond_cutoff=2.0,
-                       precision=precision, flags=pkg.FSD_FLAG_GRAPH)
+                       precision=precision, flags=flags)
     prm = s.params
     for name, ft in (("shear", None), ("shear+forces", np.ascontiguousarray(g["ft"]))):
         Uref, Sref = g["cases"][name]

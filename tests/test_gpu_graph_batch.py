@@ -77,10 +77,12 @@ def oracle_refs():
 
 # ------------------------------------------------------------ graph path
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-6), (MIXED, 1e-5)])
-def test_graph_solve_matches_oracle(pkg, oracle_refs, prec, tol):
+@pytest.mark.parametrize("prec,tol,extra", [(FP64, 1e-6, 0), (MIXED, 1e-5, 0), (MIXED, 1e-5, 32)])
+def test_graph_solve_matches_oracle(pkg, oracle_refs, prec, tol, extra):
+    # extra 32: FSD_FLAG_FP32_KRYLOV (FP32 inner Krylov basis)
     r = oracle_refs[0]
-    s = pkg.Suspension(r["pos"], r["body"], r["L"], precision=prec, flags=pkg.FSD_FLAG_GRAPH, **HI)
+    s = pkg.Suspension(r["pos"], r["body"], r["L"], precision=prec,
+                       flags=pkg.FSD_FLAG_GRAPH | extra, **HI)
     vel, S, st, status = s.solve(r["ft"], r["shear"])
     s.close()
     assert status == pkg.FSD_OK
@@ -92,12 +94,12 @@ def test_graph_solve_matches_oracle(pkg, oracle_refs, prec, tol):
     assert rel(S, r["ref"]["S"]) < tol
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
-def test_graph_matches_host_driven_loop(pkg, oracle_refs, prec):
+@pytest.mark.parametrize("prec,extra", [(FP64, 0), (MIXED, 0), (MIXED, 32)])
+def test_graph_matches_host_driven_loop(pkg, oracle_refs, prec, extra):
     r = oracle_refs[2]
     out = {}
     for flags in (0, 4):
-        s = pkg.Suspension(r["pos"], r["body"], r["L"], precision=prec, flags=flags, **HI)
+        s = pkg.Suspension(r["pos"], r["body"], r["L"], precision=prec, flags=flags | extra, **HI)
         vel, S, st, status = s.solve(r["ft"], r["shear"])
         s.close()
         assert status == pkg.FSD_OK
