@@ -1926,22 +1926,37 @@ TauArg tau_arg(const Ctx &c) {
 
 // Sheared-lattice Green's function factors of the current offset (built on
 // the stream; a captured step graph reads them through the same pointer).
+__global__ void k_narrow(float *out, const double *__restrict__ in, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (float)in[i];
+}
+
+// The sheared Green's factors of the current box offset (once per offset).
+// They are evaluated in FP64 in either precision, so the FP32 table is the
+// FP64 one rounded (bit for bit what an FP32 evaluation stored before).
 template <typename T>
 static void refresh_le_table(Ctx &c, OpData<T> &op) {
   if (op.green_le_tilt == c.tilt && op.green_le.p) return;
   const int n = c.n, nh = n / 2 + 1;
-  GreenLE le;
-  le.on = 1;
-  le.tau = c.tilt / c.L;
-  le.ks2 = (2.0 * kPi / c.L) * (2.0 * kPi / c.L);
-  le.xi = c.xi;
-  le.alpha = c.alpha;
-  le.a = c.a;
-  le.eta = c.eta;
-  le.inv_n3 = 1.0 / ((double)n * n * n);
   const size_t cnt = (size_t)3 * n * nh * n;
   if (op.green_le.n < cnt) op.green_le.alloc(cnt);
-  k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(n, le, op.green_le.p);
+  if constexpr (sizeof(T) == 4) {
+    OpData<double> &o64 = opd<double>(c);
+    refresh_le_table<double>(c, o64);
+    k_narrow<<<4 * c.num_sms, 256, 0, c.stream>>>(op.green_le.p, o64.green_le.p, (int64_t)cnt);
+  } else {
+    GreenLE le;
+    le.on = 1;
+    le.tau = c.tilt / c.L;
+    le.ks2 = (2.0 * kPi / c.L) * (2.0 * kPi / c.L);
+    le.xi = c.xi;
+    le.alpha = c.alpha;
+    le.a = c.a;
+    le.eta = c.eta;
+    le.inv_n3 = 1.0 / ((double)n * n * n);
+    k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(n, le, op.green_le.p);
+  }
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
   op.green_le_tilt = c.tilt;
@@ -2043,15 +2058,7 @@ void launch_wavespace(Ctx &c, const double *x, double *y) {
       le.a = c.a;
       le.eta = c.eta;
       le.inv_n3 = 1.0 / ((double)n * n * n);
-      if (op.green_le_tilt != c.tilt || !op.green_le.p) {
-        // once per box offset (a Lees-Edwards step changes it once)
-        const size_t cnt = (size_t)3 * n * nh * n;
-        if (op.green_le.n < cnt) op.green_le.alloc(cnt);
-        k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(n, le, op.green_le.p);
-        FSD_LAUNCHED(c);
-        FSD_CUDA(cudaGetLastError());
-        op.green_le_tilt = c.tilt;
-      }
+      refresh_le_table<T>(c, op);  // once per box offset
     }
     if (s144)
       k_fft_z_green<T, true><<<blocks, threads, sm, c.stream>>>(spec, plan, op.twiddle.p,
