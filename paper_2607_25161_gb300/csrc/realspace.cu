@@ -428,12 +428,63 @@ __global__ void k_neighbors(int Nt, const double4 *__restrict__ pos,
           }
         }
       }
-  ncnt[i] = min(cnt, cap);
+  const int m = min(cnt, cap);
+  ncnt[i] = m;
   lcnt[i] = min(lc, lcap);
   if (cnt > cap) atomicOr(&flags[0], 1);
   if (lc > lcap) atomicOr(&flags[1], 1);
   atomicMax(&flags[4], cnt);
   atomicMax(&flags[5], lc);
+}
+
+// Within each block of 32 consecutive neighbours of a bead (the pairs one
+// warp step of the real-space sum takes together) order by distance: the
+// lanes then read the radial table at neighbouring intervals, which fall in
+// distinct shared-memory banks, instead of at random ones; the set of pairs
+// in each block, and so the warp's global loads, stays the same.  One warp per
+// bead, a bitonic sort of (r^2, index) across the lanes per block (ties by
+// index, so the order is deterministic).
+__global__ void __launch_bounds__(256) k_nbr_order(int Nt, const float4 *__restrict__ pos32,
+                                                   float L, float tilt, int *nbr,
+                                                   const int *__restrict__ ncnt, int cap) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= Nt) return;
+  const float4 pf = pos32[i];
+  const float invL = 1.f / L;
+  const int m = ncnt[i];
+  int *row = nbr + (size_t)i * cap;
+  for (int b0 = 0; b0 < m; b0 += 32) {
+    const int q = b0 + lane;
+    float key = INFINITY;
+    int idx = INT_MAX;
+    if (q < m) {
+      idx = row[q];
+      const float4 qf = pos32[idx];
+      float e0 = qf.x - pf.x, e1 = qf.y - pf.y, e2 = qf.z - pf.z;
+      const float ny = rintf(e1 * invL);
+      e0 -= ny * tilt;
+      e1 -= ny * L;
+      e0 -= L * rintf(e0 * invL);
+      e2 -= L * rintf(e2 * invL);
+      key = e0 * e0 + e1 * e1 + e2 * e2;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, key, j);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, j);
+        const bool other_less = ok < key || (ok == key && oi < idx);
+        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+        // the lower lane of an ascending pair keeps the smaller element
+        if (lower == up ? other_less : !other_less) {
+          key = ok;
+          idx = oi;
+        }
+      }
+    if (q < m) row[q] = idx;
+  }
 }
 
 void build_neighbors(Ctx &c) {
@@ -496,6 +547,10 @@ void build_neighbors(Ctx &c) {
     }
     if (!redo) break;
   }
+  k_nbr_order<<<ceil_div((int64_t)c.Nt * 32, 256), 256, 0, c.stream>>>(
+      c.Nt, (const float4 *)c.op32.pos.p, (float)c.L, (float)c.tilt, c.nbr.p, c.ncnt.p, c.cap);
+  FSD_LAUNCHED(c);
+  FSD_CUDA(cudaGetLastError());
   if (c.h_flags[2]) c.last_warning = FSD_EOVERLAP;
 }
 
