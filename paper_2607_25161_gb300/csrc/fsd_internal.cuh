@@ -338,6 +338,10 @@ void launch_body_rows(Ctx &c, const double *x, double *y, bool with_lub);  // y2
 template <typename T>
 void launch_lub_apply(Ctx &c, const double *dU, double *out);  // out = RR dU
 void launch_precond(Ctx &c, const double *r, double *z);
+// the same on column *col_dev of the bases V and Z (leading dimension ld),
+// z also written to z2 (the captured Arnoldi step)
+void launch_precond_col(Ctx &c, const double *V, double *Z, int64_t ld, const int *col_dev,
+                        double *z2);
 void launch_rhs(Ctx &c, const double *ft_internal, double shear, double *b);
 void launch_outputs(Ctx &c, const double *x, double shear, double *vel_int,
                     double *str_int);

@@ -373,11 +373,17 @@ static void arnoldi_step(Ctx &c, GState *s, cudaGraphConditionalHandle h_arn) {
   const int nb = vec_blocks(c, n);
   const int mm = sizeof(T) == 8 ? c.m : c.m_in;
   B *V = basis_v(c, B()), *Z = basis_z(c, B());
-  k_g_get_col<B><<<nb, 256, 0, c.stream>>>(gc.vin.p, V, ld, s, n);
-  FSD_LAUNCHED(c);
-  launch_precond(c, gc.vin.p, gc.zf.p);
-  k_g_put_col<B><<<nb, 256, 0, c.stream>>>(Z, ld, gc.zf.p, s, n);
-  FSD_LAUNCHED(c);
+  if constexpr (sizeof(B) == 8) {
+    // z_j = P^-1 v_j straight from and into the bases (column j read on the
+    // device), and into the operator's fixed input buffer
+    launch_precond_col(c, V, Z, ld, &s->j, gc.zf.p);
+  } else {
+    k_g_get_col<B><<<nb, 256, 0, c.stream>>>(gc.vin.p, V, ld, s, n);
+    FSD_LAUNCHED(c);
+    launch_precond(c, gc.vin.p, gc.zf.p);
+    k_g_put_col<B><<<nb, 256, 0, c.stream>>>(Z, ld, gc.zf.p, s, n);
+    FSD_LAUNCHED(c);
+  }
   apply_saddle<T>(c, gc.zf.p, c.w.p);
   cgs_pass_dev(c, 0, V, ld, &s->j, 1, mm, c.w.p, nullptr, s->h);
   cgs_pass_dev(c, 1, V, ld, &s->j, 1, mm, c.w.p, s->h, s->h + 64);

@@ -247,13 +247,22 @@ __device__ __forceinline__ void lu_solve6(const double *LU, const int *pv, doubl
 // Sigma B^T r1 over the aggregate's beads, reduce within their group, each
 // solve the 6x6 LU system (the same numbers in every lane of the group), and
 // then write the bead rows z1 of their beads from z2 held in registers.
+// With col_dev non-null, r and z are column *col_dev of bases with leading
+// dimension ld (the captured Arnoldi step, whose column index lives on the
+// device), and z is also written to z2.
 template <int LPA>
 __global__ void __launch_bounds__(256) k_precond(int N, const int *__restrict__ body_start,
                                                  const double4 *__restrict__ lever,
                                                  const double *__restrict__ r, double *z,
                                                  const double *__restrict__ schur,
                                                  const int *__restrict__ piv, double zeta0,
-                                                 int64_t off) {
+                                                 int64_t off, const int *col_dev, int64_t ld,
+                                                 double *z2) {
+  if (col_dev) {
+    const int64_t o = (int64_t)*col_dev * ld;
+    r += o;
+    z += o;
+  }
   const int J = (blockIdx.x * blockDim.x + threadIdx.x) / LPA;
   const int sub = threadIdx.x & (LPA - 1);
   const bool active = J < N;
@@ -279,19 +288,28 @@ __global__ void __launch_bounds__(256) k_precond(int N, const int *__restrict__ 
   lu_solve6(schur + (size_t)J * 36, piv + 6 * J, v);
   // u = z2 = -v
   if (sub == 0)
-    for (int k = 0; k < 6; ++k) z[off + 6 * (size_t)J + k] = -v[k];
+    for (int k = 0; k < 6; ++k) {
+      z[off + 6 * (size_t)J + k] = -v[k];
+      if (z2) z2[off + 6 * (size_t)J + k] = -v[k];
+    }
   for (int b = b0 + sub; b < b1; b += LPA) {
     const double4 rv = lever[b];
     const double *ri = r + (size_t)b * LDB;
+    double zo[LDB];
+    zo[0] = zeta0 * (ri[0] + (v[0] + v[4] * rv.z - v[5] * rv.y));
+    zo[1] = zeta0 * (ri[1] + (v[1] + v[5] * rv.x - v[3] * rv.z));
+    zo[2] = zeta0 * (ri[2] + (v[2] + v[3] * rv.y - v[4] * rv.x));
+    zo[3] = zeta0 * (ri[3] + v[3]);
+    zo[4] = zeta0 * (ri[4] + v[4]);
+    zo[5] = zeta0 * (ri[5] + v[5]);
+    for (int k = 6; k < 11; ++k) zo[k] = zeta0 * ri[k];
+    zo[11] = 0.0;
     double *zi = z + (size_t)b * LDB;
-    zi[0] = zeta0 * (ri[0] + (v[0] + v[4] * rv.z - v[5] * rv.y));
-    zi[1] = zeta0 * (ri[1] + (v[1] + v[5] * rv.x - v[3] * rv.z));
-    zi[2] = zeta0 * (ri[2] + (v[2] + v[3] * rv.y - v[4] * rv.x));
-    zi[3] = zeta0 * (ri[3] + v[3]);
-    zi[4] = zeta0 * (ri[4] + v[4]);
-    zi[5] = zeta0 * (ri[5] + v[5]);
-    for (int k = 6; k < 11; ++k) zi[k] = zeta0 * ri[k];
-    zi[11] = 0.0;
+    for (int k = 0; k < LDB; ++k) zi[k] = zo[k];
+    if (z2) {
+      double *zj = z2 + (size_t)b * LDB;
+      for (int k = 0; k < LDB; ++k) zj[k] = zo[k];
+    }
   }
 }
 
@@ -841,13 +859,15 @@ void launch_lub_apply(Ctx &c, const double *x, double *y) {
   FSD_CUDA(cudaGetLastError());
 }
 
-void launch_precond(Ctx &c, const double *r, double *z) {
+static void precond_launch(Ctx &c, const double *r, double *z, const int *col_dev, int64_t ld,
+                           double *z2) {
   ProfScope ps(c, PG_PRECOND);
   const int64_t off = (int64_t)LDB * c.Nt;
   const double zeta0 = 6.0 * kPi * c.eta * c.a;
 #define FSD_PRECOND(LPA)                                                                  \
   k_precond<LPA><<<ceil_div((int64_t)c.N * LPA, 256), 256, 0, c.stream>>>(                \
-      c.N, c.body_start.p, (const double4 *)c.lever64.p, r, z, c.schur.p, c.piv.p, zeta0, off)
+      c.N, c.body_start.p, (const double4 *)c.lever64.p, r, z, c.schur.p, c.piv.p, zeta0, off, \
+      col_dev, ld, z2)
   switch (c.body_lanes) {
     case 4: FSD_PRECOND(4); break;
     case 8: FSD_PRECOND(8); break;
@@ -857,6 +877,13 @@ void launch_precond(Ctx &c, const double *r, double *z) {
 #undef FSD_PRECOND
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
+}
+
+void launch_precond(Ctx &c, const double *r, double *z) { precond_launch(c, r, z, nullptr, 0, nullptr); }
+
+void launch_precond_col(Ctx &c, const double *V, double *Z, int64_t ld, const int *col_dev,
+                        double *z2) {
+  precond_launch(c, V, Z, col_dev, ld, z2);
 }
 
 void launch_rhs(Ctx &c, const double *ft_int, double shear, double *b) {
