@@ -761,15 +761,30 @@ __device__ __forceinline__ void green_le(const GreenLE &g, double mp, double ms,
   t3 = A * fd * fd;
 }
 
+// z index of the q-th row a z-pass block visits: on the 144-point path the
+// rows of each group of 16 are visited in 4 x 4 transposed order (q = 4a + b
+// -> z = 4b + a), so that the 4 kx columns x 4 rows of a half-warp's
+// shared-memory accesses (lines 153 = 9 mod 16 elements apart) fall in 16
+// distinct banks; the sheared Green's table is stored in the same visiting
+// order.  The map is its own inverse.
+template <bool S144>
+__host__ __device__ __forceinline__ int zorder(int q) {
+  if constexpr (S144)
+    return (q & ~15) | ((q & 3) << 2) | ((q >> 2) & 3);
+  else
+    return q;
+}
+
 // Lees-Edwards Green factors for every half-spectrum point, laid out as the
-// z pass visits them: [ky index][kx][kz index][3].
+// z pass visits them: [ky index][kx][kz in visiting order (zorder)][3].
 template <typename T>
-__global__ void k_green_le_table(int n, GreenLE le, T *gle) {
+__global__ void k_green_le_table(int n, GreenLE le, T *gle, int s144) {
   const int nh = n / 2 + 1;
   const int64_t total = (int64_t)n * nh * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int zz = (int)(e % n);
+    const int zq = (int)(e % n);
+    const int zz = s144 ? zorder<true>(zq) : zq;
     const int kx = (int)((e / n) % nh);
     const int yy = (int)(e / ((int64_t)n * nh));
     const int ky = yy <= n / 2 ? yy : yy - n, kz = zz <= n / 2 ? zz : zz - n;
@@ -814,7 +829,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
       for (int u = 0; u < U; ++u) {
         const int e = e0 + u * blockDim.x;
         const int t = e & (TX - 1), rest = e >> LTX;
-        const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+        const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = zorder<S144>(rest - comp * n);
         const int kx = kx0 + t;
         v[u] = (e < total && kx < nh) ? g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx]
                                       : Cx<T>{T(0), T(0)};
@@ -824,7 +839,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
         const int e = e0 + u * blockDim.x;
         if (e >= total) continue;
         const int t = e & (TX - 1), rest = e >> LTX;
-        const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+        const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = zorder<S144>(rest - comp * n);
         A[(comp * TX + t) * ls + P(zz)] = v[u];
       }
     }
@@ -841,7 +856,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
   const int ky = yy <= n / 2 ? yy : yy - n;
   const double le_tau = le.dev ? *le.dev * le.invL : le.tau;
   for (int e = threadIdx.x; e < (n << LTX); e += blockDim.x) {
-    const int t = e & (TX - 1), zz = e >> LTX;
+    const int t = e & (TX - 1), zq = e >> LTX, zz = zorder<S144>(zq);
     const int kx = kx0 + t;
     const int kz = zz <= n / 2 ? zz : zz - n;
     const int m = kx * kx + ky * ky + kz * kz;
@@ -872,7 +887,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
         const double kyp = (double)ky - le_tau * (double)kx;
         const double mp = (double)kx * kx + kyp * kyp + (double)kz * kz;
         // factors of this box offset, tabulated once per offset
-        const T *gq = gle + 3 * (((size_t)yy * nh + kx) * n + zz);
+        const T *gq = gle + 3 * (((size_t)yy * nh + kx) * n + zq);
         t1 = gq[0];
         t2 = gq[1];
         t3 = gq[2];
@@ -915,7 +930,7 @@ __global__ void k_fft_z_green(Cx<T> *spec, FftPlan plan, const T *__restrict__ t
   }
   for (int e = threadIdx.x; e < NLn * n; e += blockDim.x) {
     const int t = e & (TX - 1), rest = e >> LTX;
-    const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = rest - comp * n;
+    const int comp = (int)fdiv((uint32_t)rest, plan.fn), zz = zorder<S144>(rest - comp * n);
     const int kx = kx0 + t;
     if (kx < nh) g[comp * cstride + zz * zstride + (int64_t)yy * nh + kx] = R[(comp * TX + t) * ls + P(zz)];
   }
@@ -1955,7 +1970,8 @@ static void refresh_le_table(Ctx &c, OpData<T> &op) {
     le.a = c.a;
     le.eta = c.eta;
     le.inv_n3 = 1.0 / ((double)n * n * n);
-    k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(n, le, op.green_le.p);
+    k_green_le_table<T><<<4 * c.num_sms, 256, 0, c.stream>>>(
+        n, le, op.green_le.p, is_fft144(make_plan(n, nullptr, true)) ? 1 : 0);
   }
   FSD_LAUNCHED(c);
   FSD_CUDA(cudaGetLastError());
