@@ -21,7 +21,7 @@ file reaches the configurations the 32768-bead benchmark times:
   Omega and S are printed and gated at 1e-5 each for both the mixed and the
   FP64 path: the operators' discretisation error at x_err = 1e-6 plus the
   GMRES tolerance 1e-6, amplified by the conditioning of the lubricated
-  system (Sec. 3.2 accuracy rules; the survey's stated mixed-path tolerance).
+  system (Sec. 3.2 accuracy rules).
 """
 
 import os
