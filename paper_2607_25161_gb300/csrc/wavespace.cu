@@ -1558,12 +1558,12 @@ __global__ void k_tile_bin(int Nt, const float4 *__restrict__ pos, float h, int 
 // Per chunk of kTCH beads the block stages, per bead: the x-window factors w
 // and their products with the offset, w (g h - p), for the tile's 8 x
 // points (the dipole term's x factor); (w, offset) pairs for its 8 y and 8 z
-// points; the twelve scaled moments; and an 8 + 8 bit mask of the tile's y
-// and z rows its window reaches.  Each thread then iterates over exactly the
-// beads whose window covers its (y, z) row (a bit mask over the chunk), so
-// a warp runs the largest count among its rows instead of every bead listed
-// for the tile.
-__global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, float h, float alpha,
+// points; the twelve scaled moments; and 8-bit masks of the tile's y and z
+// rows its window reaches.  Each thread then iterates over exactly the
+// beads whose window covers its (y, z) row (a bit mask over the chunk, from
+// sixteen warp ballots), so a warp runs the largest count among its rows
+// instead of every bead listed for the tile.
+__global__ void __launch_bounds__(64, 12) k_spread_gather(int n, int nt, int P, float h, float alpha,
                                                       float cnorm, TauArg ta_,
                                                       const float4 *__restrict__ pos,
                                                       const double *__restrict__ x,
@@ -1576,7 +1576,7 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
   __shared__ __align__(16) float swx[kTCH][20];      // w[8], w * offset[8], pad
   __shared__ __align__(16) float2 syz[kTCH][2][9];   // (w, offset) of y[8] and z[8], pad
   __shared__ __align__(16) float sm[kTCH][12];
-  __shared__ unsigned scov[kTCH];
+  __shared__ unsigned scov[2][kTCH];  // y and z rows of the tile each bead's window reaches
   const int tile = blockIdx.x;
   const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
   const int x0 = tx * kTS, y0 = ty * kTS, z0 = tz * kTS;
@@ -1591,30 +1591,39 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
   for (int cb = b0; cb < b1; cb += kTCH) {
     const int nc = min(kTCH, b1 - cb);
     __syncthreads();
-    // 1D window factors and offsets of each bead at this tile's coordinates
-    for (int e = threadIdx.x; e < nc * 3 * kTS; e += blockDim.x) {
-      const int bi = e / (3 * kTS), r = e - bi * 3 * kTS, d = r / kTS, k = r - d * kTS;
+    // 1D window factors and offsets of each bead at this tile's coordinates:
+    // one (bead, axis) pair per task, its window start from one division; the
+    // y and z rows the window reaches as bit masks
+    for (int e = threadIdx.x; e < nc * 3; e += blockDim.x) {
+      const int bi = e / 3, d = e - bi * 3;
       const float4 p = pos[tile_beads[cb + bi]];
       const float pc = d == 0 ? p.x : (d == 1 ? p.y : p.z);
       const int g0 = (int)floorf(pc / h) - P / 2 + 1;
-      const int gt = (d == 0 ? x0 : (d == 1 ? y0 : z0)) + k;
-      float w = 0.f, yv = 0.f;
-      if (gt < n) {
-        // slot of this grid index in the window (g0 is within one box of gt)
-        int off = gt - g0;
-        if (off < 0) off += n;
-        if (off >= n) off -= n;
-        if (off < P) {
-          yv = float(g0 + off) * h - pc;
-          w = expf(-alpha * yv * yv);
+      const int gb = d == 0 ? x0 : (d == 1 ? y0 : z0);
+      unsigned cov = 0;
+#pragma unroll 1
+      for (int k = 0; k < kTS; ++k) {
+        const int gt = gb + k;
+        float w = 0.f, yv = 0.f;
+        if (gt < n) {
+          // slot of this grid index in the window (g0 is within one box of gt)
+          int off = gt - g0;
+          if (off < 0) off += n;
+          if (off >= n) off -= n;
+          if (off < P) {
+            yv = float(g0 + off) * h - pc;
+            w = expf(-alpha * yv * yv);
+          }
+        }
+        cov |= (w != 0.f ? 1u : 0u) << k;
+        if (d == 0) {
+          swx[bi][k] = w;
+          swx[bi][kTS + k] = w * yv;
+        } else {
+          syz[bi][d - 1][k] = make_float2(w, yv);
         }
       }
-      if (d == 0) {
-        swx[bi][k] = w;
-        swx[bi][kTS + k] = w * yv;
-      } else {
-        syz[bi][d - 1][k] = make_float2(w, yv);
-      }
+      if (d > 0) scov[d - 1][bi] = cov;
     }
     // moments: F and the dipole D (= S + antisym(L); column 0 takes -tau
     // column 1 in a Lees-Edwards box), with the window norm and 2 alpha
@@ -1647,21 +1656,22 @@ __global__ void __launch_bounds__(64) k_spread_gather(int n, int nt, int P, floa
       m[11] = cd * D22;
     }
     __syncthreads();
-    // rows of the tile each bead's window reaches
-    for (int bi = threadIdx.x; bi < nc; bi += blockDim.x) {
-      unsigned cv = 0;
+    // the beads whose window covers this thread's (y, z) row, as a bit mask
+    // over the chunk: per y row and per z row a ballot across the lanes
+    // (lane b of each warp stands for bead b of the chunk)
+    unsigned mask;
+    {
+      const int lane = threadIdx.x & 31;
+      const unsigned yc = lane < nc ? scov[0][lane] : 0u, zc = lane < nc ? scov[1][lane] : 0u;
+      unsigned my = 0, mz = 0;
 #pragma unroll
       for (int k = 0; k < kTS; ++k) {
-        cv |= (syz[bi][0][k].x != 0.f ? 1u : 0u) << k;
-        cv |= (syz[bi][1][k].x != 0.f ? 1u : 0u) << (kTS + k);
+        const unsigned by = __ballot_sync(0xffffffffu, (yc >> k) & 1u);
+        const unsigned bz = __ballot_sync(0xffffffffu, (zc >> k) & 1u);
+        if (k == iy) my = by;
+        if (k == iz) mz = bz;
       }
-      scov[bi] = cv;
-    }
-    __syncthreads();
-    unsigned mask = 0;
-    for (int bi = 0; bi < nc; ++bi) {
-      const unsigned cv = scov[bi];
-      mask |= ((cv >> iy) & (cv >> (kTS + iz)) & 1u) << bi;
+      mask = my & mz;
     }
     while (mask) {
       const int bi = __ffs(mask) - 1;
