@@ -304,7 +304,12 @@ const char *fsd_profile_group_name(int g);
  * array: calls whose GPU work overlaps race on it, so order them on one
  * stream (or with events).  Each call rewrites or zeroes everything it
  * reads.  Work is enqueued on cuda_stream (NULL: the default stream); out is
- * ready when that stream is.  An error already pending in the CUDA runtime
+ * ready when that stream is.  The call may be captured into a CUDA graph
+ * (cuda_stream capturing, in any capture mode): the graph then reads
+ * bead_pos and in, and writes out, at each replay, with the parameters of
+ * the captured call; its argument checks and the address lookup are host
+ * queries made with the thread's capture mode relaxed for their duration.
+ * An error already pending in the CUDA runtime
  * when the call starts is left in place and the call returns FSD_ECUDA
  * without doing anything. */
 fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead_pos,

@@ -2295,6 +2295,16 @@ extern "C" fsd_status fsd_apply_wave_noalloc(int64_t n_beads, const double *bead
                                              double xi, int grid, int P, double m_shape,
                                              double a, double eta, void *cuda_stream) {
   using namespace fsd;
+  // The error and pointer queries and the symbol lookup below queue no GPU
+  // work, but a stream capture begun in global or thread-local mode forbids
+  // this thread runtime calls it counts as potentially unsafe.  They run with
+  // the thread's capture mode relaxed; the caller's mode is put back on
+  // every return.
+  struct RelaxCapture {
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    RelaxCapture() { cudaThreadExchangeStreamCaptureMode(&mode); }
+    ~RelaxCapture() { cudaThreadExchangeStreamCaptureMode(&mode); }
+  } relax_capture;
   // an error left pending by the caller's earlier work is not this call's:
   // leave it in place for the caller and do nothing
   if (cudaPeekAtLastError() != cudaSuccess) return FSD_ECUDA;

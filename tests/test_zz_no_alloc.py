@@ -9,8 +9,11 @@ with different inputs, and check each result against the context-based
 wave-space operator (fsd_apply_mobility, part 2, FP32) within the FP32
 operator tolerance of the parity tests (2e-5 relative L2), once at a middle
 size and once at the largest accepted one (48^3 grid, 4096 beads), whose
-layout comes closest to the array's 10 MiB.  The file is named so that
-pytest collects it last."""
+layout comes closest to the array's 10 MiB.  A third test uses the entry
+point the way it exists to be used: one plain call, then a second call
+captured into a CUDA graph on a side stream (torch's default, global capture
+mode), replayed after the positions and moments in the captured buffers have
+been rewritten.  The file is named so that pytest collects it last."""
 
 import ctypes
 
@@ -62,6 +65,57 @@ def test_noalloc_wave_matches_context_operator(n_agg, n_b, phi, grid, P, xi):
         assert np.all(np.isfinite(got))
         assert rel(got, ref) < 2e-5, (call, rel(got, ref))
     s.close()
+
+
+def test_noalloc_replays_inside_captured_graph():
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2607_25161_gb300 as pkg
+
+    lib = pkg.load()
+    xi, grid, P = 0.5, 40, 8
+    # two configurations of the same bead count and box: the replays must read
+    # the positions in the captured buffer, not those of the captured call
+    configs = [synth.suspension(48, 5, 0.08, seed) for seed in (31, 32)]
+    L = configs[0][2]
+    assert configs[1][2] == L and len(configs[1][0]) == len(configs[0][0])
+    nt = len(configs[0][0])
+    rng = np.random.default_rng(33)
+    dpos = torch.tensor(configs[0][0], dtype=torch.float64, device="cuda")
+    dF = torch.tensor(rng.normal(size=(nt, 11)), dtype=torch.float64, device="cuda")
+    dout = torch.empty((nt, 11), dtype=torch.float64, device="cuda")
+
+    def call(stream):
+        return lib.fsd_apply_wave_noalloc(nt, ctypes.c_void_p(dpos.data_ptr()),
+                                          ctypes.c_void_p(dF.data_ptr()),
+                                          ctypes.c_void_p(dout.data_ptr()), L, xi, grid, P, 0.0,
+                                          1.0, 1.0, stream)
+
+    torch.cuda.synchronize()
+    assert call(None) == pkg.FSD_OK
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=side):
+        st = call(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == pkg.FSD_OK
+    for rep, (pos, body, _) in enumerate(configs + configs[::-1]):
+        F = rng.normal(size=(nt, 11))
+        s = pkg.Suspension(pos, body, L, xi=xi, grid=grid, P=P)
+        ref = s.apply_mobility(F, part=2, precision=pkg.FSD_MIXED)
+        s.close()
+        dpos.copy_(torch.tensor(pos, dtype=torch.float64))
+        dF.copy_(torch.tensor(F, dtype=torch.float64))
+        dout.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        got = dout.cpu().numpy()
+        assert np.all(np.isfinite(got)), rep
+        assert rel(got, ref) < 2e-5, (rep, rel(got, ref))
+    del graph
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
