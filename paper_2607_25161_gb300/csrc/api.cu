@@ -648,7 +648,7 @@ static void setup_impl(Ctx &c, int64_t n_beads, const double *bead_pos, const in
   c.rhs.alloc(c.nunk);
   c.res.alloc(c.nunk);
   c.xprev.alloc(c.nunk);
-  c.partial.alloc(std::max<int64_t>((int64_t)64 * kDotPartials, cgs_partial_size(c.nunk, mm + 1)));
+  c.partial.alloc(std::max<int64_t>((int64_t)64 * kDotPartials, cgs_partial_size(c.nunk, mm + 1, c.num_sms)));
   c.hcol.alloc(512);
   c.cgs_ticket.alloc(1);
   FSD_CUDA(cudaMemset(c.cgs_ticket.p, 0, sizeof(unsigned)));

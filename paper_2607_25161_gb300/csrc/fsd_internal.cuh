@@ -388,7 +388,7 @@ void vec_round_f32(Ctx &c, float *z32, double *z);  // z32 = (float) z, z = (dou
 // SM on a 152-SM part.
 constexpr int kDotPartials = 608;
 constexpr int kMaxBasis = 64;  // longest basis a Gram-Schmidt pass takes
-int64_t cgs_partial_size(int64_t nunk, int kmax);
+int64_t cgs_partial_size(int64_t nunk, int kmax, int nsm);
 void vec_axpby(Ctx &c, double *y, double a, const double *x, double b,
                int64_t n);                          // y = a x + b y
 void norm2_dev(Ctx &c, const double *x, double *out_dev);

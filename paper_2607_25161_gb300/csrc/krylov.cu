@@ -79,10 +79,15 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, doub
 //   MODE 0:  partial dots  V_j . w
 //   MODE 1:  w -= sum_j coef_j V_j, then partial dots V_j . w
 //   MODE 2:  w -= sum_j coef_j V_j, then partial ||w||^2
-// Each thread owns kE elements spaced by the grid's thread count (coalesced);
-// basis vectors are taken four at a time so that 4 kE loads are in flight
-// per thread; block partials go to partial[j * blocks + block] and the last
-// block to finish reduces them into out (fixed reduction order throughout).
+// Each thread owns up to kE elements spaced by the grid's thread count
+// (coalesced); basis vectors are taken four at a time so that 4 kE loads are
+// in flight per thread; block partials go to partial[j * blocks + block] and
+// the last block to finish reduces them into out (fixed reduction order
+// throughout).  The grid is a whole number of waves over the SMs (two blocks
+// per SM on the benchmark's 417 792 unknowns), so that every SM carries the
+// same share of the FP64 multiply-adds that bound these passes; six elements
+// per thread keep the warp reductions of the dot products (1.5 FP64 adds per
+// basis vector and warp) small beside the 6 multiply-adds they sum.
 //
 // The basis element type B is double (the FP64 solve and the Lanczos square
 // roots: every product and sum in FP64) or float (the inner GMRES of the
@@ -91,7 +96,7 @@ void dot_multi(Ctx &c, const double *V, int64_t ld, int k, const double *w, doub
 // numbers would need FP64, whose rate is 1/74 of FP32 on this part), the
 // update sum_j coef_j V_j is formed in FP32 and subtracted from the FP64 w,
 // and the cross-warp sums stay FP64.
-constexpr int kE = 4;
+constexpr int kE = 6;
 
 // Warp sums of four values with six shuffles: after the exchange across
 // lane bit 4 each lane keeps two of the four partial sums, after bit 3 one;
@@ -239,9 +244,19 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
   if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
+  const int nb = (int)gridDim.x;
   for (int jj = warp; jj < kr; jj += 8) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (int64_t)jj * gridDim.x + b);
+    // two independent sums per lane (a dependent FP64 add is long on this
+    // part), in an order fixed by the grid size
+    const double *pj = partial + (int64_t)jj * nb;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nb; b += 64) {
+      s0 += __ldcg(pj + b);
+      s1 += __ldcg(pj + b + 32);
+    }
+    if (b < nb) s0 += __ldcg(pj + b);
+    double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[jj] = s;
@@ -249,7 +264,13 @@ __global__ void __launch_bounds__(256) k_cgs(const B *__restrict__ V, int64_t ld
   if (threadIdx.x == 0) atomicExch(ticket, 0u);
 }
 
-static int cgs_blocks(int64_t n) { return std::max(1, ceil_div(n, 256LL * kE)); }
+// enough blocks for kE elements per thread, rounded up to whole waves of
+// the SMs once there are more blocks than SMs
+static int cgs_blocks(int64_t n, int nsm) {
+  const int64_t b = std::max<int64_t>(1, ceil_div(n, 256LL * kE));
+  if (nsm < 1 || b <= nsm) return (int)b;
+  return (int)(ceil_div(b, (int64_t)nsm) * nsm);
+}
 
 // out[j] = V_j . w (j < k); mode 1 / 2 first apply w -= V coef (mode 2:
 // out[0] = ||w||^2).  With k_dev non-null the basis size is read on the
@@ -261,7 +282,7 @@ static void cgs_launch(Ctx &c, int mode, const B *V, int64_t ld, int k, const in
   ProfScope ps(c, PG_KRYLOV);
   if (std::max(k, kmax) > kMaxBasis) throw Invalid{"Krylov basis longer than 64 vectors"};
   const int64_t n = c.nunk;
-  const int blocks = cgs_blocks(n);
+  const int blocks = cgs_blocks(n, c.num_sms);
   unsigned *tk = c.cgs_ticket.p;
   double *pp = c.partial.p;
   if (mode == 0)
@@ -294,8 +315,8 @@ void cgs_pass_dev(Ctx &c, int mode, const float *V, int64_t ld, const int *k_dev
   cgs_launch(c, mode, V, ld, 0, k_dev, k_add, kmax, w, coef_dev, out_dev);
 }
 
-int64_t cgs_partial_size(int64_t nunk, int kmax) {
-  return (int64_t)cgs_blocks(nunk) * (kmax + 1);
+int64_t cgs_partial_size(int64_t nunk, int kmax, int nsm) {
+  return (int64_t)cgs_blocks(nunk, nsm) * (kmax + 1);
 }
 
 // w[i] += sign * sum_j coef[j] V_j[i]; with a float basis the sum over j is
