@@ -18,8 +18,8 @@
 // in shared memory run fused x + y kernels (k_fft_xy_fwd / k_fft_xy_inv, one
 // 1024-thread block per (component, z) plane, radix-16 / 9 / 8 register
 // DFTs) and the inverse writes planar velocity fields [6][n^3]; larger
-// grids and FP64 take separate x and y passes (radix <= 4) and interleaved
-// velocity fields [n^3][8].  k_fft_z_green does the z transforms with the
+// grids and FP64 take separate x and y passes (the same radix-16 / 9 / 8
+// plans) and interleaved velocity fields [n^3][8].  k_fft_z_green does the z transforms with the
 // Green's function applied between forward and inverse.
 //   comps 0..2  monopole density g_F = sum_j F_j W(x - x_j)
 //   comps 3..5  dipole density   g_D = sum_j 2 alpha W(x - x_j) D_j (x - x_j),
@@ -30,7 +30,8 @@
 //   A(k) = (1 + k^2/(4 xi^2)) exp(-k^2/(4 xi^2) + k^2/(2 alpha)) / (eta k^2),
 // read-outs: velocity from fM u_hat, rotation / strain from grad (fD u_hat)
 // (k_interp_v4 for FP32 planar fields on grids that are multiples of 4,
-// k_interp otherwise).
+// k_interp for other FP32 planar fields, k_interp_rows for interleaved
+// fields: FP64 and the large FP32 grids).
 #include "fsd_internal.cuh"
 
 #include <algorithm>
