@@ -3,16 +3,24 @@
 //   far-field slip      u^B  = sqrt(2 kT/dt) (M_w^(1/2) psi_w + M_r^(1/2) psi_r)
 //   near-field force    F^B  = sqrt(2 kT/dt) (R_FU^nf)^(1/2) psi_nf
 // The wave part is analytic (wavespace.cu: a random field scaled in k space,
-// inverse FFT, interpolation); the real-space and near-field square roots come
-// from Lanczos iterations (Krylov approximation of f(A) b, f = sqrt) on the
-// library's real-space operator and bead-level lubrication blocks.  The next
+// inverse FFT, interpolation); the real-space square root comes from Lanczos
+// iterations (Krylov approximation of f(A) b, f = sqrt) on the library's
+// real-space operator.  The near-field force comes either from the exact
+// pairwise sampler (the default: F = sum over lubrication pairs of the pair
+// model's dissipation factor applied to pair noise, k_nf_pairwise in
+// nearfield.cu; covariance exactly R_FU^nf) or from the paper's Lanczos
+// iteration on the bead-level lubrication blocks.  The next
 // solve adds u^B to the bead rows (all 11 components) and -Sigma F^B to the
 // body rows of its right-hand side.
 //
 // Random numbers: given by the caller, or drawn from Philox4x32-10 with the
 // counter layout (index, stream * 256 + call, step): stream 1 the wave field
-// (wavespace.cu), stream 2 psi_r (11 per bead), stream 3 psi_nf (6 per bead),
-// the index of a bead being its position in the caller's bead array.
+// (wavespace.cu), stream 2 psi_r (11 per bead), stream 3 psi_nf (6 per bead,
+// Lanczos near-field sampler), stream 4 the drift's random body vectors
+// (indexed by body),
+// stream 5 the pairwise near-field sampler's pair noise (nearfield.cu, a
+// four-word counter with both beads of the pair), the index of a bead being
+// its position in the caller's bead array.
 #include "fsd_internal.cuh"
 
 #include <algorithm>
