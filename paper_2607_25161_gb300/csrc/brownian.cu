@@ -17,10 +17,9 @@
 // counter layout (index, stream * 256 + call, step): stream 1 the wave field
 // (wavespace.cu), stream 2 psi_r (11 per bead), stream 3 psi_nf (6 per bead,
 // Lanczos near-field sampler), stream 4 the drift's random body vectors
-// (indexed by body),
-// stream 5 the pairwise near-field sampler's pair noise (nearfield.cu, a
-// four-word counter with both beads of the pair), the index of a bead being
-// its position in the caller's bead array.
+// (indexed by body), stream 5 the pairwise near-field sampler's pair noise
+// (nearfield.cu, a four-word counter holding both beads of the pair); the
+// index of a bead is its position in the caller's bead array.
 #include "fsd_internal.cuh"
 
 #include <algorithm>
