@@ -10,7 +10,7 @@ FP64 iterative refinement, FP64 Arnoldi and LU); the plain FP64 path and the
 mixed path with an FP32 inner Krylov basis are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload step|batch|rods|seeds|oracle-ladder]
+                  [--workload step|batch|rods|seeds|oracle-ladder|configs]
 
 With N > 1 (torchrun) every rank steps its own replica of the suspension (the
 single-suspension solve does not shard); value = beads x steps x ranks / the
@@ -36,7 +36,10 @@ for every point.
 --workload seeds times the step benchmark's mixed path on five independently
 generated suspensions of the same workload (median and interquartile
 range); --workload oracle-ladder times the CPU oracle on 32, 128 and 512
-beads (no GPU)."""
+beads (no GPU); --workload configs runs the scaling study's two other
+configurations: 4096 beads at phi 0.1 with xi = 25/L against xi = 0.5 (FP64
+and mixed), and the Brownian size ladder of 16-bead aggregates at phi 0.24
+(32 768 to 262 144 beads, mixed, both xi)."""
 
 import argparse
 import hashlib
