@@ -36,7 +36,13 @@ Readings of points where the paper is silent:
 * Stresslet returned: S^H + S^C (Eq. stress_comp a, d), with F^C the
   negative total bead force.
 
-Parity pins: tests/test_oracle_*.py.  None of this module is parity-unpinned.
+Parity pins: tests/test_oracle_*.py; tests/test_oracle_pin_sensitivity.py
+plants mistakes in a copy of this source and checks that the pins catch them.
+One value is parity unpinned: the rolling coefficient of the pair model,
+8 pi eta a^3 (1/10) ln(1/eps) in lub_coefficients (a reading of functions the
+paper does not print; the two-sphere rotation functions it stands in for are
+not of the dissipation form's shape, so no published number fixes it, and a
+changed value passes every pin).  Everything else is pinned.
 """
 
 import numpy as np

@@ -154,6 +154,37 @@ def test_lubrication_pair_symmetric_psd_and_rigid_invariant(gap):
     assert np.allclose(fi, -A * d, rtol=1e-12, atol=1e-12)
 
 
+def test_lubrication_coefficients_follow_equal_sphere_asymptotics():
+    # Two-sphere lubrication theory (Jeffrey & Onishi 1984, J. Fluid Mech.
+    # 139; Kim & Karrila 1991, Microhydrodynamics, ch. 11) gives, for spheres
+    # of size ratio beta at dimensionless gap eps -> 0, the singular terms
+    #   X^A_11 = g1 / eps + g2 ln(1/eps),  g1 = 2 beta^2 / (1 + beta)^3,
+    #                                     g2 = beta (1 + 7 beta + beta^2) / (5 (1 + beta)^3)
+    #   Y^A_11 = g2t ln(1/eps),            g2t = 4 beta (2 + beta + 2 beta^2) / (15 (1 + beta)^3)
+    # and for equal spheres moving apart / sliding with relative velocity V
+    # the force is 6 pi eta a X^A_11 V (squeeze) or 6 pi eta a Y^A_11 V
+    # (sliding): the pair model's A and B.  Their differences between two gaps
+    # cancel the cut-off shift.
+    beta = 1.0
+    g1 = 2 * beta ** 2 / (1 + beta) ** 3
+    g2 = beta * (1 + 7 * beta + beta ** 2) / (5 * (1 + beta) ** 3)
+    g2t = 4 * beta * (2 + beta + 2 * beta ** 2) / (15 * (1 + beta) ** 3)
+    z0 = 6 * PI
+
+    def AB(eps):
+        A, B, _ = O.lub_coefficients(eps, hmin=1e-12)
+        return A / z0, B / z0
+
+    e1, e2 = 1e-7, 1e-5
+    (A1, B1), (A2, B2) = AB(e1), AB(e2)
+    # the Reynolds limit: eps A -> g1 (squeeze force (3/2) pi eta a^2 V / h)
+    assert abs(e1 * A1 - g1) < 1e-5
+    # logarithmic terms
+    ln = np.log(e2 / e1)
+    assert abs(((A1 - g1 / e1) - (A2 - g1 / e2)) / ln - g2) < 1e-3
+    assert abs((B1 - B2) / ln - g2t) < 1e-3
+
+
 def test_lubrication_cutoff_and_intrabody():
     xi, xj = _two_body_pair(1.0 - 1e-12, 3)
     assert np.abs(O.lub_pair_matrix(xi, xj)).max() < 1e-9
@@ -234,6 +265,24 @@ def test_integrator_rotation_angle():
         X, q, x = O.integrate(X, q, r, np.array([0, 0]), U, 1e-3)
     ang = np.arctan2(x[0, 1], x[0, 0])
     assert abs(ang - 0.5) < 1e-4
+
+
+def test_integrator_rotates_in_the_lab_frame():
+    # Omega is a lab-frame angular velocity: from the orientation q0 (90
+    # degrees about x) a constant Omega along lab z turns the body about lab z,
+    # R(t) = R_z(Omega t) R(q0), not about the body's own z axis.  A dimer
+    # along body z points along lab -y at t = 0 and along
+    # (sin theta, -cos theta, 0) after theta = Omega t.
+    r = np.array([[0, 0, 1.0], [0, 0, -1.0]])
+    X = np.zeros((1, 3))
+    q = np.array([[np.cos(PI / 4), np.sin(PI / 4), 0, 0]])
+    U = np.array([[0, 0, 0, 0, 0, 0.5]])
+    _, _, x = O.integrate(X, q, r, np.array([0, 0]), np.zeros((1, 6)), 1e-3)
+    assert np.allclose(x[0], [0, -1.0, 0], atol=1e-12)
+    for _ in range(1000):
+        X, q, x = O.integrate(X, q, r, np.array([0, 0]), U, 1e-3)
+    th = 0.5
+    assert np.abs(x[0] - [np.sin(th), -np.cos(th), 0]).max() < 2e-4
 
 
 # ------------------------------------------------------- sampled-row helpers
