@@ -80,12 +80,50 @@ def test_hermitian_field_gives_real_slip():
     pos = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 1.0]])
     u = B.brownian_wave_slip(pos, 9.0, 0.4, n, f)
     assert u.shape == (2, 11) and np.all(np.isfinite(u)) and np.abs(u).max() > 0
-    # the library's generator fills the same layout with the same symmetry
+    # the library's generator fills the same layout with the same symmetry;
+    # both fields are zero on the Nyquist planes and at k = 0 (a real field
+    # has no independent Nyquist sine modes, and the k = 0 mode is excluded)
     g = B.philox_wave_field(n, seed=5, step=2)
-    for kz in range(n):
-        for ky in range(n):
-            mz, my = (n - kz) % n, (n - ky) % n
-            assert np.allclose(g[:, kz, ky, 0], np.conj(g[:, mz, my, 0]))
+    for fld in (f, g):
+        assert np.abs(fld[:, n // 2, :, :]).max() == 0.0
+        assert np.abs(fld[:, :, n // 2, :]).max() == 0.0
+        assert np.abs(fld[:, :, :, n // 2]).max() == 0.0
+        assert np.abs(fld[:, 0, 0, 0]).max() == 0.0
+        for kz in range(n):
+            for ky in range(n):
+                mz, my = (n - kz) % n, (n - ky) % n
+                assert np.allclose(fld[:, kz, ky, 0], np.conj(fld[:, mz, my, 0]))
+
+
+def test_brownian_terms_have_the_fluctuation_dissipation_amplitude():
+    # Eq. SP2: the real-space slip and the near-field force are
+    # sqrt(2 kT/dt) times square roots of M_r and R_FU^nf, so that summed
+    # over an orthonormal basis of their noise (psi_r, 11 per bead; psi_nf, 6
+    # per bead) their second moments are (2 kT/dt) M_r and (2 kT/dt) R_FU^nf.
+    # Two beads of different bodies 0.2a apart (one lubrication pair), a zero
+    # wave field.
+    L, xi, n, kT, dt = 8.0, 1.0, 4, 0.7, 0.02
+    pos = np.array([[1.0, 1.5, 2.0], [3.2, 1.5, 2.0]])
+    body = np.array([0, 1])
+    field = np.zeros((3, n, n, n // 2 + 1), dtype=np.complex128)
+    Nt = 2
+    cu = np.zeros((11 * Nt, 11 * Nt))
+    cf = np.zeros((6 * Nt, 6 * Nt))
+    for k in range(11 * Nt):
+        psi_r = np.eye(11 * Nt)[k].reshape(Nt, 11)
+        u, f = B.brownian_terms(pos, body, L, xi, n, field, psi_r, np.zeros((Nt, 6)), kT, dt)
+        assert np.abs(f).max() == 0.0
+        cu += np.outer(u.reshape(-1), u.reshape(-1))
+    for k in range(6 * Nt):
+        psi_nf = np.eye(6 * Nt)[k].reshape(Nt, 6)
+        u, f = B.brownian_terms(pos, body, L, xi, n, field, np.zeros((Nt, 11)), psi_nf, kT, dt)
+        cf += np.outer(f.reshape(-1), f.reshape(-1))
+    Mr = O.mobility_real_dense(pos, L, xi, 2.0 + np.sqrt(46.0) / xi).reshape(11 * Nt, 11 * Nt)
+    R = O.split_grand(O.lubrication_dense(pos, body, L, rcut=3.0), Nt)[0]
+    s2 = 2.0 * kT / dt
+    assert np.abs(R).max() > 0
+    assert np.abs(cu - s2 * Mr).max() < 1e-10 * np.abs(s2 * Mr).max()
+    assert np.abs(cf - s2 * R).max() < 1e-10 * np.abs(s2 * R).max()
 
 
 def test_sqrtm_apply():

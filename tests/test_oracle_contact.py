@@ -21,6 +21,17 @@ def test_single_pair_closed_form():
     assert np.allclose(out[:, 3:], 0.0, atol=1e-12)  # single beads: no lever arm
 
 
+def test_pair_forces_hertz_term_is_the_closed_form():
+    # the combined interparticle-force routine with contact only: the same
+    # Hertz law k_n delta^1.5 along the line of centres
+    L, kn, delta = 30.0, 1e4, 0.03
+    d = np.array([1.0, 2.0, -2.0]) / 3.0
+    pos = np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 5.0] + (2.0 - delta) * d])
+    out, fb = C.pair_forces(pos, np.array([0, 1]), L, kn=kn)
+    f = kn * delta ** 1.5
+    assert np.allclose(fb[1], f * d, rtol=1e-12) and np.allclose(fb[0], -f * d, rtol=1e-12)
+
+
 def test_pair_across_the_boundary():
     L, kn = 20.0, 10.0
     pos = np.array([[0.3, 4.0, 4.0], [L - 1.5, 4.0, 4.0]])  # 1.8 apart through the wall

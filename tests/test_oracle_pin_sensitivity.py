@@ -1,13 +1,13 @@
 """The oracle's pins catch plausible mistakes (CPU only).
 
-Each case plants one mistake in a copy of the oracle's source text (a wrong
-sign, a dropped term, a wrong coefficient, a transposed operand, a factor of
-two), executes the copy as a separate module, and runs the pins expected to
-catch it with that module in place of the oracle: at least one of them must
-fail.  The oracle package itself is never modified; the same pins pass on it
-in their own files.  A planted text that no longer occurs exactly once in the
-oracle makes its case fail, so an edit of the oracle cannot silently retire a
-case.
+Each case plants one mistake in a copy of one oracle module's source text (a
+wrong sign, a dropped term, a wrong coefficient or exponent, a transposed
+operand, a factor of two), executes the copy as a separate module, and runs
+the pins expected to catch it with that module in place of the original: at
+least one of them must fail.  The oracle package itself is never modified;
+the same pins pass on it in their own files.  A planted text that no longer
+occurs exactly once in its module makes the case fail, so an edit of the
+oracle cannot silently retire a case.
 
 The rolling coefficient of the lubrication pair model (8 pi eta a^3 (1/10)
 ln(1/eps)) is the one value no pin fixes: it is this build's reading of
@@ -19,13 +19,20 @@ import types
 
 import pytest
 
+import synth
+import test_oracle_brownian as TB
+import test_oracle_contact as TC
+import test_oracle_drift as TD
 import test_oracle_ewald as TE
 import test_oracle_lees_edwards as TL
 import test_oracle_solve as TS
 import test_oracle_tensors as TT
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "fsd_oracle.py")
+# the name under which the pin files hold each oracle module
+HANDLE = {"fsd_oracle": "O", "brownian_oracle": "B", "drift_oracle": "D", "contact_oracle": "C"}
+# the geometry of the drift pins' module fixture
+DOUBLETS = synth.config_doublets(2, 9.0, seed=6)
 
 # pin name -> (test module, test function, arguments)
 PINS = {
@@ -45,9 +52,29 @@ PINS = {
     "le_split": (TL, "test_split_independence_with_tilt", {}),
     "le_lattice": (TL, "test_lattice_translation_and_spd", {}),
     "le_solve": (TL, "test_solve_with_tilt_translation_invariant", {}),
+    "philox_known_answers": (TB, "test_philox_known_answers", {}),
+    "box_muller_moments": (TB, "test_box_muller_moments", {}),
+    "wave_covariance": (TB, "test_wave_sample_covariance_is_the_wave_mobility", {}),
+    "wave_covariance_tilt": (TB, "test_wave_sample_covariance_with_tilt", {}),
+    "field_layout": (TB, "test_hermitian_field_gives_real_slip", {}),
+    "fd_amplitude": (TB, "test_brownian_terms_have_the_fluctuation_dissipation_amplitude", {}),
+    "nf_noise_as_force": (TB, "test_near_field_noise_acts_like_an_aggregate_force", {}),
+    "precond_sqrt_covariance": (TB, "test_preconditioned_square_root_has_covariance_R", {}),
+    "pairwise_covariance": (TB, "test_pairwise_near_field_sampler_has_covariance_R", {}),
+    "pair_layout": (TB, "test_pair_normals_layout", {}),
+    "rigid_displacement": (TD, "test_displacement_is_rigid_and_first_order_right", {"doublets": DOUBLETS}),
+    "rfd_divergence": (TD, "test_rfd_basis_sum_is_the_mobility_divergence", {"doublets": DOUBLETS}),
+    "fixman_derivative": (TD, "test_fixman_large_m_is_the_directional_derivative", {"doublets": DOUBLETS}),
+    "hertz_closed_form": (TC, "test_single_pair_closed_form", {}),
+    "hertz_in_pair_forces": (TC, "test_pair_forces_hertz_term_is_the_closed_form", {}),
+    "dlvo_minus_gradient": (TC, "test_dlvo_force_is_minus_the_potential_derivative", {}),
+    "vdw_far_field": (TC, "test_van_der_waals_far_field_is_the_textbook_sphere_limit", {}),
+    "double_layer": (TC, "test_double_layer_screening_and_contact_value", {}),
+    "vdw_capped": (TC, "test_van_der_waals_attraction_capped_under_overlap_and_finite_at_contact", {}),
+    "newton_cutoff_intrabody": (TC, "test_dlvo_and_hertz_newton_third_law_cutoff_and_intrabody", {}),
 }
 
-# (case, planted text, replacement, pins expected to catch it)
+# (case, planted text, replacement, pins expected to catch it): fsd_oracle
 MUTATIONS = [
     ("constraint stresslet factor 1/2 doubled",
      "SC[J] += 0.5 * (np.outer", "SC[J] += 1.0 * (np.outer", ["reciprocity"]),
@@ -115,25 +142,93 @@ MUTATIONS = [
     ("preconditioner scalar zeta0 -> 1/zeta0",
      "Mid[:n1, :n1] = z0 * np.eye(n1)", "Mid[:n1, :n1] = np.eye(n1) / z0", ["precond_exact"]),
 ]
+CASES = [("fsd_oracle",) + m for m in MUTATIONS]
+
+# brownian_oracle, drift_oracle, contact_oracle
+CASES += [
+    ("brownian_oracle", "Philox key schedule constant",
+     "k0 = (k0 + 0x9E3779B9) & M32", "k0 = (k0 + 0x9E3779B8) & M32", ["philox_known_answers"]),
+    ("brownian_oracle", "Box-Muller radius without the factor 2",
+     "r0 = np.sqrt(-2.0 * np.log(u[0]))", "r0 = np.sqrt(-np.log(u[0]))", ["box_muller_moments"]),
+    ("brownian_oracle", "wave sample without its -k half",
+     "wts.append(1.0 if kx == 0 else 2.0)", "wts.append(1.0 if kx == 0 else 1.0)", ["wave_covariance"]),
+    ("brownian_oracle", "wave sample on the sheared lattice with the offset sign flipped",
+     "m[:, 1] -= (tilt / L) * m[:, 0]", "m[:, 1] += (tilt / L) * m[:, 0]", ["wave_covariance_tilt"]),
+    ("brownian_oracle", "conjugate mirror of the kx = 0 plane dropped",
+     "xi[:, kz, ky, kx] = np.conj(v) if conj else v", "xi[:, kz, ky, kx] = v", ["field_layout"]),
+    ("brownian_oracle", "Nyquist plane of the random field kept",
+     "xi[:, :, :, n // 2] = 0", "xi[:, :, :, n // 2] *= 1", ["field_layout"]),
+    ("brownian_oracle", "Brownian amplitude sqrt(kT/dt) instead of sqrt(2 kT/dt)",
+     "s = np.sqrt(2.0 * kT / dt)", "s = np.sqrt(kT / dt)", ["fd_amplitude"]),
+    ("brownian_oracle", "near-field Brownian force added with the wrong sign",
+     'b[11 * N:] -= sys_["ST"].T', 'b[11 * N:] += sys_["ST"].T', ["nf_noise_as_force"]),
+    ("brownian_oracle", "preconditioned square root with the transposed factor",
+     "return Lm @ sqrtm_apply(G @ R @ G.T, v)", "return Lm.T @ sqrtm_apply(G @ R @ G.T, v)",
+     ["precond_sqrt_covariance"]),
+    ("brownian_oracle", "pair noise scattered to bead j with the wrong sign",
+     "out[j] += v[6:]", "out[j] -= v[6:]", ["pairwise_covariance"]),
+    ("brownian_oracle", "pair counter on another generator stream",
+     "(i & M32, (5 << 8) | call, j & M32, step & M32)", "(i & M32, (4 << 8) | call, j & M32, step & M32)",
+     ["pair_layout"]),
+    ("drift_oracle", "random displacement rotated by twice the angle",
+     "0.5 * h * v[:, 3:6]", "h * v[:, 3:6]", ["rigid_displacement"]),
+    ("drift_oracle", "RFD with the full step on each side",
+     "p = displaced(pos, body, L, dq, 0.5 * s * eps, tilt)", "p = displaced(pos, body, L, dq, s * eps, tilt)",
+     ["rfd_divergence"]),
+    ("drift_oracle", "modified Fixman factor m instead of m/2",
+     '0.5 * m * (o1["U"] - o0["U"])', 'm * (o1["U"] - o0["U"])', ["fixman_derivative"]),
+    ("drift_oracle", "modified Fixman stresslet sign",
+     '-0.5 * m * (o1["SH"] - o0["SH"])', '0.5 * m * (o1["SH"] - o0["SH"])', ["fixman_derivative"]),
+    ("contact_oracle", "Hertz exponent 1 instead of 3/2",
+     "f = kn * delta ** 1.5 * d / dist", "f = kn * delta ** 1.0 * d / dist", ["hertz_closed_form"]),
+    ("contact_oracle", "Hertz exponent 1 in the combined force routine",
+     "f += kn * (2.0 * a - dist) ** 1.5", "f += kn * (2.0 * a - dist) ** 1.0", ["hertz_in_pair_forces"]),
+    ("contact_oracle", "sign of the van der Waals logarithm",
+     "+ np.log((rv * rv - s2) / (rv * rv)))", "- np.log((rv * rv - s2) / (rv * rv)))",
+     ["dlvo_minus_gradient", "vdw_far_field"]),
+    ("contact_oracle", "van der Waals prefactor A/3 instead of A/6",
+     "vdw = -A_H / 6.0 * (2.0 * a * a / (rv * rv - s2)", "vdw = -A_H / 3.0 * (2.0 * a * a / (rv * rv - s2)",
+     ["vdw_far_field"]),
+    ("contact_oracle", "double layer screened twice as fast",
+     "el = a * a / r * Z * np.exp(-kappa * (r - 2.0 * a))",
+     "el = a * a / r * Z * np.exp(-2 * kappa * (r - 2.0 * a))", ["double_layer"]),
+    ("contact_oracle", "power of one van der Waals force term",
+     "d2 = -2.0 * a * a * 2.0 / rv ** 3", "d2 = -2.0 * a * a * 2.0 / rv ** 2", ["dlvo_minus_gradient"]),
+    ("contact_oracle", "sign of the double-layer force's screening term",
+     "del_ = a * a * Z * e * (-1.0 / (r * r) - kappa / r)", "del_ = a * a * Z * e * (-1.0 / (r * r) + kappa / r)",
+     ["dlvo_minus_gradient"]),
+    ("contact_oracle", "van der Waals attraction not capped under overlap",
+     "rv = max(r, 2.0 * a) + h_c", "rv = r + h_c", ["vdw_capped"]),
+    ("contact_oracle", "Newton's third law broken for bead j",
+     "fb[j] -= f * d / dist", "fb[j] += f * d / dist", ["newton_cutoff_intrabody"]),
+    ("contact_oracle", "aggregate torque as F x r",
+     "fb[j] -= f * d / dist\n    nb = int(body.max()) + 1\n    out = np.zeros((nb, 6))\n    for b in range(Nt):\n"
+     "        out[body[b], :3] += fb[b]\n        out[body[b], 3:] += np.cross(r[b], fb[b])",
+     "fb[j] -= f * d / dist\n    nb = int(body.max()) + 1\n    out = np.zeros((nb, 6))\n    for b in range(Nt):\n"
+     "        out[body[b], :3] += fb[b]\n        out[body[b], 3:] += np.cross(fb[b], r[b])",
+     ["newton_cutoff_intrabody"]),
+]
 
 
-def _mutant(old, new):
-    with open(SRC) as f:
+def _mutant(module, old, new):
+    src = os.path.join(ROOT, "oracle", module + ".py")
+    with open(src) as f:
         text = f.read()
-    assert text.count(old) == 1, "planted text no longer occurs exactly once in the oracle"
-    mod = types.ModuleType("fsd_oracle_mutant")
-    mod.__file__ = SRC
-    exec(compile(text.replace(old, new), SRC + " (mutant)", "exec"), mod.__dict__)
+    assert text.count(old) == 1, "planted text no longer occurs exactly once in " + module
+    mod = types.ModuleType("oracle." + module + "_mutant")
+    mod.__file__ = src
+    mod.__package__ = "oracle"  # its relative imports resolve to the real oracle modules
+    exec(compile(text.replace(old, new), src + " (mutant)", "exec"), mod.__dict__)
     return mod
 
 
-@pytest.mark.parametrize("case,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_fails_a_pin(case, old, new, pins, monkeypatch):
-    mod = _mutant(old, new)
+@pytest.mark.parametrize("module,case,old,new,pins", CASES, ids=[c[1] for c in CASES])
+def test_planted_mistake_fails_a_pin(module, case, old, new, pins, monkeypatch):
+    mod = _mutant(module, old, new)
     failed = []
     for name in pins:
         tmod, fn, kw = PINS[name]
-        monkeypatch.setattr(tmod, "O", mod)
+        monkeypatch.setattr(tmod, HANDLE[module], mod)
         try:
             getattr(tmod, fn)(**kw)
         except AssertionError:
