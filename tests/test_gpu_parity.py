@@ -110,6 +110,24 @@ def test_saddle_operator_matches_oracle(sysA):
     assert rel(s.apply_saddle(x, MIXED), ref) < 2e-5
 
 
+def test_fp32_operator_and_mixed_solve_repeat_bit_for_bit(sysA, pkg):
+    # every reduction of the FP32 operator and of the Krylov passes has a
+    # fixed order, so repeating a call on the same inputs repeats its bits
+    s = sysA["s"]
+    x = np.random.default_rng(18).normal(size=sysA["sys"]["A"].shape[0])
+    y1 = s.apply_saddle(x, MIXED)
+    y2 = s.apply_saddle(x, MIXED)
+    assert np.array_equal(y1, y2)
+    ft = synth.random_forces(sysA["sys"]["nb"], 3)
+    m = pkg.Suspension(sysA["pos"], sysA["body"], sysA["L"], precision=MIXED,
+                       flags=pkg.FSD_FLAG_GRAPH, **HI)
+    v1, S1, st1, _ = m.solve(ft, 1.0)
+    v2, S2, st2, _ = m.solve(ft, 1.0)
+    m.close()
+    assert st1["iters"] == st2["iters"]
+    assert np.array_equal(v1, v2) and np.array_equal(S1, S2)
+
+
 def test_lubrication_operator_matches_oracle(sysA):
     s, sd = sysA["s"], sysA["sys"]
     rng = np.random.default_rng(9)
