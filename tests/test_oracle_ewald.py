@@ -14,7 +14,8 @@ def test_mobility_independent_of_splitting():
     rng = np.random.default_rng(11)
     L = 12.0
     pos = np.array([[1.0, 1.0, 1.0], [3.05, 1.2, 0.8], [7.0, 6.0, 9.0], [10.5, 2.0, 5.0]])
-    Ms = [O.mobility_dense(pos, L, xi=x) for x in (0.55, 0.8, 1.3)]
+    # None: the oracle's own splitting and cut-offs (oracle_split)
+    Ms = [O.mobility_dense(pos, L, xi=x) for x in (None, 0.55, 0.8, 1.3)]
     scale = np.abs(Ms[0]).max()
     for M in Ms[1:]:
         assert np.abs(M - Ms[0]).max() / scale < 1e-11

@@ -52,6 +52,19 @@ PINS = {
     "le_split": (TL, "test_split_independence_with_tilt", {}),
     "le_lattice": (TL, "test_lattice_translation_and_spd", {}),
     "le_solve": (TL, "test_solve_with_tilt_translation_invariant", {}),
+    "lub_lowers_mobility": (TS, "test_lubrication_lowers_the_body_mobility", {}),
+    "precond_within_rp": (TS, "test_preconditioner_counts_only_pairs_within_rp", {}),
+    "force_balance": (TS, "test_bead_forces_balance_each_body", {}),
+    "comoving_update": (TS, "test_comoving_update_leaves_affine_motion_in_place", {}),
+    "sampled_real_rows": (TS, "test_sampled_real_rows_equal_dense_rows", {}),
+    "sampled_lub_rows": (TS, "test_sampled_lubrication_rows_equal_dense", {}),
+    "lub_pair_psd": (TS, "test_lubrication_pair_symmetric_psd_and_rigid_invariant", {"gap": 0.05}),
+    "rotation_blocks": (TT, "test_rotlet_and_rotation_blocks_are_textbook", {"r": 3.3}),
+    "faxen_MM": (TT, "test_free_phi_closed_form_matches_kspace_quadrature", {"kind": "MM"}),
+    "overlap_clamp": (TT, "test_overlapping_pairs_take_the_contact_blocks", {}),
+    "split_independence": (TE, "test_mobility_independent_of_splitting", {}),
+    "applied_wave_sum": (TE, "test_applied_wave_sum_equals_dense_wave_matrix", {}),
+    "pair_factor": (TB, "test_pairwise_near_field_sampler_has_covariance_R", {}),
     "philox_known_answers": (TB, "test_philox_known_answers", {}),
     "box_muller_moments": (TB, "test_box_muller_moments", {}),
     "wave_covariance": (TB, "test_wave_sample_covariance_is_the_wave_mobility", {}),
@@ -141,6 +154,77 @@ MUTATIONS = [
      "R[..., 0, 1] = 2 * (x * y - w * z)", "R[..., 0, 1] = 2 * (x * y + w * z)", ["rigid_update"]),
     ("preconditioner scalar zeta0 -> 1/zeta0",
      "Mid[:n1, :n1] = z0 * np.eye(n1)", "Mid[:n1, :n1] = np.eye(n1) / z0", ["precond_exact"]),
+    ("near-field block of the saddle matrix with the wrong sign",
+     "A[n1:, n1:] = -RRFU", "A[n1:, n1:] = RRFU", ["lub_lowers_mobility"]),
+    ("constraint rows of the saddle matrix negated",
+     "A[n1:, :n1] = BST.T", "A[n1:, :n1] = -BST.T", ["precond_exact"]),
+    ("preconditioner's upper factor sign",
+     "Upper[:n1, n1:] = -z0 * BST", "Upper[:n1, n1:] = z0 * BST", ["precond_exact"]),
+    ("preconditioner's lower factor sign",
+     "Lower[n1:, :n1] = -z0 * BST.T", "Lower[n1:, :n1] = z0 * BST.T", ["precond_exact"]),
+    ("preconditioner's Schur blocks without their minus sign",
+     "Sinv[6 * J:6 * J + 6, 6 * J:6 * J + 6] = -np.linalg.inv(blk)",
+     "Sinv[6 * J:6 * J + 6, 6 * J:6 * J + 6] = np.linalg.inv(blk)", ["precond_exact"]),
+    ("preconditioner pairs up to the lubrication cut-off instead of r_p",
+     "if np.linalg.norm(d) >= min(rpair, rlub):", "if np.linalg.norm(d) >= max(rpair, rlub):",
+     ["precond_within_rp"]),
+    ("near-field force taken at u - u_inf + 2 E.r",
+     'dv = sys_["ST"] @ sol[n1:] - sys_["Er"]', 'dv = sys_["ST"] @ sol[n1:] + sys_["Er"]',
+     ["force_balance"]),
+    ("near-field force sign in the outputs",
+     'Fnf = -(sys_["RFU"] @ dv) + sys_["RFE"] @ sys_["Erep"]',
+     'Fnf = (sys_["RFU"] @ dv) + sys_["RFE"] @ sys_["Erep"]', ["force_balance"]),
+    ("imposed rotation added with the wrong sign to Omega",
+     'U[:, 3:6] += sys_["Om"]', 'U[:, 3:6] -= sys_["Om"]', ["sphere_in_shear"]),
+    ("velocity gradient instead of the rate of strain",
+     "E[0, 1] = E[1, 0] = 0.5 * gamma", "E[0, 1] = gamma", ["doublet_in_shear"]),
+    ("z component left out of the minimum image",
+     "d[..., 2] -= L * np.round(d[..., 2] / L)", "d[..., 2] -= 0.0 * np.round(d[..., 2] / L)",
+     ["sampled_lub_rows"]),
+    ("co-moving update with the imposed rotation's sign flipped",
+     "Ut[:, 5] += 0.5 * comoving_gamma", "Ut[:, 5] -= 0.5 * comoving_gamma", ["comoving_update"]),
+    ("co-moving update with the imposed velocity read from x",
+     "Ut[:, 0] -= comoving_gamma * X[:, 1]", "Ut[:, 0] -= comoving_gamma * X[:, 0]", ["comoving_update"]),
+    ("strain basis element (2zz - xx - yy)/sqrt6 with zz halved",
+     "E[1, 0, 0], E[1, 1, 1], E[1, 2, 2] = -1 / s6, -1 / s6, 2 / s6",
+     "E[1, 0, 0], E[1, 1, 1], E[1, 2, 2] = -1 / s6, -1 / s6, 1 / s6", ["affine_strain"]),
+    ("strain basis element sqrt2 xy normalised to 1/2",
+     "E[2, 0, 1] = E[2, 1, 0] = 1 / s2", "E[2, 0, 1] = E[2, 1, 0] = 1 / 2", ["sphere_in_shear"]),
+    ("one delta-delta term of the fourth derivative dropped",
+     '+ np.einsum("ad,bc->abcd", d, d))', ")", ["rotation_blocks"]),
+    ("sign of the Bessel series recursion",
+     "term = term * (-(zs * zs) / 2.0) / (k * (2 * n + 2 * k + 1))",
+     "term = term * ((zs * zs) / 2.0) / (k * (2 * n + 2 * k + 1))", ["faxen_MM"]),
+    ("wave-part quadrature truncated early",
+     "K = 2.0 * xi * np.sqrt(46.0)", "K = 2.0 * xi * np.sqrt(8.0)", ["hasimoto_coefficient"]),
+    ("strain self mobility 1/(20 pi) instead of 3/(20 pi)",
+     "3.0 / (20 * PI * eta * a ** 3)", "1.0 / (20 * PI * eta * a ** 3)", ["sphere_in_shear"]),
+    ("real-space self term without the wave part removed",
+     "selfb = self_block(a, eta) - w0\n    for i in range(N):", "selfb = self_block(a, eta)\n    for i in range(N):",
+     ["sphere_in_shear"]),
+    ("rotlet block factor 1/2 dropped",
+     "M[:, 0:3, 3:6] = 0.5 * np.einsum", "M[:, 0:3, 3:6] = 1.0 * np.einsum", ["symmetry"]),
+    ("relative rotation of the pair with bead j's sign flipped",
+     "Lt[:, 14:17] = I3", "Lt[:, 14:17] = -I3", ["lub_pair_psd"]),
+    ("lever of bead i's rotation in the surface velocity negated",
+     "Ls[:, 3:6] = -0.5 * r * nx      # (r/2) n x dw_i with dw_i = -nu",
+     "Ls[:, 3:6] = 0.5 * r * nx      # (r/2) n x dw_i with dw_i = -nu", ["lub_pair_psd"]),
+    ("pair factor with bead j's rotation lever negated",
+     "Ls[:, 9:12] = -0.5 * r * nx\n    Lt = np.zeros((3, 12))", "Ls[:, 9:12] = 0.5 * r * nx\n    Lt = np.zeros((3, 12))",
+     ["pair_factor"]),
+    ("free-space blocks of overlapping pairs not clamped to 2a",
+     "reff = np.maximum(r, 2.0 * a)", "reff = r", ["overlap_clamp"]),
+    ("oracle's own real-space cut-off too short",
+     "rc = 2.0 + np.sqrt(46.0) / xi\n    kmax = 2.0 * xi * np.sqrt(46.0)\n    return",
+     "rc = 2.0 + np.sqrt(9.0) / xi\n    kmax = 2.0 * xi * np.sqrt(46.0)\n    return", ["split_independence"]),
+    ("matrix-free wave sum without the projection I - kk",
+     'g = g - kh * np.einsum("pa,pa->p", kh, g)[:, None]  # (I - kk) g', "g = g  # (I - kk) g",
+     ["applied_wave_sum"]),
+    ("sampled real-space rows without the self term",
+     "        out[k] += selfb @ F[i]\n", "        out[k] += 0.0 * selfb @ F[i]\n", ["sampled_real_rows"]),
+    ("sampled lubrication rows with the torque lever negated",
+     "out[k, 3:6] += f[3:6] + np.cross(r[b], f[0:3])", "out[k, 3:6] += f[3:6] - np.cross(r[b], f[0:3])",
+     ["sampled_lub_rows"]),
 ]
 CASES = [("fsd_oracle",) + m for m in MUTATIONS]
 

@@ -185,6 +185,32 @@ def test_lubrication_coefficients_follow_equal_sphere_asymptotics():
     assert abs((B1 - B2) / ln - g2t) < 1e-3
 
 
+def test_lubrication_lowers_the_body_mobility():
+    # near-field resistance can only lower the mobility: the body mobility N
+    # (disturbance velocities per unit applied force and torque, Eq. FH_agg)
+    # stays symmetric positive definite, and N without lubrication minus N
+    # with it is positive semi-definite, and nonzero when pairs are near
+    rng = np.random.default_rng(21)
+    shapes = [synth.random_attachment_aggregate(k, rng) for k in (2, 3, 2)]
+    L = synth.box_for_phi(7, 0.2)
+    pos, body = synth.pack_suspension(shapes, L, rng, h_gen=0.05)
+    M = O.mobility_dense(pos, L)
+    nb = 3
+
+    def N(rlub):
+        return np.column_stack([O.solve(pos, body, L, gamma=0.0, FT=np.eye(6 * nb)[j].reshape(nb, 6),
+                                        rlub=rlub, M=M)["U"].reshape(-1) for j in range(6 * nb)])
+
+    N0, N1 = N(0.0), N(3.0)
+    scale = np.abs(N0).max()
+    for Nm in (N0, N1):
+        assert np.abs(Nm - Nm.T).max() < 1e-10 * scale
+        assert np.linalg.eigvalsh(0.5 * (Nm + Nm.T)).min() > 0
+    w = np.linalg.eigvalsh(0.5 * ((N0 - N1) + (N0 - N1).T))
+    assert w.min() > -1e-10 * scale
+    assert w.max() > 1e-6 * scale
+
+
 def test_lubrication_cutoff_and_intrabody():
     xi, xj = _two_body_pair(1.0 - 1e-12, 3)
     assert np.abs(O.lub_pair_matrix(xi, xj)).max() < 1e-9
@@ -221,6 +247,27 @@ def test_preconditioner_exact_for_scalar_mobility_without_lubrication():
     assert np.abs(P @ sys_["A"] - np.eye(sys_["A"].shape[0])).max() < 1e-10
 
 
+def test_preconditioner_counts_only_pairs_within_rp():
+    # R~ of Table 1 holds the pairs closer than r_p (2.1a) only: moving a pair
+    # that lies between r_p and the lubrication cut-off leaves P^-1 as it is,
+    # moving a pair inside r_p changes it
+    L = 30.0
+    base = np.array([[5.0, 5, 5], [7.05, 5, 5], [5.0, 12, 5], [7.4, 12, 5]])
+    body = np.array([0, 1, 2, 3])
+
+    def P(pos):
+        sys_ = O.assemble(pos, body, L, rlub=3.0, M=np.eye(11 * 4))
+        return O.preconditioner_dense(sys_, sys_["unw"], body, L, rp=2.1, rlub=3.0)
+
+    P0 = P(base)
+    far = base.copy()
+    far[3, 0] = 7.6  # pair (2, 3): 2.4a -> 2.6a, beyond r_p
+    near = base.copy()
+    near[1, 0] = 7.08  # pair (0, 1): 2.05a -> 2.08a, inside r_p
+    assert np.abs(P(far) - P0).max() <= 1e-14 * np.abs(P0).max()
+    assert np.abs(P(near) - P0).max() > 1e-6 * np.abs(P0).max()
+
+
 def test_preconditioner_diagonal_blocks_match_per_body_solve():
     pos, body, L = synth.suspension(10, 3, 0.15, 9)
     sys_ = O.assemble(pos, body, L, rlub=3.0, M=np.eye(11 * len(pos)))
@@ -236,6 +283,54 @@ def test_preconditioner_diagonal_blocks_match_per_body_solve():
 
 
 # --------------------------------------------------------------- integrator
+
+
+def test_bead_forces_balance_each_body():
+    # a force-free, inertia-less aggregate carries no net load (Eq. FH_agg):
+    # the far-field forces of its beads (the solution's F) and their
+    # near-field forces (F^nf of the outputs), with torques about X, balance
+    # the applied force and torque F^P
+    pos, body, L = synth.suspension(6, 3, 0.2, 8)
+    FT = synth.random_forces(6, 9)
+    out = O.solve(pos, body, L, gamma=1.0, FT=FT, rlub=3.0)
+    assert np.abs(out["Fnf"]).max() > 0
+    r = out["system"]["r"]
+    tot = np.zeros((6, 6))
+    for b in range(len(pos)):
+        J = body[b]
+        f = out["F"][b, 0:3] + out["Fnf"][b, 0:3]
+        tot[J, 0:3] += f
+        tot[J, 3:6] += out["F"][b, 3:6] + out["Fnf"][b, 3:6] + np.cross(r[b], f)
+    assert np.abs(tot + FT).max() < 1e-9 * np.abs(FT).max()
+
+
+def test_solve_is_invariant_under_translation():
+    # the periodic problem has no preferred origin: translating every bead
+    # (and wrapping it into the box) leaves the disturbance velocities and
+    # the stresslets unchanged; the shift puts aggregates and lubrication
+    # pairs across every face of the box
+    pos, body, L = synth.suspension(8, 4, 0.2, 12)
+    FT = synth.random_forces(8, 13)
+    a = O.solve(pos, body, L, gamma=0.8, FT=FT, rlub=3.0)
+    moved = np.mod(pos + np.array([0.31, 0.47, 0.59]) * L, L)
+    b = O.solve(moved, body, L, gamma=0.8, FT=FT, rlub=3.0)
+    assert np.allclose(b["dU"], a["dU"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(b["S"], a["S"], rtol=1e-9, atol=1e-12)
+
+
+def test_comoving_update_leaves_affine_motion_in_place():
+    # in the co-moving frame only the disturbance motion moves a body: one
+    # translating with the imposed flow at its centre, U_inf(X) = gamma X_y x,
+    # and turning with Omega_inf = -gamma/2 z, stays where it is
+    pos, body, L = synth.suspension(3, 4, 0.05, 2)
+    unw, X, r = O.body_geometry(pos, body, L)
+    q = np.tile([1.0, 0, 0, 0], (3, 1))
+    g = 0.7
+    U = np.zeros((3, 6))
+    U[:, 0] = g * X[:, 1]
+    U[:, 5] = -0.5 * g
+    X2, q2, _ = O.integrate(X, q, r, body, U, 0.1, comoving_gamma=g)
+    assert np.allclose(X2, X, rtol=0, atol=1e-14) and np.allclose(q2, q, rtol=0, atol=1e-14)
 
 
 def test_integrator_keeps_bodies_rigid_and_quaternions_unit():

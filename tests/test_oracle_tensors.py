@@ -103,6 +103,15 @@ def test_wave_plus_real_equals_free_at_distance():
     assert np.allclose(W, F, atol=1e-10)
 
 
+def test_overlapping_pairs_take_the_contact_blocks():
+    # reading for overlaps: a free-space pair closer than 2a is evaluated at
+    # separation 2a along its own direction
+    n = np.array([0.36, -0.48, 0.8])
+    blk = O.free_blocks(np.array([1.7 * n, 1.2 * n, 2.0 * n]))
+    assert np.abs(blk[0] - blk[2]).max() < 1e-14 * np.abs(blk[2]).max()
+    assert np.abs(blk[1] - blk[2]).max() < 1e-14 * np.abs(blk[2]).max()
+
+
 def test_jn_series_matches_scipy():
     from scipy.special import spherical_jn
     z = np.linspace(0.5, 1.99, 50)
