@@ -389,9 +389,18 @@ void fsd_destroy_batch(fsd_batch *b);
  * strain) and -Sigma F^B to the body rows of Eq. spm_agg, then forgets them.
  * The Brownian drift and stresslet are not included.
  * Random inputs (host or device; NULL: drawn from Philox4x32-10 with key
- * `seed` and counter (index, stream * 256 + call, step): stream 1 the wave
- * field at the canonical point of each Hermitian pair, stream 2 psi_real,
- * stream 3 psi_nf, index = bead position in the setup arrays):
+ * (seed mod 2^32, seed / 2^32) and counter (index, stream * 256 + call,
+ * step mod 2^32, step / 2^32); each call gives four normals by Box-Muller,
+ * from the word pairs (0, 1) and (2, 3) with u = (word + 1) 2^-32:
+ * sqrt(-2 ln u0) (cos, sin)(2 pi u1), then the same of u2, u3.  Stream 2:
+ * psi_real of a bead, the first 11 normals of calls 0-2; stream 3: psi_nf,
+ * the first 6 of calls 0-1; index = bead position in the setup arrays.
+ * Stream 1: the wave field, drawn at the canonical point (kz, ky, kx) of
+ * each Hermitian pair (the point itself when kx > 0; for kx = 0 the one of
+ * (kz, ky) and ((n - kz) mod n, (n - ky) mod n) that comes first in (kz, ky)
+ * order, the other holding its conjugate), index (kz n + ky)(n/2 + 1) + kx,
+ * the six normals of calls 0-1 giving components 0, 1, 2 as
+ * (normal 2c + i normal 2c+1) / sqrt 2):
  *   wave_field [3][n][n][n/2+1] complex (re, im) doubles, layout [c][kz][ky][kx]
  *     (k = 2 pi m / L, m_i = index, or index - n past n/2): standard complex
  *     Gaussians, Hermitian in the kx = 0 plane; Nyquist points and k = 0 are

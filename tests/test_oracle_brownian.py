@@ -37,6 +37,36 @@ def test_philox_known_answers():
                            (0xA4093822, 0x299F31D0)) == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
 
 
+def test_generators_follow_the_documented_counter_layout():
+    # the library's documented layout for its own draws: key (seed mod 2^32,
+    # seed / 2^32), counter (index, stream * 256 + call, step mod 2^32,
+    # step / 2^32), four Box-Muller normals per call; a bead's psi takes the
+    # first `width` normals of its calls, a wave-field point the six normals
+    # of its canonical index (kz n + ky)(n/2 + 1) + kx, the mirror of a kx = 0
+    # point their conjugate
+    seed, step = 0x123456789ABC, (7 << 32) + 5
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+
+    def normals(index, stream, call):
+        ctr = (index, stream * 256 + call, step & 0xFFFFFFFF, step >> 32)
+        return B.box_muller4(B.philox4x32_10(ctr, key))
+
+    psi = B.philox_psi(3, seed, step, 2, 11)
+    for b in range(3):
+        z = normals(b, 2, 0) + normals(b, 2, 1) + normals(b, 2, 2)
+        assert np.array_equal(psi[b], np.array(z[:11]))
+    n = 6
+    nh = n // 2 + 1
+    f = B.philox_wave_field(n, seed, step)
+    for kz, ky, kx in [(1, 2, 1), (4, 5, 2), (2, 1, 0)]:
+        idx = (kz * n + ky) * nh + kx
+        z = normals(idx, 1, 0) + normals(idx, 1, 1)
+        v = np.array([z[0] + 1j * z[1], z[2] + 1j * z[3], z[4] + 1j * z[5]]) / np.sqrt(2.0)
+        assert np.abs(f[:, kz, ky, kx] - v).max() < 1e-15
+    # (2, 1, 0) comes before its mirror (4, 5, 0), which holds the conjugate
+    assert np.abs(f[:, 4, 5, 0] - np.conj(f[:, 2, 1, 0])).max() == 0.0
+
+
 def test_box_muller_moments():
     z = np.array([B._normals(7, 3, 2, i, 1) for i in range(20000)]).reshape(-1, 4)
     assert abs(z.mean()) < 0.02

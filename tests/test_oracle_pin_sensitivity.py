@@ -75,6 +75,7 @@ PINS = {
     "precond_sqrt_covariance": (TB, "test_preconditioned_square_root_has_covariance_R", {}),
     "pairwise_covariance": (TB, "test_pairwise_near_field_sampler_has_covariance_R", {}),
     "pair_layout": (TB, "test_pair_normals_layout", {}),
+    "generator_layout": (TB, "test_generators_follow_the_documented_counter_layout", {}),
     "rigid_displacement": (TD, "test_displacement_is_rigid_and_first_order_right", {"doublets": DOUBLETS}),
     "rfd_divergence": (TD, "test_rfd_basis_sum_is_the_mobility_divergence", {"doublets": DOUBLETS}),
     "fixman_derivative": (TD, "test_fixman_large_m_is_the_directional_derivative", {"doublets": DOUBLETS}),
@@ -285,6 +286,27 @@ CASES += [
      "rv = max(r, 2.0 * a) + h_c", "rv = r + h_c", ["vdw_capped"]),
     ("contact_oracle", "Newton's third law broken for bead j",
      "fb[j] -= f * d / dist", "fb[j] += f * d / dist", ["newton_cutoff_intrabody"]),
+    ("brownian_oracle", "slip added to the bead rows with the wrong sign",
+     "b[:11 * N] += np.asarray(uB).reshape(-1)", "b[:11 * N] -= np.asarray(uB).reshape(-1)",
+     ["fixman_derivative"]),
+    ("brownian_oracle", "the two words of the step swapped in the counter",
+     "ctr = (index & M32, (stream << 8) | call, step & M32, (step >> 32) & M32)",
+     "ctr = (index & M32, (stream << 8) | call, (step >> 32) & M32, step & M32)", ["generator_layout"]),
+    ("brownian_oracle", "a bead's noise from the last normals of its calls",
+     "_normals(seed, step, stream, b, calls)[:width]", "_normals(seed, step, stream, b, calls)[-width:]",
+     ["generator_layout"]),
+    ("brownian_oracle", "wave-field draw index with kz and ky transposed",
+     "(cz * n + cy) * nh + kx, 2)", "(cy * n + cz) * nh + kx, 2)", ["generator_layout"]),
+    ("brownian_oracle", "real-space square root on a cut-off too short",
+     "    rc = 2.0 + np.sqrt(46.0) / xi\n    Mr", "    rc = 2.0 + np.sqrt(9.0) / xi\n    Mr", ["fd_amplitude"]),
+    ("drift_oracle", "random displacement translated backwards",
+     "Xn = X + h * v[:, 0:3]", "Xn = X - h * v[:, 0:3]", ["rigid_displacement"]),
+    ("contact_oracle", "Hertz force pointing from i to j (attraction)",
+     "            d = F.min_image(unw[i] - unw[j], L, tilt)\n            dist = np.linalg.norm(d)\n            delta",
+     "            d = F.min_image(unw[j] - unw[i], L, tilt)\n            dist = np.linalg.norm(d)\n            delta",
+     ["hertz_closed_form"]),
+    ("contact_oracle", "DLVO forces beyond their cut-off",
+     "if dist < r_cut and (A_H", "if dist < 2 * r_cut and (A_H", ["newton_cutoff_intrabody"]),
     ("contact_oracle", "aggregate torque as F x r",
      "fb[j] -= f * d / dist\n    nb = int(body.max()) + 1\n    out = np.zeros((nb, 6))\n    for b in range(Nt):\n"
      "        out[body[b], :3] += fb[b]\n        out[body[b], 3:] += np.cross(r[b], fb[b])",
