@@ -16,7 +16,9 @@ it stands in for are not of the pair model's form."""
 
 import os
 import types
+import warnings
 
+import numpy as np
 import pytest
 
 import synth
@@ -65,6 +67,8 @@ PINS = {
     "split_independence": (TE, "test_mobility_independent_of_splitting", {}),
     "applied_wave_sum": (TE, "test_applied_wave_sum_equals_dense_wave_matrix", {}),
     "pair_factor": (TB, "test_pairwise_near_field_sampler_has_covariance_R", {}),
+    "wave_point_limit": (TT, "test_wave_self_block_closed_form_in_the_point_limit", {}),
+    "assembled_strain": (TS, "test_assembled_strain_blocks_equal_affine_bead_motion", {}),
     "philox_known_answers": (TB, "test_philox_known_answers", {}),
     "box_muller_moments": (TB, "test_box_muller_moments", {}),
     "wave_covariance": (TB, "test_wave_sample_covariance_is_the_wave_mobility", {}),
@@ -223,6 +227,44 @@ MUTATIONS = [
      ["applied_wave_sum"]),
     ("sampled real-space rows without the self term",
      "        out[k] += selfb @ F[i]\n", "        out[k] += 0.0 * selfb @ F[i]\n", ["sampled_real_rows"]),
+    ("odd permutations of the Levi-Civita symbol positive",
+     "e[0, 2, 1] = e[2, 1, 0] = e[1, 0, 2] = -1.0", "e[0, 2, 1] = e[2, 1, 0] = e[1, 0, 2] = 1.0", ["symmetry"]),
+    ("radial derivative (1/r d/dr) r^p with the factor p - 1",
+     "return {p - 2: p * c for p, c in poly.items() if p != 0 and c != 0.0}",
+     "return {p - 2: (p - 1) * c for p, c in poly.items() if p != 0 and c != 0.0}", ["rpy"]),
+    ("sign of the wave part's radial integrals",
+     "out[:, n - 1] = (-1.0) ** (n + 1) / (2 * PI * PI * eta) * (integrand @ w)",
+     "out[:, n - 1] = (-1.0) ** n / (2 * PI * PI * eta) * (integrand @ w)", ["wave_point_limit"]),
+    ("wave part's radial integrals over 2 pi instead of 2 pi^2",
+     "out[:, n - 1] = (-1.0) ** (n + 1) / (2 * PI * PI * eta) * (integrand @ w)",
+     "out[:, n - 1] = (-1.0) ** (n + 1) / (2 * PI * eta) * (integrand @ w)", ["wave_point_limit"]),
+    ("Hasimoto exponent k^2/(2 xi^2) (a consistent change of the splitting)",
+     "x = k * k / (4.0 * xi * xi)", "x = k * k / (2.0 * xi * xi)", ["wave_point_limit"]),
+    ("monopole and dipole form factors swapped in wave space",
+     'fM = form_factor("M", kn * a)\n    fD = form_factor("D", kn * a)',
+     'fM = form_factor("D", kn * a)\n    fD = form_factor("M", kn * a)', ["split_independence"]),
+    ("dipole form factor j1(z)/z without its 3",
+     "return 3.0 * jn_over_zn(1, z)", "return jn_over_zn(1, z)", ["faxen_DD"]),
+    ("lever block of Sigma^T transposed",
+     '= -np.einsum("abc,b->ac", EPS, r[b])', '= -np.einsum("abc,b->ca", EPS, r[b])', ["force_balance"]),
+    ("strain rows picked one place early from the grand resistance",
+     "e = np.concatenate([np.arange(11 * b + 6, 11 * b + 11) for b in range(Nt)])",
+     "e = np.concatenate([np.arange(11 * b + 5, 11 * b + 10) for b in range(Nt)])", ["assembled_strain"]),
+    ("squeeze and sliding coefficients exchanged in the pair matrix",
+     'G = A * nn + B * (I3 - nn)\n    Gt = D * (I3 - nn)\n    nx = np.einsum("abc,b->ac", EPS, n)  # n x v = [n]x v',
+     'G = B * nn + A * (I3 - nn)\n    Gt = D * (I3 - nn)\n    nx = np.einsum("abc,b->ac", EPS, n)  # n x v = [n]x v',
+     ["lub_pair_psd"]),
+    ("real-space image sum stored with the wrong transpose",
+     "M[i] += acc.transpose(1, 0, 2)", "M[i] += acc.transpose(2, 0, 1)", ["sampled_real_rows"]),
+    ("wave vectors with zero first component counted twice",
+     "n = n[first > 0]", "n = n[first >= 0]", ["hasimoto_coefficient"]),
+    ("sign of the imaginary terms of the wave sum",
+     "- (S * ai[:, None]).T @ C + (C * ai[:, None]).T @ S)", "+ (S * ai[:, None]).T @ C - (C * ai[:, None]).T @ S)",
+     ["applied_wave_sum"]),
+    ("body rows of the right-hand side with the wrong sign",
+     "b[n1:] = -(FP + RRFE_E)", "b[n1:] = (FP + RRFE_E)", ["force_balance"]),
+    ("squeeze coefficient not shifted to vanish at the cut-off",
+     "A = 6 * PI * eta * a * (sq(e) - sq(ec))", "A = 6 * PI * eta * a * sq(e)", ["intrabody"]),
     ("sampled lubrication rows with the torque lever negated",
      "out[k, 3:6] += f[3:6] + np.cross(r[b], f[0:3])", "out[k, 3:6] += f[3:6] - np.cross(r[b], f[0:3])",
      ["sampled_lub_rows"]),
@@ -336,7 +378,11 @@ def test_planted_mistake_fails_a_pin(module, case, old, new, pins, monkeypatch):
         tmod, fn, kw = PINS[name]
         monkeypatch.setattr(tmod, HANDLE[module], mod)
         try:
-            getattr(tmod, fn)(**kw)
+            # a mutant may divide by zero or take the log of a negative
+            # number on its way to failing a pin
+            with np.errstate(all="ignore"), warnings.catch_warnings():
+                warnings.simplefilter("ignore", RuntimeWarning)
+                getattr(tmod, fn)(**kw)
         except AssertionError:
             failed.append(name)
     assert failed, "no pin caught: " + case

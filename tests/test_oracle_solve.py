@@ -185,6 +185,32 @@ def test_lubrication_coefficients_follow_equal_sphere_asymptotics():
     assert abs((B1 - B2) / ln - g2t) < 1e-3
 
 
+def test_assembled_strain_blocks_equal_affine_bead_motion():
+    # the pair model sees only relative surface velocities, so on the whole
+    # suspension the strain response equals the response to every bead
+    # moving with -E.x_b (no pair crosses the box here, so x_j - x_i needs no
+    # image): R_FE e = R_FU (-E x, 0) and R_SE e = R_SU (-E x, 0), with the
+    # blocks taken from the grand resistance by split_grand
+    rng = np.random.default_rng(23)
+    shapes = [synth.random_attachment_aggregate(k, rng) for k in (3, 2, 4)]
+    L = 60.0
+    pos, body = synth.pack_suspension(shapes, 9.0, rng, h_gen=0.05)
+    pos = pos + 20.0  # a 9-box cluster in the middle of a 60-box
+    Nt = len(pos)
+    R = O.lubrication_dense(pos, body, L, rcut=3.0)
+    RFU, RFE, RSU, RSE = O.split_grand(R, Nt)
+    assert np.abs(RFE).max() > 0
+    E = rng.normal(size=(3, 3))
+    E = 0.5 * (E + E.T)
+    E -= np.trace(E) / 3.0 * np.eye(3)
+    e = np.tile(O.sym_to_vec5(E), Nt)
+    v = np.zeros((Nt, 6))
+    v[:, 0:3] = -(pos @ E.T)
+    v = v.reshape(-1)
+    assert np.abs(RFE @ e - RFU @ v).max() < 1e-10 * np.abs(RFU @ v).max()
+    assert np.abs(RSE @ e - RSU @ v).max() < 1e-10 * np.abs(RSU @ v).max()
+
+
 def test_lubrication_lowers_the_body_mobility():
     # near-field resistance can only lower the mobility: the body mobility N
     # (disturbance velocities per unit applied force and torque, Eq. FH_agg)

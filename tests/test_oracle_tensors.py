@@ -103,6 +103,17 @@ def test_wave_plus_real_equals_free_at_distance():
     assert np.allclose(W, F, atol=1e-10)
 
 
+def test_wave_self_block_closed_form_in_the_point_limit():
+    # the wave part's self block at r = 0 is (1/(3 pi^2 eta)) int_0^inf H f^2 dk I
+    # with H = (1 + k^2/(4 xi^2)) exp(-k^2/(4 xi^2)); for a point particle
+    # (f = 1) the two Gaussian integrals give xi sqrt(pi) + xi sqrt(pi)/2, so
+    # the block is xi / (2 pi^(3/2) eta) I.  Radius 1e-4 stands in for a point.
+    for xi in (0.4, 1.1):
+        W = O.wave_blocks_free(np.zeros((1, 3)), xi=xi, a=1e-4)[0]
+        ref = xi / (2.0 * np.pi ** 1.5)
+        assert np.abs(W[0:3, 0:3] - ref * np.eye(3)).max() < 1e-7 * ref
+
+
 def test_overlapping_pairs_take_the_contact_blocks():
     # reading for overlaps: a free-space pair closer than 2a is evaluated at
     # separation 2a along its own direction
