@@ -107,11 +107,13 @@ def test_van_der_waals_far_field_is_the_textbook_sphere_limit():
 
 
 def test_double_layer_screening_and_contact_value():
-    a, Z, kappa = 1.0, 4.0, 2.0
-    v0 = C.dlvo_potential(2.0 * a, a, 0.0, Z, kappa, 0.0)
-    assert abs(v0 - a * a / (2 * a) * Z) < 1e-14
-    v1 = C.dlvo_potential(2.0 * a + 1.0 / kappa, a, 0.0, Z, kappa, 0.0)
-    assert abs(v1 / v0 - (2 * a / (2 * a + 1.0 / kappa)) * np.exp(-1.0)) < 1e-14
+    # two radii, so that a and a^2 cannot stand in for each other
+    for a in (1.0, 1.7):
+        Z, kappa = 4.0, 2.0
+        v0 = C.dlvo_potential(2.0 * a, a, 0.0, Z, kappa, 0.0)
+        assert abs(v0 - a * a / (2 * a) * Z) < 1e-14 * max(1.0, abs(v0))
+        v1 = C.dlvo_potential(2.0 * a + 1.0 / kappa, a, 0.0, Z, kappa, 0.0)
+        assert abs(v1 / v0 - (2 * a / (2 * a + 1.0 / kappa)) * np.exp(-1.0)) < 1e-14
 
 
 def test_van_der_waals_attraction_capped_under_overlap_and_finite_at_contact():

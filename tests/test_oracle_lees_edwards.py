@@ -6,7 +6,8 @@ simple-shear run; lattice e1 = (L, 0, 0), e2 = (tilt, L, 0), e3 = (0, 0, L)):
 * the Ewald split stays exact: the mobility does not depend on xi;
 * moving a bead by the lattice vector e2 changes nothing;
 * the mobility stays symmetric and positive definite;
-* the saddle solve with a tilt is translation invariant under e2 too.
+* the saddle solve with a tilt is translation invariant under e2 too;
+* the minimum image returns a lattice-equivalent displacement inside the box.
 """
 
 import numpy as np
@@ -27,6 +28,24 @@ def beads(seed=3, n=4, L=12.0):
 
 def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
+
+
+def test_minimum_image_reduces_into_the_box():
+    # the reduced displacement differs from the input by a lattice vector
+    # n1 e1 + n2 e2 + n3 e3 (integer n) and lies within half a box along every
+    # axis (wrapped across y first, which moves it by the offset along x)
+    rng = np.random.default_rng(17)
+    L = 10.0
+    for tilt in (0.0, 0.37 * L, -0.49 * L):
+        d = rng.uniform(-1.6 * L, 1.6 * L, size=(400, 3))
+        m = O.min_image(d, L, tilt)
+        assert np.abs(m).max() <= 0.5 * L + 1e-12
+        t = d - m
+        n2 = t[:, 1] / L
+        n1 = (t[:, 0] - n2 * tilt) / L
+        n3 = t[:, 2] / L
+        for nk in (n1, n2, n3):
+            assert np.abs(nk - np.round(nk)).max() < 1e-9
 
 
 def test_tilt_is_defined_modulo_L():

@@ -54,6 +54,7 @@ PINS = {
     "le_split": (TL, "test_split_independence_with_tilt", {}),
     "le_lattice": (TL, "test_lattice_translation_and_spd", {}),
     "le_solve": (TL, "test_solve_with_tilt_translation_invariant", {}),
+    "le_minimum_image": (TL, "test_minimum_image_reduces_into_the_box", {}),
     "lub_lowers_mobility": (TS, "test_lubrication_lowers_the_body_mobility", {}),
     "precond_within_rp": (TS, "test_preconditioner_counts_only_pairs_within_rp", {}),
     "force_balance": (TS, "test_bead_forces_balance_each_body", {}),
@@ -85,6 +86,7 @@ PINS = {
     "fixman_derivative": (TD, "test_fixman_large_m_is_the_directional_derivative", {"doublets": DOUBLETS}),
     "hertz_closed_form": (TC, "test_single_pair_closed_form", {}),
     "hertz_in_pair_forces": (TC, "test_pair_forces_hertz_term_is_the_closed_form", {}),
+    "hertz_rods_newton": (TC, "test_newton_third_law_for_rods", {}),
     "dlvo_minus_gradient": (TC, "test_dlvo_force_is_minus_the_potential_derivative", {}),
     "vdw_far_field": (TC, "test_van_der_waals_far_field_is_the_textbook_sphere_limit", {}),
     "double_layer": (TC, "test_double_layer_screening_and_contact_value", {}),
@@ -265,6 +267,11 @@ MUTATIONS = [
      "b[n1:] = -(FP + RRFE_E)", "b[n1:] = (FP + RRFE_E)", ["force_balance"]),
     ("squeeze coefficient not shifted to vanish at the cut-off",
      "A = 6 * PI * eta * a * (sq(e) - sq(ec))", "A = 6 * PI * eta * a * sq(e)", ["intrabody"]),
+    ("Lees-Edwards minimum image wrapping x before the offset shift",
+     "    ny = np.round(d[..., 1] / L)\n    d[..., 0] -= ny * tilt\n    d[..., 1] -= ny * L\n"
+     "    d[..., 0] -= L * np.round(d[..., 0] / L)",
+     "    ny = np.round(d[..., 1] / L)\n    d[..., 0] -= L * np.round(d[..., 0] / L)\n"
+     "    d[..., 0] -= ny * tilt\n    d[..., 1] -= ny * L", ["le_minimum_image"]),
     ("sampled lubrication rows with the torque lever negated",
      "out[k, 3:6] += f[3:6] + np.cross(r[b], f[0:3])", "out[k, 3:6] += f[3:6] - np.cross(r[b], f[0:3])",
      ["sampled_lub_rows"]),
@@ -349,6 +356,15 @@ CASES += [
      ["hertz_closed_form"]),
     ("contact_oracle", "DLVO forces beyond their cut-off",
      "if dist < r_cut and (A_H", "if dist < 2 * r_cut and (A_H", ["newton_cutoff_intrabody"]),
+    ("contact_oracle", "double-layer potential a/r instead of a^2/r",
+     "el = a * a / r * Z * np.exp", "el = a / r * Z * np.exp", ["double_layer"]),
+    ("contact_oracle", "Hertz contact acting beyond touching",
+     "if kn > 0.0 and dist < 2.0 * a:", "if kn > 0.0 and dist < 2.0 * a + 0.2:", ["newton_cutoff_intrabody"]),
+    ("contact_oracle", "Hertz torque as F x r",
+     "                fb[j] -= f\n    nb = int(body.max()) + 1\n    out = np.zeros((nb, 6))\n    for b in range(Nt):\n"
+     "        out[body[b], :3] += fb[b]\n        out[body[b], 3:] += np.cross(r[b], fb[b])",
+     "                fb[j] -= f\n    nb = int(body.max()) + 1\n    out = np.zeros((nb, 6))\n    for b in range(Nt):\n"
+     "        out[body[b], :3] += fb[b]\n        out[body[b], 3:] += np.cross(fb[b], r[b])", ["hertz_rods_newton"]),
     ("contact_oracle", "aggregate torque as F x r",
      "fb[j] -= f * d / dist\n    nb = int(body.max()) + 1\n    out = np.zeros((nb, 6))\n    for b in range(Nt):\n"
      "        out[body[b], :3] += fb[b]\n        out[body[b], 3:] += np.cross(r[b], fb[b])",
