@@ -190,7 +190,8 @@ class Suspension:
         pos = bead_pos if hasattr(bead_pos, "data_ptr") else np.ascontiguousarray(bead_pos, dtype=np.float64)
         ids = agg_id if hasattr(agg_id, "data_ptr") else np.ascontiguousarray(agg_id, dtype=np.int32)
         self.n_beads = int(pos.shape[0])
-        self.n_agg = int(ids.max()) + 1
+        # an empty suspension reaches fsd_setup, which rejects it (FSD_EINVAL)
+        self.n_agg = int(ids.max()) + 1 if self.n_beads > 0 else 0
         self.params_in = default_params(box=float(box), **params)
         self.ctx = ctypes.c_void_p()
         st = self.lib.fsd_setup(ctypes.byref(self.ctx), self.n_beads, _ptr(pos), _ptr(ids),

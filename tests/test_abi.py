@@ -77,3 +77,10 @@ def test_struct_layout_matches_header(lib):
     body = hdr[hdr.index("typedef struct {\n  int iters;"):hdr.index("} fsd_stats;")]
     fields = re.findall(r"\b(?:double|int|int64_t)\s+([a-zA-Z_0-9]+)\s*;", body)
     assert fields == [f for f, _ in pkg.FsdStats._fields_]
+
+
+def test_binding_passes_an_empty_suspension_to_the_library_checks(lib):
+    import paper_2607_25161_gb300 as pkg
+
+    with pytest.raises(pkg.FsdError, match="n_beads"):
+        pkg.Suspension(np.zeros((0, 3)), np.zeros(0, dtype=np.int32), 20.0)
